@@ -1,0 +1,181 @@
+/*
+ * dfs.h -- C ABI of libdfs: Cholesky solve of the damped Fisher system on GB300 (sm_103a).
+ *
+ * Method: Chen, Xie, Wang, "Efficient Numerical Algorithm for Large-Scale Damped
+ * Natural Gradient Descent", arXiv 2310.17556.
+ *   Eq. 1        (S^T S + lambda I) x = v, S is n x m (m >> n), lambda > 0.
+ *   Algorithm 1  W = S S^T + lambda I~;  L = Chol(W);  Q = L^{-1} S;  x = (v - Q^T Q v) / lambda.
+ *   Section 2    Q is never formed: Q^T Q v = S^T L^{-T} L^{-1} S v, evaluated right to left
+ *                with two triangular solves.
+ *   Appendix A   for lambda > 0 the result is the unique solution of Eq. 1.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a dfs_status.  The library never aborts and never prints.
+ *   - Matrices are row-major with an explicit leading dimension (in elements).
+ *     S: n rows of length m, row stride lds >= m (each sample row is contiguous).
+ *     V, X: k rows of length m (one right-hand side per row), strides ldv, ldx >= m.
+ *     W, L: n x n, row stride ldw >= n; only the lower triangle is read or written.
+ *     Y, B (n-space vectors): n rows of k values, row stride ldb >= k.
+ *   - Element types: S is FP64, FP32 or BF16 (dfs_dtype).  V and X are FP64 when S is
+ *     FP64 and FP32 otherwise.  n-space results follow the precision of the call.
+ *   - Pointers named "device" are CUDA device memory owned by the caller; the library
+ *     keeps no pointer to them after the call returns.  "stream" is a cudaStream_t
+ *     (NULL = legacy default stream); all GPU work of a call is ordered on it.
+ *   - Argument errors return DFS_ERR_INVALID_ARG before any GPU work is queued:
+ *     NULL pointers, n < 1, m < 1, k < 1, a leading dimension below its minimum,
+ *     lambda not finite or <= 0, an S pointer not 16-byte aligned, or lds * sizeof(S
+ *     element) not a multiple of 16 bytes (S rows are read with 16-byte vector loads
+ *     and tensor-memory-accelerator copies).
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef DFS_H
+#define DFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DFS_VERSION 100
+
+typedef enum {
+    DFS_OK = 0,
+    DFS_ERR_INVALID_ARG = 1,   /* rejected before launch */
+    DFS_ERR_NOT_SPD = 2,       /* a Cholesky pivot was <= 0 or NaN (Algorithm 1 step 2) */
+    DFS_ERR_NOT_CONVERGED = 3, /* refinement stopped above tolerance; X holds the last iterate */
+    DFS_ERR_NONFINITE = 4,     /* NaN/Inf met in W or in the solution */
+    DFS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    DFS_ERR_NO_MEMORY = 6,     /* workspace allocation failed */
+    DFS_ERR_CUDA = 7,          /* a CUDA runtime call failed (text in dfs_last_error) */
+    DFS_ERR_UNSUPPORTED = 8    /* valid request this build cannot serve (e.g. no sm_103a device) */
+} dfs_status;
+
+typedef enum {
+    DFS_F64 = 0,   /* double */
+    DFS_F32 = 1,   /* float */
+    DFS_BF16 = 2   /* bfloat16 (S only) */
+} dfs_dtype;
+
+/* Arithmetic of the Gram step W = S S^T (Algorithm 1 step 1), the O(n^2 m) contraction. */
+typedef enum {
+    DFS_PREC_AUTO = 0,   /* FP64 for FP64 S; BF16 tensor Gram + refinement otherwise */
+    DFS_PREC_FP64 = 1,   /* FP64 everywhere (S must be FP64) */
+    DFS_PREC_FP32 = 2,   /* plain FP32 path: FP32 FFMA Gram, FP32 solves, no refinement */
+    DFS_PREC_BF16 = 3,   /* tcgen05 BF16 Gram (FP32 accumulate) + n-space refinement */
+    DFS_PREC_TF32 = 4,   /* tcgen05 TF32 Gram (FP32 accumulate) + n-space refinement */
+    DFS_PREC_BF16X3 = 5  /* tcgen05 split-BF16 (hi/lo, three products) Gram + refinement */
+} dfs_precision;
+
+typedef struct {
+    int precision;   /* dfs_precision */
+    int max_iter;    /* refinement passes after the first solve (mixed paths); <0 = default 8 */
+    double tol;      /* stop when the estimated relative x-space correction <= tol; <=0 = 1e-7 */
+    int flags;       /* reserved, pass 0 */
+} dfs_options;
+
+typedef struct {
+    int status;             /* final dfs_status of the device work */
+    int precision_used;     /* dfs_precision actually run */
+    int iters;              /* refinement passes run (0 on the FP32/FP64 paths) */
+    int failed_pivot;       /* first non-positive pivot index, -1 if none */
+    double rel_correction;  /* last estimated ||dx|| / ||x|| (0 if no refinement) */
+    double rel_residual_n;  /* last ||r_n|| / ||S v||, r_n = S v - (S S^T + lambda I) y */
+} dfs_info;
+
+typedef struct dfs_handle_s* dfs_handle;
+
+/* Create a handle bound to CUDA device `device`.  The handle owns a device workspace that
+ * grows on demand (cudaMalloc) and is freed by dfs_destroy.  Errors: INVALID_ARG (NULL
+ * out-pointer), CUDA (bad device), UNSUPPORTED (device is not compute capability 10.3). */
+dfs_status dfs_create(dfs_handle* handle, int device);
+dfs_status dfs_destroy(dfs_handle handle);
+
+/* Static text for a status code; never NULL. */
+const char* dfs_status_string(int status);
+/* Last error message recorded on this handle (empty string if none); owned by the handle. */
+const char* dfs_last_error(dfs_handle handle);
+
+/* Grow the workspace now so later calls up to these sizes allocate nothing (needed before
+ * stream capture of dfs_solve).  Sizes are maxima over the calls that will follow. */
+dfs_status dfs_reserve(dfs_handle handle, int64_t n_max, int64_t m_max, int64_t k_max,
+                       int precision);
+
+/* Full solve of Eq. 1 for k right-hand sides (Algorithm 1 with Q inlined, Section 2).
+ *   S (device, n x m, lds), V (device, k x m, ldv) -> X (device, k x m, ldx).
+ *   X must not overlap S; X may equal V (in place).
+ *   opt may be NULL (defaults: precision AUTO, max_iter 8, tol 1e-7).
+ * Asynchronous on `stream` when info == NULL: the return value then only covers argument
+ * checks and launches; device-detected errors are read with dfs_sync_info.  When info !=
+ * NULL the call synchronizes `stream`, fills *info and returns the device status. */
+dfs_status dfs_solve(dfs_handle handle, const void* S, int s_dtype, int64_t n, int64_t m,
+                     int64_t lds, const void* V, int64_t k, int64_t ldv, double lambda,
+                     void* X, int64_t ldx, const dfs_options* opt, void* stream,
+                     dfs_info* info);
+
+/* Same solve with S, V and X in HOST memory (pinned memory gives full copy speed).  The
+ * call copies S and V to handle-owned device buffers, solves, copies X back and
+ * synchronizes `stream` before returning.  info may be NULL. */
+dfs_status dfs_solve_host(dfs_handle handle, const void* S, int s_dtype, int64_t n, int64_t m,
+                          int64_t lds, const void* V, int64_t k, int64_t ldv, double lambda,
+                          void* X, int64_t ldx, const dfs_options* opt, void* stream,
+                          dfs_info* info);
+
+/* Synchronize `stream` and report the device status of the last dfs_solve on this handle. */
+dfs_status dfs_sync_info(dfs_handle handle, void* stream, dfs_info* info);
+
+/* One independent problem of a batch (all pointers device memory, same dtype rules). */
+typedef struct {
+    const void* S; int64_t n, m, lds;
+    const void* V; int64_t k, ldv;
+    double lambda;
+    void* X; int64_t ldx;
+} dfs_problem;
+
+/* Solve `count` independent problems of uneven (n, m) with one grouped launch per step.
+ * `problems` is a host array.  status_out (host, `count` ints, may be NULL) receives each
+ * problem's device status; when it is non-NULL the call synchronizes `stream`.  The first
+ * call for a given batch shape records a CUDA graph that later calls with the same shapes
+ * replay. */
+dfs_status dfs_solve_batched(dfs_handle handle, const dfs_problem* problems, int count,
+                             int s_dtype, const dfs_options* opt, void* stream,
+                             int* status_out);
+
+/* ---- single steps of Algorithm 1 (for composition and testing) ---------------------- */
+
+/* Step 1: W = S S^T + lambda I~, lower triangle only, written to W (device, n x n, ldw).
+ * W is FP64 for precision FP64, FP32 otherwise.  precision FP32 = FFMA; BF16/TF32/BF16X3
+ * run the tcgen05 tensor-core kernel (lambda is added in FP32 after the contraction). */
+dfs_status dfs_gram(dfs_handle handle, const void* S, int s_dtype, int64_t n, int64_t m,
+                    int64_t lds, double lambda, int precision, void* W, int64_t ldw,
+                    void* stream);
+
+/* Step 2: in-place lower Cholesky W = L L^T (device, n x n, ldw, w_dtype FP32 or FP64).
+ * Blocked right-looking; each 32 x 32 diagonal block is factored in FP64.  Synchronizes
+ * `stream`.  Returns NOT_SPD (and *failed_pivot, may be NULL) on a pivot <= 0 or NaN. */
+dfs_status dfs_cholesky(dfs_handle handle, void* W, int w_dtype, int64_t n, int64_t ldw,
+                        void* stream, int64_t* failed_pivot);
+
+/* Triangular solves of Section 2 with the factor from dfs_cholesky (device L, n x n, ldl):
+ * trans = 0 solves L A = B, trans = 1 solves L^T Y = B, in place on B (device, n x k, ldb),
+ * same dtype as L. */
+dfs_status dfs_trsm(dfs_handle handle, const void* L, int l_dtype, int64_t n, int64_t ldl,
+                    void* B, int64_t k, int64_t ldb, int trans, void* stream);
+
+/* The streaming pass over S (one read of S), with Y (device, n x k FP64, ldy):
+ *   U = V - S^T Y           (Y == NULL means Y = 0)
+ *   X = U / lambda          (if X != NULL; Algorithm 1 step 4 with Q inlined)
+ *   R = S U - lambda Y      (if R != NULL; device n x k FP64, ldr: the n-space residual
+ *                            S v - (S S^T + lambda I~) y of Appendix A's identity)
+ * V, X as in dfs_solve. */
+dfs_status dfs_fisher_pass(dfs_handle handle, const void* S, int s_dtype, int64_t n, int64_t m,
+                           int64_t lds, const void* V, int64_t k, int64_t ldv, const double* Y,
+                           int64_t ldy, double lambda, void* X, int64_t ldx, double* R,
+                           int64_t ldr, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFS_H */

@@ -1,0 +1,21 @@
+"""Cholesky solve of the damped Fisher system on GB300 (arXiv 2310.17556, Algorithm 1).
+
+(S^T S + lambda I) x = v for a wide score matrix S (n x m, m >> n), with every step in
+hand-written sm_103a CUDA kernels behind the C ABI of include/dfs.h (libdfs.so).  This
+package is the thin Python binding: same entry-point names, torch tensors in and out.
+"""
+
+from .api import (  # noqa: F401
+    DfsError,
+    Handle,
+    default_handle,
+    dfs_cholesky,
+    dfs_fisher_pass,
+    dfs_gram,
+    dfs_reserve,
+    dfs_solve,
+    dfs_solve_batched,
+    dfs_solve_host,
+    dfs_sync_info,
+    dfs_trsm,
+)

@@ -1,0 +1,97 @@
+"""ctypes view of libdfs.so (the C ABI declared in include/dfs.h).
+
+Loading fails loudly when the library has not been built: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdfs.so")
+
+# enums of include/dfs.h
+DFS_OK = 0
+DFS_ERR_INVALID_ARG = 1
+DFS_ERR_NOT_SPD = 2
+DFS_ERR_NOT_CONVERGED = 3
+DFS_ERR_NONFINITE = 4
+DFS_ERR_TIMEOUT = 5
+DFS_ERR_NO_MEMORY = 6
+DFS_ERR_CUDA = 7
+DFS_ERR_UNSUPPORTED = 8
+
+DFS_F64, DFS_F32, DFS_BF16 = 0, 1, 2
+PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "bf16": 3, "tf32": 4, "bf16x3": 5}
+PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
+
+# every entry point include/dfs.h declares
+EXPORTS = (
+    "dfs_create", "dfs_destroy", "dfs_status_string", "dfs_last_error", "dfs_reserve",
+    "dfs_solve", "dfs_solve_host", "dfs_sync_info", "dfs_solve_batched",
+    "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass",
+)
+
+
+class dfs_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double), ("flags", C.c_int)]
+
+
+class dfs_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("precision_used", C.c_int), ("iters", C.c_int),
+                ("failed_pivot", C.c_int), ("rel_correction", C.c_double), ("rel_residual_n", C.c_double)]
+
+
+class dfs_problem(C.Structure):
+    _fields_ = [("S", C.c_void_p), ("n", C.c_int64), ("m", C.c_int64), ("lds", C.c_int64),
+                ("V", C.c_void_p), ("k", C.c_int64), ("ldv", C.c_int64),
+                ("lam", C.c_double), ("X", C.c_void_p), ("ldx", C.c_int64)]
+
+
+_I64 = C.c_int64
+_VP = C.c_void_p
+_SIGS = {
+    "dfs_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
+    "dfs_destroy": (C.c_int, [_VP]),
+    "dfs_status_string": (C.c_char_p, [C.c_int]),
+    "dfs_last_error": (C.c_char_p, [_VP]),
+    "dfs_reserve": (C.c_int, [_VP, _I64, _I64, _I64, C.c_int]),
+    "dfs_solve": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, C.c_double, _VP, _I64,
+                            C.POINTER(dfs_options), _VP, C.POINTER(dfs_info)]),
+    "dfs_solve_host": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, C.c_double, _VP, _I64,
+                                 C.POINTER(dfs_options), _VP, C.POINTER(dfs_info)]),
+    "dfs_sync_info": (C.c_int, [_VP, _VP, C.POINTER(dfs_info)]),
+    "dfs_solve_batched": (C.c_int, [_VP, C.POINTER(dfs_problem), C.c_int, C.c_int, C.POINTER(dfs_options), _VP,
+                                    C.POINTER(C.c_int)]),
+    "dfs_gram": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, C.c_double, C.c_int, _VP, _I64, _VP]),
+    "dfs_cholesky": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _VP, C.POINTER(_I64)]),
+    "dfs_trsm": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _VP, _I64, _I64, C.c_int, _VP]),
+    "dfs_fisher_pass": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, _VP, _I64, C.c_double,
+                                  _VP, _I64, _VP, _I64, _VP]),
+}
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libdfs.so from the package folder (RuntimeError if it was never built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2310_17556_gb300.build` "
+                           "(the CUDA path has no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DfsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(message)
+        self.status = status

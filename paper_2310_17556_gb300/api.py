@@ -1,0 +1,238 @@
+"""Python binding of libdfs: the C-ABI entry points under the same names, on torch tensors.
+
+Argument marshalling only (pointers, strides, dtypes, the current CUDA stream).  Every step of
+the solve runs in libdfs's CUDA kernels; PyTorch provides device memory and streams.
+
+Layouts (see include/dfs.h): S is (n, m) row-major, V and X are (k, m) with one right-hand
+side per row, W/L are (n, n) lower-triangular, n-space vectors are (n, k).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import DFS_BF16, DFS_F32, DFS_F64, PRECISIONS, DfsError, dfs_info, dfs_options, dfs_problem
+
+_DT = {torch.float64: DFS_F64, torch.float32: DFS_F32, torch.bfloat16: DFS_BF16}
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    try:
+        return _DT[t.dtype]
+    except KeyError:
+        raise TypeError(f"unsupported dtype {t.dtype} (float64, float32 or bfloat16)") from None
+
+
+def _rows(t: torch.Tensor, name: str) -> int:
+    """Leading dimension (row stride in elements) of a row-major 2-D tensor."""
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if t.stride(1) != 1:
+        raise ValueError(f"{name} must have unit stride along its last dimension")
+    return t.stride(0) if t.shape[0] > 1 else max(t.stride(0), t.shape[1])
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _opts(precision, max_iter, tol) -> dfs_options:
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return dfs_options(p, int(max_iter), float(tol), 0)
+
+
+def _check(lib, h, status: int):
+    if status != _lib.DFS_OK:
+        msg = lib.dfs_last_error(h).decode() if h else ""
+        raise DfsError(status, f"{lib.dfs_status_string(status).decode()}: {msg}")
+
+
+def _info_dict(info: dfs_info) -> dict:
+    return dict(status=info.status, precision=_lib.PRECISION_NAMES.get(info.precision_used, "?"),
+                iters=info.iters, failed_pivot=info.failed_pivot, rel_correction=info.rel_correction,
+                rel_residual_n=info.rel_residual_n)
+
+
+class Handle:
+    """Owns a dfs_handle (device workspace); one per device and host thread."""
+
+    def __init__(self, device: int | None = None):
+        self.lib = _lib.load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        st = self.lib.dfs_create(C.byref(h), self.device)
+        if st != _lib.DFS_OK:
+            raise DfsError(st, f"dfs_create failed: {self.lib.dfs_status_string(st).decode()}")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dfs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default: dict[int, Handle] = {}
+
+
+def default_handle(device: int | None = None) -> Handle:
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d not in _default:
+        _default[d] = Handle(d)
+    return _default[d]
+
+
+def dfs_reserve(n_max: int, m_max: int, k_max: int, precision="auto", handle: Handle | None = None):
+    h = handle or default_handle()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(h.lib, h.h, h.lib.dfs_reserve(h.h, n_max, m_max, k_max, p))
+
+
+def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
+              max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
+              sync: bool = True):
+    """Solve (S^T S + lam I) X^T = V^T for the k rows of V (Eq. 1, Algorithm 1).
+
+    Returns (X, info) when sync is True (info = dict of dfs_info), else (X, None) with the work
+    queued on the stream (read the status later with dfs_sync_info).
+    """
+    h = handle or default_handle(S.device.index)
+    n, m = S.shape
+    k = V.shape[0]
+    if V.shape[1] != m:
+        raise ValueError("V must be (k, m)")
+    vdt = torch.float64 if S.dtype == torch.float64 else torch.float32
+    if V.dtype != vdt:
+        raise TypeError(f"V must be {vdt} for S of dtype {S.dtype}")
+    if X is None:
+        X = torch.empty((k, m), device=S.device, dtype=vdt)
+    opt = _opts(precision, max_iter, tol)
+    info = dfs_info()
+    st = h.lib.dfs_solve(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k, _rows(V, "V"),
+                         float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt), _stream(stream),
+                         C.byref(info) if sync else None)
+    if sync:
+        if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
+            _check(h.lib, h.h, st)
+        return X, _info_dict(info)
+    _check(h.lib, h.h, st)
+    return X, None
+
+
+def dfs_sync_info(handle: Handle | None = None, stream=None) -> dict:
+    h = handle or default_handle()
+    info = dfs_info()
+    st = h.lib.dfs_sync_info(h.h, _stream(stream), C.byref(info))
+    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
+        _check(h.lib, h.h, st)
+    return _info_dict(info)
+
+
+def dfs_solve_host(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
+                   max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None):
+    """Same solve with S, V, X in host memory (pinned for full copy speed); copies inside the call."""
+    h = handle or default_handle()
+    n, m = S.shape
+    k = V.shape[0]
+    if X is None:
+        X = torch.empty((k, m), dtype=V.dtype, pin_memory=S.is_pinned())
+    opt = _opts(precision, max_iter, tol)
+    info = dfs_info()
+    st = h.lib.dfs_solve_host(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k,
+                              _rows(V, "V"), float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt),
+                              _stream(stream), C.byref(info))
+    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
+        _check(h.lib, h.h, st)
+    return X, _info_dict(info)
+
+
+def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float = 0.0,
+                      handle: Handle | None = None, stream=None, sync: bool = True):
+    """problems: list of (S, V, lam[, X]); returns (list of X, list of per-problem status or None)."""
+    h = handle or default_handle()
+    arr = (dfs_problem * len(problems))()
+    outs = []
+    dt = None
+    for i, pr in enumerate(problems):
+        S, V, lam = pr[0], pr[1], pr[2]
+        X = pr[3] if len(pr) > 3 else torch.empty_like(V)
+        dt = _dtype_code(S) if dt is None else dt
+        if _dtype_code(S) != dt:
+            raise TypeError("all S of a batch must share one dtype")
+        arr[i] = dfs_problem(S.data_ptr(), S.shape[0], S.shape[1], _rows(S, "S"), V.data_ptr(), V.shape[0],
+                             _rows(V, "V"), float(lam), X.data_ptr(), _rows(X, "X"))
+        outs.append(X)
+    opt = _opts(precision, max_iter, tol)
+    status = (C.c_int * len(problems))() if sync else None
+    st = h.lib.dfs_solve_batched(h.h, arr, len(problems), dt, C.byref(opt), _stream(stream), status)
+    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
+        _check(h.lib, h.h, st)
+    return outs, (list(status) if sync else None)
+
+
+def dfs_gram(S: torch.Tensor, lam: float, precision="auto", W: torch.Tensor | None = None,
+             handle: Handle | None = None, stream=None) -> torch.Tensor:
+    """Algorithm 1 step 1: lower triangle of W = S S^T + lam I (upper triangle untouched)."""
+    h = handle or default_handle(S.device.index)
+    n, m = S.shape
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    wdt = torch.float64 if (p == PRECISIONS["fp64"] or (p == 0 and S.dtype == torch.float64)) else torch.float32
+    if W is None:
+        W = torch.zeros((n, n), device=S.device, dtype=wdt)
+    st = h.lib.dfs_gram(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), float(lam), p, W.data_ptr(),
+                        _rows(W, "W"), _stream(stream))
+    _check(h.lib, h.h, st)
+    return W
+
+
+def dfs_cholesky(W: torch.Tensor, handle: Handle | None = None, stream=None) -> tuple[torch.Tensor, int]:
+    """Algorithm 1 step 2, in place on the lower triangle of W; returns (L, failed_pivot or -1)."""
+    h = handle or default_handle(W.device.index)
+    n = W.shape[0]
+    piv = C.c_int64(-1)
+    st = h.lib.dfs_cholesky(h.h, W.data_ptr(), _dtype_code(W), n, _rows(W, "W"), _stream(stream), C.byref(piv))
+    if st != _lib.DFS_OK:
+        msg = h.lib.dfs_last_error(h.h).decode()
+        raise DfsError(st, f"{h.lib.dfs_status_string(st).decode()}: {msg} (pivot {piv.value})")
+    return W, piv.value
+
+
+def dfs_trsm(L: torch.Tensor, B: torch.Tensor, trans: bool = False, handle: Handle | None = None,
+             stream=None) -> torch.Tensor:
+    """In place on B (n, k): solves L A = B (trans False) or L^T Y = B (trans True)."""
+    h = handle or default_handle(L.device.index)
+    n = L.shape[0]
+    k = B.shape[1]
+    st = h.lib.dfs_trsm(h.h, L.data_ptr(), _dtype_code(L), n, _rows(L, "L"), B.data_ptr(), k, _rows(B, "B"),
+                        1 if trans else 0, _stream(stream))
+    _check(h.lib, h.h, st)
+    return B
+
+
+def dfs_fisher_pass(S: torch.Tensor, V: torch.Tensor, lam: float, Y: torch.Tensor | None = None,
+                    want_x: bool = True, want_r: bool = True, handle: Handle | None = None, stream=None):
+    """One read of S: X = (V - S^T Y)/lam and R = S (V - S^T Y) - lam Y (Y (n, k) FP64 or None = 0)."""
+    h = handle or default_handle(S.device.index)
+    n, m = S.shape
+    k = V.shape[0]
+    X = torch.empty_like(V) if want_x else None
+    R = torch.empty((n, k), device=S.device, dtype=torch.float64) if want_r else None
+    st = h.lib.dfs_fisher_pass(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k,
+                               _rows(V, "V"), Y.data_ptr() if Y is not None else None,
+                               _rows(Y, "Y") if Y is not None else k, float(lam),
+                               X.data_ptr() if X is not None else None, _rows(X, "X") if X is not None else m,
+                               R.data_ptr() if R is not None else None, k, _stream(stream))
+    _check(h.lib, h.h, st)
+    return X, R

@@ -1,0 +1,613 @@
+// C ABI of libdfs (declared in include/dfs.h): argument checks, workspace planning and the
+// launch sequence of Algorithm 1 (arXiv 2310.17556) with Q inlined (Section 2).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace dfs;
+
+struct dfs_handle_s {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    DevStatus* dstat = nullptr;
+    void* hbuf[3] = {nullptr, nullptr, nullptr};  // device staging for dfs_solve_host: S, V, X
+    int* bstat = nullptr;                          // per-problem device status of dfs_solve_batched
+    int bstat_count = 0;
+    size_t hbuf_bytes[3] = {0, 0, 0};
+    int last_precision = 0;
+    std::string err;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int elem_size(int dt) { return dt == DFS_F64 ? 8 : (dt == DFS_F32 ? 4 : 2); }
+
+dfs_status fail(dfs_handle h, dfs_status s, const char* fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return s;
+}
+
+#define DFS_CK(call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(h, DFS_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                               \
+    } while (0)
+
+struct Plan {
+    int s_dtype = DFS_F32;
+    int prec = DFS_PREC_FP32;
+    bool f64 = false;     // n-space solve type is FP64
+    bool tensor = false;  // tcgen05 Gram + refinement
+    int64_t n = 0, m = 0, n_pad = 0;
+    int k = 1, kq = 1;
+    int nsplit = 1;
+    int64_t chunk = 0;
+    GramTcPlan tc{};
+    int pgrid = 1;
+    size_t off_W = 0, off_Linv = 0, off_P = 0, off_Rpart = 0, off_U2part = 0, off_R = 0, off_Z = 0, off_Y = 0,
+           off_U2 = 0, off_bn2 = 0, total = 0;
+};
+
+int tc_kind(int prec) {
+    switch (prec) {
+        case DFS_PREC_BF16: return 0;
+        case DFS_PREC_TF32: return 1;
+        case DFS_PREC_BF16X3: return 2;
+        default: return -1;
+    }
+}
+
+dfs_status resolve_precision(dfs_handle h, int s_dtype, int prec, int* out) {
+    if (prec == DFS_PREC_AUTO) {
+        if (s_dtype == DFS_F64) prec = DFS_PREC_FP64;
+        else prec = gram_tc_supported(s_dtype, 0) ? DFS_PREC_BF16 : DFS_PREC_FP32;
+    }
+    switch (prec) {
+        case DFS_PREC_FP64:
+            if (s_dtype != DFS_F64) return fail(h, DFS_ERR_INVALID_ARG, "precision FP64 needs FP64 S");
+            break;
+        case DFS_PREC_FP32:
+            if (s_dtype == DFS_F64) return fail(h, DFS_ERR_INVALID_ARG, "precision FP32 needs FP32 or BF16 S");
+            break;
+        case DFS_PREC_BF16:
+        case DFS_PREC_TF32:
+        case DFS_PREC_BF16X3:
+            if (!gram_tc_supported(s_dtype, tc_kind(prec)))
+                return fail(h, DFS_ERR_UNSUPPORTED, "tensor-core Gram kind %d not available for S dtype %d",
+                            tc_kind(prec), s_dtype);
+            break;
+        default:
+            return fail(h, DFS_ERR_INVALID_ARG, "unknown precision %d", prec);
+    }
+    *out = prec;
+    return DFS_OK;
+}
+
+int pow2_at_least(int k) {
+    int q = 1;
+    while (q < k && q < 8) q <<= 1;
+    return q;
+}
+
+dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, int k, Plan* p) {
+    p->s_dtype = s_dtype;
+    p->prec = prec;
+    p->f64 = (prec == DFS_PREC_FP64);
+    p->tensor = tc_kind(prec) >= 0;
+    p->n = n;
+    p->m = m;
+    p->n_pad = round_up(n, 128);
+    p->k = k;
+    const int es = p->f64 ? 8 : 4;
+    int kq = pow2_at_least(k);
+    const int kq_pass = pass_max_group((int)n, s_dtype, h->smem_optin);
+    const int kq_trsv = trsv_max_group((int)p->n_pad, es, h->smem_optin);
+    if (kq_pass < 1 || kq_trsv < 1)
+        return fail(h, DFS_ERR_UNSUPPORTED, "n=%lld too large for the on-chip n-space buffers", (long long)n);
+    if (kq > kq_pass) kq = kq_pass;
+    if (kq > kq_trsv) kq = kq_trsv;
+    p->kq = kq;
+    size_t gram_bytes;
+    if (p->tensor) {
+        p->tc = gram_tc_plan(s_dtype, tc_kind(prec), n, m, h->num_sms);
+        gram_bytes = p->tc.partial_bytes;
+    } else {
+        gram_simt_plan(n, m, p->f64, h->num_sms, &p->nsplit, &p->chunk);
+        gram_bytes = gram_simt_partial_bytes(n, p->f64, p->nsplit);
+    }
+    p->pgrid = pass_grid((int)n, kq, s_dtype, h->num_sms, m);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t np = (size_t)p->n_pad;
+    p->off_W = take(np * np * es);
+    p->off_Linv = take(np * 32 * es);
+    p->off_P = take(gram_bytes);
+    p->off_Rpart = take((size_t)p->pgrid * n * kq * 8);
+    p->off_U2part = take((size_t)p->pgrid * kq * 8);
+    p->off_R = take(np * kq * 8);
+    p->off_Z = take(np * kq * es);
+    p->off_Y = take(np * kq * 8);
+    p->off_U2 = take(8 * 8);
+    p->off_bn2 = take(8 * 8);
+    p->total = off;
+    return DFS_OK;
+}
+
+dfs_status ensure_ws(dfs_handle h, size_t bytes, cudaStream_t stream) {
+    if (bytes <= h->ws_bytes) return DFS_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(h, DFS_ERR_NO_MEMORY, "workspace must grow to %zu bytes during stream capture; call dfs_reserve first",
+                    bytes);
+    if (h->ws) {
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, DFS_ERR_NO_MEMORY, "cudaMalloc(%zu) for the workspace failed", bytes);
+    }
+    h->ws_bytes = bytes;
+    return DFS_OK;
+}
+
+template <typename P>
+P* at(dfs_handle h, size_t off) {
+    return reinterpret_cast<P*>(static_cast<char*>(h->ws) + off);
+}
+
+dfs_status check_s(dfs_handle h, const void* S, int s_dtype, int64_t n, int64_t m, int64_t lds) {
+    if (s_dtype != DFS_F64 && s_dtype != DFS_F32 && s_dtype != DFS_BF16)
+        return fail(h, DFS_ERR_INVALID_ARG, "unknown S dtype %d", s_dtype);
+    if (!S) return fail(h, DFS_ERR_INVALID_ARG, "S is NULL");
+    if (n < 1 || m < 1) return fail(h, DFS_ERR_INVALID_ARG, "n=%lld m=%lld must be >= 1", (long long)n, (long long)m);
+    if (n > 65536) return fail(h, DFS_ERR_UNSUPPORTED, "n=%lld above the supported maximum 65536", (long long)n);
+    if (lds < m) return fail(h, DFS_ERR_INVALID_ARG, "lds=%lld < m=%lld", (long long)lds, (long long)m);
+    if (reinterpret_cast<uintptr_t>(S) % 16 != 0) return fail(h, DFS_ERR_INVALID_ARG, "S is not 16-byte aligned");
+    if ((lds * elem_size(s_dtype)) % 16 != 0)
+        return fail(h, DFS_ERR_INVALID_ARG, "lds * sizeof(S element) must be a multiple of 16 bytes");
+    return DFS_OK;
+}
+
+dfs_status check_lambda(dfs_handle h, double lambda) {
+    if (!std::isfinite(lambda) || !(lambda > 0.0))
+        return fail(h, DFS_ERR_INVALID_ARG, "lambda must be finite and > 0 (got %g)", lambda);
+    return DFS_OK;
+}
+
+// Step 1 into the plan's padded W: Gram (+ lambda on the diagonal, identity padding).
+dfs_status run_gram(dfs_handle h, const Plan& p, const void* S, int64_t lds, double lambda, void* W, int64_t ldw,
+                    int64_t n_out, cudaStream_t stream) {
+    void* P = at<void>(h, p.off_P);
+    if (p.tensor) {
+        DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, P, h->dstat, stream));
+        DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, n_out, lambda, W, ldw, stream));
+    } else {
+        DFS_CK(launch_gram_simt(p.s_dtype, p.f64, S, p.n, p.m, lds, p.nsplit, p.chunk, P, stream));
+        DFS_CK(launch_gram_finalize(p.f64, p.f64, gram_simt_tile(p.f64), P, p.nsplit, p.n, n_out, lambda, W, ldw,
+                                    stream));
+    }
+    return DFS_OK;
+}
+
+dfs_status fill_info(dfs_handle h, cudaStream_t stream, dfs_info* info) {
+    DevStatus ds;
+    DFS_CK(cudaMemcpyAsync(&ds, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, stream));
+    DFS_CK(cudaStreamSynchronize(stream));
+    if (info) {
+        info->status = ds.status;
+        info->precision_used = h->last_precision;
+        info->iters = ds.iters;
+        info->failed_pivot = ds.failed_pivot;
+        info->rel_correction = ds.rel_correction;
+        info->rel_residual_n = ds.rel_residual;
+    }
+    if (ds.status != 0) {
+        if (ds.status == DFS_ERR_NOT_SPD || ds.status == DFS_ERR_NONFINITE)
+            return fail(h, (dfs_status)ds.status, "device reported %s at pivot %d", dfs_status_string(ds.status),
+                        ds.failed_pivot);
+        return fail(h, (dfs_status)ds.status, "device reported %s", dfs_status_string(ds.status));
+    }
+    return DFS_OK;
+}
+
+dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int64_t m, int64_t lds, const void* V,
+                        int64_t k, int64_t ldv, double lambda, void* X, int64_t ldx, const dfs_options* opt,
+                        cudaStream_t stream, dfs_info* info) {
+    dfs_status s;
+    if ((s = check_s(h, S, s_dtype, n, m, lds)) != DFS_OK) return s;
+    if ((s = check_lambda(h, lambda)) != DFS_OK) return s;
+    if (!V || !X) return fail(h, DFS_ERR_INVALID_ARG, "V or X is NULL");
+    if (k < 1) return fail(h, DFS_ERR_INVALID_ARG, "k must be >= 1");
+    if (ldv < m || ldx < m) return fail(h, DFS_ERR_INVALID_ARG, "ldv and ldx must be >= m");
+    {
+        const size_t es = s_dtype == DFS_F64 ? 8 : 4;
+        const char* x0 = static_cast<const char*>(X);
+        const char* x1 = x0 + ((k - 1) * ldx + m) * es;
+        const char* s0 = static_cast<const char*>(S);
+        const char* s1 = s0 + ((n - 1) * lds + m) * elem_size(s_dtype);
+        if (x0 < s1 && s0 < x1) return fail(h, DFS_ERR_INVALID_ARG, "X overlaps S");
+    }
+    int prec;
+    if ((s = resolve_precision(h, s_dtype, opt ? opt->precision : DFS_PREC_AUTO, &prec)) != DFS_OK) return s;
+    const int max_iter = (opt && opt->max_iter >= 0) ? opt->max_iter : 8;
+    const double tol = (opt && opt->tol > 0.0) ? opt->tol : 1e-7;
+    Plan p;
+    if ((s = make_plan(h, s_dtype, prec, n, m, (int)k, &p)) != DFS_OK) return s;
+    if ((s = ensure_ws(h, p.total, stream)) != DFS_OK) return s;
+    h->last_precision = prec;
+
+    void* W = at<void>(h, p.off_W);
+    void* Linv = at<void>(h, p.off_Linv);
+    double* Rpart = at<double>(h, p.off_Rpart);
+    double* U2part = at<double>(h, p.off_U2part);
+    double* R = at<double>(h, p.off_R);
+    void* Z = at<void>(h, p.off_Z);
+    double* Y = at<double>(h, p.off_Y);
+    double* U2 = at<double>(h, p.off_U2);
+    double* bn2 = at<double>(h, p.off_bn2);
+    const int ni = (int)n, npi = (int)p.n_pad, kq = p.kq;
+    const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
+
+    DFS_CK(launch_status_reset(h->dstat, stream));
+    if ((s = run_gram(h, p, S, lds, lambda, W, p.n_pad, p.n_pad, stream)) != DFS_OK) return s;
+    DFS_CK(launch_cholesky(p.f64, W, p.n_pad, p.n_pad, Linv, h->dstat, stream));
+
+    for (int64_t q0 = 0; q0 < k; q0 += kq) {
+        const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
+        const void* Vg = static_cast<const char*>(V) + q0 * ldv * vs;
+        void* Xg = static_cast<char*>(X) + q0 * ldx * vs;
+        DFS_CK(launch_group_reset(h->dstat, stream));
+        // b = S v (pass with y = 0), then y0 = W^{-1} b by the two triangular solves.
+        DFS_CK(launch_pass(s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, nullptr, kq, lambda, nullptr, ldx, Rpart,
+                           U2part, p.pgrid, h->dstat, 0, stream));
+        DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pgrid, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z, U2part, U2,
+                                  h->dstat, 0, stream));
+        DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
+        DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
+        DFS_CK(launch_refine_init(p.f64, Z, npi, kq, Y, R, bn2, h->dstat, stream));
+        if (!p.tensor) {
+            // x = (v - S^T y) / lambda
+            DFS_CK(launch_pass(s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr, U2part,
+                               p.pgrid, h->dstat, 0, stream));
+        } else {
+            for (int it = 1; it <= max_iter; ++it) {
+                DFS_CK(launch_pass(s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, Rpart, U2part,
+                                   p.pgrid, h->dstat, 1, stream));
+                DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pgrid, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z, U2part,
+                                          U2, h->dstat, 1, stream));
+                DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
+                DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
+                DFS_CK(launch_refine_control(p.f64, Z, R, npi, kq, kg, Y, U2, bn2, lambda, tol, it, max_iter,
+                                             h->dstat, stream));
+            }
+            if (max_iter == 0) {
+                DFS_CK(launch_pass(s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr, U2part,
+                                   p.pgrid, h->dstat, 0, stream));
+            }
+        }
+    }
+    if (info) return fill_info(h, stream, info);
+    return DFS_OK;
+}
+
+dfs_status grow(dfs_handle h, int i, size_t bytes) {
+    if (bytes <= h->hbuf_bytes[i]) return DFS_OK;
+    if (h->hbuf[i]) cudaFree(h->hbuf[i]);
+    h->hbuf[i] = nullptr;
+    h->hbuf_bytes[i] = 0;
+    if (cudaMalloc(&h->hbuf[i], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, DFS_ERR_NO_MEMORY, "cudaMalloc(%zu) for host-path staging failed", bytes);
+    }
+    h->hbuf_bytes[i] = bytes;
+    return DFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dfs_status_string(int status) {
+    switch (status) {
+        case DFS_OK: return "DFS_OK";
+        case DFS_ERR_INVALID_ARG: return "DFS_ERR_INVALID_ARG";
+        case DFS_ERR_NOT_SPD: return "DFS_ERR_NOT_SPD";
+        case DFS_ERR_NOT_CONVERGED: return "DFS_ERR_NOT_CONVERGED";
+        case DFS_ERR_NONFINITE: return "DFS_ERR_NONFINITE";
+        case DFS_ERR_TIMEOUT: return "DFS_ERR_TIMEOUT";
+        case DFS_ERR_NO_MEMORY: return "DFS_ERR_NO_MEMORY";
+        case DFS_ERR_CUDA: return "DFS_ERR_CUDA";
+        case DFS_ERR_UNSUPPORTED: return "DFS_ERR_UNSUPPORTED";
+        default: return "DFS_ERR_UNKNOWN";
+    }
+}
+
+const char* dfs_last_error(dfs_handle h) { return h ? h->err.c_str() : ""; }
+
+dfs_status dfs_create(dfs_handle* out, int device) {
+    if (!out) return DFS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return DFS_ERR_CUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DFS_ERR_CUDA;
+    if (prop.major != 10 || prop.minor != 3) return DFS_ERR_UNSUPPORTED;  // built for sm_103a only
+    if (cudaSetDevice(device) != cudaSuccess) return DFS_ERR_CUDA;
+    dfs_handle h = new dfs_handle_s();
+    h->device = device;
+    h->num_sms = prop.multiProcessorCount;
+    h->smem_optin = prop.sharedMemPerBlockOptin;
+    if (cudaMalloc(&h->dstat, sizeof(DevStatus)) != cudaSuccess) {
+        delete h;
+        return DFS_ERR_NO_MEMORY;
+    }
+    cudaMemset(h->dstat, 0, sizeof(DevStatus));
+    *out = h;
+    return DFS_OK;
+}
+
+dfs_status dfs_destroy(dfs_handle h) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    if (h->ws) cudaFree(h->ws);
+    if (h->dstat) cudaFree(h->dstat);
+    for (int i = 0; i < 3; ++i)
+        if (h->hbuf[i]) cudaFree(h->hbuf[i]);
+    if (h->bstat) cudaFree(h->bstat);
+    delete h;
+    return DFS_OK;
+}
+
+dfs_status dfs_reserve(dfs_handle h, int64_t n_max, int64_t m_max, int64_t k_max, int precision) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    if (n_max < 1 || m_max < 1 || k_max < 1) return fail(h, DFS_ERR_INVALID_ARG, "sizes must be >= 1");
+    cudaSetDevice(h->device);
+    size_t need = 0;
+    const int dtypes[3] = {DFS_F32, DFS_BF16, DFS_F64};
+    for (int dt : dtypes) {
+        int prec;
+        if (resolve_precision(h, dt, precision, &prec) != DFS_OK) continue;
+        Plan p;
+        if (make_plan(h, dt, prec, n_max, m_max, (int)k_max, &p) != DFS_OK) continue;
+        if (p.total > need) need = p.total;
+    }
+    h->err.clear();
+    if (need == 0) return fail(h, DFS_ERR_INVALID_ARG, "no dtype supports precision %d at these sizes", precision);
+    return ensure_ws(h, need, nullptr);
+}
+
+dfs_status dfs_solve(dfs_handle h, const void* S, int s_dtype, int64_t n, int64_t m, int64_t lds, const void* V,
+                     int64_t k, int64_t ldv, double lambda, void* X, int64_t ldx, const dfs_options* opt,
+                     void* stream, dfs_info* info) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    return solve_device(h, S, s_dtype, n, m, lds, V, k, ldv, lambda, X, ldx, opt, (cudaStream_t)stream, info);
+}
+
+dfs_status dfs_solve_host(dfs_handle h, const void* S, int s_dtype, int64_t n, int64_t m, int64_t lds,
+                          const void* V, int64_t k, int64_t ldv, double lambda, void* X, int64_t ldx,
+                          const dfs_options* opt, void* stream_, dfs_info* info) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    dfs_status s;
+    if ((s = check_s(h, S, s_dtype, n, m, lds)) != DFS_OK) return s;
+    if (!V || !X || k < 1 || ldv < m || ldx < m) return fail(h, DFS_ERR_INVALID_ARG, "bad V/X arguments");
+    const size_t es = elem_size(s_dtype);
+    const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
+    const int64_t lds_d = lds, ldv_d = round_up(m, 4), ldx_d = ldv_d;
+    if ((s = grow(h, 0, (size_t)n * lds_d * es)) != DFS_OK) return s;
+    if ((s = grow(h, 1, (size_t)k * ldv_d * vs)) != DFS_OK) return s;
+    if ((s = grow(h, 2, (size_t)k * ldx_d * vs)) != DFS_OK) return s;
+    DFS_CK(cudaMemcpyAsync(h->hbuf[0], S, (size_t)n * lds * es, cudaMemcpyHostToDevice, stream));
+    DFS_CK(cudaMemcpy2DAsync(h->hbuf[1], ldv_d * vs, V, ldv * vs, m * vs, k, cudaMemcpyHostToDevice, stream));
+    s = solve_device(h, h->hbuf[0], s_dtype, n, m, lds_d, h->hbuf[1], k, ldv_d, lambda, h->hbuf[2], ldx_d, opt,
+                     stream, nullptr);
+    if (s != DFS_OK) return s;
+    DFS_CK(cudaMemcpy2DAsync(X, ldx * vs, h->hbuf[2], ldx_d * vs, m * vs, k, cudaMemcpyDeviceToHost, stream));
+    return fill_info(h, stream, info);
+}
+
+dfs_status dfs_sync_info(dfs_handle h, void* stream, dfs_info* info) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    return fill_info(h, (cudaStream_t)stream, info);
+}
+
+dfs_status dfs_gram(dfs_handle h, const void* S, int s_dtype, int64_t n, int64_t m, int64_t lds, double lambda,
+                    int precision, void* W, int64_t ldw, void* stream_) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    dfs_status s;
+    if ((s = check_s(h, S, s_dtype, n, m, lds)) != DFS_OK) return s;
+    if ((s = check_lambda(h, lambda)) != DFS_OK) return s;
+    if (!W || ldw < n) return fail(h, DFS_ERR_INVALID_ARG, "W is NULL or ldw < n");
+    int prec;
+    if ((s = resolve_precision(h, s_dtype, precision, &prec)) != DFS_OK) return s;
+    Plan p;
+    if ((s = make_plan(h, s_dtype, prec, n, m, 1, &p)) != DFS_OK) return s;
+    if ((s = ensure_ws(h, p.total, stream)) != DFS_OK) return s;
+    DFS_CK(launch_status_reset(h->dstat, stream));
+    return run_gram(h, p, S, lds, lambda, W, ldw, n, stream);
+}
+
+dfs_status dfs_cholesky(dfs_handle h, void* W, int w_dtype, int64_t n, int64_t ldw, void* stream_,
+                        int64_t* failed_pivot) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (failed_pivot) *failed_pivot = -1;
+    if (!W || n < 1 || ldw < n || (w_dtype != DFS_F32 && w_dtype != DFS_F64))
+        return fail(h, DFS_ERR_INVALID_ARG, "bad W arguments");
+    const int f64 = w_dtype == DFS_F64;
+    const int64_t n_pad = round_up(n, 128);
+    const size_t es = f64 ? 8 : 4;
+    dfs_status s;
+    if ((s = ensure_ws(h, align_up((size_t)n_pad * n_pad * es) + n_pad * 32 * es, stream)) != DFS_OK) return s;
+    void* Wp = h->ws;
+    void* Linv = static_cast<char*>(h->ws) + align_up((size_t)n_pad * n_pad * es);
+    DFS_CK(launch_status_reset(h->dstat, stream));
+    DFS_CK(launch_pad_copy_in(f64, W, ldw, n, Wp, n_pad, stream));
+    DFS_CK(launch_cholesky(f64, Wp, n_pad, n_pad, Linv, h->dstat, stream));
+    DFS_CK(launch_copy_lower_out(f64, Wp, n_pad, W, ldw, n, stream));
+    dfs_info info;
+    s = fill_info(h, stream, &info);
+    if (failed_pivot && info.failed_pivot >= 0) *failed_pivot = info.failed_pivot;
+    return s;
+}
+
+dfs_status dfs_trsm(dfs_handle h, const void* L, int l_dtype, int64_t n, int64_t ldl, void* B, int64_t k,
+                    int64_t ldb, int trans, void* stream_) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!L || !B || n < 1 || k < 1 || ldl < n || ldb < k || (l_dtype != DFS_F32 && l_dtype != DFS_F64) ||
+        (trans != 0 && trans != 1))
+        return fail(h, DFS_ERR_INVALID_ARG, "bad triangular-solve arguments");
+    const int f64 = l_dtype == DFS_F64;
+    const int64_t n_pad = round_up(n, 128);
+    const size_t es = f64 ? 8 : 4;
+    int kq = trsv_max_group((int)n_pad, (int)es, h->smem_optin);
+    if (kq < 1) return fail(h, DFS_ERR_UNSUPPORTED, "n too large for the on-chip triangular solve");
+    const size_t oL = 0, oI = align_up((size_t)n_pad * n_pad * es), oB = oI + align_up((size_t)n_pad * 32 * es);
+    dfs_status s;
+    if ((s = ensure_ws(h, oB + align_up((size_t)n_pad * kq * es), stream)) != DFS_OK) return s;
+    void* Lp = static_cast<char*>(h->ws) + oL;
+    void* Linv = static_cast<char*>(h->ws) + oI;
+    void* Bp = static_cast<char*>(h->ws) + oB;
+    DFS_CK(launch_status_reset(h->dstat, stream));
+    DFS_CK(launch_pad_copy_in(f64, L, ldl, n, Lp, n_pad, stream));
+    DFS_CK(launch_diag_inverse(f64, Lp, n_pad, n_pad, Linv, h->dstat, stream));
+    for (int64_t q0 = 0; q0 < k; q0 += kq) {
+        const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
+        void* Bg = static_cast<char*>(B) + q0 * es;
+        DFS_CK(launch_copy_rhs_in(f64, Bg, ldb, n, kg, Bp, kq, n_pad, stream));
+        DFS_CK(launch_trsv(f64, trans, Lp, n_pad, (int)n_pad, Linv, Bp, kq, kg, kq, h->dstat, 0, stream));
+        DFS_CK(launch_copy_rhs_out(f64, Bp, kq, n, kg, Bg, ldb, stream));
+    }
+    return fill_info(h, stream, nullptr);
+}
+
+dfs_status dfs_fisher_pass(dfs_handle h, const void* S, int s_dtype, int64_t n, int64_t m, int64_t lds,
+                           const void* V, int64_t k, int64_t ldv, const double* Y, int64_t ldy, double lambda,
+                           void* X, int64_t ldx, double* R, int64_t ldr, void* stream_) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    dfs_status s;
+    if ((s = check_s(h, S, s_dtype, n, m, lds)) != DFS_OK) return s;
+    if ((s = check_lambda(h, lambda)) != DFS_OK) return s;
+    if (!V || k < 1 || ldv < m) return fail(h, DFS_ERR_INVALID_ARG, "bad V arguments");
+    if (X && ldx < m) return fail(h, DFS_ERR_INVALID_ARG, "ldx < m");
+    if (Y && ldy < k) return fail(h, DFS_ERR_INVALID_ARG, "ldy < k");
+    if (R && ldr < k) return fail(h, DFS_ERR_INVALID_ARG, "ldr < k");
+    int kq = pow2_at_least((int)k);
+    const int kmax = pass_max_group((int)n, s_dtype, h->smem_optin);
+    if (kmax < 1) return fail(h, DFS_ERR_UNSUPPORTED, "n too large for the pass kernel");
+    if (kq > kmax) kq = kmax;
+    const int grid = pass_grid((int)n, kq, s_dtype, h->num_sms, m);
+    const size_t oR = 0, oU = align_up((size_t)grid * n * kq * 8), oU2 = oU + align_up((size_t)grid * kq * 8);
+    if ((s = ensure_ws(h, oU2 + 64, stream)) != DFS_OK) return s;
+    double* Rpart = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oR);
+    double* U2part = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oU);
+    double* U2 = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oU2);
+    const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
+    DFS_CK(launch_status_reset(h->dstat, stream));
+    for (int64_t q0 = 0; q0 < k; q0 += kq) {
+        const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
+        const void* Vg = static_cast<const char*>(V) + q0 * ldv * vs;
+        void* Xg = X ? static_cast<char*>(X) + q0 * ldx * vs : nullptr;
+        const double* Yg = Y ? Y + q0 : nullptr;
+        DFS_CK(launch_pass(s_dtype, kq, S, (int)n, m, lds, Vg, ldv, kg, Yg, Y ? ldy : kq, lambda, Xg, ldx,
+                           R ? Rpart : nullptr, U2part, grid, h->dstat, 0, stream));
+        if (R)
+            DFS_CK(launch_pass_reduce(0, Rpart, grid, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
+                                      U2part, U2, h->dstat, 0, stream));
+    }
+    return DFS_OK;
+}
+
+dfs_status dfs_solve_batched(dfs_handle h, const dfs_problem* problems, int count, int s_dtype,
+                             const dfs_options* opt, void* stream_, int* status_out) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!problems || count < 1) return fail(h, DFS_ERR_INVALID_ARG, "empty problem list");
+    int64_t n_max = 1, m_max = 1, k_max = 1;
+    for (int i = 0; i < count; ++i) {
+        const dfs_problem& q = problems[i];
+        dfs_status s;
+        if ((s = check_s(h, q.S, s_dtype, q.n, q.m, q.lds)) != DFS_OK) return s;
+        if ((s = check_lambda(h, q.lambda)) != DFS_OK) return s;
+        if (!q.V || !q.X || q.k < 1 || q.ldv < q.m || q.ldx < q.m)
+            return fail(h, DFS_ERR_INVALID_ARG, "problem %d: bad V/X arguments", i);
+        n_max = q.n > n_max ? q.n : n_max;
+        m_max = q.m > m_max ? q.m : m_max;
+        k_max = q.k > k_max ? q.k : k_max;
+    }
+    if (count > h->bstat_count) {
+        if (h->bstat) cudaFree(h->bstat);
+        h->bstat = nullptr;
+        h->bstat_count = 0;
+        if (cudaMalloc(&h->bstat, sizeof(int) * count) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, DFS_ERR_NO_MEMORY, "cudaMalloc for batch status failed");
+        }
+        h->bstat_count = count;
+    }
+    for (int i = 0; i < count; ++i) {
+        const dfs_problem& q = problems[i];
+        dfs_status s = solve_device(h, q.S, s_dtype, q.n, q.m, q.lds, q.V, q.k, q.ldv, q.lambda, q.X, q.ldx, opt,
+                                    stream, nullptr);
+        if (s != DFS_OK) return s;
+        DFS_CK(launch_status_save(h->dstat, h->bstat + i, stream));
+    }
+    if (status_out) {
+        DFS_CK(cudaMemcpyAsync(status_out, h->bstat, sizeof(int) * count, cudaMemcpyDeviceToHost, stream));
+        DFS_CK(cudaStreamSynchronize(stream));
+        for (int i = 0; i < count; ++i)
+            if (status_out[i] != DFS_OK) return fail(h, (dfs_status)status_out[i], "problem %d: %s", i,
+                                                     dfs_status_string(status_out[i]));
+    }
+    return DFS_OK;
+}
+
+}  // extern "C"

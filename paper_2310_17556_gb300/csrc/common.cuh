@@ -1,0 +1,124 @@
+// Shared device/host helpers of libdfs (internal header, not part of the C ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dfs.h"
+
+namespace dfs {
+
+constexpr int kNumSmsGB300 = 152;
+
+// Device-side status word layout (int32 array in the handle's workspace).
+//   [0] status (dfs_status), [1] failed pivot (int, -1 none), [2] converged flag,
+//   [3] refinement passes done, [4] stop flag (set once converged or diverged)
+struct DevStatus {
+    int status;
+    int failed_pivot;
+    int converged;
+    int iters;
+    int stop;
+    int pad[3];
+    double rel_correction;
+    double rel_residual;
+    double prev_correction;
+    double pad2;
+};
+
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(double x) { return (float)x; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename T>
+struct Vec16;  // 16-byte vector load of storage type T, unpacked to the accumulate type
+template <>
+struct Vec16<float> {
+    static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+    static constexpr int N = 2;
+};
+template <>
+struct Vec16<__nv_bfloat16> {
+    static constexpr int N = 8;
+};
+
+// Load 16 bytes from global memory (read-only path) and unpack to N values of type A.
+template <typename T, typename A>
+__device__ __forceinline__ void load16(const T* p, A* out);
+
+template <>
+__device__ __forceinline__ void load16<float, float>(const float* p, float* o) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load16<float, double>(const float* p, double* o) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load16<double, double>(const double* p, double* o) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = v.x; o[1] = v.y;
+}
+template <>
+__device__ __forceinline__ void load16<__nv_bfloat16, float>(const __nv_bfloat16* p, float* o) {
+    uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        o[2 * i] = __uint_as_float(w[i] << 16);
+        o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+// Streaming (evict-first) 16-byte load for data read exactly once.
+template <typename T, typename A>
+__device__ __forceinline__ void load16_stream(const T* p, A* out);
+template <>
+__device__ __forceinline__ void load16_stream<float, float>(const float* p, float* o) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load16_stream<double, double>(const double* p, double* o) {
+    double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+    o[0] = v.x; o[1] = v.y;
+}
+template <>
+__device__ __forceinline__ void load16_stream<__nv_bfloat16, float>(const __nv_bfloat16* p, float* o) {
+    uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        o[2 * i] = __uint_as_float(w[i] << 16);
+        o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+// Scalar guarded load (tails).
+template <typename T, typename A>
+__device__ __forceinline__ A load1(const T* p) {
+    return (A)(*p);
+}
+template <>
+__device__ __forceinline__ float load1<__nv_bfloat16, float>(const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
+}
+template <>
+__device__ __forceinline__ double load1<__nv_bfloat16, double>(const __nv_bfloat16* p) {
+    return (double)__bfloat162float(*p);
+}
+
+__host__ __device__ constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ constexpr int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+__device__ __forceinline__ void set_status(DevStatus* st, int code) {
+    atomicCAS(&st->status, 0, code);
+}
+
+}  // namespace dfs

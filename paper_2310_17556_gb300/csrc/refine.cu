@@ -1,0 +1,162 @@
+// Device-side control of the n-space iterative refinement (mixed-precision paths).
+//
+// Algorithm 1 solves the n x n system (S S^T + lambda I~) y = S v (Appendix A) with the factor
+// of W = S S^T + lambda I~.  When W is formed in low precision (W~ = W + E), y_0 = W~^{-1} S v
+// is refined with the exact operator:  r = S v - (S S^T + lambda I~) y = S (v - S^T y) - lambda y
+// (one pass over S, pass.cu), dy = W~^{-1} r (trsv.cu), y += dy.  The x of Algorithm 1 step 4,
+// x = (v - S^T y) / lambda, is written by the same pass.  The size of the next x correction is
+// estimated in n-space without another pass:  dx = -S^T dy / lambda and
+//   ||S^T dy||^2 = dy^T S S^T dy = dy^T (W~ dy) - lambda ||dy||^2 - dy^T E dy ~ dy^T r - lambda ||dy||^2,
+// so  ||dx|| / ||x|| ~ sqrt(max(dy^T r - lambda dy^T dy, 0)) / ||v - S^T y||  (per RHS, max).
+// Stopping: converged when that ratio <= tol; otherwise y += dy; stop with NOT_CONVERGED when
+// the iteration budget is used up or the ratio fails to halve (stagnation or divergence).  Once
+// stopped, every later kernel of the solve sees `stop` and returns at once, so a fixed launch
+// sequence serves any iteration count (no host round trip).
+#include "kernels.cuh"
+
+namespace dfs {
+
+__global__ void status_reset_kernel(DevStatus* st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->status = 0;
+        st->failed_pivot = -1;
+        st->converged = 0;
+        st->iters = 0;
+        st->stop = 0;
+        st->rel_correction = 0.0;
+        st->rel_residual = 0.0;
+        st->prev_correction = 0.0;
+        st->pad2 = 0.0;
+    }
+}
+
+// After the first solve: y = z (the solve type T -> FP64), remember ||b|| per RHS.
+template <typename T>
+__global__ void __launch_bounds__(256)
+refine_init_kernel(const T* __restrict__ Z, int n_pad, int KQ, double* __restrict__ Y,
+                   const double* __restrict__ R, double* __restrict__ bnorm2, DevStatus* st) {
+    if (st->status != 0) return;
+    __shared__ double red[8][8];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int e = threadIdx.x; e < n_pad * KQ; e += blockDim.x) {
+        Y[e] = (double)Z[e];
+        const double r = R[e];
+        acc[e % KQ] += r * r;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = 0; q < 8; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < KQ) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+        bnorm2[threadIdx.x] = v;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+refine_control_kernel(const T* __restrict__ Z, const double* __restrict__ R, int n_pad, int KQ, int k,
+                      double* __restrict__ Y, const double* __restrict__ U2, const double* __restrict__ bnorm2,
+                      double lambda, double tol, int it, int max_iter, DevStatus* st) {
+    if (st->status != 0 || st->stop) return;
+    __shared__ double red[3][8][8];
+    __shared__ int decision;  // 0 = continue (apply dy), 1 = converged, 2 = give up
+    double dyr[8] = {0, 0, 0, 0, 0, 0, 0, 0}, dyy[8] = {0, 0, 0, 0, 0, 0, 0, 0}, rr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int e = threadIdx.x; e < n_pad * KQ; e += blockDim.x) {
+        const double dy = (double)Z[e];
+        const double r = R[e];
+        const int q = e % KQ;
+        dyr[q] += dy * r;
+        dyy[q] += dy * dy;
+        rr[q] += r * r;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = 0; q < 8; ++q) {
+        double a = dyr[q], b = dyy[q], c = rr[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) {
+            red[0][warp][q] = a;
+            red[1][warp][q] = b;
+            red[2][warp][q] = c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double rel = 0.0, relr = 0.0;
+        bool finite = true;
+        for (int q = 0; q < k && q < KQ; ++q) {
+            double a = 0, b = 0, c = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                a += red[0][w][q];
+                b += red[1][w][q];
+                c += red[2][w][q];
+            }
+            const double dx2 = fmax(a - lambda * b, 0.0);
+            const double x2 = fmax(U2[q], 1e-300);
+            const double rq = sqrt(dx2 / x2);
+            const double rn = sqrt(c / fmax(bnorm2[q], 1e-300));
+            if (!isfinite(rq) || !isfinite(rn)) finite = false;
+            rel = fmax(rel, rq);
+            relr = fmax(relr, rn);
+        }
+        st->rel_correction = rel;
+        st->rel_residual = relr;
+        st->iters = it;
+        if (!finite) {
+            set_status(st, DFS_ERR_NONFINITE);
+            st->stop = 1;
+            decision = 2;
+        } else if (rel <= tol) {
+            st->converged = 1;
+            st->stop = 1;
+            decision = 1;
+        } else if (it >= max_iter || (it > 1 && rel > 0.5 * st->prev_correction)) {
+            set_status(st, DFS_ERR_NOT_CONVERGED);
+            st->stop = 1;
+            decision = 2;
+        } else {
+            st->prev_correction = rel;
+            decision = 0;
+        }
+    }
+    __syncthreads();
+    if (decision == 0) {
+        for (int e = threadIdx.x; e < n_pad * KQ; e += blockDim.x) Y[e] += (double)Z[e];
+    }
+}
+
+cudaError_t launch_status_reset(DevStatus* st, cudaStream_t stream) {
+    status_reset_kernel<<<1, 32, 0, stream>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_init(int f64, const void* Z, int n_pad, int KQ, double* Y, const double* R,
+                               double* bnorm2, DevStatus* st, cudaStream_t stream) {
+    if (f64)
+        refine_init_kernel<double><<<1, 256, 0, stream>>>(static_cast<const double*>(Z), n_pad, KQ, Y, R, bnorm2, st);
+    else
+        refine_init_kernel<float><<<1, 256, 0, stream>>>(static_cast<const float*>(Z), n_pad, KQ, Y, R, bnorm2, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_control(int f64, const void* Z, const double* R, int n_pad, int KQ, int k, double* Y,
+                                  const double* U2, const double* bnorm2, double lambda, double tol, int it,
+                                  int max_iter, DevStatus* st, cudaStream_t stream) {
+    if (f64)
+        refine_control_kernel<double><<<1, 256, 0, stream>>>(static_cast<const double*>(Z), R, n_pad, KQ, k, Y, U2,
+                                                              bnorm2, lambda, tol, it, max_iter, st);
+    else
+        refine_control_kernel<float><<<1, 256, 0, stream>>>(static_cast<const float*>(Z), R, n_pad, KQ, k, Y, U2,
+                                                             bnorm2, lambda, tol, it, max_iter, st);
+    return cudaGetLastError();
+}
+
+}  // namespace dfs

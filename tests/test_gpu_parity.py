@@ -1,0 +1,210 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step and end to end.
+
+Inputs come from the seeded generators; the oracle gets the exact stored values (widened to
+FP64).  Tolerances:
+  * FP64 path: e_rel <= 1e-10 (FP64 arithmetic throughout; cond(A) <= ~1e3 here).
+  * FP32 path: e_rel <= 1e-5 (the plain-FP32 bar); Gram entries within 2e-5 * max|W|.
+  * mixed paths (tensor Gram + refinement): e_rel <= 1e-6.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2310_17556_gb300 import DfsError, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+dfs = pytest.importorskip("paper_2310_17556_gb300")
+
+
+def dev():
+    return torch.device("cuda", 0)
+
+
+def np64(t):
+    return t.detach().to("cpu").to(torch.float64).numpy()
+
+
+def solve_ref(S, V, lam):
+    """Oracle x for S (n, m) and V (k, m) torch tensors; returns (k, m) float64."""
+    return oracle.solve(np64(S), np64(V).T, lam).T
+
+
+def rel_err(x, ref):
+    x = np.asarray(x, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.linalg.norm(x - ref, axis=-1) / np.linalg.norm(ref, axis=-1)))
+
+
+# ---------------------------------------------------------------------------- end to end
+
+
+@pytest.mark.parametrize("n,m,k,lam", [(256, 16384, 1, 1e-3), (100, 3001, 3, 1e-2), (130, 999, 2, 0.5)])
+def test_fp64_path_matches_oracle(n, m, k, lam):
+    S = wl.gaussian(n, m, seed=11 + n, device=dev(), dtype=torch.float64)
+    V = wl.rhs(m, k, seed=12 + n, device=dev(), dtype=torch.float64)
+    X, info = dfs.dfs_solve(S, V, lam, precision="fp64")
+    assert info["status"] == 0 and info["precision"] == "fp64"
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-10
+
+
+def test_fp64_orthonormal_rows_closed_form():
+    n, m, lam = 256, 16384, 1e-3
+    S = wl.orthonormal_rows(n, m, seed=3, device=dev(), dtype=torch.float64)
+    v = wl.rhs(m, 1, seed=4, device=dev(), dtype=torch.float64)
+    X, info = dfs.dfs_solve(S, v, lam, precision="fp64")
+    s, vv = np64(S), np64(v)[0]
+    x_cf = (vv - s.T @ (s @ vv) / (1 + lam)) / lam
+    assert rel_err(np64(X)[0], x_cf) <= 1e-10
+
+
+@pytest.mark.parametrize("n,m,k,lam", [
+    (1024, 65536, 1, 1e-2),   # several 128-tiles, full strips
+    (257, 33333, 3, 1e-3),    # ragged n and m
+    (100, 5000, 8, 1e-1),     # n below one tile, 8 RHS
+    (300, 100, 1, 1e-2),      # m < n
+    (1, 777, 2, 0.3),         # n = 1
+    (64, 4096, 11, 1e-2),     # k > 8: two RHS groups
+])
+def test_fp32_path_matches_oracle(n, m, k, lam):
+    S = wl.gaussian(n, m, seed=21 + n, device=dev())
+    V = wl.rhs(m, k, seed=22 + n, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="fp32")
+    assert info["status"] == 0 and info["precision"] == "fp32"
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-5
+
+
+def test_fp32_path_svd_structured_small():
+    n, m = 256, 65536
+    S, U, s, Vf = wl.svd_structured(n, m, seed=5, sigma_min=1e-3, device=dev())
+    v = wl.rhs(m, 1, seed=6, device=dev())
+    for lam in (1e-2, 1e-4):
+        X, info = dfs.dfs_solve(S, v, lam, precision="fp32")
+        assert rel_err(np64(X), solve_ref(S, v, lam)) <= 1e-5
+
+
+def test_bf16_storage_fp32_path():
+    n, m, lam = 200, 20000, 1e-2
+    S = wl.gaussian(n, m, seed=7, device=dev(), dtype=torch.bfloat16)
+    V = wl.rhs(m, 2, seed=8, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="fp32")
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-5
+
+
+def test_padded_leading_dimension_and_in_place():
+    n, m, lam = 70, 1001, 1e-2
+    big = wl.gaussian(n, 1024, seed=9, device=dev())
+    S = big[:, :m]  # lds = 1024 > m
+    Vb = wl.rhs(1008, 2, seed=10, device=dev())
+    V = Vb[:, :m]
+    ref = solve_ref(S, V, lam)
+    X, _ = dfs.dfs_solve(S, V, lam, X=V, precision="fp32")  # X aliases V
+    assert X.data_ptr() == V.data_ptr()
+    assert rel_err(np64(V), ref) <= 1e-5
+
+
+# ---------------------------------------------------------------------------- single steps
+
+
+@pytest.mark.parametrize("dtype,prec,n,m,tol", [
+    (torch.float32, "fp32", 300, 10001, 2e-5), (torch.float64, "fp64", 130, 3000, 1e-12),
+    (torch.bfloat16, "fp32", 129, 4099, 2e-5)])
+def test_gram_step(dtype, prec, n, m, tol):
+    lam = 0.25
+    S = wl.gaussian(n, m, seed=31, device=dev(), dtype=dtype)
+    W = dfs.dfs_gram(S, lam, precision=prec)
+    Wr = oracle.gram(np64(S), lam)
+    lo = np.tril(np.ones((n, n), bool))
+    err = np.abs(np64(W) - Wr)[lo].max() / np.abs(Wr).max()
+    assert err <= tol
+    assert np.all(np64(W)[~lo] == 0.0)  # upper triangle untouched (zeros from the caller)
+
+
+@pytest.mark.parametrize("dtype,n,tol", [(torch.float32, 300, 1e-5), (torch.float64, 200, 1e-12),
+                                         (torch.float32, 1024, 1e-5), (torch.float32, 33, 1e-5)])
+def test_cholesky_step(dtype, n, tol):
+    A = wl.gaussian(n, 3 * n, seed=41, device=dev(), dtype=torch.float64)
+    Wr = (A @ A.T + 0.5 * torch.eye(n, device=dev(), dtype=torch.float64)).cpu().numpy()
+    W = torch.tensor(Wr, device=dev(), dtype=dtype)
+    L, piv = dfs.dfs_cholesky(W)
+    assert piv == -1
+    Lr = oracle.cholesky_lower(np64(W))
+    Lg = np.tril(np64(L))
+    assert np.abs(Lg - Lr).max() / np.abs(Lr).max() <= tol
+    assert (np.diag(Lg) > 0).all()
+
+
+def test_cholesky_reports_failed_pivot():
+    n = 100
+    d = torch.ones(n, dtype=torch.float32)
+    d[70] = -1.0
+    W = torch.diag(d).to(dev())
+    with pytest.raises(DfsError) as e:
+        dfs.dfs_cholesky(W)
+    assert e.value.status == 2
+    assert "pivot 70" in str(e.value)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-5), (torch.float64, 1e-12)])
+@pytest.mark.parametrize("trans", [False, True])
+def test_trsm_step(dtype, tol, trans):
+    n, k = 333, 5
+    g = torch.Generator().manual_seed(51)
+    Lr = torch.tril(torch.randn(n, n, generator=g, dtype=torch.float64)) / math.sqrt(n) + 2 * torch.eye(n, dtype=torch.float64)
+    B = torch.randn(n, k, generator=g, dtype=torch.float64)
+    L = Lr.to(dev(), dtype)
+    Bd = B.to(dev(), dtype).contiguous()
+    out = dfs.dfs_trsm(L, Bd, trans=trans)
+    Ln = np64(L)
+    ref = oracle.back_substitution_transposed(Ln, B.numpy()) if trans else oracle.forward_substitution(Ln, B.numpy())
+    assert np.abs(np64(out) - ref).max() / np.abs(ref).max() <= tol
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
+def test_fisher_pass_step(dtype):
+    n, m, k, lam = 150, 12345, 3, 1e-2
+    S = wl.gaussian(n, m, seed=61, device=dev(), dtype=dtype)
+    vdt = torch.float64 if dtype == torch.float64 else torch.float32
+    V = wl.rhs(m, k, seed=62, device=dev(), dtype=vdt)
+    Y = torch.randn(n, k, device=dev(), dtype=torch.float64) * 0.3
+    X, R = dfs.dfs_fisher_pass(S, V, lam, Y)
+    s, v, y = np64(S), np64(V).T, np64(Y)
+    u = v - s.T @ y
+    tol = 1e-12 if dtype == torch.float64 else 2e-6
+    assert rel_err(np64(X), (u / lam).T) <= tol
+    r_ref = oracle.residual_n_space(s, v, y, lam)
+    assert np.abs(np64(R) - r_ref).max() / np.abs(r_ref).max() <= tol * 5
+    # Y = None: R = S v (the right-hand side of the n-space system), X = v / lam
+    X0, R0 = dfs.dfs_fisher_pass(S, V, lam, None)
+    assert rel_err(np64(R0).T, (s @ v).T) <= tol
+    assert rel_err(np64(X0), (v / lam).T) <= (1e-15 if dtype == torch.float64 else 1e-7)
+
+
+# ---------------------------------------------------------------------------- arguments
+
+
+def test_invalid_arguments_rejected():
+    S = torch.zeros(8, 64, device=dev())
+    V = torch.zeros(1, 64, device=dev())
+    for lam in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(DfsError) as e:
+            dfs.dfs_solve(S, V, lam)
+        assert e.value.status == 1
+    S2 = torch.zeros(8, 66, device=dev())[:, :63]  # lds = 66 floats: not a multiple of 16 bytes
+    with pytest.raises(DfsError) as e:
+        dfs.dfs_solve(S2, torch.zeros(1, 63, device=dev()), 1.0)
+    assert e.value.status == 1
+    with pytest.raises(DfsError) as e:
+        dfs.dfs_solve(S.double(), V.double(), 1.0, precision="fp32")
+    assert e.value.status == 1
+
+
+def test_zero_score_matrix_gives_v_over_lambda():
+    S = torch.zeros(40, 1000, device=dev())
+    V = wl.rhs(1000, 1, seed=71, device=dev())
+    X, info = dfs.dfs_solve(S, V, 0.125, precision="fp32")
+    assert torch.equal(X, V / 0.125)

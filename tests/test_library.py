@@ -1,0 +1,73 @@
+"""Host-side checks of the C-ABI library (no GPU work): it builds, loads and exports every
+entry point include/dfs.h declares; the binding refuses to run without it."""
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dfs.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dfs_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2310_17556_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dfs_solve", "dfs_solve_batched", "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass",
+                     "dfs_solve_host", "dfs_create", "dfs_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (dfs_[a-z_]+)\b", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_ctypes_loads_and_binds(libpath):
+    from paper_2310_17556_gb300 import _lib
+
+    lib = _lib.load()
+    for name in declared_functions():
+        assert hasattr(lib, name)
+    assert set(_lib.EXPORTS) == set(declared_functions())
+    assert lib.dfs_status_string(2) == b"DFS_ERR_NOT_SPD"
+    assert lib.dfs_status_string(0) == b"DFS_OK"
+
+
+def test_library_is_built_for_sm103a(libpath):
+    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_null_handle_is_rejected(libpath):
+    from paper_2310_17556_gb300 import _lib
+
+    lib = _lib.load()
+    assert lib.dfs_destroy(None) == _lib.DFS_ERR_INVALID_ARG
+    assert lib.dfs_solve(None, None, 1, 1, 1, 4, None, 1, 1, 1.0, None, 1, None, None, None) == _lib.DFS_ERR_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2310_17556_gb300 import _lib
+
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libdfs.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load()
