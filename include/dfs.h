@@ -68,11 +68,17 @@ typedef enum {
     DFS_PREC_BF16X3 = 5  /* tcgen05 split-BF16 (hi/lo, three products) Gram + refinement */
 } dfs_precision;
 
+/* dfs_options.flags */
+#define DFS_FLAG_STEP_TIMING 1  /* record CUDA events around the steps; dfs_info.ms is filled */
+#define DFS_FLAG_FP32_PANEL 2   /* factor the 32 x 32 diagonal blocks of the Cholesky step in FP32
+                                   instead of FP64 (FP32 and mixed paths only; faster on GB300,
+                                   whose FP64 pipe is narrow and long-latency) */
+
 typedef struct {
     int precision;   /* dfs_precision */
     int max_iter;    /* refinement passes after the first solve (mixed paths); <0 = default 8 */
-    double tol;      /* stop when the estimated relative x-space correction <= tol; <=0 = 1e-7 */
-    int flags;       /* reserved, pass 0 */
+    double tol;      /* stop when the estimated relative error left in x <= tol; <=0 = 1e-7 */
+    int flags;       /* DFS_FLAG_* bits, 0 for none */
 } dfs_options;
 
 typedef struct {
@@ -80,8 +86,12 @@ typedef struct {
     int precision_used;     /* dfs_precision actually run */
     int iters;              /* refinement passes run (0 on the FP32/FP64 paths) */
     int failed_pivot;       /* first non-positive pivot index, -1 if none */
-    double rel_correction;  /* last estimated ||dx|| / ||x|| (0 if no refinement) */
+    double rel_correction;  /* estimated relative error left in x (0 if no refinement) */
     double rel_residual_n;  /* last ||r_n|| / ||S v||, r_n = S v - (S S^T + lambda I) y */
+    float ms[5];            /* with DFS_FLAG_STEP_TIMING: [0] Gram kernel, [1] Gram finalize +
+                               Cholesky, [2] first n-space solve (S v pass, two triangular
+                               solves), [3] the rest (refinement or the x pass), [4] whole call;
+                               zeros otherwise */
 } dfs_info;
 
 typedef struct dfs_handle_s* dfs_handle;
@@ -91,6 +101,9 @@ typedef struct dfs_handle_s* dfs_handle;
  * out-pointer), CUDA (bad device), UNSUPPORTED (device is not compute capability 10.3). */
 dfs_status dfs_create(dfs_handle* handle, int device);
 dfs_status dfs_destroy(dfs_handle handle);
+
+/* Number of CUDA kernels this library has launched in the calling process (all handles). */
+int64_t dfs_kernel_launches(void);
 
 /* Static text for a status code; never NULL. */
 const char* dfs_status_string(int status);
@@ -124,6 +137,11 @@ dfs_status dfs_solve_host(dfs_handle handle, const void* S, int s_dtype, int64_t
 
 /* Synchronize `stream` and report the device status of the last dfs_solve on this handle. */
 dfs_status dfs_sync_info(dfs_handle handle, void* stream, dfs_info* info);
+
+/* Mean step times in ms (layout of dfs_info.ms) over the solves run with DFS_FLAG_STEP_TIMING
+ * since the previous call, at most the last 64; waits for the last of their events.
+ * *count (may be NULL) receives how many solves were averaged (0: mean_ms all zero). */
+dfs_status dfs_step_times(dfs_handle handle, float* mean_ms, int* count);
 
 /* One independent problem of a batch (all pointers device memory, same dtype rules). */
 typedef struct {

@@ -12,10 +12,12 @@ from .api import (  # noqa: F401
     dfs_cholesky,
     dfs_fisher_pass,
     dfs_gram,
+    dfs_kernel_launches,
     dfs_reserve,
     dfs_solve,
     dfs_solve_batched,
     dfs_solve_host,
+    dfs_step_times,
     dfs_sync_info,
     dfs_trsm,
 )

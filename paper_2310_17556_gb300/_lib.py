@@ -28,8 +28,8 @@ PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 
 # every entry point include/dfs.h declares
 EXPORTS = (
-    "dfs_create", "dfs_destroy", "dfs_status_string", "dfs_last_error", "dfs_reserve",
-    "dfs_solve", "dfs_solve_host", "dfs_sync_info", "dfs_solve_batched",
+    "dfs_create", "dfs_destroy", "dfs_status_string", "dfs_last_error", "dfs_reserve", "dfs_kernel_launches",
+    "dfs_solve", "dfs_solve_host", "dfs_sync_info", "dfs_step_times", "dfs_solve_batched",
     "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass",
 )
 
@@ -40,7 +40,12 @@ class dfs_options(C.Structure):
 
 class dfs_info(C.Structure):
     _fields_ = [("status", C.c_int), ("precision_used", C.c_int), ("iters", C.c_int),
-                ("failed_pivot", C.c_int), ("rel_correction", C.c_double), ("rel_residual_n", C.c_double)]
+                ("failed_pivot", C.c_int), ("rel_correction", C.c_double), ("rel_residual_n", C.c_double),
+                ("ms", C.c_float * 5)]
+
+
+DFS_FLAG_STEP_TIMING = 1
+DFS_FLAG_FP32_PANEL = 2
 
 
 class dfs_problem(C.Structure):
@@ -55,6 +60,7 @@ _SIGS = {
     "dfs_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
     "dfs_destroy": (C.c_int, [_VP]),
     "dfs_status_string": (C.c_char_p, [C.c_int]),
+    "dfs_kernel_launches": (C.c_int64, []),
     "dfs_last_error": (C.c_char_p, [_VP]),
     "dfs_reserve": (C.c_int, [_VP, _I64, _I64, _I64, C.c_int]),
     "dfs_solve": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, C.c_double, _VP, _I64,
@@ -62,6 +68,7 @@ _SIGS = {
     "dfs_solve_host": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, C.c_double, _VP, _I64,
                                  C.POINTER(dfs_options), _VP, C.POINTER(dfs_info)]),
     "dfs_sync_info": (C.c_int, [_VP, _VP, C.POINTER(dfs_info)]),
+    "dfs_step_times": (C.c_int, [_VP, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
     "dfs_solve_batched": (C.c_int, [_VP, C.POINTER(dfs_problem), C.c_int, C.c_int, C.POINTER(dfs_options), _VP,
                                     C.POINTER(C.c_int)]),
     "dfs_gram": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, C.c_double, C.c_int, _VP, _I64, _VP]),

@@ -43,9 +43,10 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def _opts(precision, max_iter, tol) -> dfs_options:
+def _opts(precision, max_iter, tol, timing=False, fp32_panel=False) -> dfs_options:
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return dfs_options(p, int(max_iter), float(tol), 0)
+    flags = (_lib.DFS_FLAG_STEP_TIMING if timing else 0) | (_lib.DFS_FLAG_FP32_PANEL if fp32_panel else 0)
+    return dfs_options(p, int(max_iter), float(tol), flags)
 
 
 def _check(lib, h, status: int):
@@ -57,7 +58,7 @@ def _check(lib, h, status: int):
 def _info_dict(info: dfs_info) -> dict:
     return dict(status=info.status, precision=_lib.PRECISION_NAMES.get(info.precision_used, "?"),
                 iters=info.iters, failed_pivot=info.failed_pivot, rel_correction=info.rel_correction,
-                rel_residual_n=info.rel_residual_n)
+                rel_residual_n=info.rel_residual_n, ms=[float(x) for x in info.ms])
 
 
 class Handle:
@@ -94,6 +95,11 @@ def default_handle(device: int | None = None) -> Handle:
     return _default[d]
 
 
+def dfs_kernel_launches() -> int:
+    """Kernels libdfs has launched in this process."""
+    return int(_lib.load().dfs_kernel_launches())
+
+
 def dfs_reserve(n_max: int, m_max: int, k_max: int, precision="auto", handle: Handle | None = None):
     h = handle or default_handle()
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -102,7 +108,7 @@ def dfs_reserve(n_max: int, m_max: int, k_max: int, precision="auto", handle: Ha
 
 def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
               max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
-              sync: bool = True):
+              sync: bool = True, timing: bool = False, fp32_panel: bool = False):
     """Solve (S^T S + lam I) X^T = V^T for the k rows of V (Eq. 1, Algorithm 1).
 
     Returns (X, info) when sync is True (info = dict of dfs_info), else (X, None) with the work
@@ -118,7 +124,7 @@ def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | No
         raise TypeError(f"V must be {vdt} for S of dtype {S.dtype}")
     if X is None:
         X = torch.empty((k, m), device=S.device, dtype=vdt)
-    opt = _opts(precision, max_iter, tol)
+    opt = _opts(precision, max_iter, tol, timing, fp32_panel)
     info = dfs_info()
     st = h.lib.dfs_solve(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k, _rows(V, "V"),
                          float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt), _stream(stream),
@@ -138,6 +144,15 @@ def dfs_sync_info(handle: Handle | None = None, stream=None) -> dict:
     if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
         _check(h.lib, h.h, st)
     return _info_dict(info)
+
+
+def dfs_step_times(handle: Handle | None = None) -> tuple[list[float], int]:
+    """Mean [gram, finalize+cholesky, first solve, rest, total] ms over recent timed solves."""
+    h = handle or default_handle()
+    out = (C.c_float * 5)()
+    cnt = C.c_int(0)
+    _check(h.lib, h.h, h.lib.dfs_step_times(h.h, out, C.byref(cnt)))
+    return [float(x) for x in out], int(cnt.value)
 
 
 def dfs_solve_host(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",

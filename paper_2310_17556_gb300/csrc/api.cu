@@ -1,6 +1,7 @@
 // C ABI of libdfs (declared in include/dfs.h): argument checks, workspace planning and the
 // launch sequence of Algorithm 1 (arXiv 2310.17556) with Q inlined (Section 2).
 #include <cmath>
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,13 @@
 #include "kernels.cuh"
 
 using namespace dfs;
+
+namespace dfs {
+std::atomic<long long>& launch_counter() {
+    static std::atomic<long long> c{0};
+    return c;
+}
+}  // namespace dfs
 
 struct dfs_handle_s {
     int device = 0;
@@ -23,6 +31,15 @@ struct dfs_handle_s {
     int bstat_count = 0;
     size_t hbuf_bytes[3] = {0, 0, 0};
     int last_precision = 0;
+    // Step-timing events: a ring of kTimingSlots solves x kMarks marks (DFS_FLAG_STEP_TIMING).
+    // Marks: 0 start, 1 Gram kernel start, 2 Gram kernel end, 3 Cholesky end, 4 first n-space
+    // solve end, 5 end of the call.
+    static constexpr int kTimingSlots = 64;
+    static constexpr int kMarks = 6;
+    cudaEvent_t ev[kTimingSlots][kMarks] = {};
+    int tslot = 0;      // slot of the last timed solve
+    int tpending = 0;   // timed solves not yet summarised by dfs_step_times
+    bool timed = false;  // last solve recorded the step events
     std::string err;
 };
 
@@ -64,9 +81,11 @@ struct Plan {
     int nsplit = 1;
     int64_t chunk = 0;
     GramTcPlan tc{};
-    int pgrid = 1;
+    PassPlan pp{};
+    int pgrid = 1;  // rows of the pass partial buffers
+    int pack = 0;   // tile packing done by the first S v pass: 0 none, 1 BF16, 2 TF32
     size_t off_W = 0, off_Linv = 0, off_P = 0, off_Rpart = 0, off_U2part = 0, off_R = 0, off_Z = 0, off_Y = 0,
-           off_U2 = 0, off_bn2 = 0, total = 0;
+           off_U2 = 0, off_V = 0, off_bn2 = 0, off_Sp = 0, total = 0;
 };
 
 int tc_kind(int prec) {
@@ -81,7 +100,9 @@ int tc_kind(int prec) {
 dfs_status resolve_precision(dfs_handle h, int s_dtype, int prec, int* out) {
     if (prec == DFS_PREC_AUTO) {
         if (s_dtype == DFS_F64) prec = DFS_PREC_FP64;
-        else prec = gram_tc_supported(s_dtype, 0) ? DFS_PREC_BF16 : DFS_PREC_FP32;
+        else if (gram_tc_supported(s_dtype, 0)) prec = DFS_PREC_BF16;
+        else if (gram_tc_supported(s_dtype, 1)) prec = DFS_PREC_TF32;
+        else prec = DFS_PREC_FP32;
     }
     switch (prec) {
         case DFS_PREC_FP64:
@@ -136,7 +157,9 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
         gram_simt_plan(n, m, p->f64, h->num_sms, &p->nsplit, &p->chunk);
         gram_bytes = gram_simt_partial_bytes(n, p->f64, p->nsplit);
     }
-    p->pgrid = pass_grid((int)n, kq, s_dtype, h->num_sms, m);
+    p->pp = pass_make_plan((int)n, kq, s_dtype, h->num_sms, m, h->smem_optin);
+    p->pgrid = pass_partial_rows(p->pp);
+    p->pack = (p->tensor && p->tc.packed) ? (p->tc.kind == 1 ? 2 : 1) : 0;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -148,12 +171,14 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     p->off_Linv = take(np * 32 * es);
     p->off_P = take(gram_bytes);
     p->off_Rpart = take((size_t)p->pgrid * n * kq * 8);
-    p->off_U2part = take((size_t)p->pgrid * kq * 8);
+    p->off_U2part = take((size_t)p->pgrid * 2 * kq * 8);
     p->off_R = take(np * kq * 8);
     p->off_Z = take(np * kq * es);
     p->off_Y = take(np * kq * 8);
-    p->off_U2 = take(8 * 8);
+    p->off_U2 = take(16 * 8);
+    p->off_V = take(p->tensor ? (size_t)k * round_up(m, 4) * (p->f64 ? 8 : 4) : 0);
     p->off_bn2 = take(8 * 8);
+    p->off_Sp = take(pack_bytes(s_dtype, p->pack, n, m));
     p->total = off;
     return DFS_OK;
 }
@@ -201,12 +226,17 @@ dfs_status check_lambda(dfs_handle h, double lambda) {
     return DFS_OK;
 }
 
-// Step 1 into the plan's padded W: Gram (+ lambda on the diagonal, identity padding).
+// Step 1 into W (rows < n_out, stride ldw): Gram + lambda on the diagonal (identity padding).
+// The tensor-core Gram on packed tiles first runs the S v pass in packing mode (with no V).
 dfs_status run_gram(dfs_handle h, const Plan& p, const void* S, int64_t lds, double lambda, void* W, int64_t ldw,
                     int64_t n_out, cudaStream_t stream) {
     void* P = at<void>(h, p.off_P);
     if (p.tensor) {
-        DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, P, h->dstat, stream));
+        void* Sp = p.pack ? at<void>(h, p.off_Sp) : nullptr;
+        if (p.pack)
+            DFS_CK(launch_sv_pack(p.pp, p.s_dtype, 1, p.pack, S, (int)p.n, p.m, lds, nullptr, p.m, 0,
+                                  at<double>(h, p.off_Rpart), Sp, h->dstat, stream));
+        DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, Sp, P, h->dstat, stream));
         DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, n_out, lambda, W, ldw, stream));
     } else {
         DFS_CK(launch_gram_simt(p.s_dtype, p.f64, S, p.n, p.m, lds, p.nsplit, p.chunk, P, stream));
@@ -214,6 +244,17 @@ dfs_status run_gram(dfs_handle h, const Plan& p, const void* S, int64_t lds, dou
                                     stream));
     }
     return DFS_OK;
+}
+
+// dfs_info.ms layout from the six marks of one solve.
+void step_ms(cudaEvent_t* e, float* ms) {
+    float t[5];
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], e[i], e[i + 1]);
+    ms[0] = t[1];         // Gram kernel
+    ms[1] = t[2];         // Gram finalize + Cholesky
+    ms[2] = t[0] + t[3];  // S v pass (with tile packing) + first triangular solves
+    ms[3] = t[4];         // refinement passes (or the x pass)
+    cudaEventElapsedTime(&ms[4], e[0], e[5]);
 }
 
 dfs_status fill_info(dfs_handle h, cudaStream_t stream, dfs_info* info) {
@@ -227,6 +268,8 @@ dfs_status fill_info(dfs_handle h, cudaStream_t stream, dfs_info* info) {
         info->failed_pivot = ds.failed_pivot;
         info->rel_correction = ds.rel_correction;
         info->rel_residual_n = ds.rel_residual;
+        for (int i = 0; i < 5; ++i) info->ms[i] = 0.0f;
+        if (h->timed) step_ms(h->ev[h->tslot], info->ms);
     }
     if (ds.status != 0) {
         if (ds.status == DFS_ERR_NOT_SPD || ds.status == DFS_ERR_NONFINITE)
@@ -275,43 +318,95 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
     const int ni = (int)n, npi = (int)p.n_pad, kq = p.kq;
     const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
 
-    DFS_CK(launch_status_reset(h->dstat, stream));
-    if ((s = run_gram(h, p, S, lds, lambda, W, p.n_pad, p.n_pad, stream)) != DFS_OK) return s;
-    DFS_CK(launch_cholesky(p.f64, W, p.n_pad, p.n_pad, Linv, h->dstat, stream));
+    const bool timed = opt && (opt->flags & DFS_FLAG_STEP_TIMING);
+    h->timed = false;
+    int slot = 0;
+    if (timed) {
+        slot = (h->tslot + 1) % dfs_handle_s::kTimingSlots;
+        if (!h->ev[slot][0])
+            for (int i = 0; i < dfs_handle_s::kMarks; ++i) DFS_CK(cudaEventCreate(&h->ev[slot][i]));
+    }
+    auto mark = [&](int i) -> cudaError_t {
+        return timed ? cudaEventRecord(h->ev[slot][i], stream) : cudaSuccess;
+    };
+    const int fp64_panel = !(opt && (opt->flags & DFS_FLAG_FP32_PANEL));
 
+    if (p.tensor) {
+        // Refinement reads V in every pass: when X overlaps V, work from a private copy of V.
+        const char* v0 = static_cast<const char*>(V);
+        const char* v1 = v0 + ((k - 1) * ldv + m) * vs;
+        const char* x0 = static_cast<const char*>(X);
+        const char* x1 = x0 + ((k - 1) * ldx + m) * vs;
+        if (x0 < v1 && v0 < x1) {
+            const int64_t ldc = round_up(m, 4);
+            void* Vc = at<void>(h, p.off_V);
+            DFS_CK(cudaMemcpy2DAsync(Vc, ldc * vs, V, ldv * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
+            V = Vc;
+            ldv = ldc;
+        }
+    }
+    void* Sp = p.pack ? at<void>(h, p.off_Sp) : nullptr;
+
+    DFS_CK(launch_status_reset(h->dstat, stream));
+    DFS_CK(mark(0));
     for (int64_t q0 = 0; q0 < k; q0 += kq) {
         const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
         const void* Vg = static_cast<const char*>(V) + q0 * ldv * vs;
         void* Xg = static_cast<char*>(X) + q0 * ldx * vs;
         DFS_CK(launch_group_reset(h->dstat, stream));
-        // b = S v (pass with y = 0), then y0 = W^{-1} b by the two triangular solves.
-        DFS_CK(launch_pass(s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, nullptr, kq, lambda, nullptr, ldx, Rpart,
-                           U2part, p.pgrid, h->dstat, 0, stream));
-        DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pgrid, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z, U2part, U2,
-                                  h->dstat, 0, stream));
+        // b = S v; the first group's pass also writes the packed tensor-core tiles of S
+        DFS_CK(launch_sv_pack(p.pp, s_dtype, kq, q0 == 0 ? p.pack : 0, S, ni, m, lds, Vg, ldv, kg, Rpart, Sp,
+                              h->dstat, stream));
+        DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.sv_grid, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z, nullptr,
+                                  nullptr, h->dstat, 0, stream));
+        if (q0 == 0) {
+            // Algorithm 1 steps 1-2: W = S S^T + lambda I~ and its Cholesky factor
+            void* P = at<void>(h, p.off_P);
+            DFS_CK(mark(1));
+            if (p.tensor)
+                DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, Sp, P, h->dstat, stream));
+            else
+                DFS_CK(launch_gram_simt(p.s_dtype, p.f64, S, p.n, p.m, lds, p.nsplit, p.chunk, P, stream));
+            DFS_CK(mark(2));
+            if (p.tensor)
+                DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, p.n_pad, lambda, W, p.n_pad, stream));
+            else
+                DFS_CK(launch_gram_finalize(p.f64, p.f64, gram_simt_tile(p.f64), P, p.nsplit, p.n, p.n_pad, lambda,
+                                            W, p.n_pad, stream));
+            DFS_CK(launch_cholesky(p.f64, W, p.n_pad, p.n_pad, Linv, h->dstat, stream, fp64_panel));
+            DFS_CK(mark(3));
+        }
+        // y0 = W^{-1} b by the two triangular solves
         DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
         DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
         DFS_CK(launch_refine_init(p.f64, Z, npi, kq, Y, R, bn2, h->dstat, stream));
+        if (q0 == 0) DFS_CK(mark(4));
         if (!p.tensor) {
             // x = (v - S^T y) / lambda
-            DFS_CK(launch_pass(s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr, U2part,
-                               p.pgrid, h->dstat, 0, stream));
+            DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr,
+                               U2part, 0, h->dstat, 0, stream));
         } else {
             for (int it = 1; it <= max_iter; ++it) {
-                DFS_CK(launch_pass(s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, Rpart, U2part,
-                                   p.pgrid, h->dstat, 1, stream));
-                DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pgrid, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z, U2part,
+                // x_0 = v / lambda for the first pass; afterwards x_{j-1} is read from X itself
+                DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, Rpart,
+                                   U2part, it == 1 ? 2 : 1, h->dstat, 1, stream));
+                DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.grid, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z, U2part,
                                           U2, h->dstat, 1, stream));
                 DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
                 DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
                 DFS_CK(launch_refine_control(p.f64, Z, R, npi, kq, kg, Y, U2, bn2, lambda, tol, it, max_iter,
                                              h->dstat, stream));
             }
-            if (max_iter == 0) {
-                DFS_CK(launch_pass(s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr, U2part,
-                                   p.pgrid, h->dstat, 0, stream));
-            }
+            if (max_iter == 0)
+                DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr,
+                                   U2part, 0, h->dstat, 0, stream));
         }
+    }
+    DFS_CK(mark(5));
+    h->timed = timed;
+    if (timed) {
+        h->tslot = slot;
+        if (h->tpending < dfs_handle_s::kTimingSlots) ++h->tpending;
     }
     if (info) return fill_info(h, stream, info);
     return DFS_OK;
@@ -351,6 +446,8 @@ const char* dfs_status_string(int status) {
 
 const char* dfs_last_error(dfs_handle h) { return h ? h->err.c_str() : ""; }
 
+int64_t dfs_kernel_launches(void) { return (int64_t)launch_counter().load(); }
+
 dfs_status dfs_create(dfs_handle* out, int device) {
     if (!out) return DFS_ERR_INVALID_ARG;
     *out = nullptr;
@@ -381,6 +478,9 @@ dfs_status dfs_destroy(dfs_handle h) {
     cudaSetDevice(h->device);
     if (h->ws) cudaFree(h->ws);
     if (h->dstat) cudaFree(h->dstat);
+    for (int sl = 0; sl < dfs_handle_s::kTimingSlots; ++sl)
+        for (int i = 0; i < dfs_handle_s::kMarks; ++i)
+            if (h->ev[sl][i]) cudaEventDestroy(h->ev[sl][i]);
     for (int i = 0; i < 3; ++i)
         if (h->hbuf[i]) cudaFree(h->hbuf[i]);
     if (h->bstat) cudaFree(h->bstat);
@@ -438,6 +538,26 @@ dfs_status dfs_solve_host(dfs_handle h, const void* S, int s_dtype, int64_t n, i
     if (s != DFS_OK) return s;
     DFS_CK(cudaMemcpy2DAsync(X, ldx * vs, h->hbuf[2], ldx_d * vs, m * vs, k, cudaMemcpyDeviceToHost, stream));
     return fill_info(h, stream, info);
+}
+
+dfs_status dfs_step_times(dfs_handle h, float* mean_ms, int* count) {
+    if (!h || !mean_ms) return DFS_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    const int nsl = h->tpending;
+    for (int i = 0; i < 5; ++i) mean_ms[i] = 0.0f;
+    if (count) *count = nsl;
+    if (nsl == 0) return DFS_OK;
+    DFS_CK(cudaEventSynchronize(h->ev[h->tslot][dfs_handle_s::kMarks - 1]));
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int j = 0; j < nsl; ++j) {
+        const int sl = (h->tslot - j + dfs_handle_s::kTimingSlots) % dfs_handle_s::kTimingSlots;
+        float ms[5];
+        step_ms(h->ev[sl], ms);
+        for (int i = 0; i < 5; ++i) acc[i] += ms[i];
+    }
+    for (int i = 0; i < 5; ++i) mean_ms[i] = (float)(acc[i] / nsl);
+    h->tpending = 0;
+    return DFS_OK;
 }
 
 dfs_status dfs_sync_info(dfs_handle h, void* stream, dfs_info* info) {
@@ -542,9 +662,10 @@ dfs_status dfs_fisher_pass(dfs_handle h, const void* S, int s_dtype, int64_t n, 
     const int kmax = pass_max_group((int)n, s_dtype, h->smem_optin);
     if (kmax < 1) return fail(h, DFS_ERR_UNSUPPORTED, "n too large for the pass kernel");
     if (kq > kmax) kq = kmax;
-    const int grid = pass_grid((int)n, kq, s_dtype, h->num_sms, m);
-    const size_t oR = 0, oU = align_up((size_t)grid * n * kq * 8), oU2 = oU + align_up((size_t)grid * kq * 8);
-    if ((s = ensure_ws(h, oU2 + 64, stream)) != DFS_OK) return s;
+    const PassPlan pp = pass_make_plan((int)n, kq, s_dtype, h->num_sms, m, h->smem_optin);
+    const int grid = pass_partial_rows(pp);
+    const size_t oR = 0, oU = align_up((size_t)grid * n * kq * 8), oU2 = oU + align_up((size_t)grid * 2 * kq * 8);
+    if ((s = ensure_ws(h, oU2 + 128, stream)) != DFS_OK) return s;
     double* Rpart = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oR);
     double* U2part = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oU);
     double* U2 = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oU2);
@@ -555,10 +676,10 @@ dfs_status dfs_fisher_pass(dfs_handle h, const void* S, int s_dtype, int64_t n, 
         const void* Vg = static_cast<const char*>(V) + q0 * ldv * vs;
         void* Xg = X ? static_cast<char*>(X) + q0 * ldx * vs : nullptr;
         const double* Yg = Y ? Y + q0 : nullptr;
-        DFS_CK(launch_pass(s_dtype, kq, S, (int)n, m, lds, Vg, ldv, kg, Yg, Y ? ldy : kq, lambda, Xg, ldx,
-                           R ? Rpart : nullptr, U2part, grid, h->dstat, 0, stream));
+        DFS_CK(launch_pass(pp, s_dtype, kq, S, (int)n, m, lds, Vg, ldv, kg, Yg, Y ? ldy : kq, lambda, Xg, ldx,
+                           R ? Rpart : nullptr, U2part, 0, h->dstat, 0, stream));
         if (R)
-            DFS_CK(launch_pass_reduce(0, Rpart, grid, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
+            DFS_CK(launch_pass_reduce(0, Rpart, pp.grid, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
                                       U2part, U2, h->dstat, 0, stream));
     }
     return DFS_OK;

@@ -19,82 +19,123 @@ namespace dfs {
 constexpr int NB = 32;
 constexpr int TU = 64;
 
-// Inverse of a lower-triangular NB x NB block held in shared memory (FP64), one column per
-// thread by forward substitution; written to dst (NB x NB row-major, zeros above the diagonal).
-template <typename T>
-__device__ void invert_lower_block(const double (*a)[NB + 1], double (*inv)[NB + 1], T* dst) {
-    const int tid = threadIdx.x;
-    if (tid < NB) {
-        const int c = tid;
-        for (int i = 0; i < c; ++i) inv[i][c] = 0.0;
-        inv[c][c] = 1.0 / a[c][c];
-        for (int i = c + 1; i < NB; ++i) {
-            double s = 0.0;
-            for (int p = c; p < i; ++p) s = fma(a[i][p], inv[p][c], s);
-            inv[i][c] = -s / a[i][i];
-        }
-    }
+// Inverse of the lower-triangular NB x NB factor l (shared memory, compute type CT), in the
+// storage precision T.  One warp per column c (columns c = warp, warp + 8, ...; needs 256
+// threads), lane i holds x_i of L x = e_c: for p = c..NB-1, lane p finalises x_p = x_p / L_pp,
+// broadcasts it, and lanes i > p subtract L_ip x_p.  Written to dst (NB x NB row-major, zeros
+// above the diagonal).
+template <typename T, typename CT>
+__device__ void invert_lower_block(const CT (*l)[NB + 1], T* dst) {
+    __shared__ T rd[NB];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < NB) rd[tid] = (T)1 / (T)l[tid][tid];
     __syncthreads();
-    for (int e = tid; e < NB * NB; e += blockDim.x) dst[e] = (T)inv[e / NB][e % NB];
+    for (int c = warp; c < NB; c += (int)(blockDim.x >> 5)) {
+        T x = (lane == c) ? (T)1 : (T)0;
+        for (int p = c; p < NB; ++p) {
+            if (lane == p) x *= rd[p];
+            const T xp = __shfl_sync(0xffffffffu, x, p);
+            if (lane > p) x = fma(-(T)l[lane][p], xp, x);
+        }
+        dst[lane * NB + c] = (lane >= c) ? x : (T)0;
+    }
     __syncthreads();
 }
 
-// Factor diagonal block kb in FP64 and write L_kb (storage type T) plus its inverse.
-// Needs blockDim.x >= 32 and `scratch` >= 2 * NB * (NB + 1) doubles of shared memory.
-template <typename T>
-__device__ void factor_diag_block(T* W, int64_t ld, int kb, T* Linv, DevStatus* st, double* scratch) {
-    double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(scratch);
-    double(*inv)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(scratch + NB * (NB + 1));
+// 1/sqrt(d): FP32 hardware estimate, then (FP64) two Newton steps r <- r (3 - d r^2) / 2, each
+// doubling the correct bits (~2^-22 -> 2^-44 -> below FP64 rounding).  A short dependent chain:
+// the pivots of the diagonal factor are the critical path of the whole Cholesky.
+__device__ __forceinline__ double rsqrt_ct(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return rsqrt(d);  // outside the FP32 estimate's safe range
+    double r = (double)rsqrtf((float)d);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double h = 0.5 * d * r;
+        r = fma(-h, r * r, 1.5 * r);  // r (1.5 - 0.5 d r^2)
+    }
+    return r;
+}
+__device__ __forceinline__ float rsqrt_ct(float d) { return rsqrtf(d); }
+
+// Factor diagonal block kb in the compute type CT (double: the FP64 diagonal panel; float: the
+// fast variant) and write L_kb (storage type T) plus its inverse.
+// Column j: d = a[j][j]; r = 1/sqrt(d) (one thread); L[j][j] = d r, L[i][j] = a[i][j] r (one
+// thread per row); then a[i][p] -= L[i][j] L[p][j] for j < p <= i (one FMA per element).  The
+// elements of the trailing triangle are enumerated by a table sorted by column descending, so
+// the trailing triangle of step j is exactly the first (31-j)(32-j)/2 table entries.
+// Needs 256 threads and `scratch` >= 2 * NB * (NB + 1) CT values of shared memory.
+template <typename T, typename CT>
+__device__ void factor_diag_block(T* W, int64_t ld, int kb, T* Linv, DevStatus* st, CT* scratch) {
+    CT(*a)[NB + 1] = reinterpret_cast<CT(*)[NB + 1]>(scratch);
+    CT(*l)[NB + 1] = reinterpret_cast<CT(*)[NB + 1]>(scratch + NB * (NB + 1));
     __shared__ int fail;
+    __shared__ CT rcol;
+    __shared__ unsigned short tab[NB * (NB + 1) / 2];
     const int tid = threadIdx.x;
     const int nth = blockDim.x;
     const int64_t o = (int64_t)kb * NB;
     for (int e = tid; e < NB * NB; e += nth) {
         const int i = e / NB, j = e % NB;
-        a[i][j] = (j <= i) ? (double)W[(o + i) * ld + o + j] : 0.0;
+        a[i][j] = (j <= i) ? (CT)W[(o + i) * ld + o + j] : (CT)0;
+        l[i][j] = (CT)0;
+    }
+    // tab[e] = (i << 8) | p over the lower triangle, p descending, i ascending within p
+    for (int e = tid; e < NB * (NB + 1) / 2; e += nth) {
+        int p = NB - 1, rem = e;
+        while (rem >= NB - p) {
+            rem -= NB - p;
+            --p;
+        }
+        tab[e] = (unsigned short)(((p + rem) << 8) | p);
     }
     if (tid == 0) fail = -1;
     __syncthreads();
     for (int j = 0; j < NB; ++j) {
-        const double d = a[j][j];
-        // d is the same in every thread, so the exit is uniform.
-        if (!(d > 0.0) || !isfinite(d)) {
-            if (tid == 0) fail = isfinite(d) ? j : -2 - j;  // -2 - j encodes a NaN/Inf pivot
-            break;
+        if (tid == 0) {
+            const CT d = a[j][j];
+            if (!(d > (CT)0) || !isfinite(d)) {
+                fail = isfinite(d) ? j : -2 - j;  // -2 - j encodes a NaN/Inf pivot
+            } else {
+                const CT r = rsqrt_ct(d);
+                rcol = r;
+                l[j][j] = d * r;
+            }
         }
-        const double ljj = sqrt(d);
         __syncthreads();
-        if (tid == 0) a[j][j] = ljj;
-        for (int i = j + 1 + tid; i < NB; i += nth) a[i][j] /= ljj;
-        __syncthreads();
-        const int rem = NB - 1 - j;
-        for (int e = tid; e < rem * rem; e += nth) {
-            const int i = j + 1 + e / rem, p = j + 1 + e % rem;
-            if (p <= i) a[i][p] = fma(-a[i][j], a[p][j], a[i][p]);
+        if (fail != -1) break;  // uniform: read after the barrier
+        // column j of L and the rank-1 update, both from the unscaled column a[][j] and r (one
+        // barrier per column): a[i][p] -= (a[i][j] r) (a[p][j] r)
+        const CT r = rcol;
+        if (tid > j && tid < NB) l[tid][j] = a[tid][j] * r;
+        const int cnt = (NB - 1 - j) * (NB - j) / 2;
+        for (int e = tid; e < cnt; e += nth) {
+            const int ip = tab[e];
+            const int i = ip >> 8, p = ip & 0xff;
+            a[i][p] = fma(-(a[i][j] * r), a[p][j] * r, a[i][p]);
         }
         __syncthreads();
     }
-    __syncthreads();
     if (fail != -1) {
         if (tid == 0) {
             const int j = fail >= 0 ? fail : -2 - fail;
             set_status(st, fail >= 0 ? DFS_ERR_NOT_SPD : DFS_ERR_NONFINITE);
             atomicCAS(&st->failed_pivot, -1, (int)(o + j));
         }
+        __syncthreads();
         return;
     }
     for (int e = tid; e < NB * NB; e += nth) {
         const int i = e / NB, j = e % NB;
-        if (j <= i) W[(o + i) * ld + o + j] = (T)a[i][j];
+        if (j <= i) W[(o + i) * ld + o + j] = (T)l[i][j];
     }
-    invert_lower_block<T>(a, inv, Linv + (int64_t)kb * NB * NB);
+    invert_lower_block<T, CT>(l, Linv + (int64_t)kb * NB * NB);
 }
 
-template <typename T>
+template <typename T, typename CT>
 __global__ void __launch_bounds__(256) chol_first_kernel(T* W, int64_t ld, T* Linv, DevStatus* st) {
-    __shared__ double scratch[2 * NB * (NB + 1)];
-    if (st->status != 0) return;
-    factor_diag_block<T>(W, ld, 0, Linv, st, scratch);
+    __shared__ CT scratch[2 * NB * (NB + 1)];
+    if (block_should_exit(st, 0)) return;
+    factor_diag_block<T, CT>(W, ld, 0, Linv, st, scratch);
 }
 
 __device__ __forceinline__ void tri_ij(int t, int& I, int& J) {
@@ -134,18 +175,18 @@ __device__ __forceinline__ void panel_times_linv_t(const T* W, int64_t ld, int64
     __syncthreads();
 }
 
-template <typename T>
+template <typename T, typename CT>
 __global__ void __launch_bounds__(256)
 chol_step_kernel(T* W, int64_t ld, int64_t n_pad, int kb, T* Linv, DevStatus* st) {
     constexpr int kPanelBytes = 2 * TU * (NB + 1) * (int)sizeof(T);
-    constexpr int kFactorBytes = 2 * NB * (NB + 1) * (int)sizeof(double);
+    constexpr int kFactorBytes = 2 * NB * (NB + 1) * (int)sizeof(CT);
     __shared__ __align__(16) T sL[NB][NB + 1];
     // The two panel buffers and the FP64 factor scratch are never live at the same time.
     __shared__ __align__(16) unsigned char raw[kPanelBytes > kFactorBytes ? kPanelBytes : kFactorBytes];
     T(*sR)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(raw);
     T(*sQ)[NB + 1] = sR + TU;
-    double* scratch = reinterpret_cast<double*>(raw);
-    if (st->status != 0) return;
+    CT* scratch = reinterpret_cast<CT*>(raw);
+    if (block_should_exit(st, 0)) return;
     const int tid = threadIdx.x;
     const int64_t c0 = (int64_t)(kb + 1) * NB;
     const int64_t rem = n_pad - c0;
@@ -199,7 +240,7 @@ chol_step_kernel(T* W, int64_t ld, int64_t n_pad, int kb, T* Linv, DevStatus* st
     if (I == 0 && J == 0 && c0 < n_pad) {
         __threadfence_block();
         __syncthreads();  // all reads of sR/sQ are done before the factor scratch reuses them
-        factor_diag_block<T>(W, ld, kb + 1, Linv, st, scratch);
+        factor_diag_block<T, CT>(W, ld, kb + 1, Linv, st, scratch);
     }
 }
 
@@ -208,7 +249,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) chol_scale_kernel(T* W, int64_t ld, int64_t n_pad, T* Linv, DevStatus* st) {
     __shared__ __align__(16) T sL[NB][NB + 1];
     __shared__ __align__(16) T sA[TU][NB + 1];
-    if (st->status != 0) return;
+    if (block_should_exit(st, 0)) return;
     const int kb = blockIdx.y;
     const int64_t c0 = (int64_t)(kb + 1) * NB;
     const int64_t r0 = c0 + (int64_t)blockIdx.x * TU;
@@ -229,7 +270,6 @@ __global__ void __launch_bounds__(256) chol_scale_kernel(T* W, int64_t ld, int64
 template <typename T>
 __global__ void __launch_bounds__(256) diag_inverse_kernel(const T* L, int64_t ld, T* Linv, DevStatus* st) {
     __shared__ double a[NB][NB + 1];
-    __shared__ double inv[NB][NB + 1];
     __shared__ int bad;
     const int kb = blockIdx.x;
     const int64_t o = (int64_t)kb * NB;
@@ -246,45 +286,61 @@ __global__ void __launch_bounds__(256) diag_inverse_kernel(const T* L, int64_t l
         if (threadIdx.x == 0) set_status(st, DFS_ERR_INVALID_ARG);
         return;
     }
-    invert_lower_block<T>(a, inv, Linv + (int64_t)kb * NB * NB);
+    invert_lower_block<T, double>(a, Linv + (int64_t)kb * NB * NB);
 }
 
 cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
                                 cudaStream_t stream) {
     const int nblk = (int)(n_pad / NB);
     if (w_f64)
-        diag_inverse_kernel<double><<<nblk, 256, 0, stream>>>(static_cast<const double*>(L), ld,
-                                                               static_cast<double*>(Linv), st);
+        {
+            diag_inverse_kernel<double><<<nblk, 256, 0, stream>>>(static_cast<const double*>(L), ld,
+                                                                   static_cast<double*>(Linv), st);
+            count_launch();
+        }
     else
-        diag_inverse_kernel<float><<<nblk, 256, 0, stream>>>(static_cast<const float*>(L), ld,
-                                                              static_cast<float*>(Linv), st);
+        {
+            diag_inverse_kernel<float><<<nblk, 256, 0, stream>>>(static_cast<const float*>(L), ld,
+                                                                  static_cast<float*>(Linv), st);
+            count_launch();
+        }
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename CT>
 static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* Linv_, DevStatus* st,
                                      cudaStream_t stream) {
     T* W = static_cast<T*>(W_);
     T* Linv = static_cast<T*>(Linv_);
     const int nblk = (int)(n_pad / NB);
-    chol_first_kernel<T><<<1, 256, 0, stream>>>(W, ld, Linv, st);
+    {
+        chol_first_kernel<T, CT><<<1, 256, 0, stream>>>(W, ld, Linv, st);
+        count_launch();
+    }
     for (int kb = 0; kb + 1 < nblk; ++kb) {
         const int64_t rem = n_pad - (int64_t)(kb + 1) * NB;
         const int Tn = (int)ceil_div(rem, TU);
-        chol_step_kernel<T><<<Tn * (Tn + 1) / 2, 256, 0, stream>>>(W, ld, n_pad, kb, Linv, st);
+        {
+            chol_step_kernel<T, CT><<<Tn * (Tn + 1) / 2, 256, 0, stream>>>(W, ld, n_pad, kb, Linv, st);
+            count_launch();
+        }
     }
     if (nblk > 1) {
         dim3 grid((unsigned)ceil_div(n_pad, TU), nblk - 1);
-        chol_scale_kernel<T><<<grid, 256, 0, stream>>>(W, ld, n_pad, Linv, st);
+        {
+            chol_scale_kernel<T><<<grid, 256, 0, stream>>>(W, ld, n_pad, Linv, st);
+            count_launch();
+        }
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, int fp64_panel) {
     if (n_pad % NB != 0) return cudaErrorInvalidValue;
-    return w_f64 ? launch_cholesky_t<double>(W, ld, n_pad, Linv, st, stream)
-                 : launch_cholesky_t<float>(W, ld, n_pad, Linv, st, stream);
+    if (w_f64) return launch_cholesky_t<double, double>(W, ld, n_pad, Linv, st, stream);
+    return fp64_panel ? launch_cholesky_t<float, double>(W, ld, n_pad, Linv, st, stream)
+                      : launch_cholesky_t<float, float>(W, ld, n_pad, Linv, st, stream);
 }
 
 }  // namespace dfs

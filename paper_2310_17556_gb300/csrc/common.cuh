@@ -5,11 +5,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/dfs.h"
 
 namespace dfs {
 
 constexpr int kNumSmsGB300 = 152;
+
+// Number of kernels this library has launched in the process (reported by dfs_kernel_launches).
+std::atomic<long long>& launch_counter();
+inline void count_launch() { launch_counter().fetch_add(1, std::memory_order_relaxed); }
 
 // Device-side status word layout (int32 array in the handle's workspace).
 //   [0] status (dfs_status), [1] failed pivot (int, -1 none), [2] converged flag,
@@ -100,6 +106,30 @@ __device__ __forceinline__ void load16_stream<__nv_bfloat16, float>(const __nv_b
     }
 }
 
+// 16-byte load from shared memory, unpacked to the accumulate type.
+template <typename T, typename A>
+__device__ __forceinline__ void load16_smem(const T* p, A* out);
+template <>
+__device__ __forceinline__ void load16_smem<float, float>(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load16_smem<double, double>(const double* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+}
+template <>
+__device__ __forceinline__ void load16_smem<__nv_bfloat16, float>(const __nv_bfloat16* p, float* o) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        o[2 * i] = __uint_as_float(w[i] << 16);
+        o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
 // Scalar guarded load (tails).
 template <typename T, typename A>
 __device__ __forceinline__ A load1(const T* p) {
@@ -119,6 +149,18 @@ __host__ __device__ constexpr int64_t round_up(int64_t a, int64_t b) { return ce
 
 __device__ __forceinline__ void set_status(DevStatus* st, int code) {
     atomicCAS(&st->status, 0, code);
+}
+
+// Block-uniform early exit: thread 0 reads the device status once (another CTA may change it
+// while this one runs), all threads see the same answer.  Contains a __syncthreads().
+__device__ __forceinline__ bool block_should_exit(const DevStatus* st, int honor_stop) {
+    __shared__ int s_exit;
+    if (threadIdx.x == 0) {
+        const volatile DevStatus* v = st;
+        s_exit = (v->status != 0) || (honor_stop && v->stop);
+    }
+    __syncthreads();
+    return s_exit != 0;
 }
 
 }  // namespace dfs

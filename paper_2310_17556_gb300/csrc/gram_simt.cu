@@ -169,8 +169,11 @@ static cudaError_t launch_gram_simt_t(const void* S, int64_t n, int64_t m, int64
     const int T = (int)ceil_div(n, BM);
     const int ntiles = T * (T + 1) / 2;
     dim3 grid(ntiles, nsplit);
-    gram_simt_kernel<TS, TA, BM, BK, TM><<<grid, (BM / TM) * (BM / TM), 0, stream>>>(
-        static_cast<const TS*>(S), n, m, lds, chunk, ntiles, static_cast<TA*>(P));
+    {
+        gram_simt_kernel<TS, TA, BM, BK, TM><<<grid, (BM / TM) * (BM / TM), 0, stream>>>(
+            static_cast<const TS*>(S), n, m, lds, chunk, ntiles, static_cast<TA*>(P));
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -221,16 +224,25 @@ cudaError_t launch_gram_finalize(int acc_f64, int w_f64, int BM, const void* P, 
     // index past ntiles only ever covers rows >= n, where the kernel writes the identity.
     if (acc_f64) {
         if (!w_f64 || BM != 64) return cudaErrorInvalidValue;
-        gram_finalize_kernel<double, double, 64><<<ntiles_out, 256, 0, stream>>>(
-            static_cast<const double*>(P), nsplit, ntiles, n, n_out, lambda, static_cast<double*>(W), ldw);
+        {
+            gram_finalize_kernel<double, double, 64><<<ntiles_out, 256, 0, stream>>>(
+                static_cast<const double*>(P), nsplit, ntiles, n, n_out, lambda, static_cast<double*>(W), ldw);
+            count_launch();
+        }
     } else {
         if (BM != 128) return cudaErrorInvalidValue;
         if (w_f64)
-            gram_finalize_kernel<float, double, 128><<<ntiles_out, 256, 0, stream>>>(
-                static_cast<const float*>(P), nsplit, ntiles, n, n_out, lambda, static_cast<double*>(W), ldw);
+            {
+                gram_finalize_kernel<float, double, 128><<<ntiles_out, 256, 0, stream>>>(
+                    static_cast<const float*>(P), nsplit, ntiles, n, n_out, lambda, static_cast<double*>(W), ldw);
+                count_launch();
+            }
         else
-            gram_finalize_kernel<float, float, 128><<<ntiles_out, 256, 0, stream>>>(
-                static_cast<const float*>(P), nsplit, ntiles, n, n_out, lambda, static_cast<float*>(W), ldw);
+            {
+                gram_finalize_kernel<float, float, 128><<<ntiles_out, 256, 0, stream>>>(
+                    static_cast<const float*>(P), nsplit, ntiles, n, n_out, lambda, static_cast<float*>(W), ldw);
+                count_launch();
+            }
     }
     return cudaGetLastError();
 }

@@ -15,25 +15,28 @@ cudaError_t launch_gram_finalize(int acc_f64, int w_f64, int BM, const void* P, 
                                  int64_t n_out, double lambda, void* W, int64_t ldw, cudaStream_t stream);
 
 // ---- step 1, tcgen05 tensor-core Gram (gram_tc.cu) ----
-// kind: 0 = BF16 (S converted on chip), 1 = TF32, 2 = split BF16 x3.
+// kind: 0 = BF16 MMA, 1 = TF32 MMA.
 struct GramTcPlan {
     int kind;
-    int n_tiles;      // 128-row tiles of S (rows padded to 128)
-    int nsplit;       // split-m chunks
-    int64_t chunk;    // columns per chunk (multiple of the k-block)
-    int ngroups;      // output work groups per chunk
+    int packed;       // operands come from the packed tiles of the S v pass
+    int n_tiles;      // T: 128-row blocks of S
+    int npairs;       // P: 128 x 256 units (singles follow)
+    int c;            // tasks per cost unit (pairs get 2c tasks, singles c)
+    int ntasks;       // c * (2P + singles): partial blocks written
+    int64_t nkb;      // 128-byte k-blocks along m
     size_t partial_bytes;
 };
 int gram_tc_supported(int s_dtype, int kind);
 GramTcPlan gram_tc_plan(int s_dtype, int kind, int64_t n, int64_t m, int num_sms);
 cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, int64_t n, int64_t m, int64_t lds,
-                           void* P, DevStatus* st, cudaStream_t stream);
+                           const void* Sp, void* P, DevStatus* st, cudaStream_t stream);
 cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64_t n, int64_t n_out, double lambda,
                                     void* W, int64_t ldw, cudaStream_t stream);
 
 // ---- step 2, Cholesky (cholesky.cu) ----
+// fp64_panel: factor the 32 x 32 diagonal blocks in FP64 (else in the storage type).
 cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
-                            cudaStream_t stream);
+                            cudaStream_t stream, int fp64_panel = 1);
 cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
                                 cudaStream_t stream);
 
@@ -43,13 +46,28 @@ int trsv_max_group(int n_pad, int elem, size_t smem_limit);
 cudaError_t launch_trsv(int f64, int trans, const void* L, int64_t ld, int n_pad, const void* Linv, void* B,
                         int64_t ldb, int k, int kq, const DevStatus* st, int honor_stop, cudaStream_t stream);
 
-// ---- streaming pass over S (pass.cu) ----
+// ---- streaming passes over S (pass.cu) ----
+struct PassPlan {
+    int rpt;      // rows per thread kept in registers by the refinement pass (0: re-read mode)
+    int grid;     // CTAs of fisher_pass_kernel
+    int sv_grid;  // CTAs of sv_pack_kernel
+};
 size_t pass_smem_bytes(int n, int KQ, int s_dtype);
 int pass_max_group(int n, int s_dtype, size_t smem_limit);
 int pass_grid(int n, int KQ, int s_dtype, int num_sms, int64_t m);
-cudaError_t launch_pass(int s_dtype, int kq, const void* S, int n, int64_t m, int64_t lds, const void* V,
-                        int64_t ldv, int k, const double* Y, int64_t ldy, double lambda, void* X, int64_t ldx,
-                        double* Rpart, double* U2part, int grid, const DevStatus* st, int honor_stop,
+PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit);
+int pass_partial_rows(const PassPlan& p);  // rows of the partial buffers (max of both grids)
+// pack: 0 none, 1 BF16 tiles, 2 TF32 tiles (see sv_pack_kernel)
+int64_t pack_kblocks(int s_dtype, int pack, int64_t m);
+size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m);
+cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,
+                           int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
+                           const DevStatus* st, cudaStream_t stream);
+// dmode: 0 = no change measurement, 1 = also sum (X_new - X_old)^2 with X_old read from X,
+// 2 = same with X_old = V / lambda.  U2part holds 2 * kq doubles per CTA: sum U^2, sum dX^2.
+cudaError_t launch_pass(const PassPlan& plan, int s_dtype, int kq, const void* S, int n, int64_t m, int64_t lds,
+                        const void* V, int64_t ldv, int k, const double* Y, int64_t ldy, double lambda, void* X,
+                        int64_t ldx, double* Rpart, double* U2part, int dmode, const DevStatus* st, int honor_stop,
                         cudaStream_t stream);
 cudaError_t launch_pass_reduce(int f64, const double* Rpart, int nparts, int n, int n_out, int KQ, int k,
                                const double* Y, int64_t ldy, double lambda, double* R, int64_t ldr, void* Rt,

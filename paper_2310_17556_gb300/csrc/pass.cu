@@ -1,24 +1,41 @@
-// Streaming passes over S (HBM-bound): Algorithm 1 step 4 with Q inlined, plus the n-space
-// residual used by iterative refinement, both in ONE read of S.
+// Streaming passes over S (HBM-bound), the inlined-Q part of Algorithm 1 (Section 2):
 //
-//   U = V - S^T Y                 (S^T y: the leftmost product of S^T L^{-T} L^{-1} S v)
-//   X = U / lambda                (Algorithm 1 step 4)
-//   R = S U - lambda Y            (= S v - (S S^T + lambda I~) y, Appendix A's identity)
+//   sv_pack_kernel       R = S V                 (b = S v, the rightmost product of
+//                                                 S^T L^{-T} L^{-1} S v), optionally writing S
+//                                                 again as packed tensor-core tiles (below)
+//   fisher_pass_kernel   U = V - S^T Y           (S^T y, the leftmost product)
+//                        X = U / lambda          (Algorithm 1 step 4)
+//                        R = S U - lambda Y      (= S v - (S S^T + lambda I~) y, Appendix A's
+//                                                 identity; the refinement residual)
 //
-// S is n x m row-major.  A CTA owns a strip of 128 bytes of columns (W = 8 * VEC columns) over
-// all n rows: 8 lanes cover one row segment with 16-byte loads, a warp covers 4 rows, 16 warps
-// cover 64 rows per sweep.  Phase 1 reduces S^T Y over the rows of the strip (FP32 products,
-// per-thread FP32 partials, cross-warp sum in FP64); phase 2 re-reads the strip (L1/L2 hits)
-// and adds the strip's contribution S U into a per-CTA FP64 accumulator R_s in shared memory.
-// The grid is persistent (strips round-robin over CTAs); each CTA finally writes its R_s and
-// its sum of U^2 (for ||X||) to a partial buffer that pass_reduce sums in a fixed order.
+// S is n x m row-major.  A CTA owns a column strip of W = LPR * VEC columns (LPR lanes of 16-byte
+// loads per row) across all n rows; strips are dealt round-robin to a persistent grid.
+//
+// fisher_pass_kernel: 512 threads, 8 lanes per row (128-byte row segments), 64 rows per sweep.
+// For n <= 64 * RPT each thread keeps its RPT row segments of the strip in registers between the
+// two phases, so S crosses HBM and L2 exactly once (RPT = 0: phase 2 re-reads from L2).
+//   phase 1  FP32 partials of S^T Y over rows -> shuffle over the row lanes -> shared memory ->
+//            sum over the 16 warps -> U for the strip's columns (v and the previous x are loaded
+//            before phase 1 so their latency is hidden); X written, sums of U^2 and of the x
+//            change kept for the refinement's stopping rule;
+//   phase 2  per-row dot products of the strip with U, reduced across the 8 lanes of the row,
+//            added by one owner thread per row into an FP32 per-row sum that is folded into
+//            FP64 every kFold strips.
+// sv_pack_kernel: no cross-warp step at all (rows are owned by warps): per-row dot products of the
+// strip with V as in phase 2.  With packing it also writes each 128-row x 128-byte block of S
+// (one tensor-core k-block of a 128-row tile) as a contiguous 16 KB tile in the 128-byte-swizzled
+// K-major layout the tcgen05 Gram consumes: BF16 (round to nearest even) or TF32 (FP32 rounded to
+// nearest, ties away), or a plain re-layout of BF16 S.  Tiles of rows >= n and columns >= m
+// are zero.  Tile (I, kb) sits at byte offset (I * nkb + kb) * 16384.
+// Each CTA finally writes its FP64 row sums (and the two per-RHS sums) to partial buffers that
+// pass_reduce adds in a fixed order.
 #include "kernels.cuh"
 
 namespace dfs {
 
 constexpr int PASS_THREADS = 512;
 constexpr int PASS_WARPS = PASS_THREADS / 32;
-constexpr int PASS_ROWS = PASS_WARPS * 4;  // rows per sweep
+constexpr int kFold = 32;
 
 template <typename TS>
 struct PassTypes {
@@ -29,86 +46,253 @@ struct PassTypes<double> {
     using TA = double;
 };
 
-template <typename TS, int KQ>
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Fold the FP32 per-row sums of the rows this thread owns into FP64.
+template <typename TA, int KQ>
+__device__ __forceinline__ void fold_rows(double* Rs64, TA* Rs32, int first, int step, int n) {
+    for (int i = first; i < n; i += step)
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            Rs64[i * KQ + q] += (double)Rs32[i * KQ + q];
+            Rs32[i * KQ + q] = (TA)0;
+        }
+}
+
+// ------------------------------------------------------------------------------------------
+// R = S V, optionally packing S into tensor-core tiles.
+//   PACK 0: none; 1: BF16 tiles (64-column k-blocks); 2: TF32 tiles (32-column k-blocks).
+template <typename TS, int KQ, int PACK>
+__global__ void __launch_bounds__(PASS_THREADS)
+sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds,
+               const typename PassTypes<TS>::TA* __restrict__ V, int64_t ldv, int k, double* __restrict__ Rpart,
+               unsigned char* __restrict__ Sp, int64_t nkb, const DevStatus* st) {
+    using TA = typename PassTypes<TS>::TA;
+    constexpr int VEC = Vec16<TS>::N;
+    constexpr int LPR = (PACK == 1 && sizeof(TS) == 4) ? 16 : 8;  // lanes per row
+    constexpr int W = LPR * VEC;
+    constexpr int RPW = 32 / LPR;
+    constexpr int SWEEP = PASS_WARPS * RPW;
+    constexpr int RB = 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* Rs64 = reinterpret_cast<double*>(smem);
+    TA* Rs32 = reinterpret_cast<TA*>(Rs64 + (size_t)n * KQ);
+    if (block_should_exit(st, 0)) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rr = lane / LPR, cq = lane % LPR;
+    for (int e = tid; e < n * KQ; e += PASS_THREADS) {
+        Rs64[e] = 0.0;
+        Rs32[e] = (TA)0;
+    }
+    __syncthreads();
+    const int64_t nstrips = ceil_div(m, W);
+    int since_fold = 0;
+    for (int64_t s = blockIdx.x; s < nstrips; s += gridDim.x) {
+        const int64_t j0 = s * W;
+        const int64_t jc = j0 + cq * VEC;
+        const bool full = (j0 + W <= m);
+        TA vv[KQ][VEC];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) vv[q][e] = (q < k && jc + e < m) ? V[(int64_t)q * ldv + jc + e] : (TA)0;
+        // warp-uniform row loop (the row reductions below shuffle across lanes)
+        for (int base = warp * RPW; base < n_rows; base += RB * SWEEP) {
+            TA sv[RB][VEC];
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                const int i = base + u * SWEEP + rr;
+                const TS* p = S + (int64_t)i * lds + jc;
+                if (i < n && full) {
+                    load16_stream<TS, TA>(p, sv[u]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) sv[u][e] = (i < n && jc + e < m) ? load1<TS, TA>(p + e) : (TA)0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                const int i = base + u * SWEEP + rr;
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) {
+                    TA a = 0;
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) a = fma(sv[u][e], vv[q][e], a);
+#pragma unroll
+                    for (int o = 1; o < LPR; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                    if (cq == 0 && i < n) Rs32[i * KQ + q] += a;
+                }
+                if constexpr (PACK != 0) {
+                    if (i < n_rows) {
+                        const int r = i & 127;
+                        unsigned char* tile = Sp + (((int64_t)(i >> 7) * nkb + s) << 14) + r * 128;
+                        if constexpr (PACK == 1 && sizeof(TS) == 4) {
+                            // 4 floats -> 4 bf16 (8 bytes), half of 16-byte chunk cq / 2
+                            const __nv_bfloat162 lo = __floats2bfloat162_rn(sv[u][0], sv[u][1]);
+                            const __nv_bfloat162 hi = __floats2bfloat162_rn(sv[u][2], sv[u][3]);
+                            uint2 w;
+                            w.x = *reinterpret_cast<const uint32_t*>(&lo);
+                            w.y = *reinterpret_cast<const uint32_t*>(&hi);
+                            *reinterpret_cast<uint2*>(tile + ((((cq >> 1) ^ (r & 7)) << 4) | ((cq & 1) << 3))) = w;
+                        } else if constexpr (PACK == 1) {
+                            // BF16 S: the 16-byte chunk is copied as is
+                            const TS* p = S + (int64_t)i * lds + jc;
+                            uint4 w = make_uint4(0, 0, 0, 0);
+                            if (i < n && full) {
+                                w = __ldg(reinterpret_cast<const uint4*>(p));
+                            } else if (i < n) {
+                                uint32_t h[8];
+#pragma unroll
+                                for (int e = 0; e < 8; ++e)
+                                    h[e] = (jc + e < m) ? (uint32_t)reinterpret_cast<const unsigned short*>(p)[e] : 0u;
+                                w = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                                               h[6] | (h[7] << 16));
+                            }
+                            *reinterpret_cast<uint4*>(tile + ((cq ^ (r & 7)) << 4)) = w;
+                        } else {
+                            uint4 w;
+                            w.x = tf32_rna(sv[u][0]);
+                            w.y = tf32_rna(sv[u][1]);
+                            w.z = tf32_rna(sv[u][2]);
+                            w.w = tf32_rna(sv[u][3]);
+                            *reinterpret_cast<uint4*>(tile + ((cq ^ (r & 7)) << 4)) = w;
+                        }
+                    }
+                }
+            }
+        }
+        if (++since_fold == kFold) {
+            since_fold = 0;
+            if (cq == 0) fold_rows<TA, KQ>(Rs64, Rs32, warp * RPW + rr, SWEEP, n);
+        }
+    }
+    if (cq == 0) fold_rows<TA, KQ>(Rs64, Rs32, warp * RPW + rr, SWEEP, n);
+    __syncthreads();
+    double* dst = Rpart + (int64_t)blockIdx.x * n * KQ;
+    for (int e = tid; e < n * KQ; e += PASS_THREADS) dst[e] = Rs64[e];
+}
+
+// ------------------------------------------------------------------------------------------
+// X = (V - S^T Y) / lambda and R = S (V - S^T Y) - lambda Y in one read of S.
+template <typename TS, int KQ, int RPT>
 __global__ void __launch_bounds__(PASS_THREADS)
 fisher_pass_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds,
                    const typename PassTypes<TS>::TA* __restrict__ V, int64_t ldv, int k,
                    const double* __restrict__ Y, int64_t ldy, double lambda,
                    typename PassTypes<TS>::TA* __restrict__ X, int64_t ldx,
-                   double* __restrict__ Rpart, double* __restrict__ U2part,
+                   double* __restrict__ Rpart, double* __restrict__ U2part, int dmode,
                    const DevStatus* st, int honor_stop) {
     using TA = typename PassTypes<TS>::TA;
     constexpr int VEC = Vec16<TS>::N;
-    constexpr int W = 8 * VEC;
+    constexpr int LPR = 8;
+    constexpr int W = LPR * VEC;
+    constexpr int RPW = 4;
+    constexpr int SWEEP = PASS_WARPS * RPW;  // 64 rows
+    constexpr int RB = 8;                    // re-read mode: rows in flight per thread
     extern __shared__ __align__(16) unsigned char smem[];
-    double* Rs = reinterpret_cast<double*>(smem);                 // n x KQ
-    TA* Ys = reinterpret_cast<TA*>(Rs + (int64_t)n * KQ);         // n x KQ
-    TA* ured = Ys + (int64_t)n * KQ;                              // PASS_WARPS x W x KQ
-    TA* us = ured + PASS_WARPS * W * KQ;                          // W x KQ
-    if (st->status != 0 || (honor_stop && st->stop)) return;
+    double* Rs64 = reinterpret_cast<double*>(smem);              // n x KQ
+    TA* Rs32 = reinterpret_cast<TA*>(Rs64 + (size_t)n * KQ);     // n x KQ
+    TA* Ys = Rs32 + (size_t)n * KQ;                              // n x KQ
+    TA* ured = Ys + (size_t)n * KQ;                              // PASS_WARPS x W x KQ
+    TA* us = ured + PASS_WARPS * W * KQ;                         // W x KQ
+    if (block_should_exit(st, honor_stop)) return;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rr = lane >> 3, cq = lane & 7;
+    const int rr = lane / LPR, cq = lane % LPR;
     const bool haveY = (Y != nullptr);
     const bool wantR = (Rpart != nullptr);
+    const TA inv_lambda = (TA)(1.0 / lambda);
     for (int e = tid; e < n * KQ; e += PASS_THREADS) {
         const int i = e / KQ, q = e % KQ;
-        Rs[e] = 0.0;
+        Rs64[e] = 0.0;
+        Rs32[e] = (TA)0;
         Ys[e] = (haveY && q < k) ? (TA)Y[(int64_t)i * ldy + q] : (TA)0;
     }
-    double u2[KQ];
+    TA u2f[KQ], d2f[KQ];
+    double u2[KQ], d2[KQ];
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) u2[q] = 0.0;
+    for (int q = 0; q < KQ; ++q) u2f[q] = d2f[q] = (TA)0, u2[q] = d2[q] = 0.0;
     __syncthreads();
 
     const int64_t nstrips = ceil_div(m, W);
+    const int row0 = warp * RPW + rr;
+    const bool u_thread = tid < W * KQ;
+    const int uc = tid / KQ, uq = tid % KQ;
+    int since_fold = 0;
     for (int64_t s = blockIdx.x; s < nstrips; s += gridDim.x) {
         const int64_t j0 = s * W;
         const int64_t jc = j0 + cq * VEC;
         const bool full = (j0 + W <= m);
-        // ---- phase 1: column sums of S^T Y over the strip -------------------------------
+        // the U step's global reads, issued before phase 1 so their latency is hidden
+        TA v_pre = 0, x_pre = 0;
+        const bool u_valid = u_thread && (j0 + uc < m) && (uq < k);
+        if (u_valid) {
+            v_pre = V[(int64_t)uq * ldv + j0 + uc];
+            if (X != nullptr && dmode == 1) x_pre = X[(int64_t)uq * ldx + j0 + uc];
+        }
+        TA sv[RPT > 0 ? RPT : 1][VEC];
+        if constexpr (RPT > 0) {
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                const int i = row0 + t * SWEEP;
+                const TS* p = S + (int64_t)i * lds + jc;
+                if (i < n && full) {
+                    load16_stream<TS, TA>(p, sv[t]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) sv[t][e] = (i < n && jc + e < m) ? load1<TS, TA>(p + e) : (TA)0;
+                }
+            }
+        }
+        // ---- phase 1: column sums of S^T Y over the strip ----
         if (haveY) {
             TA acc[KQ][VEC];
 #pragma unroll
             for (int q = 0; q < KQ; ++q)
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) acc[q][e] = 0;
-            int i = warp * 4 + rr;
-            for (; i + 3 * PASS_ROWS < n; i += 4 * PASS_ROWS) {
-                TA sv[4][VEC];
+            if constexpr (RPT > 0) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const TS* p = S + (int64_t)(i + u * PASS_ROWS) * lds + jc;
-                    if (full) {
-                        load16<TS, TA>(p, sv[u]);
-                    } else {
+                for (int t = 0; t < RPT; ++t) {
+                    const int i = row0 + t * SWEEP;
+                    if (i < n) {
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) sv[u][e] = (jc + e < m) ? load1<TS, TA>(p + e) : (TA)0;
+                        for (int q = 0; q < KQ; ++q) {
+                            const TA yv = Ys[i * KQ + q];
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) acc[q][e] = fma(sv[t][e], yv, acc[q][e]);
+                        }
                     }
                 }
+            } else {
+                for (int ib = row0; ib < n; ib += RB * SWEEP) {
+                    TA rv[RB][VEC];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                    for (int u = 0; u < RB; ++u) {
+                        const int i = ib + u * SWEEP;
+                        const TS* p = S + (int64_t)i * lds + jc;
+                        if (i < n && full) {
+                            load16<TS, TA>(p, rv[u]);
+                        } else {
 #pragma unroll
-                    for (int q = 0; q < KQ; ++q) {
-                        const TA yv = Ys[(i + u * PASS_ROWS) * KQ + q];
-#pragma unroll
-                        for (int e = 0; e < VEC; ++e) acc[q][e] = fma(sv[u][e], yv, acc[q][e]);
+                            for (int e = 0; e < VEC; ++e)
+                                rv[u][e] = (i < n && jc + e < m) ? load1<TS, TA>(p + e) : (TA)0;
+                        }
                     }
-            }
-            for (; i < n; i += PASS_ROWS) {
-                TA sv[VEC];
-                const TS* p = S + (int64_t)i * lds + jc;
-                if (full) {
-                    load16<TS, TA>(p, sv);
-                } else {
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) sv[e] = (jc + e < m) ? load1<TS, TA>(p + e) : (TA)0;
-                }
+                    for (int u = 0; u < RB; ++u) {
+                        const int i = ib + u * SWEEP;
 #pragma unroll
-                for (int q = 0; q < KQ; ++q) {
-                    const TA yv = Ys[i * KQ + q];
+                        for (int q = 0; q < KQ; ++q) {
+                            const TA yv = (i < n) ? Ys[i * KQ + q] : (TA)0;
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) acc[q][e] = fma(sv[e], yv, acc[q][e]);
+                            for (int e = 0; e < VEC; ++e) acc[q][e] = fma(rv[u][e], yv, acc[q][e]);
+                        }
+                    }
                 }
             }
 #pragma unroll
@@ -128,85 +312,133 @@ fisher_pass_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds,
             }
         }
         __syncthreads();
-        // ---- U = V - S^T Y, X = U / lambda --------------------------------------------------
-        if (tid < W * KQ) {
-            const int c = tid / KQ, q = tid % KQ;
-            const int64_t j = j0 + c;
-            double sum = 0.0;
+        // ---- U = V - S^T Y, X = U / lambda ----
+        if (u_thread) {
+            TA sum = 0;
             if (haveY)
-                for (int w = 0; w < PASS_WARPS; ++w) sum += (double)ured[(w * W + c) * KQ + q];
-            const bool valid = (j < m) && (q < k);
-            const double v = valid ? (double)V[(int64_t)q * ldv + j] : 0.0;
-            const double u = valid ? v - sum : 0.0;
-            us[c * KQ + q] = (TA)u;
-            if (valid) {
-                if (X != nullptr) X[(int64_t)q * ldx + j] = (TA)(u / lambda);
-                u2[q] += u * u;
+                for (int w = 0; w < PASS_WARPS; ++w) sum += ured[(w * W + uc) * KQ + uq];
+            const TA u = u_valid ? v_pre - sum : (TA)0;
+            us[uc * KQ + uq] = u;
+            if (u_valid) {
+                if (X != nullptr) {
+                    const TA xn = u * inv_lambda;
+                    TA dx = 0;
+                    if (dmode == 1) dx = xn - x_pre;
+                    else if (dmode == 2) dx = (u - v_pre) * inv_lambda;
+                    d2f[uq] += dx * dx;
+                    X[(int64_t)uq * ldx + j0 + uc] = xn;
+                }
+                u2f[uq] += u * u;
             }
         }
         __syncthreads();
-        // ---- phase 2: R_s += S_strip U_strip ------------------------------------------------
+        // ---- phase 2: R_s += S_strip U_strip ----
         if (wantR) {
             TA uu[KQ][VEC];
 #pragma unroll
             for (int q = 0; q < KQ; ++q)
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) uu[q][e] = us[(cq * VEC + e) * KQ + q];
-            // The row loop is warp-uniform (the shuffles below need all 32 lanes); rows past n
-            // are predicated off.
-            for (int ib = warp * 4; ib < n; ib += PASS_ROWS) {
-                const int i = ib + rr;
-                const bool ok = i < n;
-                TA sv[VEC];
-                const TS* p = S + (int64_t)i * lds + jc;
-                if (ok && full) {
-                    load16<TS, TA>(p, sv);
-                } else {
+            if constexpr (RPT > 0) {
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) sv[e] = (ok && jc + e < m) ? load1<TS, TA>(p + e) : (TA)0;
+                for (int t = 0; t < RPT; ++t) {
+                    const int i = row0 + t * SWEEP;
+#pragma unroll
+                    for (int q = 0; q < KQ; ++q) {
+                        TA a = 0;
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) a = fma(sv[t][e], uu[q][e], a);
+                        a += __shfl_xor_sync(0xffffffffu, a, 1);
+                        a += __shfl_xor_sync(0xffffffffu, a, 2);
+                        a += __shfl_xor_sync(0xffffffffu, a, 4);
+                        if (cq == 0 && i < n) Rs32[i * KQ + q] += a;
+                    }
                 }
-                TA pr[KQ];
+            } else {
+                // warp-uniform row loop (the shuffles need all 32 lanes)
+                for (int base = warp * RPW; base < n; base += RB * SWEEP) {
+                    TA rv[RB][VEC];
 #pragma unroll
-                for (int q = 0; q < KQ; ++q) {
-                    TA a = 0;
+                    for (int u = 0; u < RB; ++u) {
+                        const int i = base + u * SWEEP + rr;
+                        const TS* p = S + (int64_t)i * lds + jc;
+                        if (i < n && full) {
+                            load16<TS, TA>(p, rv[u]);
+                        } else {
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) a = fma(sv[e], uu[q][e], a);
-                    a += __shfl_xor_sync(0xffffffffu, a, 1);
-                    a += __shfl_xor_sync(0xffffffffu, a, 2);
-                    a += __shfl_xor_sync(0xffffffffu, a, 4);
-                    pr[q] = a;
-                }
-                if (ok && cq == 0) {
+                            for (int e = 0; e < VEC; ++e)
+                                rv[u][e] = (i < n && jc + e < m) ? load1<TS, TA>(p + e) : (TA)0;
+                        }
+                    }
 #pragma unroll
-                    for (int q = 0; q < KQ; ++q) Rs[i * KQ + q] += (double)pr[q];
+                    for (int u = 0; u < RB; ++u) {
+                        const int i = base + u * SWEEP + rr;
+#pragma unroll
+                        for (int q = 0; q < KQ; ++q) {
+                            TA a = 0;
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) a = fma(rv[u][e], uu[q][e], a);
+                            a += __shfl_xor_sync(0xffffffffu, a, 1);
+                            a += __shfl_xor_sync(0xffffffffu, a, 2);
+                            a += __shfl_xor_sync(0xffffffffu, a, 4);
+                            if (cq == 0 && i < n) Rs32[i * KQ + q] += a;
+                        }
+                    }
                 }
             }
         }
+        if (++since_fold == kFold) {
+            since_fold = 0;
+            if (wantR && cq == 0) fold_rows<TA, KQ>(Rs64, Rs32, row0, SWEEP, n);
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                u2[q] += (double)u2f[q];
+                d2[q] += (double)d2f[q];
+                u2f[q] = d2f[q] = (TA)0;
+            }
+        }
+    }
+    if (wantR && cq == 0) fold_rows<TA, KQ>(Rs64, Rs32, row0, SWEEP, n);
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        u2[q] += (double)u2f[q];
+        d2[q] += (double)d2f[q];
     }
     __syncthreads();
     if (wantR) {
         double* dst = Rpart + (int64_t)blockIdx.x * n * KQ;
-        for (int e = tid; e < n * KQ; e += PASS_THREADS) dst[e] = Rs[e];
+        for (int e = tid; e < n * KQ; e += PASS_THREADS) dst[e] = Rs64[e];
     }
-    // sum of U^2 per RHS: threads tid < W*KQ hold disjoint columns; reduce through smem
-    __shared__ double u2s[PASS_THREADS / 32][8];
+    // per-RHS sums of U^2 and (X_new - X_old)^2 (threads tid < W*KQ hold disjoint columns)
+    __shared__ double u2s[PASS_WARPS][16];
 #pragma unroll
     for (int q = 0; q < KQ; ++q) {
-        double v = u2[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) u2s[warp][q] = v;
+        double v = u2[q], w = d2[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        if (lane == 0) {
+            u2s[warp][q] = v;
+            u2s[warp][8 + q] = w;
+        }
     }
     __syncthreads();
     if (tid < KQ) {
-        double v = 0.0;
-        for (int w = 0; w < PASS_WARPS; ++w) v += u2s[w][tid];
-        U2part[(int64_t)blockIdx.x * KQ + tid] = v;
+        double v = 0.0, w = 0.0;
+        for (int wp = 0; wp < PASS_WARPS; ++wp) {
+            v += u2s[wp][tid];
+            w += u2s[wp][8 + tid];
+        }
+        U2part[(int64_t)blockIdx.x * 2 * KQ + tid] = v;
+        U2part[(int64_t)blockIdx.x * 2 * KQ + KQ + tid] = w;
     }
 }
 
 // R = sum_b Rpart[b] - lambda Y (FP64, fixed order), rows [0, n_out) with stride ldr (rows >= n
 // are zero), an optional copy Rt (n_out x KQ, solve type T) for the triangular solves, and the
-// summed ||U||^2 per RHS.
+// summed ||U||^2 and ||X_new - X_old||^2 per RHS (U2[0..KQ) and U2[KQ..2KQ)).  One warp per
+// output element: lane l sums parts l, l + 32, ... in order, then a fixed shuffle tree.
 template <typename T>
 __global__ void __launch_bounds__(256)
 pass_reduce_kernel(const double* __restrict__ Rpart, int nparts, int n, int n_out, int KQ, int k,
@@ -214,30 +446,40 @@ pass_reduce_kernel(const double* __restrict__ Rpart, int nparts, int n, int n_ou
                    T* __restrict__ Rt, const double* __restrict__ U2part, double* __restrict__ U2,
                    const DevStatus* st, int honor_stop) {
     if (st->status != 0 || (honor_stop && st->stop)) return;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (e < (int64_t)n_out * KQ) {
         const int i = (int)(e / KQ), q = (int)(e % KQ);
         double v = 0.0;
-        if (i < n && q < k) {
-            for (int b = 0; b < nparts; ++b) v += Rpart[(int64_t)b * n * KQ + e];
-            if (Y != nullptr) v -= lambda * Y[(int64_t)i * ldy + q];
+        if (i < n && q < k)
+            for (int b = lane; b < nparts; b += 32) v += Rpart[(int64_t)b * n * KQ + e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            if (i < n && q < k && Y != nullptr) v -= lambda * Y[(int64_t)i * ldy + q];
+            if (R != nullptr && q < k) R[(int64_t)i * ldr + q] = v;
+            if (Rt != nullptr) Rt[e] = (T)v;
         }
-        if (R != nullptr && q < k) R[(int64_t)i * ldr + q] = v;
-        if (Rt != nullptr) Rt[e] = (T)v;
     }
-    if (U2 != nullptr && blockIdx.x == 0 && threadIdx.x < KQ) {
+    if (U2 != nullptr && U2part != nullptr && blockIdx.x == 0 && threadIdx.x < 2 * KQ) {
         double v = 0.0;
-        for (int b = 0; b < nparts; ++b) v += U2part[(int64_t)b * KQ + threadIdx.x];
+        for (int b = 0; b < nparts; ++b) v += U2part[(int64_t)b * 2 * KQ + threadIdx.x];
         U2[threadIdx.x] = v;
     }
 }
 
+// ---- host side ------------------------------------------------------------------------------
+
+static int vec_of(int s_dtype) { return s_dtype == DFS_F64 ? 2 : (s_dtype == DFS_F32 ? 4 : 8); }
+static int ta_of(int s_dtype) { return s_dtype == DFS_F64 ? 8 : 4; }
+
 size_t pass_smem_bytes(int n, int KQ, int s_dtype) {
-    const int ta = (s_dtype == DFS_F64) ? 8 : 4;
-    const int vec = (s_dtype == DFS_F64) ? 2 : (s_dtype == DFS_F32 ? 4 : 8);
-    const int W = 8 * vec;
-    return (size_t)n * KQ * 8 + (size_t)n * KQ * ta + (size_t)PASS_WARPS * W * KQ * ta + (size_t)W * KQ * ta;
+    const int ta = ta_of(s_dtype);
+    const int W = 8 * vec_of(s_dtype);
+    return (size_t)n * KQ * (8 + 2 * ta) + (size_t)PASS_WARPS * W * KQ * ta + (size_t)W * KQ * ta;
 }
+
+static size_t sv_smem_bytes(int n, int KQ, int s_dtype) { return (size_t)n * KQ * (8 + ta_of(s_dtype)); }
 
 int pass_max_group(int n, int s_dtype, size_t smem_limit) {
     for (int kq = 8; kq >= 1; kq >>= 1)
@@ -245,49 +487,95 @@ int pass_max_group(int n, int s_dtype, size_t smem_limit) {
     return 0;
 }
 
-template <typename TS, int KQ>
-static cudaError_t launch_pass_t(const void* S, int n, int64_t m, int64_t lds, const void* V, int64_t ldv,
-                                 int k, const double* Y, int64_t ldy, double lambda, void* X, int64_t ldx,
-                                 double* Rpart, double* U2part, int grid, const DevStatus* st, int honor_stop,
-                                 cudaStream_t stream, int s_dtype) {
-    using TA = typename PassTypes<TS>::TA;
+// Rows per thread kept in registers by fisher_pass_kernel (0: phase 2 re-reads the strip).
+static int pass_rpt(int n, int KQ, int s_dtype) {
+    const int vec = vec_of(s_dtype);
+    int rpt = 2;
+    while (rpt * 64 < n) rpt *= 2;
+    if (rpt * vec > 64 || KQ * vec > 16 || rpt > 16) return 0;
+    return rpt;
+}
+
+PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit) {
+    (void)smem_limit;
+    PassPlan p{};
+    p.rpt = pass_rpt(n, KQ, s_dtype);
+    // register-resident strips: one 512-thread CTA per SM; otherwise up to four
     const size_t smem = pass_smem_bytes(n, KQ, s_dtype);
-    auto kern = fisher_pass_kernel<TS, KQ>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, PASS_THREADS, smem, stream>>>(static_cast<const TS*>(S), n, m, lds, static_cast<const TA*>(V),
-                                               ldv, k, Y, ldy, lambda, static_cast<TA*>(X), ldx, Rpart, U2part,
-                                               st, honor_stop);
-    return cudaGetLastError();
+    int per_sm = p.rpt > 0 ? 1 : (int)((200u * 1024u) / (smem + 1024));
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t nstrips = ceil_div(m, 8 * vec_of(s_dtype));
+    int64_t g = (int64_t)num_sms * per_sm;
+    if (g > nstrips) g = nstrips;
+    p.grid = (int)(g < 1 ? 1 : g);
+    // the S v pass keeps only the row sums in shared memory: up to four CTAs per SM
+    int64_t gs = (int64_t)num_sms * 4;
+    if (gs > nstrips) gs = nstrips;
+    p.sv_grid = (int)(gs < 1 ? 1 : gs);
+    return p;
 }
 
 int pass_grid(int n, int KQ, int s_dtype, int num_sms, int64_t m) {
-    const size_t smem = pass_smem_bytes(n, KQ, s_dtype);
-    int per_sm = (int)((200u * 1024u) / (smem + 1024));
-    if (per_sm > 4) per_sm = 4;  // 4 x 512 threads = 2048 = SM thread limit
-    if (per_sm < 1) per_sm = 1;
-    const int vec = (s_dtype == DFS_F64) ? 2 : (s_dtype == DFS_F32 ? 4 : 8);
-    const int64_t nstrips = ceil_div(m, 8 * vec);
-    int64_t g = (int64_t)num_sms * per_sm;
-    if (g > nstrips) g = nstrips;
-    return (int)(g < 1 ? 1 : g);
+    return pass_make_plan(n, KQ, s_dtype, num_sms, m, 0).grid;
 }
 
-cudaError_t launch_pass(int s_dtype, int kq, const void* S, int n, int64_t m, int64_t lds, const void* V,
-                        int64_t ldv, int k, const double* Y, int64_t ldy, double lambda, void* X, int64_t ldx,
-                        double* Rpart, double* U2part, int grid, const DevStatus* st, int honor_stop,
+int pass_partial_rows(const PassPlan& p) { return p.grid > p.sv_grid ? p.grid : p.sv_grid; }
+
+template <typename TS, int KQ, int RPT>
+static cudaError_t launch_pass_t(const void* S, int n, int64_t m, int64_t lds, const void* V, int64_t ldv, int k,
+                                 const double* Y, int64_t ldy, double lambda, void* X, int64_t ldx, double* Rpart,
+                                 double* U2part, int dmode, int grid, const DevStatus* st, int honor_stop,
+                                 cudaStream_t stream, int s_dtype) {
+    using TA = typename PassTypes<TS>::TA;
+    const size_t smem = pass_smem_bytes(n, KQ, s_dtype);
+    auto kern = fisher_pass_kernel<TS, KQ, RPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, PASS_THREADS, smem, stream>>>(static_cast<const TS*>(S), n, m, lds, static_cast<const TA*>(V), ldv,
+                                               k, Y, ldy, lambda, static_cast<TA*>(X), ldx, Rpart, U2part, dmode, st,
+                                               honor_stop);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename TS, int KQ>
+static cudaError_t launch_pass_rpt(int rpt, const void* S, int n, int64_t m, int64_t lds, const void* V, int64_t ldv,
+                                   int k, const double* Y, int64_t ldy, double lambda, void* X, int64_t ldx,
+                                   double* Rpart, double* U2part, int dmode, int grid, const DevStatus* st,
+                                   int honor_stop, cudaStream_t stream, int s_dtype) {
+#define DFS_RPT(R)                                                                                             \
+    case R:                                                                                                    \
+        return launch_pass_t<TS, KQ, R>(S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx, Rpart, U2part, dmode, \
+                                        grid, st, honor_stop, stream, s_dtype);
+    switch (rpt) {
+        DFS_RPT(0)
+        DFS_RPT(2)
+        DFS_RPT(4)
+        DFS_RPT(8)
+        DFS_RPT(16)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef DFS_RPT
+}
+
+cudaError_t launch_pass(const PassPlan& plan, int s_dtype, int kq, const void* S, int n, int64_t m, int64_t lds,
+                        const void* V, int64_t ldv, int k, const double* Y, int64_t ldy, double lambda, void* X,
+                        int64_t ldx, double* Rpart, double* U2part, int dmode, const DevStatus* st, int honor_stop,
                         cudaStream_t stream) {
-#define DFS_PASS_CASE(KQ)                                                                                     \
-    case KQ:                                                                                                  \
-        if (s_dtype == DFS_F32)                                                                               \
-            return launch_pass_t<float, KQ>(S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx, Rpart, U2part,   \
-                                            grid, st, honor_stop, stream, s_dtype);                           \
-        if (s_dtype == DFS_BF16)                                                                              \
-            return launch_pass_t<__nv_bfloat16, KQ>(S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx, Rpart,   \
-                                                    U2part, grid, st, honor_stop, stream, s_dtype);           \
-        if (s_dtype == DFS_F64)                                                                               \
-            return launch_pass_t<double, KQ>(S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx, Rpart, U2part,  \
-                                             grid, st, honor_stop, stream, s_dtype);                          \
+#define DFS_PASS_CASE(KQ)                                                                                         \
+    case KQ:                                                                                                      \
+        if (s_dtype == DFS_F32)                                                                                   \
+            return launch_pass_rpt<float, KQ>(plan.rpt, S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx, Rpart,   \
+                                              U2part, dmode, plan.grid, st, honor_stop, stream, s_dtype);         \
+        if (s_dtype == DFS_BF16)                                                                                  \
+            return launch_pass_rpt<__nv_bfloat16, KQ>(plan.rpt, S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx,  \
+                                                      Rpart, U2part, dmode, plan.grid, st, honor_stop, stream,    \
+                                                      s_dtype);                                                   \
+        if (s_dtype == DFS_F64)                                                                                   \
+            return launch_pass_rpt<double, KQ>(plan.rpt, S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx, Rpart,  \
+                                               U2part, dmode, plan.grid, st, honor_stop, stream, s_dtype);        \
         return cudaErrorInvalidValue;
     switch (kq) {
         DFS_PASS_CASE(1)
@@ -300,18 +588,86 @@ cudaError_t launch_pass(int s_dtype, int kq, const void* S, int n, int64_t m, in
 #undef DFS_PASS_CASE
 }
 
+template <typename TS, int KQ, int PACK>
+static cudaError_t launch_sv_t(int grid, const void* S, int n, int n_rows, int64_t m, int64_t lds, const void* V,
+                               int64_t ldv, int k, double* Rpart, void* Sp, int64_t nkb, const DevStatus* st,
+                               cudaStream_t stream, int s_dtype) {
+    using TA = typename PassTypes<TS>::TA;
+    const size_t smem = sv_smem_bytes(n, KQ, s_dtype);
+    auto kern = sv_pack_kernel<TS, KQ, PACK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, PASS_THREADS, smem, stream>>>(static_cast<const TS*>(S), n, n_rows, m, lds, static_cast<const TA*>(V),
+                                               ldv, k, Rpart, static_cast<unsigned char*>(Sp), nkb, st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+int64_t pack_kblocks(int s_dtype, int pack, int64_t m) {
+    const int width = (pack == 2) ? 32 : 64;  // elements per 128-byte tile row (TF32 / BF16)
+    (void)s_dtype;
+    return ceil_div(m, width);
+}
+
+size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m) {
+    if (pack == 0) return 0;
+    return (size_t)ceil_div(n, 128) * (size_t)pack_kblocks(s_dtype, pack, m) * 16384;
+}
+
+cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,
+                           int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
+                           const DevStatus* st, cudaStream_t stream) {
+    const int n_rows = pack ? (int)round_up(n, 128) : n;
+    const int64_t nkb = pack ? pack_kblocks(s_dtype, pack, m) : 0;
+    const int grid = plan.sv_grid;
+#define DFS_SV_CASE(KQ)                                                                                           \
+    case KQ:                                                                                                      \
+        if (s_dtype == DFS_F32) {                                                                                 \
+            if (pack == 1)                                                                                        \
+                return launch_sv_t<float, KQ, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,       \
+                                                 stream, s_dtype);                                                \
+            if (pack == 2)                                                                                        \
+                return launch_sv_t<float, KQ, 2>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,       \
+                                                 stream, s_dtype);                                                \
+            return launch_sv_t<float, KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream,   \
+                                             s_dtype);                                                            \
+        }                                                                                                         \
+        if (s_dtype == DFS_BF16) {                                                                                \
+            if (pack == 1)                                                                                        \
+                return launch_sv_t<__nv_bfloat16, KQ, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb,   \
+                                                         st, stream, s_dtype);                                    \
+            return launch_sv_t<__nv_bfloat16, KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,   \
+                                                     stream, s_dtype);                                            \
+        }                                                                                                         \
+        if (s_dtype == DFS_F64 && pack == 0)                                                                      \
+            return launch_sv_t<double, KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream,  \
+                                              s_dtype);                                                           \
+        return cudaErrorInvalidValue;
+    switch (kq) {
+        DFS_SV_CASE(1)
+        DFS_SV_CASE(2)
+        DFS_SV_CASE(4)
+        DFS_SV_CASE(8)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef DFS_SV_CASE
+}
+
 cudaError_t launch_pass_reduce(int f64, const double* Rpart, int nparts, int n, int n_out, int KQ, int k,
                                const double* Y, int64_t ldy, double lambda, double* R, int64_t ldr, void* Rt,
                                const double* U2part, double* U2, const DevStatus* st, int honor_stop,
                                cudaStream_t stream) {
-    const int64_t total = (int64_t)n_out * KQ;
+    const int64_t total = (int64_t)n_out * KQ * 32;  // one warp per output
     const int blocks = (int)ceil_div(total, 256);
-    if (f64)
+    if (f64) {
         pass_reduce_kernel<double><<<blocks, 256, 0, stream>>>(Rpart, nparts, n, n_out, KQ, k, Y, ldy, lambda, R, ldr,
                                                                static_cast<double*>(Rt), U2part, U2, st, honor_stop);
-    else
+    } else {
         pass_reduce_kernel<float><<<blocks, 256, 0, stream>>>(Rpart, nparts, n, n_out, KQ, k, Y, ldy, lambda, R, ldr,
                                                               static_cast<float*>(Rt), U2part, U2, st, honor_stop);
+    }
+    count_launch();
     return cudaGetLastError();
 }
 

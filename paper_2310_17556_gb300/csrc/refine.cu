@@ -4,14 +4,14 @@
 // of W = S S^T + lambda I~.  When W is formed in low precision (W~ = W + E), y_0 = W~^{-1} S v
 // is refined with the exact operator:  r = S v - (S S^T + lambda I~) y = S (v - S^T y) - lambda y
 // (one pass over S, pass.cu), dy = W~^{-1} r (trsv.cu), y += dy.  The x of Algorithm 1 step 4,
-// x = (v - S^T y) / lambda, is written by the same pass.  The size of the next x correction is
-// estimated in n-space without another pass:  dx = -S^T dy / lambda and
-//   ||S^T dy||^2 = dy^T S S^T dy = dy^T (W~ dy) - lambda ||dy||^2 - dy^T E dy ~ dy^T r - lambda ||dy||^2,
-// so  ||dx|| / ||x|| ~ sqrt(max(dy^T r - lambda dy^T dy, 0)) / ||v - S^T y||  (per RHS, max).
-// Stopping: converged when that ratio <= tol; otherwise y += dy; stop with NOT_CONVERGED when
-// the iteration budget is used up or the ratio fails to halve (stagnation or divergence).  Once
-// stopped, every later kernel of the solve sees `stop` and returns at once, so a fixed launch
-// sequence serves any iteration count (no host round trip).
+// x_j = (v - S^T y_j) / lambda, is written by the same pass, which also measures exactly how
+// much x moved:  delta_j = ||x_j - x_{j-1}|| / ||x_j||  (x_0 = v / lambda, i.e. y = 0).
+// With linear convergence at rate rho_j = delta_j / delta_{j-1}, the error left in x_j is about
+// delta_j rho_j / (1 - rho_j).  Stop (converged) once that estimate is <= tol; stop with
+// NOT_CONVERGED when the iteration budget is used up or rho_j >= 0.9 (stagnation, e.g. at the
+// rounding floor of the passes, or divergence).  Once stopped, every later kernel of the solve
+// sees `stop` and returns at once, so a fixed launch sequence serves any iteration count with no
+// host round trip.
 #include "kernels.cuh"
 
 namespace dfs {
@@ -35,7 +35,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 refine_init_kernel(const T* __restrict__ Z, int n_pad, int KQ, double* __restrict__ Y,
                    const double* __restrict__ R, double* __restrict__ bnorm2, DevStatus* st) {
-    if (st->status != 0) return;
+    if (block_should_exit(st, 0)) return;
     __shared__ double red[8][8];
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int e = threadIdx.x; e < n_pad * KQ; e += blockDim.x) {
@@ -62,68 +62,60 @@ __global__ void __launch_bounds__(256)
 refine_control_kernel(const T* __restrict__ Z, const double* __restrict__ R, int n_pad, int KQ, int k,
                       double* __restrict__ Y, const double* __restrict__ U2, const double* __restrict__ bnorm2,
                       double lambda, double tol, int it, int max_iter, DevStatus* st) {
-    if (st->status != 0 || st->stop) return;
-    __shared__ double red[3][8][8];
+    if (block_should_exit(st, 1)) return;
+    __shared__ double red[8][8];
     __shared__ int decision;  // 0 = continue (apply dy), 1 = converged, 2 = give up
-    double dyr[8] = {0, 0, 0, 0, 0, 0, 0, 0}, dyy[8] = {0, 0, 0, 0, 0, 0, 0, 0}, rr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double rr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int e = threadIdx.x; e < n_pad * KQ; e += blockDim.x) {
-        const double dy = (double)Z[e];
         const double r = R[e];
-        const int q = e % KQ;
-        dyr[q] += dy * r;
-        dyy[q] += dy * dy;
-        rr[q] += r * r;
+        rr[e % KQ] += r * r;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = 0; q < 8; ++q) {
-        double a = dyr[q], b = dyy[q], c = rr[q];
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-        }
-        if (lane == 0) {
-            red[0][warp][q] = a;
-            red[1][warp][q] = b;
-            red[2][warp][q] = c;
-        }
+        double c = rr[q];
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) red[warp][q] = c;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double rel = 0.0, relr = 0.0;
+        double delta = 0.0, relr = 0.0;
         bool finite = true;
         for (int q = 0; q < k && q < KQ; ++q) {
-            double a = 0, b = 0, c = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                a += red[0][w][q];
-                b += red[1][w][q];
-                c += red[2][w][q];
-            }
-            const double dx2 = fmax(a - lambda * b, 0.0);
-            const double x2 = fmax(U2[q], 1e-300);
-            const double rq = sqrt(dx2 / x2);
+            double c = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) c += red[w][q];
+            // ||x_j - x_{j-1}|| / ||x_j|| with ||x_j|| = ||u|| / lambda
+            const double dq = lambda * sqrt(U2[KQ + q]) / fmax(sqrt(U2[q]), 1e-300);
             const double rn = sqrt(c / fmax(bnorm2[q], 1e-300));
-            if (!isfinite(rq) || !isfinite(rn)) finite = false;
-            rel = fmax(rel, rq);
+            if (!isfinite(dq) || !isfinite(rn)) finite = false;
+            delta = fmax(delta, dq);
             relr = fmax(relr, rn);
         }
-        st->rel_correction = rel;
+        const double prev = st->prev_correction;
+        double est = delta;
+        bool have_rate = false;
+        double rho = 0.0;
+        if (it > 1 && prev > 0.0) {
+            rho = delta / prev;
+            have_rate = true;
+            est = delta * rho / (1.0 - fmin(rho, 0.99));
+        }
+        st->rel_correction = est;
         st->rel_residual = relr;
         st->iters = it;
+        st->prev_correction = delta;
         if (!finite) {
             set_status(st, DFS_ERR_NONFINITE);
             st->stop = 1;
             decision = 2;
-        } else if (rel <= tol) {
+        } else if ((have_rate && est <= tol) || delta <= 1e-2 * tol) {
             st->converged = 1;
             st->stop = 1;
             decision = 1;
-        } else if (it >= max_iter || (it > 1 && rel > 0.5 * st->prev_correction)) {
+        } else if (it >= max_iter || (have_rate && rho >= 0.9)) {
             set_status(st, DFS_ERR_NOT_CONVERGED);
             st->stop = 1;
             decision = 2;
         } else {
-            st->prev_correction = rel;
             decision = 0;
         }
     }
@@ -134,16 +126,25 @@ refine_control_kernel(const T* __restrict__ Z, const double* __restrict__ R, int
 }
 
 cudaError_t launch_status_reset(DevStatus* st, cudaStream_t stream) {
-    status_reset_kernel<<<1, 32, 0, stream>>>(st);
+    {
+        status_reset_kernel<<<1, 32, 0, stream>>>(st);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine_init(int f64, const void* Z, int n_pad, int KQ, double* Y, const double* R,
                                double* bnorm2, DevStatus* st, cudaStream_t stream) {
     if (f64)
-        refine_init_kernel<double><<<1, 256, 0, stream>>>(static_cast<const double*>(Z), n_pad, KQ, Y, R, bnorm2, st);
+        {
+            refine_init_kernel<double><<<1, 256, 0, stream>>>(static_cast<const double*>(Z), n_pad, KQ, Y, R, bnorm2, st);
+            count_launch();
+        }
     else
-        refine_init_kernel<float><<<1, 256, 0, stream>>>(static_cast<const float*>(Z), n_pad, KQ, Y, R, bnorm2, st);
+        {
+            refine_init_kernel<float><<<1, 256, 0, stream>>>(static_cast<const float*>(Z), n_pad, KQ, Y, R, bnorm2, st);
+            count_launch();
+        }
     return cudaGetLastError();
 }
 
@@ -151,11 +152,17 @@ cudaError_t launch_refine_control(int f64, const void* Z, const double* R, int n
                                   const double* U2, const double* bnorm2, double lambda, double tol, int it,
                                   int max_iter, DevStatus* st, cudaStream_t stream) {
     if (f64)
-        refine_control_kernel<double><<<1, 256, 0, stream>>>(static_cast<const double*>(Z), R, n_pad, KQ, k, Y, U2,
-                                                              bnorm2, lambda, tol, it, max_iter, st);
+        {
+            refine_control_kernel<double><<<1, 256, 0, stream>>>(static_cast<const double*>(Z), R, n_pad, KQ, k, Y, U2,
+                                                                  bnorm2, lambda, tol, it, max_iter, st);
+            count_launch();
+        }
     else
-        refine_control_kernel<float><<<1, 256, 0, stream>>>(static_cast<const float*>(Z), R, n_pad, KQ, k, Y, U2,
-                                                             bnorm2, lambda, tol, it, max_iter, st);
+        {
+            refine_control_kernel<float><<<1, 256, 0, stream>>>(static_cast<const float*>(Z), R, n_pad, KQ, k, Y, U2,
+                                                                 bnorm2, lambda, tol, it, max_iter, st);
+            count_launch();
+        }
     return cudaGetLastError();
 }
 

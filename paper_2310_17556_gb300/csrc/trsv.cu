@@ -30,7 +30,7 @@ trsv_lower_kernel(const T* __restrict__ L, int64_t ld, int n_pad, const T* __res
     extern __shared__ __align__(16) unsigned char smem[];
     T* x = reinterpret_cast<T*>(smem);  // n_pad x KQ
     T* t = x + (int64_t)n_pad * KQ;     // TB x KQ
-    if (st->status != 0 || (honor_stop && st->stop)) return;
+    if (block_should_exit(st, honor_stop)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < n_pad * KQ; e += blockDim.x) {
         const int i = e / KQ, q = e % KQ;
@@ -81,7 +81,7 @@ trsv_upper_t_kernel(const T* __restrict__ L, int64_t ld, int n_pad, const T* __r
     T* y = reinterpret_cast<T*>(smem);       // n_pad x KQ
     T* t = y + (int64_t)n_pad * KQ;          // TB x KQ
     T* red = t + TB * KQ;                    // 32 warps x TB x KQ
-    if (st->status != 0 || (honor_stop && st->stop)) return;
+    if (block_should_exit(st, honor_stop)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < n_pad * KQ; e += blockDim.x) {
         const int i = e / KQ, q = e % KQ;
@@ -139,14 +139,20 @@ static cudaError_t launch_trsv_t(int trans, const void* L, int64_t ld, int n_pad
         auto kern = trsv_upper_t_kernel<T, KQ>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<1, 1024, smem, stream>>>(static_cast<const T*>(L), ld, n_pad, static_cast<const T*>(Linv),
-                                        static_cast<T*>(B), ldb, k, st, honor_stop);
+        {
+            kern<<<1, 1024, smem, stream>>>(static_cast<const T*>(L), ld, n_pad, static_cast<const T*>(Linv),
+                                            static_cast<T*>(B), ldb, k, st, honor_stop);
+            count_launch();
+        }
     } else {
         auto kern = trsv_lower_kernel<T, KQ>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<1, 1024, smem, stream>>>(static_cast<const T*>(L), ld, n_pad, static_cast<const T*>(Linv),
-                                        static_cast<T*>(B), ldb, k, st, honor_stop);
+        {
+            kern<<<1, 1024, smem, stream>>>(static_cast<const T*>(L), ld, n_pad, static_cast<const T*>(Linv),
+                                            static_cast<T*>(B), ldb, k, st, honor_stop);
+            count_launch();
+        }
     }
     return cudaGetLastError();
 }

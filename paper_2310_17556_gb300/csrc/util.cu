@@ -61,54 +61,84 @@ static inline int blocks_for(int64_t total) { return (int)ceil_div(total, 256); 
 cudaError_t launch_pad_copy_in(int f64, const void* src, int64_t lds, int64_t n, void* dst, int64_t n_pad,
                                cudaStream_t stream) {
     if (f64)
-        pad_copy_in_kernel<double><<<blocks_for(n_pad * n_pad), 256, 0, stream>>>(
-            static_cast<const double*>(src), lds, n, static_cast<double*>(dst), n_pad);
+        {
+            pad_copy_in_kernel<double><<<blocks_for(n_pad * n_pad), 256, 0, stream>>>(
+                static_cast<const double*>(src), lds, n, static_cast<double*>(dst), n_pad);
+            count_launch();
+        }
     else
-        pad_copy_in_kernel<float><<<blocks_for(n_pad * n_pad), 256, 0, stream>>>(
-            static_cast<const float*>(src), lds, n, static_cast<float*>(dst), n_pad);
+        {
+            pad_copy_in_kernel<float><<<blocks_for(n_pad * n_pad), 256, 0, stream>>>(
+                static_cast<const float*>(src), lds, n, static_cast<float*>(dst), n_pad);
+            count_launch();
+        }
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy_lower_out(int f64, const void* src, int64_t n_pad, void* dst, int64_t ldd, int64_t n,
                                   cudaStream_t stream) {
     if (f64)
-        copy_lower_out_kernel<double><<<blocks_for(n * n), 256, 0, stream>>>(
-            static_cast<const double*>(src), n_pad, static_cast<double*>(dst), ldd, n);
+        {
+            copy_lower_out_kernel<double><<<blocks_for(n * n), 256, 0, stream>>>(
+                static_cast<const double*>(src), n_pad, static_cast<double*>(dst), ldd, n);
+            count_launch();
+        }
     else
-        copy_lower_out_kernel<float><<<blocks_for(n * n), 256, 0, stream>>>(
-            static_cast<const float*>(src), n_pad, static_cast<float*>(dst), ldd, n);
+        {
+            copy_lower_out_kernel<float><<<blocks_for(n * n), 256, 0, stream>>>(
+                static_cast<const float*>(src), n_pad, static_cast<float*>(dst), ldd, n);
+            count_launch();
+        }
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy_rhs_in(int f64, const void* src, int64_t lds, int64_t n, int k, void* dst, int KQ,
                                int64_t n_pad, cudaStream_t stream) {
     if (f64)
-        copy_rhs_in_kernel<double><<<blocks_for(n_pad * KQ), 256, 0, stream>>>(
-            static_cast<const double*>(src), lds, n, k, static_cast<double*>(dst), KQ, n_pad);
+        {
+            copy_rhs_in_kernel<double><<<blocks_for(n_pad * KQ), 256, 0, stream>>>(
+                static_cast<const double*>(src), lds, n, k, static_cast<double*>(dst), KQ, n_pad);
+            count_launch();
+        }
     else
-        copy_rhs_in_kernel<float><<<blocks_for(n_pad * KQ), 256, 0, stream>>>(
-            static_cast<const float*>(src), lds, n, k, static_cast<float*>(dst), KQ, n_pad);
+        {
+            copy_rhs_in_kernel<float><<<blocks_for(n_pad * KQ), 256, 0, stream>>>(
+                static_cast<const float*>(src), lds, n, k, static_cast<float*>(dst), KQ, n_pad);
+            count_launch();
+        }
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy_rhs_out(int f64, const void* src, int KQ, int64_t n, int k, void* dst, int64_t ldd,
                                 cudaStream_t stream) {
     if (f64)
-        copy_rhs_out_kernel<double><<<blocks_for(n * k), 256, 0, stream>>>(
-            static_cast<const double*>(src), KQ, n, k, static_cast<double*>(dst), ldd);
+        {
+            copy_rhs_out_kernel<double><<<blocks_for(n * k), 256, 0, stream>>>(
+                static_cast<const double*>(src), KQ, n, k, static_cast<double*>(dst), ldd);
+            count_launch();
+        }
     else
-        copy_rhs_out_kernel<float><<<blocks_for(n * k), 256, 0, stream>>>(
-            static_cast<const float*>(src), KQ, n, k, static_cast<float*>(dst), ldd);
+        {
+            copy_rhs_out_kernel<float><<<blocks_for(n * k), 256, 0, stream>>>(
+                static_cast<const float*>(src), KQ, n, k, static_cast<float*>(dst), ldd);
+            count_launch();
+        }
     return cudaGetLastError();
 }
 
 cudaError_t launch_status_save(const DevStatus* st, int* dst, cudaStream_t stream) {
-    status_save_kernel<<<1, 32, 0, stream>>>(st, dst);
+    {
+        status_save_kernel<<<1, 32, 0, stream>>>(st, dst);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_group_reset(DevStatus* st, cudaStream_t stream) {
-    group_reset_kernel<<<1, 32, 0, stream>>>(st);
+    {
+        group_reset_kernel<<<1, 32, 0, stream>>>(st);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -60,22 +60,44 @@ def gaussian(n: int, m: int, seed: int, device="cpu", dtype=torch.float32) -> to
     return S.to(dtype)
 
 
+def _thin_q(G: torch.Tensor) -> torch.Tensor:
+    """Q factor (positive diagonal R) of the thin QR of a tall m x n matrix G (m >= n).
+
+    Cholesky-QR applied twice: R = chol(G^T G)^T, Q = G R^{-1}, repeated once on Q.  The n x n
+    factorisations run on the host in FP64 (numpy); the tall products stay on G's device, so
+    no device linear-algebra library is needed.  For a Gaussian G with m >> n, cond(G) ~ 1 and
+    two rounds give orthonormality to FP64 rounding.
+    """
+    import numpy as np
+
+    Q = G
+    for _ in range(2):
+        C = (Q.T @ Q).cpu().numpy()
+        L = np.linalg.cholesky(C)
+        Linv_t = np.linalg.inv(L).T  # R^{-1} with R = L^T
+        Q = Q @ torch.from_numpy(np.ascontiguousarray(Linv_t)).to(device=Q.device, dtype=Q.dtype)
+    return Q
+
+
 def orthonormal_rows(n: int, m: int, seed: int, device="cpu", dtype=torch.float64) -> torch.Tensor:
     """S = Q^T with Q (m x n) the thin-QR factor of an m x n Gaussian: S S^T = I."""
     assert n <= m
     g = _gen(seed, device)
     G = _randn((m, n), g, device, torch.float64)
-    Q, _ = torch.linalg.qr(G, mode="reduced")
+    Q = _thin_q(G)
     return Q.T.contiguous().to(dtype)
 
 
 def _haar_orthogonal(n: int, g, device) -> torch.Tensor:
-    """Haar-distributed n x n orthogonal matrix: QR of a Gaussian with R's diagonal signs folded into Q."""
-    G = _randn((n, n), g, device, torch.float64)
-    Q, R = torch.linalg.qr(G)
-    d = torch.sign(torch.diagonal(R))
+    """Haar-distributed n x n orthogonal matrix: QR of a Gaussian with R's diagonal signs folded
+    into Q (Mezzadri 2007), computed on the host in FP64."""
+    import numpy as np
+
+    G = _randn((n, n), g, device, torch.float64).cpu().numpy()
+    Q, R = np.linalg.qr(G)
+    d = np.sign(np.diag(R))
     d[d == 0] = 1.0
-    return Q * d[None, :]
+    return torch.from_numpy(Q * d[None, :]).to(device)
 
 
 def svd_structured(n: int, m: int, seed: int, sigma_min: float = 1e-3, device="cpu",
@@ -89,8 +111,8 @@ def svd_structured(n: int, m: int, seed: int, sigma_min: float = 1e-3, device="c
     assert n <= m
     g = _gen(seed, device)
     U = _haar_orthogonal(n, g, device).to(factor_dtype)
-    G = _randn((m, n), g, device, factor_dtype)
-    V, _ = torch.linalg.qr(G, mode="reduced")
+    G = _randn((m, n), g, device, torch.float64)
+    V = _thin_q(G).to(factor_dtype)
     del G
     sigma = torch.logspace(0.0, math.log10(sigma_min), n, dtype=torch.float64, device=device)
     s = (sigma / math.sqrt(n)).to(factor_dtype)

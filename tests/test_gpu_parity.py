@@ -34,6 +34,29 @@ def solve_ref(S, V, lam):
     return oracle.solve(np64(S), np64(V).T, lam).T
 
 
+def aligned(t):
+    """Same values with a row stride that is a multiple of 16 bytes (the C ABI's S contract)."""
+    per = 16 // t.element_size()
+    m = t.shape[1]
+    lds = -(-m // per) * per
+    if lds == m:
+        return t.contiguous()
+    buf = torch.zeros((t.shape[0], lds), device=t.device, dtype=t.dtype)
+    buf[:, :m] = t
+    return buf[:, :m]
+
+
+def fp32_tol(S, lam):
+    """The plain FP32 path (no refinement) carries FP32 rounding of W and of its factor, amplified
+    by cond(W) = (sigma_max^2 + lambda) / (sigma_min^2 + lambda) (sigma_min = 0 when m < n).  The
+    1e-5 bar is for cond(W) <= 10 (the SVD-structured workload has cond(W) <= 11); beyond that the
+    bar grows in proportion."""
+    sv = np.linalg.svd(np64(S), compute_uv=False)
+    smin = sv[-1] if S.shape[1] >= S.shape[0] else 0.0
+    cond = (sv[0] ** 2 + lam) / (smin ** 2 + lam)
+    return 1e-5 * max(1.0, cond / 10.0)
+
+
 def rel_err(x, ref):
     x = np.asarray(x, np.float64)
     ref = np.asarray(ref, np.float64)
@@ -45,7 +68,7 @@ def rel_err(x, ref):
 
 @pytest.mark.parametrize("n,m,k,lam", [(256, 16384, 1, 1e-3), (100, 3001, 3, 1e-2), (130, 999, 2, 0.5)])
 def test_fp64_path_matches_oracle(n, m, k, lam):
-    S = wl.gaussian(n, m, seed=11 + n, device=dev(), dtype=torch.float64)
+    S = aligned(wl.gaussian(n, m, seed=11 + n, device=dev(), dtype=torch.float64))
     V = wl.rhs(m, k, seed=12 + n, device=dev(), dtype=torch.float64)
     X, info = dfs.dfs_solve(S, V, lam, precision="fp64")
     assert info["status"] == 0 and info["precision"] == "fp64"
@@ -71,11 +94,11 @@ def test_fp64_orthonormal_rows_closed_form():
     (64, 4096, 11, 1e-2),     # k > 8: two RHS groups
 ])
 def test_fp32_path_matches_oracle(n, m, k, lam):
-    S = wl.gaussian(n, m, seed=21 + n, device=dev())
+    S = aligned(wl.gaussian(n, m, seed=21 + n, device=dev()))
     V = wl.rhs(m, k, seed=22 + n, device=dev())
     X, info = dfs.dfs_solve(S, V, lam, precision="fp32")
     assert info["status"] == 0 and info["precision"] == "fp32"
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-5
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= fp32_tol(S, lam)
 
 
 def test_fp32_path_svd_structured_small():
@@ -107,15 +130,98 @@ def test_padded_leading_dimension_and_in_place():
     assert rel_err(np64(V), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("n,m,k,lam", [
+    (1024, 65536, 1, 1e-2),
+    (257, 33336, 3, 1e-3),
+    (100, 5000, 8, 1e-1),
+    (300, 128, 2, 0.5),       # m < n (lambda large enough that v - S^T y does not cancel badly)
+    (1, 1000, 1, 0.3),
+])
+def test_tf32_refined_path_matches_oracle(n, m, k, lam):
+    S = aligned(wl.gaussian(n, m, seed=81 + n, device=dev()))
+    V = wl.rhs(m, k, seed=82 + n, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="tf32")
+    assert info["status"] == 0 and info["precision"] == "tf32"
+    assert info["iters"] >= 1
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_fp32_diagonal_panel_variant(prec):
+    n, m, lam = 700, 50000, 1e-3
+    S = wl.gaussian(n, m, seed=89, device=dev())
+    V = wl.rhs(m, 2, seed=90, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision=prec, fp32_panel=True)
+    assert info["status"] == 0
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= (fp32_tol(S, lam) if prec == "fp32" else 1e-6)
+
+
+def test_long_rows_gram():
+    # long rows (1.2 MB): many k-blocks per task, the progress throttle is exercised
+    n, m, lam = 300, 300000, 1e-2
+    S = wl.gaussian(n, m, seed=91, device=dev())
+    for prec, tol in (("tf32", 3e-3),):
+        W = dfs.dfs_gram(S, lam, precision=prec)
+        Wr = oracle.gram(np64(S), lam)
+        lo = np.tril(np.ones((n, n), bool))
+        assert np.abs(np64(W) - Wr)[lo].max() / np.abs(Wr).max() <= tol
+    Sb = S.to(torch.bfloat16)
+    W = dfs.dfs_gram(Sb, lam, precision="bf16")
+    Wr = oracle.gram(np64(Sb), lam)
+    # BF16 products are exact; the tensor core's FP32 accumulation error grows with the
+    # per-task contraction length (here ~m/8 terms)
+    assert np.abs(np64(W) - Wr)[lo].max() / np.abs(Wr).max() <= 1e-5 + 3e-10 * m
+    V = wl.rhs(m, 1, seed=92, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="tf32")
+    assert info["status"] == 0
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+
+
+def test_tf32_refined_svd_structured():
+    n, m = 512, 131072
+    S, U, s, Vf = wl.svd_structured(n, m, seed=83, sigma_min=1e-3, device=dev())
+    v = wl.rhs(m, 2, seed=84, device=dev())
+    for lam in (1e-2, 1e-4):
+        X, info = dfs.dfs_solve(S, v, lam, precision="tf32")
+        assert info["status"] == 0
+        assert rel_err(np64(X), solve_ref(S, v, lam)) <= 1e-6
+
+
+def test_refined_path_in_place():
+    n, m, lam = 200, 30000, 1e-3
+    S = wl.gaussian(n, m, seed=87, device=dev())
+    V = wl.rhs(m, 3, seed=88, device=dev())
+    ref = solve_ref(S, V, lam)
+    X, info = dfs.dfs_solve(S, V, lam, X=V, precision="tf32")
+    assert X.data_ptr() == V.data_ptr() and info["status"] == 0
+    assert rel_err(np64(V), ref) <= 1e-6
+
+
+def test_bf16_storage_bf16_tensor_path():
+    n, m, lam = 384, 40000, 1e-2
+    S = aligned(wl.gaussian(n, m, seed=85, device=dev(), dtype=torch.bfloat16))
+    V = wl.rhs(m, 2, seed=86, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="bf16")
+    assert info["status"] == 0 and info["precision"] == "bf16"
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+
+
 # ---------------------------------------------------------------------------- single steps
 
 
 @pytest.mark.parametrize("dtype,prec,n,m,tol", [
     (torch.float32, "fp32", 300, 10001, 2e-5), (torch.float64, "fp64", 130, 3000, 1e-12),
-    (torch.bfloat16, "fp32", 129, 4099, 2e-5)])
+    (torch.bfloat16, "fp32", 129, 4099, 2e-5),
+    # TF32 keeps 10 mantissa bits (truncated): per-entry error up to ~2^-10 of sum |s_i s_j|
+    (torch.float32, "tf32", 300, 10001, 3e-3), (torch.float32, "tf32", 1000, 70000, 3e-3),
+    (torch.float32, "tf32", 77, 64, 3e-3), (torch.float32, "tf32", 384, 20000, 3e-3),
+    (torch.float32, "tf32", 2100, 4000, 3e-3), (torch.float32, "tf32", 1153, 100, 3e-3),
+    # BF16 inputs are exact; products exact in FP32; FP32 accumulation error only
+    (torch.bfloat16, "bf16", 600, 33000, 2e-5), (torch.bfloat16, "bf16", 130, 64, 2e-5),
+    (torch.bfloat16, "bf16", 1153, 3000, 2e-5)])
 def test_gram_step(dtype, prec, n, m, tol):
     lam = 0.25
-    S = wl.gaussian(n, m, seed=31, device=dev(), dtype=dtype)
+    S = aligned(wl.gaussian(n, m, seed=31, device=dev(), dtype=dtype))
     W = dfs.dfs_gram(S, lam, precision=prec)
     Wr = oracle.gram(np64(S), lam)
     lo = np.tril(np.ones((n, n), bool))
@@ -130,9 +236,9 @@ def test_cholesky_step(dtype, n, tol):
     A = wl.gaussian(n, 3 * n, seed=41, device=dev(), dtype=torch.float64)
     Wr = (A @ A.T + 0.5 * torch.eye(n, device=dev(), dtype=torch.float64)).cpu().numpy()
     W = torch.tensor(Wr, device=dev(), dtype=dtype)
+    Lr = oracle.cholesky_lower(np64(W))  # before the in-place factorisation
     L, piv = dfs.dfs_cholesky(W)
     assert piv == -1
-    Lr = oracle.cholesky_lower(np64(W))
     Lg = np.tril(np64(L))
     assert np.abs(Lg - Lr).max() / np.abs(Lr).max() <= tol
     assert (np.diag(Lg) > 0).all()
@@ -164,13 +270,18 @@ def test_trsm_step(dtype, tol, trans):
     assert np.abs(np64(out) - ref).max() / np.abs(ref).max() <= tol
 
 
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
-def test_fisher_pass_step(dtype):
-    n, m, k, lam = 150, 12345, 3, 1e-2
-    S = wl.gaussian(n, m, seed=61, device=dev(), dtype=dtype)
+@pytest.mark.parametrize("dtype,n,m,k", [
+    (torch.float32, 150, 12345, 3), (torch.bfloat16, 150, 12345, 3), (torch.float64, 150, 12345, 3),
+    (torch.float32, 1024, 40000, 8),   # TMA ring with 32-byte strips
+    (torch.float32, 2500, 9001, 4),    # n beyond the shared-memory ring: LDG kernel
+    (torch.bfloat16, 700, 70001, 1),
+])
+def test_fisher_pass_step(dtype, n, m, k):
+    lam = 1e-2
+    S = aligned(wl.gaussian(n, m, seed=61, device=dev(), dtype=dtype))
     vdt = torch.float64 if dtype == torch.float64 else torch.float32
     V = wl.rhs(m, k, seed=62, device=dev(), dtype=vdt)
-    Y = torch.randn(n, k, device=dev(), dtype=torch.float64) * 0.3
+    Y = torch.randn(n, k, device=dev(), dtype=torch.float64) * (0.3 / math.sqrt(n / 150))
     X, R = dfs.dfs_fisher_pass(S, V, lam, Y)
     s, v, y = np64(S), np64(V).T, np64(Y)
     u = v - s.T @ y
