@@ -192,6 +192,41 @@ dfs_status dfs_fisher_pass(dfs_handle handle, const void* S, int s_dtype, int64_
                            int64_t ldy, double lambda, void* X, int64_t ldx, double* R,
                            int64_t ldr, void* stream);
 
+/* ---- no-allocation variant ---------------------------------------------------------- */
+
+/* Size of the fixed device scratch used by dfs_fisher_pass_noalloc (8 MiB per device). */
+#define DFS_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* The pass of dfs_fisher_pass (same arguments, same results up to rounding order) with no
+ * handle and no device-memory allocation.  The paper has no counterpart: this is for callers
+ * that cannot allocate device memory around the call, e.g. one whose device memory is fully
+ * reserved by its own pool allocator, or one that cannot afford the implicit device-wide
+ * synchronisation that cudaMalloc / cudaFree may perform.
+ *
+ * Device: the calling thread's current device; S, V, Y, X, R must live on it.
+ * Scratch: a fixed array of DFS_NOALLOC_SCRATCH_BYTES in the library's device image holds the
+ *   per-CTA partial sums and the status word.  It is reserved when the library's CUDA module
+ *   is loaded on the device, not by this call.  The first call with a given device current
+ *   looks up the array's address (cudaGetSymbolAddress) and the device's SM count and
+ *   shared-memory limit; make that first call before any stream capture.
+ * Size limit: with R != NULL the pass needs about (grid * n * kq + 2 * grid * kq) * 8 bytes of
+ *   scratch, grid = one CTA per SM when n <= 1024 (up to four per SM above), kq = right-hand
+ *   sides per pass (the next power of two >= k, capped by shared memory, halved here until
+ *   the partials fit).  On a 152-SM GB300 that is n <= 1024 with 4 RHS per pass, or n up to
+ *   about 6800 (FP32 / BF16 S) one RHS at a time.  A call that does not fit even with one RHS
+ *   per pass launches nothing and returns DFS_ERR_NO_MEMORY; *scratch_bytes (host, may be
+ *   NULL) receives the bytes the call needs (or needed).
+ * Concurrency: all calls on one device share the one scratch array.  Calls whose work
+ *   overlaps on the device (different streams with no ordering between them, or several host
+ *   threads) race on it and give wrong results: order them on one stream or with events.
+ * Errors: DFS_ERR_INVALID_ARG / DFS_ERR_UNSUPPORTED as dfs_fisher_pass (no message string:
+ *   there is no handle), DFS_ERR_CUDA if the set-up query or a launch fails.  Asynchronous
+ *   on `stream`. */
+dfs_status dfs_fisher_pass_noalloc(const void* S, int s_dtype, int64_t n, int64_t m, int64_t lds,
+                                   const void* V, int64_t k, int64_t ldv, const double* Y,
+                                   int64_t ldy, double lambda, void* X, int64_t ldx, double* R,
+                                   int64_t ldr, void* stream, int64_t* scratch_bytes);
+
 #ifdef __cplusplus
 }
 #endif

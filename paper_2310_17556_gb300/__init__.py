@@ -11,6 +11,7 @@ from .api import (  # noqa: F401
     default_handle,
     dfs_cholesky,
     dfs_fisher_pass,
+    dfs_fisher_pass_noalloc,
     dfs_gram,
     dfs_kernel_launches,
     dfs_reserve,

@@ -30,7 +30,7 @@ PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 EXPORTS = (
     "dfs_create", "dfs_destroy", "dfs_status_string", "dfs_last_error", "dfs_reserve", "dfs_kernel_launches",
     "dfs_solve", "dfs_solve_host", "dfs_sync_info", "dfs_step_times", "dfs_solve_batched",
-    "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass",
+    "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass", "dfs_fisher_pass_noalloc",
 )
 
 
@@ -46,6 +46,7 @@ class dfs_info(C.Structure):
 
 DFS_FLAG_STEP_TIMING = 1
 DFS_FLAG_FP32_PANEL = 2
+DFS_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class dfs_problem(C.Structure):
@@ -76,6 +77,8 @@ _SIGS = {
     "dfs_trsm": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _VP, _I64, _I64, C.c_int, _VP]),
     "dfs_fisher_pass": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, _VP, _I64, C.c_double,
                                   _VP, _I64, _VP, _I64, _VP]),
+    "dfs_fisher_pass_noalloc": (C.c_int, [_VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, _VP, _I64, C.c_double,
+                                          _VP, _I64, _VP, _I64, _VP, C.POINTER(_I64)]),
 }
 
 _lib = None

@@ -251,3 +251,31 @@ def dfs_fisher_pass(S: torch.Tensor, V: torch.Tensor, lam: float, Y: torch.Tenso
                                R.data_ptr() if R is not None else None, k, _stream(stream))
     _check(h.lib, h.h, st)
     return X, R
+
+
+def dfs_fisher_pass_noalloc(S: torch.Tensor, V: torch.Tensor, lam: float, Y: torch.Tensor | None = None,
+                            X: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None):
+    """dfs_fisher_pass without a handle or any device allocation inside the library call.
+
+    Writes X = (V - S^T Y)/lam into X and R = S (V - S^T Y) - lam Y into R (n x k FP64) when
+    they are given; the caller owns (and allocates) both.  Scratch is the library's fixed
+    per-device array of DFS_NOALLOC_SCRATCH_BYTES, shared by all calls on the device: calls
+    that overlap on the device race.  Runs on the current device.
+    """
+    lib = _lib.load()
+    n, m = S.shape
+    k = V.shape[0]
+    need = C.c_int64(0)
+    st = lib.dfs_fisher_pass_noalloc(S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k,
+                                     _rows(V, "V"), Y.data_ptr() if Y is not None else None,
+                                     _rows(Y, "Y") if Y is not None else k, float(lam),
+                                     X.data_ptr() if X is not None else None, _rows(X, "X") if X is not None else m,
+                                     R.data_ptr() if R is not None else None, _rows(R, "R") if R is not None else k,
+                                     _stream(stream), C.byref(need))
+    if st != _lib.DFS_OK:
+        detail = ""
+        if st == _lib.DFS_ERR_NO_MEMORY:
+            detail = (f": needs {need.value} bytes of scratch, the fixed array holds "
+                      f"{_lib.DFS_NOALLOC_SCRATCH_BYTES}")
+        raise DfsError(st, lib.dfs_status_string(st).decode() + detail)
+    return X, R
