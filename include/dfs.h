@@ -70,9 +70,10 @@ typedef enum {
 
 /* dfs_options.flags */
 #define DFS_FLAG_STEP_TIMING 1  /* record CUDA events around the steps; dfs_info.ms is filled */
-#define DFS_FLAG_FP32_PANEL 2   /* factor the 32 x 32 diagonal blocks of the Cholesky step in FP32
-                                   instead of FP64 (FP32 and mixed paths only; faster on GB300,
-                                   whose FP64 pipe is narrow and long-latency) */
+#define DFS_FLAG_FP64_PANEL 2   /* factor the 32 x 32 diagonal blocks of the Cholesky in FP64
+                                   (FP32 and mixed paths; the FP64 path always does).  Off by
+                                   default: GB300's FP64 rate makes each block ~4x slower, and
+                                   the trailing updates are FP32 in any case */
 
 typedef struct {
     int precision;   /* dfs_precision */

@@ -45,7 +45,7 @@ class dfs_info(C.Structure):
 
 
 DFS_FLAG_STEP_TIMING = 1
-DFS_FLAG_FP32_PANEL = 2
+DFS_FLAG_FP64_PANEL = 2
 DFS_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 

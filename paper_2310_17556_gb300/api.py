@@ -43,9 +43,9 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def _opts(precision, max_iter, tol, timing=False, fp32_panel=False) -> dfs_options:
+def _opts(precision, max_iter, tol, timing=False, fp64_panel=False) -> dfs_options:
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    flags = (_lib.DFS_FLAG_STEP_TIMING if timing else 0) | (_lib.DFS_FLAG_FP32_PANEL if fp32_panel else 0)
+    flags = (_lib.DFS_FLAG_STEP_TIMING if timing else 0) | (_lib.DFS_FLAG_FP64_PANEL if fp64_panel else 0)
     return dfs_options(p, int(max_iter), float(tol), flags)
 
 
@@ -108,7 +108,7 @@ def dfs_reserve(n_max: int, m_max: int, k_max: int, precision="auto", handle: Ha
 
 def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
               max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
-              sync: bool = True, timing: bool = False, fp32_panel: bool = False):
+              sync: bool = True, timing: bool = False, fp64_panel: bool = False):
     """Solve (S^T S + lam I) X^T = V^T for the k rows of V (Eq. 1, Algorithm 1).
 
     Returns (X, info) when sync is True (info = dict of dfs_info), else (X, None) with the work
@@ -124,7 +124,7 @@ def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | No
         raise TypeError(f"V must be {vdt} for S of dtype {S.dtype}")
     if X is None:
         X = torch.empty((k, m), device=S.device, dtype=vdt)
-    opt = _opts(precision, max_iter, tol, timing, fp32_panel)
+    opt = _opts(precision, max_iter, tol, timing, fp64_panel)
     info = dfs_info()
     st = h.lib.dfs_solve(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k, _rows(V, "V"),
                          float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt), _stream(stream),

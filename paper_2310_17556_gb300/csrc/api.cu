@@ -85,7 +85,7 @@ struct Plan {
     int pgrid = 1;  // rows of the pass partial buffers
     int pack = 0;   // tile packing done by the first S v pass: 0 none, 1 BF16, 2 TF32
     size_t off_W = 0, off_Linv = 0, off_P = 0, off_Rpart = 0, off_U2part = 0, off_R = 0, off_Z = 0, off_Y = 0,
-           off_U2 = 0, off_V = 0, off_bn2 = 0, off_Sp = 0, total = 0;
+           off_U2 = 0, off_V = 0, off_bn2 = 0, off_Sp = 0, off_Cf = 0, total = 0;
 };
 
 int tc_kind(int prec) {
@@ -179,6 +179,7 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     p->off_V = take(p->tensor ? (size_t)k * round_up(m, 4) * (p->f64 ? 8 : 4) : 0);
     p->off_bn2 = take(8 * 8);
     p->off_Sp = take(pack_bytes(s_dtype, p->pack, n, m));
+    p->off_Cf = take(cholesky_flag_bytes(p->n_pad));
     p->total = off;
     return DFS_OK;
 }
@@ -329,7 +330,7 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
     auto mark = [&](int i) -> cudaError_t {
         return timed ? cudaEventRecord(h->ev[slot][i], stream) : cudaSuccess;
     };
-    const int fp64_panel = !(opt && (opt->flags & DFS_FLAG_FP32_PANEL));
+    const int fp64_panel = opt && (opt->flags & DFS_FLAG_FP64_PANEL);
 
     if (p.tensor) {
         // Refinement reads V in every pass: when X overlaps V, work from a private copy of V.
@@ -373,7 +374,8 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
             else
                 DFS_CK(launch_gram_finalize(p.f64, p.f64, gram_simt_tile(p.f64), P, p.nsplit, p.n, p.n_pad, lambda,
                                             W, p.n_pad, stream));
-            DFS_CK(launch_cholesky(p.f64, W, p.n_pad, p.n_pad, Linv, h->dstat, stream, fp64_panel));
+            DFS_CK(launch_cholesky(p.f64, W, p.n_pad, p.n_pad, Linv, at<int>(h, p.off_Cf), h->dstat, stream,
+                                   fp64_panel));
             DFS_CK(mark(3));
         }
         // y0 = W^{-1} b by the two triangular solves
@@ -390,7 +392,7 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                 // x_0 = v / lambda for the first pass; afterwards x_{j-1} is read from X itself
                 DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, Rpart,
                                    U2part, it == 1 ? 2 : 1, h->dstat, 1, stream));
-                DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.grid, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z, U2part,
+                DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.nparts, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z, U2part,
                                           U2, h->dstat, 1, stream));
                 DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
                 DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
@@ -598,12 +600,14 @@ dfs_status dfs_cholesky(dfs_handle h, void* W, int w_dtype, int64_t n, int64_t l
     const int64_t n_pad = round_up(n, 128);
     const size_t es = f64 ? 8 : 4;
     dfs_status s;
-    if ((s = ensure_ws(h, align_up((size_t)n_pad * n_pad * es) + n_pad * 32 * es, stream)) != DFS_OK) return s;
+    const size_t oI = align_up((size_t)n_pad * n_pad * es), oF = oI + align_up((size_t)n_pad * 32 * es);
+    if ((s = ensure_ws(h, oF + cholesky_flag_bytes(n_pad), stream)) != DFS_OK) return s;
     void* Wp = h->ws;
-    void* Linv = static_cast<char*>(h->ws) + align_up((size_t)n_pad * n_pad * es);
+    void* Linv = static_cast<char*>(h->ws) + oI;
+    int* flags = reinterpret_cast<int*>(static_cast<char*>(h->ws) + oF);
     DFS_CK(launch_status_reset(h->dstat, stream));
     DFS_CK(launch_pad_copy_in(f64, W, ldw, n, Wp, n_pad, stream));
-    DFS_CK(launch_cholesky(f64, Wp, n_pad, n_pad, Linv, h->dstat, stream));
+    DFS_CK(launch_cholesky(f64, Wp, n_pad, n_pad, Linv, flags, h->dstat, stream));
     DFS_CK(launch_copy_lower_out(f64, Wp, n_pad, W, ldw, n, stream));
     dfs_info info;
     s = fill_info(h, stream, &info);
@@ -623,8 +627,10 @@ dfs_status dfs_trsm(dfs_handle h, const void* L, int l_dtype, int64_t n, int64_t
     const int f64 = l_dtype == DFS_F64;
     const int64_t n_pad = round_up(n, 128);
     const size_t es = f64 ? 8 : 4;
-    int kq = trsv_max_group((int)n_pad, (int)es, h->smem_optin);
-    if (kq < 1) return fail(h, DFS_ERR_UNSUPPORTED, "n too large for the on-chip triangular solve");
+    const int kmax = trsv_max_group((int)n_pad, (int)es, h->smem_optin);
+    if (kmax < 1) return fail(h, DFS_ERR_UNSUPPORTED, "n too large for the on-chip triangular solve");
+    int kq = pow2_at_least((int)(k < 8 ? k : 8));
+    if (kq > kmax) kq = kmax;
     const size_t oL = 0, oI = align_up((size_t)n_pad * n_pad * es), oB = oI + align_up((size_t)n_pad * 32 * es);
     dfs_status s;
     if ((s = ensure_ws(h, oB + align_up((size_t)n_pad * kq * es), stream)) != DFS_OK) return s;
@@ -634,6 +640,7 @@ dfs_status dfs_trsm(dfs_handle h, const void* L, int l_dtype, int64_t n, int64_t
     DFS_CK(launch_status_reset(h->dstat, stream));
     DFS_CK(launch_pad_copy_in(f64, L, ldl, n, Lp, n_pad, stream));
     DFS_CK(launch_diag_inverse(f64, Lp, n_pad, n_pad, Linv, h->dstat, stream));
+    if (trans) DFS_CK(launch_mirror_lower(f64, Lp, n_pad, (int)n_pad, stream));
     for (int64_t q0 = 0; q0 < k; q0 += kq) {
         const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
         void* Bg = static_cast<char*>(B) + q0 * es;
@@ -679,7 +686,7 @@ dfs_status dfs_fisher_pass(dfs_handle h, const void* S, int s_dtype, int64_t n, 
         DFS_CK(launch_pass(pp, s_dtype, kq, S, (int)n, m, lds, Vg, ldv, kg, Yg, Y ? ldy : kq, lambda, Xg, ldx,
                            R ? Rpart : nullptr, U2part, 0, h->dstat, 0, stream));
         if (R)
-            DFS_CK(launch_pass_reduce(0, Rpart, pp.grid, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
+            DFS_CK(launch_pass_reduce(0, Rpart, pp.nparts, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
                                       U2part, U2, h->dstat, 0, stream));
     }
     return DFS_OK;

@@ -1,50 +1,90 @@
 // Algorithm 1 step 2: L = Chol(W), W = L L^T, L lower triangular with a positive diagonal.
 //
 // Blocked right-looking factorisation of the padded n_pad x n_pad matrix W (row-major, lower
-// triangle), with NB = 32 diagonal blocks:
-//   step kb:  for every trailing tile (I, J) (TU x TU, I >= J) below/right of block kb,
-//               P_r = A[r, kb] Linv_kb^T,  P_q = A[q, kb] Linv_kb^T     (panel TRSM, recomputed)
-//               A[r, q] -= P_r P_q^T                                     (SYRK/GEMM update)
-//             and the CTA owning the next diagonal block factors it right after its update.
-//   each diagonal block is factored in FP64 (whatever the storage type) and its inverse
-//   Linv_kb is kept for the panel TRSM and for the triangular solves.
-//   after the last step, one kernel scales every panel: L[i, kb] = A[i, kb] Linv_kb^T.
-// The panels are left unscaled while the steps run, so no CTA ever reads a value another CTA
-// of the same launch writes.  A pivot <= 0 (or NaN/Inf) sets DFS_ERR_NOT_SPD and the pivot
-// index in the device status; later steps see the status and return without work.
+// triangle) in NB x NB tiles, as ONE persistent cooperative kernel (one CTA per SM, every CTA
+// resident).  Tile t = (i, p), i >= p, t = i (i + 1) / 2 + p, is owned by CTA t mod G for the
+// whole factorisation.  Step j applies column block j to the trailing matrix:
+//   A[i, p] -= P_i P_p^T,   P_i = A[i, j] Linv_j^T   (panel TRSM, recomputed where needed)
+// for all i >= p > j.  The panels A[i, j] stay unscaled while the steps run (so no tile is read
+// after its owner overwrote it) and are scaled in place once every CTA has finished; that last
+// pass also writes U = L^T into the (otherwise unused) upper triangle for the backward solve.
+// Dependencies are tracked per tile instead of with grid-wide barriers:
+//   done[t]   tile t = (i, p) has received its last update (after step p - 1);
+//   diag[j]   diagonal block j is factored: L_jj written and Linv_j = L_jj^{-1} published.
+// Within a step a CTA first updates its tiles of column j + 1 (the next panel), the diagonal
+// tile first; the owner of diagonal tile j + 1 factors it right away, so the factor of the
+// next block overlaps the rest of step j's trailing update (look-ahead).
+// Each diagonal block is factored by one warp with the block's rows in registers: column j's
+// pivot, scale and rank-1 update use shuffles only, in the compute type CT (double: the FP64
+// diagonal panel; float: the fast variant).  Its inverse (all 8 warps, 4 columns each) feeds
+// the panel TRSM and the triangular solves.
+// Every wait is bounded (DFS_ERR_TIMEOUT after 2 s) and also ends when another CTA has set an
+// error status: a pivot <= 0 (DFS_ERR_NOT_SPD) or NaN/Inf (DFS_ERR_NONFINITE) with its index.
 #include "kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace dfs {
 
 constexpr int NB = 32;
-constexpr int TU = 64;
+constexpr int CC_THREADS = 256;
+constexpr uint64_t kCholWaitNs = 2000000000ull;
 
-// Inverse of the lower-triangular NB x NB factor l (shared memory, compute type CT), in the
-// storage precision T.  One warp per column c (columns c = warp, warp + 8, ...; needs 256
-// threads), lane i holds x_i of L x = e_c: for p = c..NB-1, lane p finalises x_p = x_p / L_pp,
-// broadcasts it, and lanes i > p subtract L_ip x_p.  Written to dst (NB x NB row-major, zeros
-// above the diagonal).
-template <typename T, typename CT>
-__device__ void invert_lower_block(const CT (*l)[NB + 1], T* dst) {
-    __shared__ T rd[NB];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid < NB) rd[tid] = (T)1 / (T)l[tid][tid];
-    __syncthreads();
-    for (int c = warp; c < NB; c += (int)(blockDim.x >> 5)) {
-        T x = (lane == c) ? (T)1 : (T)0;
-        for (int p = c; p < NB; ++p) {
-            if (lane == p) x *= rd[p];
-            const T xp = __shfl_sync(0xffffffffu, x, p);
-            if (lane > p) x = fma(-(T)l[lane][p], xp, x);
-        }
-        dst[lane * NB + c] = (lane >= c) ? x : (T)0;
-    }
-    __syncthreads();
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Thread 0 waits (acquire) until *f >= target.  Block-uniform result: false when the device
+// status is or becomes non-zero, or after kCholWaitNs (then DFS_ERR_TIMEOUT is recorded).
+// Contains a __syncthreads().
+__device__ bool block_wait(const int* f, int target, DevStatus* st, int* s_ok, int sleep_ns) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (ld_acquire_gpu(f) < target) {
+            const volatile int* vs = &st->status;
+            const uint64_t t0 = tc::globaltimer_ns();
+            for (;;) {
+                if (ld_acquire_gpu(f) >= target) break;
+                if (*vs != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (tc::globaltimer_ns() - t0 > kCholWaitNs) {
+                    set_status(st, DFS_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if (sleep_ns) __nanosleep(sleep_ns);
+            }
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Make this CTA's global writes visible, then thread 0 sets *f = 1 (release).
+__device__ __forceinline__ void block_publish(int* f) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release_gpu(f, 1);
+}
+
+__device__ __forceinline__ void tile_ij(int t, int& i, int& p) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    i = r;
+    p = t - r * (r + 1) / 2;
+}
+__device__ __forceinline__ int tile_id(int i, int p) { return i * (i + 1) / 2 + p; }
+
 // 1/sqrt(d): FP32 hardware estimate, then (FP64) two Newton steps r <- r (3 - d r^2) / 2, each
-// doubling the correct bits (~2^-22 -> 2^-44 -> below FP64 rounding).  A short dependent chain:
-// the pivots of the diagonal factor are the critical path of the whole Cholesky.
+// doubling the correct bits (~2^-22 -> 2^-44 -> below FP64 rounding): a short dependent chain.
 __device__ __forceinline__ double rsqrt_ct(double d) {
     if (!(d > 1e-30 && d < 1e30)) return rsqrt(d);  // outside the FP32 estimate's safe range
     double r = (double)rsqrtf((float)d);
@@ -57,219 +97,241 @@ __device__ __forceinline__ double rsqrt_ct(double d) {
 }
 __device__ __forceinline__ float rsqrt_ct(float d) { return rsqrtf(d); }
 
-// Factor diagonal block kb in the compute type CT (double: the FP64 diagonal panel; float: the
-// fast variant) and write L_kb (storage type T) plus its inverse.
-// Column j: d = a[j][j]; r = 1/sqrt(d) (one thread); L[j][j] = d r, L[i][j] = a[i][j] r (one
-// thread per row); then a[i][p] -= L[i][j] L[p][j] for j < p <= i (one FMA per element).  The
-// elements of the trailing triangle are enumerated by a table sorted by column descending, so
-// the trailing triangle of step j is exactly the first (31-j)(32-j)/2 table entries.
-// Needs 256 threads and `scratch` >= 2 * NB * (NB + 1) CT values of shared memory.
+// dst = L^{-1} (NB x NB row-major, zeros above the diagonal) for the lower-triangular L in sF,
+// with s_rinv[i] = 1 / L[i][i].  Needs 256 threads: warp w forms columns c = w + 8 u (u < 4) of
+// X = L^{-1} by forward substitution on L x = e_c, lane i holding x_i; the four chains are
+// interleaved.  Arithmetic in T.
 template <typename T, typename CT>
-__device__ void factor_diag_block(T* W, int64_t ld, int kb, T* Linv, DevStatus* st, CT* scratch) {
-    CT(*a)[NB + 1] = reinterpret_cast<CT(*)[NB + 1]>(scratch);
-    CT(*l)[NB + 1] = reinterpret_cast<CT(*)[NB + 1]>(scratch + NB * (NB + 1));
-    __shared__ int fail;
-    __shared__ CT rcol;
-    __shared__ unsigned short tab[NB * (NB + 1) / 2];
-    const int tid = threadIdx.x;
-    const int nth = blockDim.x;
-    const int64_t o = (int64_t)kb * NB;
-    for (int e = tid; e < NB * NB; e += nth) {
-        const int i = e / NB, j = e % NB;
-        a[i][j] = (j <= i) ? (CT)W[(o + i) * ld + o + j] : (CT)0;
-        l[i][j] = (CT)0;
-    }
-    // tab[e] = (i << 8) | p over the lower triangle, p descending, i ascending within p
-    for (int e = tid; e < NB * (NB + 1) / 2; e += nth) {
-        int p = NB - 1, rem = e;
-        while (rem >= NB - p) {
-            rem -= NB - p;
-            --p;
+__device__ __forceinline__ void invert_lower_32(const CT (*sF)[NB + 1], const T* s_rinv, T* dst) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = (lane == warp + 8 * u) ? (T)1 : (T)0;
+#pragma unroll
+    for (int p = 0; p < NB; ++p) {
+        const T rp = s_rinv[p];
+        const T lip = (T)sF[lane][p];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (lane == p) x[u] *= rp;
+            const T xp = __shfl_sync(0xffffffffu, x[u], p);
+            if (lane > p) x[u] = fma(-lip, xp, x[u]);
         }
-        tab[e] = (unsigned short)(((p + rem) << 8) | p);
     }
-    if (tid == 0) fail = -1;
-    __syncthreads();
-    for (int j = 0; j < NB; ++j) {
-        if (tid == 0) {
-            const CT d = a[j][j];
-            if (!(d > (CT)0) || !isfinite(d)) {
-                fail = isfinite(d) ? j : -2 - j;  // -2 - j encodes a NaN/Inf pivot
-            } else {
-                const CT r = rsqrt_ct(d);
-                rcol = r;
-                l[j][j] = d * r;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = warp + 8 * u;
+        dst[lane * NB + c] = (lane >= c) ? x[u] : (T)0;
+    }
+}
+
+// Factor diagonal block kb (all threads of the CTA call it).  Warp 0: lane i holds row i of the
+// block in registers; for each column j the pivot is broadcast, every lane scales its entry and
+// applies the rank-1 update to the entries right of column j with the scaled column shuffled in.
+// Then L_kb goes to W (lower part) and sF, and all 8 warps form Linv_kb (4 columns per warp,
+// forward substitution on L x = e_c with the 4 chains interleaved).  Returns false (uniformly)
+// on a bad pivot, after recording it.
+template <typename T, typename CT>
+__device__ __noinline__ bool factor_diag(T* W, int64_t ld, int kb, T* Linv, DevStatus* st, CT (*sF)[NB + 1], T* s_rinv,
+                            int* s_fail) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t o = (int64_t)kb * NB;
+    if (warp == 0) {
+        CT a[NB];
+        const T* row = W + (o + lane) * ld + o;
+#pragma unroll
+        for (int p = 0; p < NB; ++p) a[p] = (p <= lane) ? (CT)__ldcg(row + p) : (CT)0;
+        int fail = -1;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const CT d = __shfl_sync(0xffffffffu, a[j], j);
+            if (fail < 0 && (!(d > (CT)0) || !isfinite(d))) fail = isfinite(d) ? j : -2 - j;
+            const CT r = rsqrt_ct(d);
+            const CT l = a[j] * r;
+            a[j] = (lane >= j) ? l : (CT)0;
+            // constant trip count (fully unrolled, a[] stays in registers); p <= j is skipped
+#pragma unroll
+            for (int p = 0; p < NB; ++p) {
+                if (p > j) {
+                    const CT lp = __shfl_sync(0xffffffffu, l, p);
+                    a[p] = (lane >= p) ? fma(-l, lp, a[p]) : a[p];
+                }
             }
         }
-        __syncthreads();
-        if (fail != -1) break;  // uniform: read after the barrier
-        // column j of L and the rank-1 update, both from the unscaled column a[][j] and r (one
-        // barrier per column): a[i][p] -= (a[i][j] r) (a[p][j] r)
-        const CT r = rcol;
-        if (tid > j && tid < NB) l[tid][j] = a[tid][j] * r;
-        const int cnt = (NB - 1 - j) * (NB - j) / 2;
-        for (int e = tid; e < cnt; e += nth) {
-            const int ip = tab[e];
-            const int i = ip >> 8, p = ip & 0xff;
-            a[i][p] = fma(-(a[i][j] * r), a[p][j] * r, a[i][p]);
+        if (lane == 0) *s_fail = fail;
+        if (fail < 0) {
+            T* wr = W + (o + lane) * ld + o;
+#pragma unroll
+            for (int p = 0; p < NB; ++p) {
+                sF[lane][p] = a[p];
+                if (p <= lane) wr[p] = (T)a[p];
+                if (p == lane) s_rinv[lane] = (T)1 / (T)a[p];
+            }
         }
-        __syncthreads();
     }
+    __syncthreads();
+    const int fail = *s_fail;
     if (fail != -1) {
         if (tid == 0) {
             const int j = fail >= 0 ? fail : -2 - fail;
             set_status(st, fail >= 0 ? DFS_ERR_NOT_SPD : DFS_ERR_NONFINITE);
             atomicCAS(&st->failed_pivot, -1, (int)(o + j));
         }
-        __syncthreads();
-        return;
+        return false;
     }
-    for (int e = tid; e < NB * NB; e += nth) {
-        const int i = e / NB, j = e % NB;
-        if (j <= i) W[(o + i) * ld + o + j] = (T)l[i][j];
-    }
-    invert_lower_block<T, CT>(l, Linv + (int64_t)kb * NB * NB);
+    invert_lower_32<T, CT>(sF, s_rinv, Linv + (int64_t)kb * NB * NB);
+    return true;
 }
 
-template <typename T, typename CT>
-__global__ void __launch_bounds__(256) chol_first_kernel(T* W, int64_t ld, T* Linv, DevStatus* st) {
-    __shared__ CT scratch[2 * NB * (NB + 1)];
-    if (block_should_exit(st, 0)) return;
-    factor_diag_block<T, CT>(W, ld, 0, Linv, st, scratch);
-}
-
-__device__ __forceinline__ void tri_ij(int t, int& I, int& J) {
-    int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= t) ++i;
-    while (i * (i + 1) / 2 > t) --i;
-    I = i;
-    J = t - i * (i + 1) / 2;
-}
-
-// Load a rows x NB panel block into smem and replace it by P = A Linv^T (rows beyond `rows`
-// are zero).  Linv is lower triangular, so P[i][j] = sum_{p <= j} A[i][p] Linv[j][p].
+// sOut = A[r0.., c0..] Linv^T for one NB x NB tile: sOut[r][c] = sum_q A[r][q] Li[c][q] (Li is
+// lower triangular with zeros above the diagonal).  Thread: row tid / 8, columns tid % 8 + 8 u.
 template <typename T>
-__device__ __forceinline__ void panel_times_linv_t(const T* W, int64_t ld, int64_t r0, int rows,
-                                                   int64_t col0, const T (*sL)[NB + 1], T (*sA)[NB + 1]) {
+__device__ __forceinline__ void tile_times_linv_t(const T* W, int64_t ld, int64_t r0, int64_t c0,
+                                                  const T (*sLi)[NB + 1], T (*sOut)[NB + 1]) {
     const int tid = threadIdx.x;
-    for (int e = tid; e < TU * NB; e += blockDim.x) {
-        const int i = e / NB, p = e % NB;
-        sA[i][p] = (i < rows) ? W[(r0 + i) * ld + col0 + p] : (T)0;
+#pragma unroll
+    for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
+        const int e = tid + u * CC_THREADS;
+        sOut[e / NB][e % NB] = __ldcg(W + (r0 + e / NB) * ld + c0 + e % NB);
     }
     __syncthreads();
-    T out[TU * NB / 256];
+    const int r = tid >> 3, c = tid & 7;
+    T acc[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int u = 0; u < TU * NB / 256; ++u) {
-        const int e = tid + u * 256;
-        const int i = e / NB, j = e % NB;
-        T s = 0;
-        for (int p = 0; p <= j; ++p) s = fma(sA[i][p], sL[j][p], s);
-        out[u] = s;
+    for (int q = 0; q < NB; ++q) {
+        const T a = sOut[r][q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(a, sLi[c + 8 * u][q], acc[u]);
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < TU * NB / 256; ++u) {
-        const int e = tid + u * 256;
-        sA[e / NB][e % NB] = out[u];
+    for (int u = 0; u < 4; ++u) sOut[r][c + 8 * u] = acc[u];
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void load_linv(const T* Linv, int kb, T (*sLi)[NB + 1]) {
+    const T* src = Linv + (int64_t)kb * NB * NB;
+#pragma unroll
+    for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
+        const int e = threadIdx.x + u * CC_THREADS;
+        sLi[e / NB][e % NB] = __ldcg(src + e);
     }
     __syncthreads();
 }
 
+// flags (int32, zeroed before the launch): diag[nb] | done[nb (nb + 1) / 2] | finished-CTA count
 template <typename T, typename CT>
-__global__ void __launch_bounds__(256)
-chol_step_kernel(T* W, int64_t ld, int64_t n_pad, int kb, T* Linv, DevStatus* st) {
-    constexpr int kPanelBytes = 2 * TU * (NB + 1) * (int)sizeof(T);
-    constexpr int kFactorBytes = 2 * NB * (NB + 1) * (int)sizeof(CT);
-    __shared__ __align__(16) T sL[NB][NB + 1];
-    // The two panel buffers and the FP64 factor scratch are never live at the same time.
-    __shared__ __align__(16) unsigned char raw[kPanelBytes > kFactorBytes ? kPanelBytes : kFactorBytes];
-    T(*sR)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(raw);
-    T(*sQ)[NB + 1] = sR + TU;
-    CT* scratch = reinterpret_cast<CT*>(raw);
+__global__ void __launch_bounds__(CC_THREADS)
+chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
+    __shared__ __align__(16) T sLi[NB][NB + 1];
+    __shared__ __align__(16) T sP[NB][NB + 1];
+    __shared__ __align__(16) T sQ[NB][NB + 1];
+    __shared__ __align__(16) CT sF[NB][NB + 1];
+    __shared__ T s_rinv[NB];
+    __shared__ int s_ok, s_fail;
     if (block_should_exit(st, 0)) return;
-    const int tid = threadIdx.x;
-    const int64_t c0 = (int64_t)(kb + 1) * NB;
-    const int64_t rem = n_pad - c0;
-    int I, J;
-    tri_ij(blockIdx.x, I, J);
-    const int64_t r0 = c0 + (int64_t)I * TU, q0 = c0 + (int64_t)J * TU;
-    const int rows_r = (int)min((int64_t)TU, rem - (int64_t)I * TU);
-    const int rows_q = (int)min((int64_t)TU, rem - (int64_t)J * TU);
-    const int64_t kc = (int64_t)kb * NB;
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int ntiles = nb * (nb + 1) / 2;
+    int* diag = flags;
+    int* done = flags + nb;
+    int* fin = flags + nb + ntiles;
 
-    const T* Lk = Linv + (int64_t)kb * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) sL[e / NB][e % NB] = Lk[e];
-    __syncthreads();
-    panel_times_linv_t<T>(W, ld, r0, rows_r, kc, sL, sR);
-    if (I != J) panel_times_linv_t<T>(W, ld, q0, rows_q, kc, sL, sQ);
-    const T(*pq)[NB + 1] = (I != J) ? sQ : sR;
-
-    // C[i][j] -= sum_p P_r[i][p] P_q[j][p]; thread owns rows ty + 16 a, cols tx + 16 b.
-    const int tx = tid & 15, ty = tid >> 4;
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-#pragma unroll 8
-    for (int p = 0; p < NB; ++p) {
-        T ra[4], rb[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) ra[a] = sR[ty + 16 * a][p];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) rb[b] = pq[tx + 16 * b][p];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(ra[a], rb[b], acc[a][b]);
+    if (tile_id(0, 0) % G == cta) {
+        if (!factor_diag<T, CT>(W, ld, 0, Linv, st, sF, s_rinv, &s_fail)) return;
+        block_publish(&diag[0]);
     }
+    int last_p = -1;  // the largest column index among this CTA's tiles: no work after step last_p - 1
+    for (int t = cta; t < ntiles; t += G) {
+        int i, p;
+        tile_ij(t, i, p);
+        last_p = p > last_p ? p : last_p;
+    }
+    for (int j = 0; j + 1 < nb && j < last_p; ++j) {
+        if (!block_wait(&diag[j], 1, st, &s_ok, 0)) return;
+        load_linv<T>(Linv, j, sLi);
+        // pass 0: tiles of column j + 1 (diagonal first: it has the smallest id); pass 1: the rest
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int t = cta; t < ntiles; t += G) {
+                int i, p;
+                tile_ij(t, i, p);
+                if (pass == 0 ? (p != j + 1) : (p <= j + 1)) continue;
+                if (j > 0) {
+                    if (!block_wait(&done[tile_id(i, j)], 1, st, &s_ok, 0)) return;
+                    if (p != i && !block_wait(&done[tile_id(p, j)], 1, st, &s_ok, 0)) return;
+                }
+                const int64_t c0 = (int64_t)j * NB;
+                tile_times_linv_t<T>(W, ld, (int64_t)i * NB, c0, sLi, sP);
+                if (p != i) tile_times_linv_t<T>(W, ld, (int64_t)p * NB, c0, sLi, sQ);
+                const T(*pq)[NB + 1] = (p != i) ? sQ : sP;
+                // A[i, p] -= P_i P_p^T; thread: rows ty + 16 a, columns tx + 16 b
+                const int tx = tid & 15, ty = tid >> 4;
+                T acc[2][2] = {{0, 0}, {0, 0}};
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = ty + 16 * a;
-        if (i >= rows_r) continue;
+                for (int q = 0; q < NB; ++q) {
+                    const T a0 = sP[ty][q], a1 = sP[ty + 16][q];
+                    const T b0 = pq[tx][q], b1 = pq[tx + 16][q];
+                    acc[0][0] = fma(a0, b0, acc[0][0]);
+                    acc[0][1] = fma(a0, b1, acc[0][1]);
+                    acc[1][0] = fma(a1, b0, acc[1][0]);
+                    acc[1][1] = fma(a1, b1, acc[1][1]);
+                }
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int j = tx + 16 * b;
-            if (j >= rows_q) continue;
-            const int64_t gi = r0 + i, gj = q0 + j;
-            if (gj > gi) continue;
-            T* p = W + gi * ld + gj;
-            *p = *p - acc[a][b];
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int r = ty + 16 * a, c = tx + 16 * b;
+                        if (i == p && c > r) continue;
+                        T* w = W + ((int64_t)i * NB + r) * ld + (int64_t)p * NB + c;
+                        *w = __ldcg(w) - acc[a][b];
+                    }
+                __syncthreads();  // sP / sQ are reused by the next tile
+                if (p == j + 1) {  // the tile's last update
+                    if (i == p) {
+                        __threadfence();
+                        __syncthreads();
+                        if (!factor_diag<T, CT>(W, ld, p, Linv, st, sF, s_rinv, &s_fail)) return;
+                        block_publish(&diag[p]);
+                    } else {
+                        block_publish(&done[t]);
+                    }
+                }
+            }
         }
     }
-    if (I == 0 && J == 0 && c0 < n_pad) {
-        __threadfence_block();
-        __syncthreads();  // all reads of sR/sQ are done before the factor scratch reuses them
-        factor_diag_block<T, CT>(W, ld, kb + 1, Linv, st, scratch);
+    // every CTA has applied all its steps: scale the panels in place, L[i, p] = A[i, p] Linv_p^T
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(fin, 1);
+    if (!block_wait(fin, G, st, &s_ok, 64)) return;
+    for (int t = cta; t < ntiles; t += G) {
+        int i, p;
+        tile_ij(t, i, p);
+        if (i == p) continue;
+        load_linv<T>(Linv, p, sLi);
+        tile_times_linv_t<T>(W, ld, (int64_t)i * NB, (int64_t)p * NB, sLi, sP);
+#pragma unroll
+        for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
+            const int e = tid + u * CC_THREADS;
+            W[((int64_t)i * NB + e / NB) * ld + (int64_t)p * NB + e % NB] = sP[e / NB][e % NB];
+            // U = L^T in the upper triangle: the backward triangular solve streams its rows
+            W[((int64_t)p * NB + e / NB) * ld + (int64_t)i * NB + e % NB] = sP[e % NB][e / NB];
+        }
+        __syncthreads();
     }
 }
 
-// Final panel scaling: L[i, kb] = A[i, kb] Linv_kb^T for all rows below diagonal block kb.
-template <typename T>
-__global__ void __launch_bounds__(256) chol_scale_kernel(T* W, int64_t ld, int64_t n_pad, T* Linv, DevStatus* st) {
-    __shared__ __align__(16) T sL[NB][NB + 1];
-    __shared__ __align__(16) T sA[TU][NB + 1];
-    if (block_should_exit(st, 0)) return;
-    const int kb = blockIdx.y;
-    const int64_t c0 = (int64_t)(kb + 1) * NB;
-    const int64_t r0 = c0 + (int64_t)blockIdx.x * TU;
-    if (r0 >= n_pad) return;
-    const int rows = (int)min((int64_t)TU, n_pad - r0);
-    const T* Lk = Linv + (int64_t)kb * NB * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) sL[e / NB][e % NB] = Lk[e];
-    __syncthreads();
-    panel_times_linv_t<T>(W, ld, r0, rows, (int64_t)kb * NB, sL, sA);
-    for (int e = threadIdx.x; e < rows * NB; e += blockDim.x) {
-        const int i = e / NB, p = e % NB;
-        W[(r0 + i) * ld + (int64_t)kb * NB + p] = sA[i][p];
-    }
+size_t cholesky_flag_bytes(int64_t n_pad) {
+    const int64_t nb = n_pad / NB;
+    return (size_t)(nb + nb * (nb + 1) / 2 + 1) * sizeof(int);
 }
 
 // Inverses of all diagonal blocks of an existing factor L (for triangular solves with a
 // caller-supplied L).  A zero or non-finite diagonal entry sets DFS_ERR_INVALID_ARG.
 template <typename T>
 __global__ void __launch_bounds__(256) diag_inverse_kernel(const T* L, int64_t ld, T* Linv, DevStatus* st) {
-    __shared__ double a[NB][NB + 1];
+    __shared__ T a[NB][NB + 1];
+    __shared__ T rinv[NB];
     __shared__ int bad;
     const int kb = blockIdx.x;
     const int64_t o = (int64_t)kb * NB;
@@ -277,16 +339,19 @@ __global__ void __launch_bounds__(256) diag_inverse_kernel(const T* L, int64_t l
     __syncthreads();
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int i = e / NB, j = e % NB;
-        const double v = (j <= i) ? (double)L[(o + i) * ld + o + j] : 0.0;
+        const T v = (j <= i) ? L[(o + i) * ld + o + j] : (T)0;
         a[i][j] = v;
-        if (i == j && (!(v != 0.0) || !isfinite(v))) atomicExch(&bad, 1);
+        if (i == j) {
+            if (!(v != (T)0) || !isfinite(v)) atomicExch(&bad, 1);
+            rinv[i] = (T)1 / v;
+        }
     }
     __syncthreads();
     if (bad) {
         if (threadIdx.x == 0) set_status(st, DFS_ERR_INVALID_ARG);
         return;
     }
-    invert_lower_block<T, double>(a, Linv + (int64_t)kb * NB * NB);
+    invert_lower_32<T, T>(a, rinv, Linv + (int64_t)kb * NB * NB);
 }
 
 cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
@@ -308,39 +373,35 @@ cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_
 }
 
 template <typename T, typename CT>
-static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* Linv_, DevStatus* st,
+static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* Linv_, int* flags, DevStatus* st,
                                      cudaStream_t stream) {
     T* W = static_cast<T*>(W_);
     T* Linv = static_cast<T*>(Linv_);
-    const int nblk = (int)(n_pad / NB);
-    {
-        chol_first_kernel<T, CT><<<1, 256, 0, stream>>>(W, ld, Linv, st);
-        count_launch();
-    }
-    for (int kb = 0; kb + 1 < nblk; ++kb) {
-        const int64_t rem = n_pad - (int64_t)(kb + 1) * NB;
-        const int Tn = (int)ceil_div(rem, TU);
-        {
-            chol_step_kernel<T, CT><<<Tn * (Tn + 1) / 2, 256, 0, stream>>>(W, ld, n_pad, kb, Linv, st);
-            count_launch();
-        }
-    }
-    if (nblk > 1) {
-        dim3 grid((unsigned)ceil_div(n_pad, TU), nblk - 1);
-        {
-            chol_scale_kernel<T><<<grid, 256, 0, stream>>>(W, ld, n_pad, Linv, st);
-            count_launch();
-        }
-    }
-    return cudaGetLastError();
+    int nb = (int)(n_pad / NB);
+    const int ntiles = nb * (nb + 1) / 2;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    auto kern = chol_coop_kernel<T, CT>;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CC_THREADS, 0)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // one CTA per SM (two for large n, where the trailing updates dominate); all resident
+    int G = sms * (per_sm >= 2 && ntiles >= 32 * sms ? 2 : 1);
+    if (G > ntiles) G = ntiles;
+    if ((e = cudaMemsetAsync(flags, 0, cholesky_flag_bytes(n_pad), stream)) != cudaSuccess) return e;
+    void* args[] = {&W, &ld, &nb, &Linv, &flags, &st};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(CC_THREADS), args, 0, stream);
+    count_launch();
+    return e;
 }
 
-cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
+cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void* Linv, int* flags, DevStatus* st,
                             cudaStream_t stream, int fp64_panel) {
     if (n_pad % NB != 0) return cudaErrorInvalidValue;
-    if (w_f64) return launch_cholesky_t<double, double>(W, ld, n_pad, Linv, st, stream);
-    return fp64_panel ? launch_cholesky_t<float, double>(W, ld, n_pad, Linv, st, stream)
-                      : launch_cholesky_t<float, float>(W, ld, n_pad, Linv, st, stream);
+    if (w_f64) return launch_cholesky_t<double, double>(W, ld, n_pad, Linv, flags, st, stream);
+    return fp64_panel ? launch_cholesky_t<float, double>(W, ld, n_pad, Linv, flags, st, stream)
+                      : launch_cholesky_t<float, float>(W, ld, n_pad, Linv, flags, st, stream);
 }
 
 }  // namespace dfs

@@ -402,7 +402,7 @@ gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int P, int
 
 // ---- host side ------------------------------------------------------------------------------
 
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         void* p = nullptr;

@@ -35,13 +35,16 @@ cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64
 
 // ---- step 2, Cholesky (cholesky.cu) ----
 // fp64_panel: factor the 32 x 32 diagonal blocks in FP64 (else in the storage type).
-cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
+// flags: cholesky_flag_bytes(n_pad) of device scratch (zeroed by the launcher).
+size_t cholesky_flag_bytes(int64_t n_pad);
+cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void* Linv, int* flags, DevStatus* st,
                             cudaStream_t stream, int fp64_panel = 1);
 cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
                                 cudaStream_t stream);
 
 // ---- triangular solves (trsv.cu) ----
-size_t trsv_smem_bytes(int n_pad, int KQ, int elem);
+size_t trsv_smem_bytes(int n_pad, int KQ, int elem, int nst);
+cudaError_t launch_mirror_lower(int f64, void* L, int64_t ld, int n_pad, cudaStream_t stream);
 int trsv_max_group(int n_pad, int elem, size_t smem_limit);
 cudaError_t launch_trsv(int f64, int trans, const void* L, int64_t ld, int n_pad, const void* Linv, void* B,
                         int64_t ldb, int k, int kq, const DevStatus* st, int honor_stop, cudaStream_t stream);
@@ -51,7 +54,17 @@ struct PassPlan {
     int rpt;      // rows per thread kept in registers by the refinement pass (0: re-read mode)
     int grid;     // CTAs of fisher_pass_kernel
     int sv_grid;  // CTAs of sv_pack_kernel
+    int cs;       // > 0: the refinement pass runs as clusters of cs CTAs (pass_cluster.cu)
+    int crpt;     // rows per thread of the cluster form
+    int ncl;      // clusters
+    int nparts;   // partial rows (Rpart / U2part) the refinement pass writes
 };
+int pass_cluster_plan(int s_dtype, int n, int KQ, int num_sms, int64_t m, size_t smem_limit, int* cs_out,
+                      int* rpt_out);
+cudaError_t launch_pass_cluster(int ncl, int cs, int rpt, int kq, const void* S, int n, int64_t m, int64_t lds,
+                                const void* V, int64_t ldv, int k, const double* Y, int64_t ldy, double lambda,
+                                void* X, int64_t ldx, double* Rpart, double* U2part, int dmode, const DevStatus* st,
+                                int honor_stop, cudaStream_t stream);
 size_t pass_smem_bytes(int n, int KQ, int s_dtype);
 int pass_max_group(int n, int s_dtype, size_t smem_limit);
 int pass_grid(int n, int KQ, int s_dtype, int num_sms, int64_t m);

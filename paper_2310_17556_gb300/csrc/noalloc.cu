@@ -24,7 +24,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 constexpr size_t kAlign = 256;
 
-// Layout: [DevStatus | U2 (2 KQ) | U2part (grid x 2 KQ) | Rpart (grid x n x KQ)], each 256-aligned.
+// Layout: [DevStatus | U2 (2 KQ) | U2part (parts x 2 KQ) | Rpart (parts x n x KQ)], each 256-aligned.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DFS_NOALLOC_SCRATCH_BYTES];
 
 struct DeviceSetup {
@@ -120,11 +120,11 @@ extern "C" dfs_status dfs_fisher_pass_noalloc(const void* S, int s_dtype, int64_
     int kq = pow2_ceil(k);
     if (kq > kmax) kq = kmax;
     PassPlan pp = pass_make_plan((int)n, kq, s_dtype, d.num_sms, m, d.smem_optin);
-    Layout lay = layout_for(pp.grid, n, kq, R != nullptr);
+    Layout lay = layout_for(pp.nparts, n, kq, R != nullptr);
     while (lay.total > DFS_NOALLOC_SCRATCH_BYTES && kq > 1) {
         kq >>= 1;
         pp = pass_make_plan((int)n, kq, s_dtype, d.num_sms, m, d.smem_optin);
-        lay = layout_for(pp.grid, n, kq, R != nullptr);
+        lay = layout_for(pp.nparts, n, kq, R != nullptr);
     }
     if (scratch_bytes) *scratch_bytes = (int64_t)lay.total;
     if (lay.total > DFS_NOALLOC_SCRATCH_BYTES) return DFS_ERR_NO_MEMORY;
@@ -145,7 +145,7 @@ extern "C" dfs_status dfs_fisher_pass_noalloc(const void* S, int s_dtype, int64_
         if (launch_pass(pp, s_dtype, kq, S, (int)n, m, lds, Vg, ldv, kg, Yg, Y ? ldy : kq, lambda, Xg, ldx, Rpart,
                         U2part, 0, st, 0, stream) != cudaSuccess)
             return DFS_ERR_CUDA;
-        if (R && launch_pass_reduce(0, Rpart, pp.grid, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
+        if (R && launch_pass_reduce(0, Rpart, pp.nparts, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
                                     U2part, U2, st, 0, stream) != cudaSuccess)
             return DFS_ERR_CUDA;
     }

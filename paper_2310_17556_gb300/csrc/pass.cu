@@ -194,7 +194,9 @@ fisher_pass_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds,
     constexpr int SWEEP = PASS_WARPS * RPW;  // 64 rows
     constexpr int RB = 8;                    // re-read mode: rows in flight per thread
     extern __shared__ __align__(16) unsigned char smem[];
-    double* Rs64 = reinterpret_cast<double*>(smem);              // n x KQ
+    // register-resident mode: the next strip lands here (cp.async) while this one is processed
+    uint4* stage = reinterpret_cast<uint4*>(smem);               // RPT x PASS_THREADS x 16 bytes
+    double* Rs64 = reinterpret_cast<double*>(smem + (size_t)RPT * PASS_THREADS * 16);  // n x KQ
     TA* Rs32 = reinterpret_cast<TA*>(Rs64 + (size_t)n * KQ);     // n x KQ
     TA* Ys = Rs32 + (size_t)n * KQ;                              // n x KQ
     TA* ured = Ys + (size_t)n * KQ;                              // PASS_WARPS x W x KQ
@@ -222,6 +224,27 @@ fisher_pass_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds,
     const int row0 = warp * RPW + rr;
     const bool u_thread = tid < W * KQ;
     const int uc = tid / KQ, uq = tid % KQ;
+    // This thread's RPT row segments of strip sidx -> stage (zero-filled past row n / column m).
+    // Each thread later reads back exactly the slots it filled, so no barrier is involved.
+    auto issue_strip = [&](int64_t sidx) {
+        const int64_t jn = sidx * W + cq * VEC;
+        const int64_t rem = m - jn;
+        const int bytes_col = rem >= VEC ? 16 : (rem > 0 ? (int)rem * (int)sizeof(TS) : 0);
+#pragma unroll
+        for (int t = 0; t < (RPT > 0 ? RPT : 1); ++t) {
+            const int i = row0 + t * SWEEP;
+            const int bytes = i < n ? bytes_col : 0;
+            const TS* src = bytes ? S + (int64_t)i * lds + jn : S;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             static_cast<uint32_t>(__cvta_generic_to_shared(&stage[t * PASS_THREADS + tid]))),
+                         "l"(src), "r"(bytes)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if constexpr (RPT > 0) {
+        if (blockIdx.x < nstrips) issue_strip(blockIdx.x);
+    }
     int since_fold = 0;
     for (int64_t s = blockIdx.x; s < nstrips; s += gridDim.x) {
         const int64_t j0 = s * W;
@@ -236,17 +259,11 @@ fisher_pass_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds,
         }
         TA sv[RPT > 0 ? RPT : 1][VEC];
         if constexpr (RPT > 0) {
+            asm volatile("cp.async.wait_all;" ::: "memory");
 #pragma unroll
-            for (int t = 0; t < RPT; ++t) {
-                const int i = row0 + t * SWEEP;
-                const TS* p = S + (int64_t)i * lds + jc;
-                if (i < n && full) {
-                    load16_stream<TS, TA>(p, sv[t]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) sv[t][e] = (i < n && jc + e < m) ? load1<TS, TA>(p + e) : (TA)0;
-                }
-            }
+            for (int t = 0; t < RPT; ++t)
+                load16_smem<TS, TA>(reinterpret_cast<const TS*>(&stage[t * PASS_THREADS + tid]), sv[t]);
+            if (s + gridDim.x < nstrips) issue_strip(s + gridDim.x);
         }
         // ---- phase 1: column sums of S^T Y over the strip ----
         if (haveY) {
@@ -437,34 +454,44 @@ fisher_pass_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds,
 
 // R = sum_b Rpart[b] - lambda Y (FP64, fixed order), rows [0, n_out) with stride ldr (rows >= n
 // are zero), an optional copy Rt (n_out x KQ, solve type T) for the triangular solves, and the
-// summed ||U||^2 and ||X_new - X_old||^2 per RHS (U2[0..KQ) and U2[KQ..2KQ)).  One warp per
-// output element: lane l sums parts l, l + 32, ... in order, then a fixed shuffle tree.
+// summed ||U||^2 and ||X_new - X_old||^2 per RHS (U2[0..KQ) and U2[KQ..2KQ)).
+// A CTA owns 32 consecutive outputs e; its 16 thread groups walk the parts b = g, g + 16, ...
+// (each load a coalesced 256-byte row segment), then group sums are added in group order.
+constexpr int RED_GROUPS = 16;
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(RED_GROUPS * 32)
 pass_reduce_kernel(const double* __restrict__ Rpart, int nparts, int n, int n_out, int KQ, int k,
                    const double* __restrict__ Y, int64_t ldy, double lambda, double* __restrict__ R, int64_t ldr,
                    T* __restrict__ Rt, const double* __restrict__ U2part, double* __restrict__ U2,
                    const DevStatus* st, int honor_stop) {
+    __shared__ double red[RED_GROUPS][33];
     if (st->status != 0 || (honor_stop && st->stop)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (e < (int64_t)n_out * KQ) {
-        const int i = (int)(e / KQ), q = (int)(e % KQ);
-        double v = 0.0;
-        if (i < n && q < k)
-            for (int b = lane; b < nparts; b += 32) v += Rpart[(int64_t)b * n * KQ + e];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t nin = (int64_t)n * KQ;
+    double v = 0.0;
+    if (e < nin) {
+        const double* p = Rpart + e;
+#pragma unroll 4
+        for (int b = grp; b < nparts; b += RED_GROUPS) v += p[(int64_t)b * nin];
+    }
+    red[grp][lane] = v;
+    __syncthreads();
+    if (grp == 0 && e < (int64_t)n_out * KQ) {
+        double t = 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) {
-            if (i < n && q < k && Y != nullptr) v -= lambda * Y[(int64_t)i * ldy + q];
-            if (R != nullptr && q < k) R[(int64_t)i * ldr + q] = v;
-            if (Rt != nullptr) Rt[e] = (T)v;
-        }
+        for (int g = 0; g < RED_GROUPS; ++g) t += red[g][lane];
+        const int i = (int)(e / KQ), q = (int)(e % KQ);
+        if (!(i < n && q < k)) t = 0.0;
+        if (i < n && q < k && Y != nullptr) t -= lambda * Y[(int64_t)i * ldy + q];
+        if (R != nullptr && q < k) R[(int64_t)i * ldr + q] = t;
+        if (Rt != nullptr) Rt[e] = (T)t;
     }
     if (U2 != nullptr && U2part != nullptr && blockIdx.x == 0 && threadIdx.x < 2 * KQ) {
-        double v = 0.0;
-        for (int b = 0; b < nparts; ++b) v += U2part[(int64_t)b * 2 * KQ + threadIdx.x];
-        U2[threadIdx.x] = v;
+        double u = 0.0;
+        for (int b = 0; b < nparts; ++b) u += U2part[(int64_t)b * 2 * KQ + threadIdx.x];
+        U2[threadIdx.x] = u;
     }
 }
 
@@ -473,10 +500,15 @@ pass_reduce_kernel(const double* __restrict__ Rpart, int nparts, int n, int n_ou
 static int vec_of(int s_dtype) { return s_dtype == DFS_F64 ? 2 : (s_dtype == DFS_F32 ? 4 : 8); }
 static int ta_of(int s_dtype) { return s_dtype == DFS_F64 ? 8 : 4; }
 
+static int pass_rpt(int n, int KQ, int s_dtype);
+
+// Dynamic shared memory of fisher_pass_kernel, including the strip stage of the
+// register-resident mode.
 size_t pass_smem_bytes(int n, int KQ, int s_dtype) {
     const int ta = ta_of(s_dtype);
     const int W = 8 * vec_of(s_dtype);
-    return (size_t)n * KQ * (8 + 2 * ta) + (size_t)PASS_WARPS * W * KQ * ta + (size_t)W * KQ * ta;
+    const size_t stage = (size_t)pass_rpt(n, KQ, s_dtype) * PASS_THREADS * 16;
+    return stage + (size_t)n * KQ * (8 + 2 * ta) + (size_t)PASS_WARPS * W * KQ * ta + (size_t)W * KQ * ta;
 }
 
 static size_t sv_smem_bytes(int n, int KQ, int s_dtype) { return (size_t)n * KQ * (8 + ta_of(s_dtype)); }
@@ -497,7 +529,6 @@ static int pass_rpt(int n, int KQ, int s_dtype) {
 }
 
 PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit) {
-    (void)smem_limit;
     PassPlan p{};
     p.rpt = pass_rpt(n, KQ, s_dtype);
     // register-resident strips: one 512-thread CTA per SM; otherwise up to four
@@ -513,6 +544,10 @@ PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size
     int64_t gs = (int64_t)num_sms * 4;
     if (gs > nstrips) gs = nstrips;
     p.sv_grid = (int)(gs < 1 ? 1 : gs);
+    // FP32 S with n <= 4096: clusters sharing 256-byte-wide strips (pass_cluster.cu)
+    p.ncl = smem_limit ? pass_cluster_plan(s_dtype, n, KQ, num_sms, m, smem_limit, &p.cs, &p.crpt) : 0;
+    if (p.ncl == 0) p.cs = p.crpt = 0;
+    p.nparts = p.cs > 0 ? p.ncl : p.grid;
     return p;
 }
 
@@ -564,6 +599,9 @@ cudaError_t launch_pass(const PassPlan& plan, int s_dtype, int kq, const void* S
                         const void* V, int64_t ldv, int k, const double* Y, int64_t ldy, double lambda, void* X,
                         int64_t ldx, double* Rpart, double* U2part, int dmode, const DevStatus* st, int honor_stop,
                         cudaStream_t stream) {
+    if (plan.cs > 0 && s_dtype == DFS_F32)
+        return launch_pass_cluster(plan.ncl, plan.cs, plan.crpt, kq, S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx,
+                                   Rpart, U2part, dmode, st, honor_stop, stream);
 #define DFS_PASS_CASE(KQ)                                                                                         \
     case KQ:                                                                                                      \
         if (s_dtype == DFS_F32)                                                                                   \
@@ -658,13 +696,12 @@ cudaError_t launch_pass_reduce(int f64, const double* Rpart, int nparts, int n, 
                                const double* Y, int64_t ldy, double lambda, double* R, int64_t ldr, void* Rt,
                                const double* U2part, double* U2, const DevStatus* st, int honor_stop,
                                cudaStream_t stream) {
-    const int64_t total = (int64_t)n_out * KQ * 32;  // one warp per output
-    const int blocks = (int)ceil_div(total, 256);
+    const int blocks = (int)ceil_div((int64_t)n_out * KQ, 32);
     if (f64) {
-        pass_reduce_kernel<double><<<blocks, 256, 0, stream>>>(Rpart, nparts, n, n_out, KQ, k, Y, ldy, lambda, R, ldr,
+        pass_reduce_kernel<double><<<blocks, RED_GROUPS * 32, 0, stream>>>(Rpart, nparts, n, n_out, KQ, k, Y, ldy, lambda, R, ldr,
                                                                static_cast<double*>(Rt), U2part, U2, st, honor_stop);
     } else {
-        pass_reduce_kernel<float><<<blocks, 256, 0, stream>>>(Rpart, nparts, n, n_out, KQ, k, Y, ldy, lambda, R, ldr,
+        pass_reduce_kernel<float><<<blocks, RED_GROUPS * 32, 0, stream>>>(Rpart, nparts, n, n_out, KQ, k, Y, ldy, lambda, R, ldr,
                                                               static_cast<float*>(Rt), U2part, U2, st, honor_stop);
     }
     count_launch();

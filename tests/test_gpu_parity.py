@@ -147,11 +147,11 @@ def test_tf32_refined_path_matches_oracle(n, m, k, lam):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32"])
-def test_fp32_diagonal_panel_variant(prec):
+def test_fp64_diagonal_panel_variant(prec):
     n, m, lam = 700, 50000, 1e-3
     S = wl.gaussian(n, m, seed=89, device=dev())
     V = wl.rhs(m, 2, seed=90, device=dev())
-    X, info = dfs.dfs_solve(S, V, lam, precision=prec, fp32_panel=True)
+    X, info = dfs.dfs_solve(S, V, lam, precision=prec, fp64_panel=True)
     assert info["status"] == 0
     assert rel_err(np64(X), solve_ref(S, V, lam)) <= (fp32_tol(S, lam) if prec == "fp32" else 1e-6)
 
@@ -231,7 +231,9 @@ def test_gram_step(dtype, prec, n, m, tol):
 
 
 @pytest.mark.parametrize("dtype,n,tol", [(torch.float32, 300, 1e-5), (torch.float64, 200, 1e-12),
-                                         (torch.float32, 1024, 1e-5), (torch.float32, 33, 1e-5)])
+                                         (torch.float32, 1024, 1e-5), (torch.float32, 33, 1e-5),
+                                         (torch.float32, 2500, 2e-5), (torch.float64, 1100, 1e-12),
+                                         (torch.float32, 4096, 4e-5)])
 def test_cholesky_step(dtype, n, tol):
     A = wl.gaussian(n, 3 * n, seed=41, device=dev(), dtype=torch.float64)
     Wr = (A @ A.T + 0.5 * torch.eye(n, device=dev(), dtype=torch.float64)).cpu().numpy()
@@ -242,6 +244,24 @@ def test_cholesky_step(dtype, n, tol):
     Lg = np.tril(np64(L))
     assert np.abs(Lg - Lr).max() / np.abs(Lr).max() <= tol
     assert (np.diag(Lg) > 0).all()
+
+
+@pytest.mark.parametrize("n,bad,value,status", [(1024, 700, -1.0, 2), (1024, 1023, 0.0, 2),
+                                                (600, 31, float("nan"), 4), (300, 0, -2.0, 2)])
+def test_cholesky_failure_anywhere(n, bad, value, status):
+    # every CTA of the factorisation must see the failure and stop (no wait runs out)
+    A = wl.gaussian(n, 2 * n, seed=43, device=dev(), dtype=torch.float64)
+    W = (A @ A.T + torch.eye(n, device=dev(), dtype=torch.float64)).float()
+    W[bad, :bad] = 0.0
+    W[bad, bad] = value
+    with pytest.raises(DfsError) as e:
+        dfs.dfs_cholesky(W)
+    assert e.value.status == status
+    assert f"pivot {bad}" in str(e.value)
+    # the handle stays usable afterwards
+    W2 = (A @ A.T + torch.eye(n, device=dev(), dtype=torch.float64)).float()
+    L, piv = dfs.dfs_cholesky(W2)
+    assert piv == -1 and torch.isfinite(L).all()
 
 
 def test_cholesky_reports_failed_pivot():
@@ -272,8 +292,13 @@ def test_trsm_step(dtype, tol, trans):
 
 @pytest.mark.parametrize("dtype,n,m,k", [
     (torch.float32, 150, 12345, 3), (torch.bfloat16, 150, 12345, 3), (torch.float64, 150, 12345, 3),
-    (torch.float32, 1024, 40000, 8),   # TMA ring with 32-byte strips
-    (torch.float32, 2500, 9001, 4),    # n beyond the shared-memory ring: LDG kernel
+    (torch.float32, 1024, 40000, 8),   # RHS beyond the cluster form's 4 per pass: classic kernel
+    (torch.float32, 1024, 40001, 1),   # clusters of 2 CTAs x 512 rows, ragged last strip
+    (torch.float32, 1100, 20003, 2),   # clusters of 3 (column split 22/21/21)
+    (torch.float32, 2500, 9001, 4),    # clusters of 5
+    (torch.float32, 4096, 5000, 1),    # clusters of 8 (the largest)
+    (torch.float32, 4097, 3001, 1),    # beyond the cluster form: re-read kernel
+    (torch.float32, 77, 100, 3),       # fewer strips than clusters
     (torch.bfloat16, 700, 70001, 1),
 ])
 def test_fisher_pass_step(dtype, n, m, k):
