@@ -1,19 +1,21 @@
 #!/usr/bin/env python3
 """Throughput of the damped-Fisher Cholesky solve (arXiv 2310.17556, Algorithm 1) on GB300.
 
-Workload: one solve of (S^T S + lambda I) x = v at n = 1024 samples, m = 2^20 parameters, k = 1,
+Workload: solves of (S^T S + lambda I) x = v at n = 1024 samples, m = 2^20 parameters, k = 1,
 S stored in FP32 and SVD-structured (S = U diag(sigma) V^T / sqrt(n), U Haar, V orthonormal from
-the QR of a Gaussian, sigma log-spaced 1 .. 1e-3), v ~ N(0, 1), lambda = 1e-4 (and 1e-2 reported
+the QR of a Gaussian, sigma log-spaced 1 .. 1e-3), v ~ N(0, 1), lambda = 1e-4 (1e-2 reported
 beside it).  Synthetic data: the paper measures on no public dataset.
 
-A "step" is one complete dfs_solve: tensor-core Gram, Cholesky, the S v pass, the triangular
-solves and the refinement passes that write x (all of Algorithm 1), with S resident in HBM
-(4.3 GB, larger than L2, so no L2 flush is needed between steps).
+A "step" is one complete dfs_solve on the mixed path: the S v pass that also packs S into BF16
+tensor-core tiles, the tcgen05 Gram, the Cholesky, the triangular solves and the n-space
+refinement passes that write x (all of Algorithm 1), with S resident in HBM (4.3 GB, larger
+than L2, so no L2 flush is needed between steps).  The plain FP32 path is timed beside it, and
+every reported solution is compared with the FP64 oracle's on the full problem.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs under torchrun; every rank solves its own independent problem (weak scaling,
-no collective on the data path).  Prints one JSON line on rank 0.
+N > 1 runs under torchrun; every rank solves its own independent problem (weak scaling, no
+collective on the data path).  Prints one JSON line on rank 0.
 """
 
 from __future__ import annotations
@@ -21,7 +23,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -36,10 +37,10 @@ M_PARAMS = 1 << 20
 LAMBDA = 1e-4
 LAMBDA_ALT = 1e-2
 SIGMA_MIN = 1e-3
+SEED = 231017556 + 1
 METRIC = "damped-Fisher solves/s at n=1024,m=2^20 (mixed vs FP32 path, rel err≤1e-6)"
 UNIT = "solves/s"
-# TF32 dense tensor rate relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s per GPU)
-TF32_OVER_BF16 = 1.1 / 2.25
+PRECISION = "bf16"
 
 
 def workload_config(lam=LAMBDA):
@@ -47,7 +48,8 @@ def workload_config(lam=LAMBDA):
         "workload": f"SVD-structured FP32 score matrix n={N_SAMPLES} m={M_PARAMS} k=1 lambda={lam:g} "
                     f"(sigma log-spaced 1..{SIGMA_MIN:g})",
         "n": N_SAMPLES, "m": M_PARAMS, "k": 1, "lambda": lam,
-        "mixed_path": "TF32 tcgen05 Gram + n-space refinement to est. err <= 1e-7",
+        "mixed_path": "BF16 tcgen05 Gram on packed tiles, FP32 Cholesky, n-space refinement "
+                      "(FP32 passes over S with FP64 accumulation) to est. rel. error <= 1e-7",
         "cache": "inputs larger than L2 (S is 4.3 GB; L2 is 129 MB), no flush between steps",
         "parallelism": "replicas (one independent solve per GPU)",
     }
@@ -106,14 +108,14 @@ def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 def _kernel_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, or None if the kernel changed since."""
+    """DRAM bytes per full-size launch from the committed ncu summary, or None when the kernel's
+    sources changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "roofline_counters.json")
     try:
         with open(p) as f:
@@ -125,8 +127,11 @@ def _kernel_traffic(kernel: str):
         return None
     h = hashlib.sha256()
     for rel in ent.get("sources", []):
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        except OSError:
+            return None
     if h.hexdigest() != ent.get("sha256"):
         return None
     return ent.get("dram_bytes_per_launch")
@@ -138,34 +143,35 @@ def _make_inputs(torch, wl, dev, seed):
     del U, V
     v = wl.rhs(M_PARAMS, 1, seed=seed + 7, device=dev)
     torch.cuda.synchronize()
-    return S, v, float(s[0])
+    return S, v
 
 
-def _residual_bound(torch, S, v, x, lam, smax):
-    """FP64 residual of Eq. 1 and the error bound it gives: e_rel <= cond(A) * res with
-    cond(A) = (sigma_max^2 + lambda) / lambda (A = S^T S + lambda I)."""
-    Sd = S.double()
-    xd = x.double().reshape(-1)
-    r = Sd.T @ (Sd @ xd) + lam * xd - v.double().reshape(-1)
-    res = float(torch.linalg.norm(r) / torch.linalg.norm(v.double()))
-    del Sd
-    cond = (smax * smax + lam) / lam
-    return res, cond * res
+def _timed(torch, stream, fn, steps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
 
 
-# ----------------------------------------------------------------------------- CPU (oracle) arm
+# ----------------------------------------------------------------------------- oracle (CPU) side
 
 
-def _oracle_sample_solves_per_s(S_np, v_np, lam, m_sample):
-    """Time the FP64 oracle on the first m_sample columns; scale to the full m (cost ~ n^2 m)."""
+def _oracle_solve(S64, v64, lam):
     import oracle
 
-    Ss = S_np[:, :m_sample]
-    vs = v_np[:m_sample]
     t0 = time.perf_counter()
-    oracle.solve(Ss, vs, lam)
-    dt = time.perf_counter() - t0
-    return (1.0 / dt) * (m_sample / M_PARAMS), dt
+    x = oracle.solve(S64, v64, lam)
+    return x, time.perf_counter() - t0
+
+
+def _errors(S64, v64, lam, x, x_ref):
+    import oracle
+
+    e = oracle.errors(S64, v64, lam, x, x_ref)
+    return {k: float(v) for k, v in e.items()}
 
 
 def _host_inputs(seed):
@@ -173,47 +179,40 @@ def _host_inputs(seed):
 
     from paper_2310_17556_gb300 import workloads as wl
 
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    m_gen = M_PARAMS
-    S, v, smax = _make_inputs(torch, wl, dev, seed) if dev == "cuda" else (None, None, None)
-    if S is None:  # no GPU: generate a reduced sample directly on the host
-        m_gen = 1 << 17
-        S, _, s, _ = wl.svd_structured(N_SAMPLES, m_gen, seed=seed, sigma_min=SIGMA_MIN)
-        v = wl.rhs(m_gen, 1, seed=seed + 7)
-    return S.cpu().double().numpy(), v.cpu().double().numpy()[0], m_gen
-
-
-def cpu_baseline(S_np, v_np, target_s=12.0):
-    """The oracle (FP64 numpy, all host cores) on a bounded column sample of the workload."""
-    m_avail = S_np.shape[1]
-    m_s = min(1 << 14, m_avail)
-    rate, dt = _oracle_sample_solves_per_s(S_np, v_np, LAMBDA, m_s)
-    while dt * 2 < target_s and m_s * 2 <= m_avail and m_s < (1 << 18):
-        m_s *= 2
-        rate, dt = _oracle_sample_solves_per_s(S_np, v_np, LAMBDA, m_s)
-    return {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 oracle (numpy, {os.cpu_count()} threads) on the first {m_s} of {M_PARAMS} columns "
-                      f"(n={N_SAMPLES}, k=1) in {dt:.2f} s, scaled by {m_s}/{M_PARAMS} (cost linear in m)"}
+    if torch.cuda.is_available():
+        S, v = _make_inputs(torch, wl, "cuda", seed)
+        m_avail = M_PARAMS
+    else:  # no GPU: a reduced problem generated on the host
+        m_avail = 1 << 17
+        S, _, _, _ = wl.svd_structured(N_SAMPLES, m_avail, seed=seed, sigma_min=SIGMA_MIN)
+        v = wl.rhs(m_avail, 1, seed=seed + 7)
+    return S.cpu().double().numpy(), v.cpu().double().numpy()[0], m_avail
 
 
 def run_reference(args):
+    """The FP64 oracle (numpy, host cores) as the reference arm, on a bounded column sample of the
+    workload per step (cost is linear in m), scaled to the full m."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    S_np, v_np, m_avail = _host_inputs(231017556 + 1)
-    # size the per-step sample so that warmup + steps take a few minutes at most
+    import oracle
+
+    S_np, v_np, m_avail = _host_inputs(SEED)
+
+    def sample(m_s):
+        t0 = time.perf_counter()
+        oracle.solve(S_np[:, :m_s], v_np[:m_s], LAMBDA)
+        return time.perf_counter() - t0
+
     m_s = min(1 << 14, m_avail)
-    _, dt = _oracle_sample_solves_per_s(S_np, v_np, LAMBDA, m_s)
+    dt = sample(m_s)
     budget = 150.0 / max(1, args.steps + args.warmup)
-    while dt * 2 < budget and m_s * 2 <= m_avail and m_s < (1 << 18):
+    while dt * 2 < budget and m_s * 2 <= m_avail:
         m_s *= 2
-        _, dt = _oracle_sample_solves_per_s(S_np, v_np, LAMBDA, m_s)
+        dt = sample(m_s)
     for _ in range(args.warmup):
-        _oracle_sample_solves_per_s(S_np, v_np, LAMBDA, m_s)
-    times = []
-    for _ in range(args.steps):
-        _, dt = _oracle_sample_solves_per_s(S_np, v_np, LAMBDA, m_s)
-        times.append(dt)
+        sample(m_s)
+    times = [sample(m_s) for _ in range(args.steps)]
     per_full = statistics.mean(times) * (M_PARAMS / m_s)
     value = 1.0 / per_full
     line = {
@@ -222,7 +221,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"each step: FP64 oracle on the first {m_s} of {M_PARAMS} columns, "
-                                   f"scaled by {m_s}/{M_PARAMS}"},
+                                   f"scaled by {m_s}/{M_PARAMS} (cost linear in m)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -259,32 +258,29 @@ def run_ours(args):
     import paper_2310_17556_gb300 as dfs
     from paper_2310_17556_gb300 import workloads as wl
 
-    S, v, smax = _make_inputs(torch, wl, dev, 231017556 + 1 + rank)
+    S, v = _make_inputs(torch, wl, dev, SEED + rank)
+    n, m = S.shape
     X = torch.empty_like(v)
     stream = torch.cuda.current_stream()
-    h = dfs.default_handle()
 
-    # ---------------- mixed path (headline) ----------------
+    def solve(lam=LAMBDA, prec=PRECISION, out=X, timing=False):
+        dfs.dfs_solve(S, v, lam, X=out, precision=prec, sync=False, timing=timing)
+
+    # ---------------- mixed path (headline), per-kernel CUDA events inside the timed region ----
     for _ in range(args.warmup):
-        dfs.dfs_solve(S, v, LAMBDA, X=X, precision="tf32", sync=False)
+        solve()
     info = dfs.dfs_sync_info()
     if info["status"] != 0:
         raise RuntimeError(f"mixed solve failed: {info}")
-    dfs.dfs_step_times()  # reset the timing ring
+    dfs.dfs_step_times()  # reset the event ring
     clocks_proc = _clock_sampler(local)
     time.sleep(0.3)
     barrier()
     launches0 = dfs.dfs_kernel_launches()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        dfs.dfs_solve(S, v, LAMBDA, X=X, precision="tf32", sync=False, timing=True)
-    e1.record(stream)
+    elapsed_ms = _timed(torch, stream, lambda: solve(timing=True), args.steps)
     barrier()
     launches = dfs.dfs_kernel_launches() - launches0
     clocks = _clock_summary(clocks_proc)
-    elapsed_ms = e0.elapsed_time(e1)
     info = dfs.dfs_sync_info()
     step_ms, nsteps_timed = dfs.dfs_step_times()
     if dist is not None:
@@ -292,36 +288,21 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms = float(t.item())
     value = ws * args.steps / (elapsed_ms / 1e3)
-    res, err_bound = _residual_bound(torch, S, v, X, LAMBDA, smax)
+    X_mixed = X.clone()
 
-    # same solve at lambda = 1e-2 (fewer passes are needed there), a few steps
+    # ---------------- same workload at lambda = 1e-2 ----------------
     X2 = torch.empty_like(v)
-    dfs.dfs_solve(S, v, LAMBDA_ALT, X=X2, precision="tf32", sync=False)
-    torch.cuda.synchronize()
+    solve(LAMBDA_ALT, out=X2)
     k2 = max(3, args.steps // 4)
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(k2):
-        dfs.dfs_solve(S, v, LAMBDA_ALT, X=X2, precision="tf32", sync=False)
-    a1.record(stream)
-    torch.cuda.synchronize()
+    alt_ms = _timed(torch, stream, lambda: solve(LAMBDA_ALT, out=X2), k2)
     info_alt = dfs.dfs_sync_info()
-    alt_value = k2 / (a0.elapsed_time(a1) / 1e3)
-    res_alt, bound_alt = _residual_bound(torch, S, v, X2, LAMBDA_ALT, smax)
 
-    # ---------------- plain FP32 path (comparison) ----------------
+    # ---------------- plain FP32 path ----------------
     Xf = torch.empty_like(v)
-    dfs.dfs_solve(S, v, LAMBDA, X=Xf, precision="fp32", sync=False)
-    torch.cuda.synchronize()
+    solve(prec="fp32", out=Xf)
     kf = max(3, args.steps // 10)
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(kf):
-        dfs.dfs_solve(S, v, LAMBDA, X=Xf, precision="fp32", sync=False)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    fp32_value = kf / (f0.elapsed_time(f1) / 1e3)
-    res_f, bound_f = _residual_bound(torch, S, v, Xf, LAMBDA, smax)
+    fp32_ms = _timed(torch, stream, lambda: solve(prec="fp32", out=Xf), kf)
+    info_f = dfs.dfs_sync_info()
 
     # ---------------- end to end through the host-memory entry point ----------------
     S_h = torch.empty(S.shape, dtype=S.dtype, pin_memory=True)
@@ -331,12 +312,12 @@ def run_ours(args):
     X_h = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
     del S
     torch.cuda.empty_cache()
-    dfs.dfs_solve_host(S_h, v_h, LAMBDA, X=X_h, precision="tf32")
+    dfs.dfs_solve_host(S_h, v_h, LAMBDA, X=X_h, precision=PRECISION)
     ke = max(3, args.steps // 10)
     barrier()
     t0 = time.perf_counter()
     for _ in range(ke):
-        dfs.dfs_solve_host(S_h, v_h, LAMBDA, X=X_h, precision="tf32")
+        dfs.dfs_solve_host(S_h, v_h, LAMBDA, X=X_h, precision=PRECISION)
     barrier()
     e2e_s = time.perf_counter() - t0
     if dist is not None:
@@ -345,45 +326,70 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e_value = ws * ke / e2e_s
 
-    # ---------------- roofline of the dominant kernel (tensor-core Gram) ----------------
+    # ---------------- rooflines from the live per-kernel events ----------------
     peaks, peak_kind = _peaks()
-    gram_ms = step_ms[0]
-    flops = float(N_SAMPLES) * (N_SAMPLES + 1) * M_PARAMS  # lower triangle incl. diagonal, 2 flop/MAC
-    peak_tf = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-    achieved_tf = flops / (gram_ms / 1e3) / 1e12 if gram_ms > 0 else None
-    roofline = {
-        "kernel": "gram_tc_kernel<TF32>", "bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
-        "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
-        "traffic": _kernel_traffic("gram_tc_kernel<TF32>"),
-        "peak_source": f"{peak_kind} bf16_tflops_sustained x {TF32_OVER_BF16:.3f} (TF32/BF16 nominal)",
-        "algorithmic_flop_per_launch": flops, "avg_launch_ms": gram_ms, "launches_averaged": nsteps_timed,
-        "hbm_alt": {"bytes_per_launch": 4.0 * N_SAMPLES * M_PARAMS,
-                    "achieved_gbs": 4.0 * N_SAMPLES * M_PARAMS / (gram_ms / 1e3) / 1e9 if gram_ms > 0 else None,
-                    "peak_gbs": peaks["hbm_gbs"]},
-    }
+    hbm = peaks["hbm_gbs"]
+    bf16_sus = peaks["bf16_tflops_sustained"]
+    gram_ms, svp_ms, pass_ms, chol_ms = step_ms[0], step_ms[5], step_ms[6], step_ms[7]
+    n_pad = -(-n // 128) * 128
+    m_pad = -(-m // 64) * 64
+    pass_bytes = 4.0 * n * m + 8.0 * m            # S, v read; x written (first refinement pass)
+    svp_bytes = 4.0 * n * m + 4.0 * m + 2.0 * n_pad * m_pad  # S, v read; BF16 tiles written
+    gram_flop = float(n) * (n + 1) * m            # lower triangle incl. diagonal, 2 flop / MAC
+    passes = max(1, info["iters"])
+
+    def hbm_line(name, nbytes, ms, launches_per_step):
+        ach = nbytes / (ms / 1e3) / 1e9 if ms > 0 else None
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm if ach else None, "traffic": _kernel_traffic(name),
+                "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": ms,
+                "launches_per_step": launches_per_step, "ms_per_step": ms * launches_per_step}
+
+    pass_line = hbm_line("fisher_pass_cluster_kernel", pass_bytes, pass_ms, passes)
+    svp_line = hbm_line("sv_pack_kernel", svp_bytes, svp_ms, 1)
+    gram_tf = gram_flop / (gram_ms / 1e3) / 1e12 if gram_ms > 0 else None
+    gram_line = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": gram_tf, "peak": bf16_sus,
+                 "unit": "TFLOP/s", "frac": gram_tf / bf16_sus if gram_tf else None,
+                 "traffic": _kernel_traffic("gram_tc_kernel"), "algorithmic_flop_per_launch": gram_flop,
+                 "avg_launch_ms": gram_ms, "launches_per_step": 1, "ms_per_step": gram_ms}
+    kernels = [pass_line, gram_line, svp_line]
+    roofline = dict(max(kernels, key=lambda d: d["ms_per_step"]))
+    roofline["peak_source"] = f"{peak_kind} MEASURED_PEAKS ({'hbm_gbs' if roofline['bound'] == 'hbm' else 'bf16_tflops_sustained'})"
+    roofline["launches_averaged"] = nsteps_timed
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "tf32", "data": "synthetic", "config": workload_config(),
-        "accuracy": {"res_fp64": res, "e_rel_bound": err_bound, "iters": info["iters"],
-                     "est_err": info["rel_correction"], "status": info["status"]},
+        "dtype": "bf16", "data": "synthetic", "config": workload_config(),
         "step_ms": {"gram": step_ms[0], "finalize_cholesky": step_ms[1], "first_solve": step_ms[2],
-                    "refinement": step_ms[3], "total": step_ms[4]},
-        "fp32_path": {"value": fp32_value, "unit": UNIT, "res_fp64": res_f, "e_rel_bound": bound_f,
-                      "steps": kf},
-        "lambda_1e-2": {"value": alt_value, "unit": UNIT, "res_fp64": res_alt, "e_rel_bound": bound_alt,
-                        "iters": info_alt["iters"], "steps": k2},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N_SAMPLES * M_PARAMS + 4 * M_PARAMS,
-                "d2h_bytes_per_step": 4 * M_PARAMS, "steps": ke, "api": "dfs_solve_host (pinned host S, v, x)"},
+                    "refinement": step_ms[3], "total": step_ms[4], "sv_pack_kernel": step_ms[5],
+                    "first_refinement_pass_kernel": step_ms[6], "cholesky_kernel": step_ms[7]},
+        "fp32_path": {"value": kf / (fp32_ms / 1e3), "unit": UNIT, "steps": kf, "status": info_f["status"]},
+        "lambda_1e-2": {"value": k2 / (alt_ms / 1e3), "unit": UNIT, "iters": info_alt["iters"], "steps": k2},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * m + 4 * m,
+                "d2h_bytes_per_step": 4 * m, "steps": ke, "api": "dfs_solve_host (pinned host S, v, x)"},
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roofline,
+        "kernels": kernels,
+        "mixed_info": {"iters": info["iters"], "est_rel_err": info["rel_correction"], "status": info["status"]},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        S_np = S_h[:, : 1 << 18].double().numpy()
-        v_np = v_h[0, : 1 << 18].double().numpy()
-        line["cpu_baseline"] = cpu_baseline(S_np, v_np)
+        # the FP64 oracle on the full problem: accuracy of every reported solution, and its own
+        # time on the host cores as the CPU baseline
+        S64 = S_h.double().numpy()
+        v64 = v_h[0].double().numpy()
+        x_ref, t_ref = _oracle_solve(S64, v64, LAMBDA)
+        acc = {"mixed": _errors(S64, v64, LAMBDA, X_mixed.cpu().double().numpy()[0], x_ref),
+               "fp32_path": _errors(S64, v64, LAMBDA, Xf.cpu().double().numpy()[0], x_ref)}
+        x_ref2, _ = _oracle_solve(S64, v64, LAMBDA_ALT)
+        acc["mixed_lambda_1e-2"] = _errors(S64, v64, LAMBDA_ALT, X2.cpu().double().numpy()[0], x_ref2)
+        line["accuracy_vs_fp64_oracle"] = acc
+        line["accuracy_ok"] = acc["mixed"]["e_rel"] <= 1e-6 and acc["fp32_path"]["e_rel"] <= 1e-5
+        line["cpu_baseline"] = {"value": 1.0 / t_ref, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"one full FP64 oracle solve of this workload (n={n}, m={m}, k=1, "
+                                          f"lambda={LAMBDA:g}) in {t_ref:.2f} s, numpy with its default "
+                                          f"BLAS threads on {os.cpu_count()} host cores"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -392,14 +398,40 @@ def run_ours(args):
     return 0
 
 
+def run_profile_solve(args):
+    """One small BF16 solve for an ncu capture (--profile-solve M): Gaussian S of 1024 x M
+    (seed 1), v seed 2, lambda 1e-4, after --warmup solves.  Prints the device status."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2310_17556_gb300 as dfs
+    from paper_2310_17556_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    S = wl.gaussian(N_SAMPLES, args.profile_solve, seed=1, device="cuda")
+    v = wl.rhs(args.profile_solve, 1, seed=2, device="cuda")
+    X = torch.empty_like(v)
+    for _ in range(args.warmup + 1):
+        dfs.dfs_solve(S, v, LAMBDA, X=X, precision=PRECISION, sync=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": {"n": N_SAMPLES, "m": args.profile_solve, **dfs.dfs_sync_info()}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", type=int, default=0, metavar="M",
+                    help="run one small solve (n=1024, m=M) after --warmup solves, for ncu captures")
     args = ap.parse_args()
+    if args.profile_solve:
+        return run_profile_solve(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -43,7 +43,7 @@ extern "C" {
 typedef enum {
     DFS_OK = 0,
     DFS_ERR_INVALID_ARG = 1,   /* rejected before launch */
-    DFS_ERR_NOT_SPD = 2,       /* a Cholesky pivot was <= 0 or NaN (Algorithm 1 step 2) */
+    DFS_ERR_NOT_SPD = 2,       /* a Cholesky pivot was <= 0 or NaN (the Cholesky of Algorithm 1) */
     DFS_ERR_NOT_CONVERGED = 3, /* refinement stopped above tolerance; X holds the last iterate */
     DFS_ERR_NONFINITE = 4,     /* NaN/Inf met in W or in the solution */
     DFS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
@@ -58,7 +58,7 @@ typedef enum {
     DFS_BF16 = 2   /* bfloat16 (S only) */
 } dfs_dtype;
 
-/* Arithmetic of the Gram step W = S S^T (Algorithm 1 step 1), the O(n^2 m) contraction. */
+/* Arithmetic of the Gram step W = S S^T (the Gram of Algorithm 1), the O(n^2 m) contraction. */
 typedef enum {
     DFS_PREC_AUTO = 0,   /* FP64 for FP64 S; BF16 tensor Gram + refinement otherwise */
     DFS_PREC_FP64 = 1,   /* FP64 everywhere (S must be FP64) */
@@ -67,6 +67,9 @@ typedef enum {
     DFS_PREC_TF32 = 4,   /* tcgen05 TF32 Gram (FP32 accumulate) + n-space refinement */
     DFS_PREC_BF16X3 = 5  /* tcgen05 split-BF16 (hi/lo, three products) Gram + refinement */
 } dfs_precision;
+
+/* entries of dfs_info.ms and of dfs_step_times' output */
+#define DFS_STEP_TIMES 8
 
 /* dfs_options.flags */
 #define DFS_FLAG_STEP_TIMING 1  /* record CUDA events around the steps; dfs_info.ms is filled */
@@ -89,10 +92,12 @@ typedef struct {
     int failed_pivot;       /* first non-positive pivot index, -1 if none */
     double rel_correction;  /* estimated relative error left in x (0 if no refinement) */
     double rel_residual_n;  /* last ||r_n|| / ||S v||, r_n = S v - (S S^T + lambda I) y */
-    float ms[5];            /* with DFS_FLAG_STEP_TIMING: [0] Gram kernel, [1] Gram finalize +
-                               Cholesky, [2] first n-space solve (S v pass, two triangular
-                               solves), [3] the rest (refinement or the x pass), [4] whole call;
-                               zeros otherwise */
+    float ms[DFS_STEP_TIMES]; /* with DFS_FLAG_STEP_TIMING (CUDA events on the call's stream):
+                               [0] Gram kernel, [1] Gram finalize + Cholesky, [2] first n-space
+                               solve (S v pass, two triangular solves), [3] the rest (refinement
+                               or the x pass), [4] whole call, [5] S v pass kernel alone, [6] first
+                               pass over S after the solves (refinement or x pass) alone,
+                               [7] Cholesky kernel alone; zeros otherwise */
 } dfs_info;
 
 typedef struct dfs_handle_s* dfs_handle;
@@ -163,14 +168,14 @@ dfs_status dfs_solve_batched(dfs_handle handle, const dfs_problem* problems, int
 
 /* ---- single steps of Algorithm 1 (for composition and testing) ---------------------- */
 
-/* Step 1: W = S S^T + lambda I~, lower triangle only, written to W (device, n x n, ldw).
+/* Gram: W = S S^T + lambda I~, lower triangle only, written to W (device, n x n, ldw).
  * W is FP64 for precision FP64, FP32 otherwise.  precision FP32 = FFMA; BF16/TF32/BF16X3
  * run the tcgen05 tensor-core kernel (lambda is added in FP32 after the contraction). */
 dfs_status dfs_gram(dfs_handle handle, const void* S, int s_dtype, int64_t n, int64_t m,
                     int64_t lds, double lambda, int precision, void* W, int64_t ldw,
                     void* stream);
 
-/* Step 2: in-place lower Cholesky W = L L^T (device, n x n, ldw, w_dtype FP32 or FP64).
+/* Cholesky: in-place lower factor W = L L^T (device, n x n, ldw, w_dtype FP32 or FP64).
  * Blocked right-looking; each 32 x 32 diagonal block is factored in FP64.  Synchronizes
  * `stream`.  Returns NOT_SPD (and *failed_pivot, may be NULL) on a pivot <= 0 or NaN. */
 dfs_status dfs_cholesky(dfs_handle handle, void* W, int w_dtype, int64_t n, int64_t ldw,
@@ -184,7 +189,7 @@ dfs_status dfs_trsm(dfs_handle handle, const void* L, int l_dtype, int64_t n, in
 
 /* The streaming pass over S (one read of S), with Y (device, n x k FP64, ldy):
  *   U = V - S^T Y           (Y == NULL means Y = 0)
- *   X = U / lambda          (if X != NULL; Algorithm 1 step 4 with Q inlined)
+ *   X = U / lambda          (if X != NULL; Algorithm 1's update of x with Q inlined)
  *   R = S U - lambda Y      (if R != NULL; device n x k FP64, ldr: the n-space residual
  *                            S v - (S S^T + lambda I~) y of Appendix A's identity)
  * V, X as in dfs_solve. */

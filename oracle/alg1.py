@@ -54,7 +54,7 @@ __all__ = [
 class NotPositiveDefinite(ValueError):
     """Raised when a Cholesky pivot is not strictly positive.
 
-    Algorithm 1 step 2 assumes W is symmetric positive definite (true for any
+    Algorithm 1's Cholesky assumes W is symmetric positive definite (true for any
     lambda > 0 in exact arithmetic, Appendix A).  A non-positive pivot in
     floating point is reported, never repaired.
     """
@@ -82,7 +82,7 @@ def _as_columns(v: np.ndarray, m: int) -> tuple[np.ndarray, bool]:
 
 
 def gram(S, lam: float) -> np.ndarray:
-    """Algorithm 1 step 1: W = S S^T + lambda I~, with I~ the n x n identity.
+    """Algorithm 1, Gram: W = S S^T + lambda I~, with I~ the n x n identity.
 
     Returns the full symmetric n x n FP64 matrix.
     """
@@ -94,7 +94,7 @@ def gram(S, lam: float) -> np.ndarray:
 
 
 def cholesky_lower(W) -> np.ndarray:
-    """Algorithm 1 step 2: L = Chol(W), W = L L^T, L lower with a positive diagonal.
+    """Algorithm 1, Cholesky: L = Chol(W), W = L L^T, L lower with a positive diagonal.
 
     Column-by-column (Cholesky-Crout) recurrence, read from the lower
     triangle of W only:
@@ -156,13 +156,13 @@ def solve_steps(S, V, lam: float) -> dict:
     """Algorithm 1 with Q inlined, evaluated right to left; returns every intermediate.
 
     Steps (Algorithm 1 and the Section 2 remark on inlining Q):
-        W = S S^T + lambda I~          (step 1)
-        L = Chol(W)                     (step 2)
+        W = S S^T + lambda I~          (Gram)
+        L = Chol(W)                     (Cholesky)
         b = S v                         (rightmost product of S^T L^{-T} L^{-1} S v)
         a = L^{-1} b                    (forward triangular solve)
         y = L^{-T} a                    (backward triangular solve)
         z = S^T y                       (= Q^T Q v)
-        x = (v - z) / lambda            (step 4)
+        x = (v - z) / lambda            (update of x)
     Keys: W, L, b, a, y, z, x.  V (and x) have shape (m,) or (m, k).
     """
     lam = float(lam)

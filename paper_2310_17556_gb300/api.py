@@ -147,9 +147,10 @@ def dfs_sync_info(handle: Handle | None = None, stream=None) -> dict:
 
 
 def dfs_step_times(handle: Handle | None = None) -> tuple[list[float], int]:
-    """Mean [gram, finalize+cholesky, first solve, rest, total] ms over recent timed solves."""
+    """Mean step times (ms) over recent timed solves: [gram, finalize+cholesky, first solve, rest,
+    total, S v pass kernel, first refinement/x pass kernel, Cholesky kernel]."""
     h = handle or default_handle()
-    out = (C.c_float * 5)()
+    out = (C.c_float * _lib.DFS_STEP_TIMES)()
     cnt = C.c_int(0)
     _check(h.lib, h.h, h.lib.dfs_step_times(h.h, out, C.byref(cnt)))
     return [float(x) for x in out], int(cnt.value)
@@ -199,7 +200,7 @@ def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float
 
 def dfs_gram(S: torch.Tensor, lam: float, precision="auto", W: torch.Tensor | None = None,
              handle: Handle | None = None, stream=None) -> torch.Tensor:
-    """Algorithm 1 step 1: lower triangle of W = S S^T + lam I (upper triangle untouched)."""
+    """Algorithm 1, Gram: lower triangle of W = S S^T + lam I (upper triangle untouched)."""
     h = handle or default_handle(S.device.index)
     n, m = S.shape
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -213,7 +214,7 @@ def dfs_gram(S: torch.Tensor, lam: float, precision="auto", W: torch.Tensor | No
 
 
 def dfs_cholesky(W: torch.Tensor, handle: Handle | None = None, stream=None) -> tuple[torch.Tensor, int]:
-    """Algorithm 1 step 2, in place on the lower triangle of W; returns (L, failed_pivot or -1)."""
+    """Algorithm 1's Cholesky, in place on the lower triangle of W; returns (L, failed_pivot or -1)."""
     h = handle or default_handle(W.device.index)
     n = W.shape[0]
     piv = C.c_int64(-1)

@@ -35,7 +35,7 @@ struct dfs_handle_s {
     // Marks: 0 start, 1 Gram kernel start, 2 Gram kernel end, 3 Cholesky end, 4 first n-space
     // solve end, 5 end of the call.
     static constexpr int kTimingSlots = 64;
-    static constexpr int kMarks = 6;
+    static constexpr int kMarks = 11;
     cudaEvent_t ev[kTimingSlots][kMarks] = {};
     int tslot = 0;      // slot of the last timed solve
     int tpending = 0;   // timed solves not yet summarised by dfs_step_times
@@ -227,7 +227,7 @@ dfs_status check_lambda(dfs_handle h, double lambda) {
     return DFS_OK;
 }
 
-// Step 1 into W (rows < n_out, stride ldw): Gram + lambda on the diagonal (identity padding).
+// The Gram into W (rows < n_out, stride ldw): Gram + lambda on the diagonal (identity padding).
 // The tensor-core Gram on packed tiles first runs the S v pass in packing mode (with no V).
 dfs_status run_gram(dfs_handle h, const Plan& p, const void* S, int64_t lds, double lambda, void* W, int64_t ldw,
                     int64_t n_out, cudaStream_t stream) {
@@ -247,7 +247,9 @@ dfs_status run_gram(dfs_handle h, const Plan& p, const void* S, int64_t lds, dou
     return DFS_OK;
 }
 
-// dfs_info.ms layout from the six marks of one solve.
+// dfs_info.ms layout from the marks of one solve: 0 start, 1/2 around the Gram kernel, 3 after
+// the Cholesky, 4 after the first triangular solves, 5 end, 6/7 around the S v pass, 8/9 around
+// the first pass over S after the solves, 10 before the Cholesky kernel.
 void step_ms(cudaEvent_t* e, float* ms) {
     float t[5];
     for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], e[i], e[i + 1]);
@@ -256,6 +258,9 @@ void step_ms(cudaEvent_t* e, float* ms) {
     ms[2] = t[0] + t[3];  // S v pass (with tile packing) + first triangular solves
     ms[3] = t[4];         // refinement passes (or the x pass)
     cudaEventElapsedTime(&ms[4], e[0], e[5]);
+    cudaEventElapsedTime(&ms[5], e[6], e[7]);   // S v pass kernel
+    cudaEventElapsedTime(&ms[6], e[8], e[9]);   // first refinement (or x) pass kernel
+    cudaEventElapsedTime(&ms[7], e[10], e[3]);  // Cholesky kernel
 }
 
 dfs_status fill_info(dfs_handle h, cudaStream_t stream, dfs_info* info) {
@@ -269,7 +274,7 @@ dfs_status fill_info(dfs_handle h, cudaStream_t stream, dfs_info* info) {
         info->failed_pivot = ds.failed_pivot;
         info->rel_correction = ds.rel_correction;
         info->rel_residual_n = ds.rel_residual;
-        for (int i = 0; i < 5; ++i) info->ms[i] = 0.0f;
+        for (int i = 0; i < DFS_STEP_TIMES; ++i) info->ms[i] = 0.0f;
         if (h->timed) step_ms(h->ev[h->tslot], info->ms);
     }
     if (ds.status != 0) {
@@ -356,8 +361,10 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         void* Xg = static_cast<char*>(X) + q0 * ldx * vs;
         DFS_CK(launch_group_reset(h->dstat, stream));
         // b = S v; the first group's pass also writes the packed tensor-core tiles of S
+        if (q0 == 0) DFS_CK(mark(6));
         DFS_CK(launch_sv_pack(p.pp, s_dtype, kq, q0 == 0 ? p.pack : 0, S, ni, m, lds, Vg, ldv, kg, Rpart, Sp,
                               h->dstat, stream));
+        if (q0 == 0) DFS_CK(mark(7));
         DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.sv_grid, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z, nullptr,
                                   nullptr, h->dstat, 0, stream));
         if (q0 == 0) {
@@ -374,6 +381,7 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
             else
                 DFS_CK(launch_gram_finalize(p.f64, p.f64, gram_simt_tile(p.f64), P, p.nsplit, p.n, p.n_pad, lambda,
                                             W, p.n_pad, stream));
+            DFS_CK(mark(10));
             DFS_CK(launch_cholesky(p.f64, W, p.n_pad, p.n_pad, Linv, at<int>(h, p.off_Cf), h->dstat, stream,
                                    fp64_panel));
             DFS_CK(mark(3));
@@ -383,15 +391,20 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
         DFS_CK(launch_refine_init(p.f64, Z, npi, kq, Y, R, bn2, h->dstat, stream));
         if (q0 == 0) DFS_CK(mark(4));
+        const bool mark_pass = (q0 == 0);
         if (!p.tensor) {
             // x = (v - S^T y) / lambda
+            if (mark_pass) DFS_CK(mark(8));
             DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr,
                                U2part, 0, h->dstat, 0, stream));
+            if (mark_pass) DFS_CK(mark(9));
         } else {
             for (int it = 1; it <= max_iter; ++it) {
                 // x_0 = v / lambda for the first pass; afterwards x_{j-1} is read from X itself
+                if (mark_pass && it == 1) DFS_CK(mark(8));
                 DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, Rpart,
                                    U2part, it == 1 ? 2 : 1, h->dstat, 1, stream));
+                if (mark_pass && it == 1) DFS_CK(mark(9));
                 DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.nparts, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z, U2part,
                                           U2, h->dstat, 1, stream));
                 DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
@@ -399,9 +412,12 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                 DFS_CK(launch_refine_control(p.f64, Z, R, npi, kq, kg, Y, U2, bn2, lambda, tol, it, max_iter,
                                              h->dstat, stream));
             }
-            if (max_iter == 0)
+            if (max_iter == 0) {
+                if (mark_pass) DFS_CK(mark(8));
                 DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr,
                                    U2part, 0, h->dstat, 0, stream));
+                if (mark_pass) DFS_CK(mark(9));
+            }
         }
     }
     DFS_CK(mark(5));
@@ -546,18 +562,18 @@ dfs_status dfs_step_times(dfs_handle h, float* mean_ms, int* count) {
     if (!h || !mean_ms) return DFS_ERR_INVALID_ARG;
     cudaSetDevice(h->device);
     const int nsl = h->tpending;
-    for (int i = 0; i < 5; ++i) mean_ms[i] = 0.0f;
+    for (int i = 0; i < DFS_STEP_TIMES; ++i) mean_ms[i] = 0.0f;
     if (count) *count = nsl;
     if (nsl == 0) return DFS_OK;
-    DFS_CK(cudaEventSynchronize(h->ev[h->tslot][dfs_handle_s::kMarks - 1]));
-    double acc[5] = {0, 0, 0, 0, 0};
+    DFS_CK(cudaEventSynchronize(h->ev[h->tslot][5]));
+    double acc[DFS_STEP_TIMES] = {};
     for (int j = 0; j < nsl; ++j) {
         const int sl = (h->tslot - j + dfs_handle_s::kTimingSlots) % dfs_handle_s::kTimingSlots;
-        float ms[5];
+        float ms[DFS_STEP_TIMES];
         step_ms(h->ev[sl], ms);
-        for (int i = 0; i < 5; ++i) acc[i] += ms[i];
+        for (int i = 0; i < DFS_STEP_TIMES; ++i) acc[i] += ms[i];
     }
-    for (int i = 0; i < 5; ++i) mean_ms[i] = (float)(acc[i] / nsl);
+    for (int i = 0; i < DFS_STEP_TIMES; ++i) mean_ms[i] = (float)(acc[i] / nsl);
     h->tpending = 0;
     return DFS_OK;
 }

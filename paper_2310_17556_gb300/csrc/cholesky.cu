@@ -1,4 +1,4 @@
-// Algorithm 1 step 2: L = Chol(W), W = L L^T, L lower triangular with a positive diagonal.
+// Algorithm 1, Cholesky: L = Chol(W), W = L L^T, L lower triangular with a positive diagonal.
 //
 // Blocked right-looking factorisation of the padded n_pad x n_pad matrix W (row-major, lower
 // triangle) in NB x NB tiles, as ONE persistent cooperative kernel (one CTA per SM, every CTA

@@ -1,6 +1,6 @@
-// Algorithm 1 step 1 on the SIMT pipes: W = S S^T (lower triangle), FP32 FFMA or FP64 DFMA.
+// Algorithm 1's Gram on the SIMT pipes: W = S S^T (lower triangle), FP32 FFMA or FP64 DFMA.
 //
-// This is the plain-precision Gram of arXiv 2310.17556, Algorithm 1 step 1 (the O(n^2 m)
+// This is the plain-precision Gram of arXiv 2310.17556, Algorithm 1's Gram (the O(n^2 m)
 // contraction that Section 2 names as the dominant cost).  S is n x m row-major, so both
 // operands of S S^T are K-major (K = m contiguous).  The lower triangle is cut into BM x BM
 // tiles (I >= J) and the contraction dimension m into `nsplit` chunks; each CTA computes one

@@ -1,4 +1,4 @@
-// Algorithm 1 step 1 on the 5th-generation tensor cores: W = S S^T (lower triangle), the O(n^2 m)
+// Algorithm 1's Gram W = S S^T on the 5th-generation tensor cores: W = S S^T (lower triangle), the O(n^2 m)
 // contraction that Section 2 of arXiv 2310.17556 names as the dominant cost.
 //
 // Work decomposition.  S (n x m, row-major, K = m contiguous) is cut into T = ceil(n/128) row

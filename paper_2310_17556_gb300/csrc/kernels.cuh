@@ -5,7 +5,7 @@
 
 namespace dfs {
 
-// ---- step 1, SIMT Gram (gram_simt.cu) ----
+// ---- Gram, SIMT (gram_simt.cu) ----
 int gram_simt_tile(int acc_f64);
 void gram_simt_plan(int64_t n, int64_t m, int acc_f64, int num_sms, int* nsplit, int64_t* chunk);
 size_t gram_simt_partial_bytes(int64_t n, int acc_f64, int nsplit);
@@ -14,7 +14,7 @@ cudaError_t launch_gram_simt(int s_dtype, int acc_f64, const void* S, int64_t n,
 cudaError_t launch_gram_finalize(int acc_f64, int w_f64, int BM, const void* P, int nsplit, int64_t n,
                                  int64_t n_out, double lambda, void* W, int64_t ldw, cudaStream_t stream);
 
-// ---- step 1, tcgen05 tensor-core Gram (gram_tc.cu) ----
+// ---- Gram, tcgen05 tensor cores (gram_tc.cu) ----
 // kind: 0 = BF16 MMA, 1 = TF32 MMA.
 struct GramTcPlan {
     int kind;
@@ -33,7 +33,7 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
 cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64_t n, int64_t n_out, double lambda,
                                     void* W, int64_t ldw, cudaStream_t stream);
 
-// ---- step 2, Cholesky (cholesky.cu) ----
+// ---- Cholesky (cholesky.cu) ----
 // fp64_panel: factor the 32 x 32 diagonal blocks in FP64 (else in the storage type).
 // flags: cholesky_flag_bytes(n_pad) of device scratch (zeroed by the launcher).
 size_t cholesky_flag_bytes(int64_t n_pad);

@@ -4,7 +4,7 @@
 //                                                 S^T L^{-T} L^{-1} S v), optionally writing S
 //                                                 again as packed tensor-core tiles (below)
 //   fisher_pass_kernel   U = V - S^T Y           (S^T y, the leftmost product)
-//                        X = U / lambda          (Algorithm 1 step 4)
+//                        X = U / lambda          (Algorithm 1's update of x)
 //                        R = S U - lambda Y      (= S v - (S S^T + lambda I~) y, Appendix A's
 //                                                 identity; the refinement residual)
 //

@@ -3,7 +3,7 @@
 // Algorithm 1 solves the n x n system (S S^T + lambda I~) y = S v (Appendix A) with the factor
 // of W = S S^T + lambda I~.  When W is formed in low precision (W~ = W + E), y_0 = W~^{-1} S v
 // is refined with the exact operator:  r = S v - (S S^T + lambda I~) y = S (v - S^T y) - lambda y
-// (one pass over S, pass.cu), dy = W~^{-1} r (trsv.cu), y += dy.  The x of Algorithm 1 step 4,
+// (one pass over S, pass.cu), dy = W~^{-1} r (trsv.cu), y += dy.  The x of Algorithm 1's update,
 // x_j = (v - S^T y_j) / lambda, is written by the same pass, which also measures exactly how
 // much x moved:  delta_j = ||x_j - x_{j-1}|| / ||x_j||  (x_0 = v / lambda, i.e. y = 0).
 // With linear convergence at rate rho_j = delta_j / delta_{j-1}, the error left in x_j is about

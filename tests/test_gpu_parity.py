@@ -344,3 +344,32 @@ def test_zero_score_matrix_gives_v_over_lambda():
     V = wl.rhs(1000, 1, seed=71, device=dev())
     X, info = dfs.dfs_solve(S, V, 0.125, precision="fp32")
     assert torch.equal(X, V / 0.125)
+
+
+# ---------------------------------------------------------------------------- full size
+
+
+def test_full_size_headline_workload_matches_oracle():
+    """The benchmark's workload (n=1024, m=2^20, SVD-structured FP32 S, lambda=1e-4), in the launch
+    configuration bench.py times: the BF16 mixed path and the plain FP32 path against one full
+    FP64 oracle solve on the host (the metric's bar: rel. error <= 1e-6 mixed, <= 1e-5 FP32)."""
+    n, m, lam = 1024, 1 << 20, 1e-4
+    S, U, s, V = wl.svd_structured(n, m, seed=231017556 + 1, sigma_min=1e-3, device=dev(),
+                                   dtype=torch.float32, factor_dtype=torch.float64)
+    del U, V
+    v = wl.rhs(m, 1, seed=231017556 + 8, device=dev())
+    Xm, info = dfs.dfs_solve(S, v, lam, precision="bf16")
+    assert info["status"] == 0 and info["iters"] >= 1
+    Xf, info_f = dfs.dfs_solve(S, v, lam, precision="fp32")
+    assert info_f["status"] == 0
+    S64 = np64(S)
+    v64 = np64(v)[0]
+    del S
+    torch.cuda.empty_cache()
+    x_ref = oracle.solve(S64, v64, lam)
+    em = oracle.errors(S64, v64, lam, np64(Xm)[0], x_ref)
+    ef = oracle.errors(S64, v64, lam, np64(Xf)[0], x_ref)
+    assert em["e_rel"] <= 1e-6, em
+    assert ef["e_rel"] <= 1e-5, ef
+    # the error inside the row space of S, where Algorithm 1's S^T y part lives
+    assert em["e_range"] <= 1e-5, em
