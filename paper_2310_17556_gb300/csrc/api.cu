@@ -84,6 +84,7 @@ struct Plan {
     PassPlan pp{};
     int pgrid = 1;  // rows of the pass partial buffers
     int pack = 0;   // tile packing done by the first S v pass: 0 none, 1 BF16, 2 TF32
+    bool ns = false;  // n-space steps as one cluster kernel (nspace.cu)
     size_t off_W = 0, off_Linv = 0, off_P = 0, off_Rpart = 0, off_U2part = 0, off_R = 0, off_Z = 0, off_Y = 0,
            off_U2 = 0, off_V = 0, off_bn2 = 0, off_Sp = 0, off_Cf = 0, total = 0;
 };
@@ -160,6 +161,7 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     p->pp = pass_make_plan((int)n, kq, s_dtype, h->num_sms, m, h->smem_optin);
     p->pgrid = pass_partial_rows(p->pp);
     p->pack = (p->tensor && p->tc.packed) ? (p->tc.kind == 1 ? 2 : 1) : 0;
+    p->ns = nspace_slots((int)p->n_pad, kq, (int)es, h->smem_optin) >= 2;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -365,8 +367,9 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         DFS_CK(launch_sv_pack(p.pp, s_dtype, kq, q0 == 0 ? p.pack : 0, S, ni, m, lds, Vg, ldv, kg, Rpart, Sp,
                               h->dstat, stream));
         if (q0 == 0) DFS_CK(mark(7));
-        DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.sv_grid, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z, nullptr,
-                                  nullptr, h->dstat, 0, stream));
+        if (!p.ns)
+            DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.sv_grid, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z,
+                                      nullptr, nullptr, h->dstat, 0, stream));
         if (q0 == 0) {
             // Algorithm 1 steps 1-2: W = S S^T + lambda I~ and its Cholesky factor
             void* P = at<void>(h, p.off_P);
@@ -386,9 +389,15 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                                    fp64_panel));
             DFS_CK(mark(3));
         }
-        // y0 = W^{-1} b by the two triangular solves
-        DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
-        DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
+        // y0 = W^{-1} b by the two triangular solves (with the reduction of b = S v folded in)
+        if (p.ns) {
+            DFS_CK(launch_nspace(p.f64, kq, W, p.n_pad, npi, Linv, NS_MODE_REDUCE | NS_MODE_FWD | NS_MODE_BWD, Rpart,
+                                 p.pp.sv_grid, ni, kg, nullptr, lambda, nullptr, 0, R, Z, kq, nullptr, nullptr,
+                                 h->smem_optin, h->dstat, 0, stream));
+        } else {
+            DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
+            DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));
+        }
         DFS_CK(launch_refine_init(p.f64, Z, npi, kq, Y, R, bn2, h->dstat, stream));
         if (q0 == 0) DFS_CK(mark(4));
         const bool mark_pass = (q0 == 0);
@@ -405,10 +414,17 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                 DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, Rpart,
                                    U2part, it == 1 ? 2 : 1, h->dstat, 1, stream));
                 if (mark_pass && it == 1) DFS_CK(mark(9));
-                DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.nparts, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z, U2part,
-                                          U2, h->dstat, 1, stream));
-                DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
-                DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
+                if (p.ns) {
+                    DFS_CK(launch_nspace(p.f64, kq, W, p.n_pad, npi, Linv,
+                                         NS_MODE_REDUCE | NS_MODE_LAMBDA_Y | NS_MODE_FWD | NS_MODE_BWD, Rpart,
+                                         p.pp.nparts, ni, kg, Y, lambda, nullptr, 0, R, Z, kq, U2part, U2,
+                                         h->smem_optin, h->dstat, 1, stream));
+                } else {
+                    DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.nparts, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z,
+                                              U2part, U2, h->dstat, 1, stream));
+                    DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
+                    DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
+                }
                 DFS_CK(launch_refine_control(p.f64, Z, R, npi, kq, kg, Y, U2, bn2, lambda, tol, it, max_iter,
                                              h->dstat, stream));
             }
@@ -661,7 +677,12 @@ dfs_status dfs_trsm(dfs_handle h, const void* L, int l_dtype, int64_t n, int64_t
         const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
         void* Bg = static_cast<char*>(B) + q0 * es;
         DFS_CK(launch_copy_rhs_in(f64, Bg, ldb, n, kg, Bp, kq, n_pad, stream));
-        DFS_CK(launch_trsv(f64, trans, Lp, n_pad, (int)n_pad, Linv, Bp, kq, kg, kq, h->dstat, 0, stream));
+        if (nspace_slots((int)n_pad, kq, (int)es, h->smem_optin) >= 2)
+            DFS_CK(launch_nspace(f64, kq, Lp, n_pad, (int)n_pad, Linv, trans ? NS_MODE_BWD : NS_MODE_FWD, nullptr, 0,
+                                 (int)n, kg, nullptr, 0.0, Bp, kq, nullptr, Bp, kq, nullptr, nullptr, h->smem_optin,
+                                 h->dstat, 0, stream));
+        else
+            DFS_CK(launch_trsv(f64, trans, Lp, n_pad, (int)n_pad, Linv, Bp, kq, kg, kq, h->dstat, 0, stream));
         DFS_CK(launch_copy_rhs_out(f64, Bp, kq, n, kg, Bg, ldb, stream));
     }
     return fill_info(h, stream, nullptr);

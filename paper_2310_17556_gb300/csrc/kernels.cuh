@@ -42,6 +42,17 @@ cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void*
 cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
                                 cudaStream_t stream);
 
+// ---- n-space step: reduction of the pass partials + both triangular solves (nspace.cu) ----
+constexpr int NS_MODE_REDUCE = 1;    // right-hand side = sum of Rpart (else read from B)
+constexpr int NS_MODE_LAMBDA_Y = 2;  // subtract lambda Y
+constexpr int NS_MODE_FWD = 4;       // L a = r
+constexpr int NS_MODE_BWD = 8;       // L^T z = a
+int nspace_slots(int n_pad, int KQ, int elem, size_t smem_limit);  // >= 2 when the kernel applies
+cudaError_t launch_nspace(int f64, int kq, const void* W, int64_t ld, int n_pad, const void* Linv, int mode,
+                          const double* Rpart, int nparts, int n, int k, const double* Y, double lambda, const void* B,
+                          int64_t ldb, double* R, void* Z, int64_t ldz, const double* U2part, double* U2,
+                          size_t smem_limit, DevStatus* st, int honor_stop, cudaStream_t stream);
+
 // ---- triangular solves (trsv.cu) ----
 size_t trsv_smem_bytes(int n_pad, int KQ, int elem, int nst);
 cudaError_t launch_mirror_lower(int f64, void* L, int64_t ld, int n_pad, cudaStream_t stream);

@@ -540,8 +540,9 @@ PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size
     int64_t g = (int64_t)num_sms * per_sm;
     if (g > nstrips) g = nstrips;
     p.grid = (int)(g < 1 ? 1 : g);
-    // the S v pass keeps only the row sums in shared memory: up to four CTAs per SM
-    int64_t gs = (int64_t)num_sms * 4;
+    // the S v pass: one wave of one CTA per SM (its 512 threads x 80 registers fill an SM), so
+    // that the n-space step has num_sms partial rows to add
+    int64_t gs = (int64_t)num_sms;
     if (gs > nstrips) gs = nstrips;
     p.sv_grid = (int)(gs < 1 ? 1 : gs);
     // FP32 S with n <= 4096: clusters sharing 256-byte-wide strips (pass_cluster.cu)
