@@ -1,35 +1,38 @@
-// Algorithm 1's Gram W = S S^T on the 5th-generation tensor cores: W = S S^T (lower triangle), the O(n^2 m)
+// Algorithm 1's Gram W = S S^T on the 5th-generation tensor cores (lower triangle), the O(n^2 m)
 // contraction that Section 2 of arXiv 2310.17556 names as the dominant cost.
 //
 // Work decomposition.  S (n x m, row-major, K = m contiguous) is cut into T = ceil(n/128) row
-// blocks.  The lower triangle of W (T(T+1)/2 tiles of 128 x 128) is covered exactly once by
-//   pairs   (I; J0, J0+1): one tcgen05.mma with M = 128, N = 256, A = block I, B = blocks J0, J0+1
-//   singles (I; I):        M = 128, N = 128, for the diagonal tiles no pair covers.
-// For even I the "diagonal pair" (I; I, I+1) computes tile (I, I) and tile (I, I+1), which is
-// the transpose of the lower tile (I+1, I) (W is symmetric), so no tile is computed twice:
-//   even row I: pairs J0 = 0, 2, ..., I (the last one diagonal; a single if I is the last row)
-//   odd row I:  pairs J0 = 0, 2, ..., I-3, then the single (I; I)   [(I, I-1) came transposed].
-// Each unit is split into `c` (singles) or `2c` (pairs) tasks of equal cost; task `slot` of a
-// unit with `g` tasks takes the k-blocks slot, slot+g, slot+2g, ...  Tasks are dealt round-robin
-// to a persistent grid of one CTA per SM.  Because every task advances through m at the same
-// cost per k-block position, all CTAs of a round read the same few k-blocks at any moment: S
-// is fetched from DRAM about once per round and the other reads hit L2.  Each task writes one
-// FP32 partial block; gram_tc_finalize sums the tasks of each tile in a fixed order (FP64),
-// transposes where needed and adds lambda.
+// blocks, paired into T2 = ceil(T/2) super-rows.  The lower triangle of W is covered exactly once by
+// "quad units" (I2; J2), J2 <= I2, each two tcgen05.mma chains that share their B operand:
+//   off-diagonal (J2 < I2):  A0 = block 2 I2,   A1 = block 2 I2 + 1,   B = blocks 2 J2, 2 J2 + 1
+//                            D0 = A0 B^T (M = 128, N = 256),  D1 = A1 B^T (M = 128, N = 256)
+//   diagonal (J2 = I2):      the same blocks, but D0 = A0 A0^T (N = 128: the tile (2 I2, 2 I2 + 1)
+//                            is above the diagonal) and B is read from the A tiles themselves.
+// A super-row with a single block (odd T) drops A1.  One k-step stages A0, A1, B0, B1 (64 KB, or
+// 32 KB on the diagonal) for 8.4 MFLOP: 131 flop per staged byte, 1.5x the single-product unit,
+// which is what bounds this kernel (operand supply from L2, not the tensor pipe).
+// A unit of cost c_u (128 x 128 tile products per k-step: 4 off-diagonal, 3 diagonal, fewer
+// without A1) is split into c c_u tasks; task `slot` of a unit with g tasks takes the k-blocks
+// slot, slot + g, slot + 2g, ..., so every task costs the same and all CTAs advance through m at
+// the same rate (the tiles of a few k-blocks are live in L2 at any time).  Tasks are dealt
+// round-robin, in groups of consecutive tasks of one unit, to a persistent grid of at most one CTA
+// per SM.  A group's tasks keep separate FP32 accumulation chains (at most 1024 k-blocks each) and
+// are added in task order into one FP32 partial block (256 x 256: rows 0..127 from A0, 128..255
+// from A1); gram_tc_finalize sums the groups of each tile in a fixed order and adds lambda.
+// (The finalize reads only the quadrants a unit computes.)
 //
 // Per CTA (192 threads, warp-specialised):
-//   warp 0     TMA producer: per 128-byte k-block, one 128-row box of A and one (single) or two
-//              (pair) of B land in a 4-stage ring of 48 KB stages (128-byte swizzle).
-//   warp 1     MMA issuer: 4 MMAs (K = 32 bytes each) per stage into a 128 x 256 (or 128) FP32
-//              accumulator in TMEM (two accumulators, 512 columns, so the epilogue of one task
-//              overlaps the MMAs of the next); tcgen05.commit releases stages and accumulators.
+//   warp 0     producer: per 128-byte k-block, the unit's 128-row tiles land in a 3-stage ring of
+//              64 KB stages (bulk copies of the packed tiles, or TMA boxes of S, 128-byte swizzle).
+//   warp 1     MMA issuer: per stage 4 + 4 MMAs (K = 32 bytes each) into two 128 x 256 FP32
+//              accumulators in TMEM (all 512 columns); tcgen05.commit releases stages and, at the
+//              end of a task, the accumulators.
 //   warps 2-5  epilogue: tcgen05.ld 32 columns at a time (each warp its 32-lane quarter),
 //              16-byte stores of the partial block.
 // Every mbarrier wait is bounded (2 s of wall time); a timeout sets DFS_ERR_TIMEOUT, makes the
 // other roles stop, waits for TMA copies and MMAs in flight and frees TMEM before returning.
 //
-// Kinds: TF32 MMA directly on FP32 S (the tensor core takes the top 19 bits of each value),
-// and BF16 MMA on BF16-stored S.
+// Kinds: BF16 MMA (kind::f16) on BF16 tiles, TF32 MMA (kind::tf32) on FP32 / TF32 tiles.
 #include <cudaTypedefs.h>
 
 #include <cstring>
@@ -47,18 +50,18 @@ namespace {
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
 constexpr int TC_ROW_BYTES = 128;
-constexpr int TC_STAGES = 4;
-constexpr int TC_A_BYTES = TC_BM * TC_ROW_BYTES;
-constexpr int TC_B_BYTES = TC_BN * TC_ROW_BYTES;
-constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_STAGES = 3;
+constexpr int TC_TILE_BYTES = TC_BM * TC_ROW_BYTES;  // one 128-row tile of one k-block
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;    // A0, A1, B0, B1
+constexpr int TC_PART = 2 * TC_BM * TC_BN;            // floats per partial block
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 
 struct TcSmem {
     uint64_t full[TC_STAGES];
     uint64_t empty[TC_STAGES];
-    uint64_t accf[2];
-    uint64_t acce[2];
+    uint64_t accf;
+    uint64_t acce;
     uint64_t done;
     uint32_t tmem_base;
     int abort;
@@ -67,73 +70,59 @@ struct TcSmem {
 
 constexpr size_t TC_SMEM_BYTES = 1024 + (size_t)TC_STAGES * TC_STAGE_BYTES + sizeof(TcSmem);
 
-// Warp roles: warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 epilogue.
+// Warp roles: warp 0 producer, warp 1 MMA issuer, warps 2-5 epilogue.
 constexpr int TC_THREADS = 192;
 constexpr int kMmaWarp = 1;
 
-
 }  // namespace
 
-// Units per row I of the unit enumeration (see the header comment).
-__host__ __device__ __forceinline__ int tc_row_pairs(int I, int T) {
-    return (I & 1) ? (I - 1) / 2 : I / 2 + ((I + 1 < T) ? 1 : 0);
+// Units (I2, J2), J2 <= I2 < T2, in row-major order: unit u = I2 (I2 + 1) / 2 + J2.
+__host__ __device__ __forceinline__ void tc_unit_ij(int u, int& I2, int& J2) {
+    int i = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= u) ++i;
+    while (i * (i + 1) / 2 > u) --i;
+    I2 = i;
+    J2 = u - i * (i + 1) / 2;
 }
-__host__ __device__ __forceinline__ int tc_row_single(int I, int T) { return ((I & 1) || I + 1 >= T) ? 1 : 0; }
-
-// Pairs come first (row by row, J0 ascending), then singles (row by row).
-__host__ __device__ inline void tc_unit_ij(int u, int T, int& I, int& J0, int& wide) {
-    int before = 0;
-    for (int i = 0; i < T; ++i) {
-        const int c = tc_row_pairs(i, T);
-        if (u < before + c) {
-            I = i;
-            J0 = 2 * (u - before);
-            wide = 1;
-            return;
-        }
-        before += c;
-    }
-    for (int i = 0; i < T; ++i) {
-        const int c = tc_row_single(i, T);
-        if (u < before + c) {
-            I = i;
-            J0 = i;
-            wide = 0;
-            return;
-        }
-        before += c;
-    }
-    I = J0 = wide = 0;
+// 128 x 128 tile products per k-step of unit (I2, J2)
+__host__ __device__ __forceinline__ int tc_unit_cost(int I2, int J2, int T) {
+    const bool a1 = 2 * I2 + 1 < T;
+    if (J2 < I2) return a1 ? 4 : 2;
+    return a1 ? 3 : 1;
 }
 
-__host__ __device__ inline void tc_counts(int T, int& P, int& Sg) {
-    P = 0;
-    Sg = 0;
-    for (int i = 0; i < T; ++i) {
-        P += tc_row_pairs(i, T);
-        Sg += tc_row_single(i, T);
-    }
-}
-
-// Task t -> unit, slot and stride (pairs have 2c tasks each, singles c).
 struct TcTask {
-    int I, J0, wide, slot, stride;
+    int I2, J2, slot, stride;
 };
-__host__ __device__ inline TcTask tc_task(int t, int T, int c, int P) {
-    TcTask k;
-    int u;
-    if (t < 2 * c * P) {
-        u = t / (2 * c);
-        k.slot = t % (2 * c);
-        k.stride = 2 * c;
-    } else {
-        const int t2 = t - 2 * c * P;
-        u = P + t2 / c;
-        k.slot = t2 % c;
-        k.stride = c;
+// Task t -> unit, slot and stride (unit u has c * cost(u) tasks, numbered consecutively).
+__host__ __device__ inline TcTask tc_task(int t, int T, int c) {
+    const int T2 = (T + 1) / 2;
+    const int U = T2 * (T2 + 1) / 2;
+    TcTask k{0, 0, 0, 1};
+    int before = 0;
+    for (int u = 0; u < U; ++u) {
+        int I2, J2;
+        tc_unit_ij(u, I2, J2);
+        const int g = c * tc_unit_cost(I2, J2, T);
+        if (t < before + g) {
+            k.I2 = I2;
+            k.J2 = J2;
+            k.slot = t - before;
+            k.stride = g;
+            return k;
+        }
+        before += g;
     }
-    tc_unit_ij(u, T, k.I, k.J0, k.wide);
     return k;
+}
+__host__ __device__ inline int tc_unit_first_task(int u, int T, int c) {
+    int before = 0;
+    for (int v = 0; v < u; ++v) {
+        int I2, J2;
+        tc_unit_ij(v, I2, J2);
+        before += c * tc_unit_cost(I2, J2, T);
+    }
+    return before;
 }
 
 __host__ __device__ __forceinline__ int tc_task_nk(const TcTask& k, int64_t nkb) {
@@ -145,8 +134,8 @@ __host__ __device__ __forceinline__ int tc_task_nk(const TcTask& k, int64_t nkb)
 // used when S has short rows and no tile copy was made).
 template <int KIND, int PACKED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ Sp, int T, int c, int P,
-               int ntasks, int64_t nkb, int row_elems, float* __restrict__ part, DevStatus* st) {
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ Sp, int T, int c,
+               int ntasks, int G, int64_t nkb, int row_elems, float* __restrict__ part, DevStatus* st) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* stage_mem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -158,10 +147,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
             tc::mbar_init(&sm->full[s], 1);
             tc::mbar_init(&sm->empty[s], 1);
         }
-        for (int a = 0; a < 2; ++a) {
-            tc::mbar_init(&sm->accf[a], 1);
-            tc::mbar_init(&sm->acce[a], 128);
-        }
+        tc::mbar_init(&sm->accf, 1);
+        tc::mbar_init(&sm->acce, 128);
         tc::mbar_init(&sm->done, 1);
         sm->abort = 0;
         sm->never = 0;
@@ -185,29 +172,40 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
             bool issued[TC_STAGES];
             for (int s = 0; s < TC_STAGES; ++s) issued[s] = false;
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < ntasks; t += gridDim.x) {
-                const TcTask tk = tc_task(t, T, c, P);
+            const int ngroups = ntasks / G;
+            for (int t = 0, gi = blockIdx.x; ok && gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
+                const TcTask tk = tc_task(gi * G + t, T, c);
                 const int nk = tc_task_nk(tk, nkb);
+                const int i0 = 2 * tk.I2, j0 = 2 * tk.J2;
+                const bool a1 = i0 + 1 < T, diag = tk.J2 == tk.I2;
+                // tiles: A0, A1 (if any), and for off-diagonal units B0, B1
+                const uint32_t bytes = (uint32_t)TC_TILE_BYTES * ((a1 ? 2u : 1u) + (diag ? 0u : 2u));
                 for (int kt = 0; kt < nk; ++kt) {
                     if (!tc::mbar_wait_bounded(&sm->empty[stage], phase ^ 1u, abort, TC_WAIT_NS)) {
                         ok = false;
                         break;
                     }
                     unsigned char* a = stage_mem + stage * TC_STAGE_BYTES;
-                    unsigned char* b = a + TC_A_BYTES;
-                    tc::mbar_arrive_expect_tx(&sm->full[stage], tk.wide ? TC_STAGE_BYTES : 2 * TC_A_BYTES);
+                    unsigned char* b = a + 2 * TC_TILE_BYTES;
+                    tc::mbar_arrive_expect_tx(&sm->full[stage], bytes);
                     const int64_t kb = tk.slot + (int64_t)kt * tk.stride;
                     if (PACKED) {
-                        tc::bulk_load(a, Sp + (((int64_t)tk.I * nkb + kb) << 14), TC_A_BYTES, &sm->full[stage]);
-                        tc::bulk_load(b, Sp + (((int64_t)tk.J0 * nkb + kb) << 14), TC_A_BYTES, &sm->full[stage]);
-                        if (tk.wide)
-                            tc::bulk_load(b + TC_A_BYTES, Sp + (((int64_t)(tk.J0 + 1) * nkb + kb) << 14), TC_A_BYTES,
+                        tc::bulk_load(a, Sp + ((kb * T + i0) << 14), TC_TILE_BYTES, &sm->full[stage]);
+                        if (a1) tc::bulk_load(a + TC_TILE_BYTES, Sp + ((kb * T + i0 + 1) << 14), TC_TILE_BYTES,
+                                              &sm->full[stage]);
+                        if (!diag) {
+                            tc::bulk_load(b, Sp + ((kb * T + j0) << 14), TC_TILE_BYTES, &sm->full[stage]);
+                            tc::bulk_load(b + TC_TILE_BYTES, Sp + ((kb * T + j0 + 1) << 14), TC_TILE_BYTES,
                                           &sm->full[stage]);
+                        }
                     } else {
                         const int32_t x = (int32_t)(kb * row_elems);
-                        tc::tma_load_2d(a, &tmap, x, tk.I * TC_BM, &sm->full[stage]);
-                        tc::tma_load_2d(b, &tmap, x, tk.J0 * TC_BM, &sm->full[stage]);
-                        if (tk.wide) tc::tma_load_2d(b + TC_A_BYTES, &tmap, x, tk.J0 * TC_BM + TC_BM, &sm->full[stage]);
+                        tc::tma_load_2d(a, &tmap, x, i0 * TC_BM, &sm->full[stage]);
+                        if (a1) tc::tma_load_2d(a + TC_TILE_BYTES, &tmap, x, (i0 + 1) * TC_BM, &sm->full[stage]);
+                        if (!diag) {
+                            tc::tma_load_2d(b, &tmap, x, j0 * TC_BM, &sm->full[stage]);
+                            tc::tma_load_2d(b + TC_TILE_BYTES, &tmap, x, (j0 + 1) * TC_BM, &sm->full[stage]);
+                        }
                     }
                     issued[stage] = true;
                     last_parity[stage] = phase;
@@ -229,38 +227,45 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            constexpr uint32_t idesc_wide =
-                tc::instr_desc_f32acc(KIND == 1 ? tc::kFmtTF32 : tc::kFmtBF16, TC_BM, TC_BN);
-            constexpr uint32_t idesc_single =
-                tc::instr_desc_f32acc(KIND == 1 ? tc::kFmtTF32 : tc::kFmtBF16, TC_BM, TC_BM);
+            constexpr uint32_t fmt = KIND == 1 ? tc::kFmtTF32 : tc::kFmtBF16;
+            constexpr uint32_t idesc_wide = tc::instr_desc_f32acc(fmt, TC_BM, TC_BN);
+            constexpr uint32_t idesc_half = tc::instr_desc_f32acc(fmt, TC_BM, TC_BM);
             int stage = 0;
             uint32_t phase = 0;
-            int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < ntasks; t += gridDim.x) {
-                const TcTask tk = tc_task(t, T, c, P);
+            const int ngroups = ntasks / G;
+            for (int t = 0, gi = blockIdx.x; ok && gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
+                const TcTask tk = tc_task(gi * G + t, T, c);
                 const int nk = tc_task_nk(tk, nkb);
                 if (nk == 0) continue;  // the epilogue writes zeros for an empty task
-                const uint32_t idesc = tk.wide ? idesc_wide : idesc_single;
-                if (!tc::mbar_wait_bounded(&sm->acce[acc], acc_phase ^ 1u, abort, TC_WAIT_NS)) {
+                const bool a1 = 2 * tk.I2 + 1 < T, diag = tk.J2 == tk.I2;
+                // the accumulators are free once the epilogue has read the previous task's
+                if (!tc::mbar_wait_bounded(&sm->acce, acc_phase ^ 1u, abort, TC_WAIT_NS)) {
                     ok = false;
                     break;
                 }
+                acc_phase ^= 1u;
                 tc::fence_after_sync();
-                const uint32_t d = tmem + (uint32_t)(acc * TC_BN);
                 for (int kt = 0; kt < nk; ++kt) {
                     if (!tc::mbar_wait_bounded(&sm->full[stage], phase, abort, TC_WAIT_NS)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t a_addr = tc::smem_u32(stage_mem + stage * TC_STAGE_BYTES);
-                    const uint32_t b_addr = a_addr + TC_A_BYTES;
+                    const uint32_t a0 = tc::smem_u32(stage_mem + stage * TC_STAGE_BYTES);
+                    const uint32_t a1a = a0 + TC_TILE_BYTES;
+                    const uint32_t bb = diag ? a0 : a0 + 2 * TC_TILE_BYTES;  // diagonal: B = [A0 | A1]
 #pragma unroll
                     for (int kk = 0; kk < TC_ROW_BYTES / 32; ++kk)
-                        tc::mma_ss<KIND>(d, tc::sw128_kmajor_desc(a_addr + kk * 32),
-                                         tc::sw128_kmajor_desc(b_addr + kk * 32), idesc, (kt | kk) != 0);
+                        tc::mma_ss<KIND>(tmem, tc::sw128_kmajor_desc(a0 + kk * 32), tc::sw128_kmajor_desc(bb + kk * 32),
+                                         diag ? idesc_half : idesc_wide, (kt | kk) != 0);
+                    if (a1) {
+#pragma unroll
+                        for (int kk = 0; kk < TC_ROW_BYTES / 32; ++kk)
+                            tc::mma_ss<KIND>(tmem + (uint32_t)TC_BN, tc::sw128_kmajor_desc(a1a + kk * 32),
+                                             tc::sw128_kmajor_desc(bb + kk * 32), idesc_wide, (kt | kk) != 0);
+                    }
                     tc::mma_commit(&sm->empty[stage]);
                     if (++stage == TC_STAGES) {
                         stage = 0;
@@ -268,9 +273,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
                     }
                 }
                 if (!ok) break;
-                tc::mma_commit(&sm->accf[acc]);
-                acc ^= 1;
-                if (acc == 0) acc_phase ^= 1u;
+                tc::mma_commit(&sm->accf);
             }
             if (!ok) {
                 *abort = 1;
@@ -284,17 +287,24 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
         // ---------------- epilogue (the four warps after the MMA warp) ----------------
         const int q = warp & 3;  // TMEM lane quarter accessible to this warp
         const int row = q * 32 + lane;
-        int acc = 0;
         uint32_t acc_phase = 0;
-        for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
-            const TcTask tk = tc_task(t, T, c, P);
-            const int ncols = tk.wide ? TC_BN : TC_BM;
-            float* dst = part + (size_t)t * (TC_BM * TC_BN) + (size_t)row * TC_BN;
+        const int ngroups = ntasks / G;
+        for (int t = 0, gi = blockIdx.x; gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
+            const TcTask tk = tc_task(gi * G + t, T, c);
+            const bool a1 = 2 * tk.I2 + 1 < T, diag = tk.J2 == tk.I2;
+            // the group's tasks (separate FP32 accumulation chains) are added into one partial
+            // block in task order: the first stores, the others add (read-modify-write)
+            const bool first = (t == 0);
+            float* blk = part + (size_t)gi * TC_PART;
             if (tc_task_nk(tk, nkb) == 0) {
-                for (int j = 0; j < ncols; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (first)
+                    for (int h = 0; h < 2; ++h)
+                        for (int j = 0; j < TC_BN; j += 4)
+                            *reinterpret_cast<float4*>(blk + (size_t)(h * TC_BM + row) * TC_BN + j) =
+                                make_float4(0.f, 0.f, 0.f, 0.f);
                 continue;
             }
-            bool ok = tc::mbar_wait_bounded(&sm->accf[acc], acc_phase, abort, TC_WAIT_NS);
+            bool ok = tc::mbar_wait_bounded(&sm->accf, acc_phase, abort, TC_WAIT_NS);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) {
@@ -303,23 +313,35 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
                 }
                 break;
             }
+            acc_phase ^= 1u;
             tc::fence_after_sync();
-            const uint32_t tbase = tmem + (uint32_t)(acc * TC_BN) + ((uint32_t)(q * 32) << 16);
+            for (int h = 0; h < (a1 ? 2 : 1); ++h) {
+                const int ncols = (h == 0 && diag) ? TC_BM : TC_BN;
+                const uint32_t tbase = tmem + (uint32_t)(h * TC_BN) + ((uint32_t)(q * 32) << 16);
+                float* dst = blk + (size_t)(h * TC_BM + row) * TC_BN;
 #pragma unroll 1
-            for (int cc = 0; cc < ncols / 32; ++cc) {
-                uint32_t v[32];
-                tc::tmem_ld_32x32b_x32(tbase + (uint32_t)(cc * 32), v);
-                tc::tmem_ld_wait();
-                float4* d4 = reinterpret_cast<float4*>(dst + cc * 32);
+                for (int cc = 0; cc < ncols / 32; ++cc) {
+                    uint32_t v[32];
+                    tc::tmem_ld_32x32b_x32(tbase + (uint32_t)(cc * 32), v);
+                    tc::tmem_ld_wait();
+                    float4* d4 = reinterpret_cast<float4*>(dst + cc * 32);
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    d4[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                        __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+                    for (int j = 0; j < 8; ++j) {
+                        float4 o = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                               __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+                        if (!first) {
+                            const float4 p = d4[j];
+                            o.x += p.x;
+                            o.y += p.y;
+                            o.z += p.z;
+                            o.w += p.w;
+                        }
+                        d4[j] = o;
+                    }
+                }
             }
             tc::fence_before_sync();
-            tc::mbar_arrive(&sm->acce[acc]);
-            acc ^= 1;
-            if (acc == 0) acc_phase ^= 1u;
+            tc::mbar_arrive(&sm->acce);
         }
     }
     tc::fence_before_sync();
@@ -330,12 +352,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
     }
 }
 
-// W[gi][gj] (lower, rows < n_out) = sum over the tasks of the unit holding tile (I, J) (FP64, in
-// task order), plus lambda on the diagonal; rows/cols in [n, n_out) get the identity.  Tile
-// (I, I-1) for odd I is read transposed from the diagonal pair of row I-1.  One CTA per 8 rows
-// of a 128 x 128 tile; thread = (row, 4 consecutive columns).
+// W[gi][gj] (lower, rows < n_out) = sum over the task groups of the unit holding tile (I, J) (FP32,
+// in group order), plus lambda on the diagonal; rows/cols in [n, n_out) get the identity.  Tile (I, J)
+// is block (I mod 2, J mod 2) of unit (I / 2, J / 2).  One CTA per 8 rows of a 128 x 128 tile;
+// thread = (row, 4 consecutive columns).
 __global__ void __launch_bounds__(256)
-gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int P, int64_t n, int64_t n_out, double lambda,
+gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int G, int64_t n, int64_t n_out, double lambda,
                         float* __restrict__ W, int64_t ldw) {
     int I, J;
     {
@@ -350,53 +372,46 @@ gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int P, int
     const int c4 = (threadIdx.x & 31) * 4;
     const int64_t gi = (int64_t)I * TC_BM + r;
     if (gi >= n_out) return;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    // FP32 sum of the FP32 partial blocks in block order: each block already carries FP32
+    // accumulation error of a few 1e-6 to 1e-5, adding a handful of them in FP32 changes nothing
+    // measurable, and FP64 adds are too slow on GB300 to be worth it here
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (gi < n && I < T) {
-        // locate the unit, its first task and task count, the column offset, transposition
-        int unit, coff = 0;
-        bool transposed = false;
-        int pairs_before = 0;
-        for (int i = 0; i < I; ++i) pairs_before += tc_row_pairs(i, T);
-        if (J == I && !tc_row_single(I, T)) {
-            unit = pairs_before + I / 2;  // diagonal pair of an even row
-        } else if (J == I) {
-            int singles_before = 0;
-            for (int i = 0; i < I; ++i) singles_before += tc_row_single(i, T);
-            unit = P + singles_before;
-        } else if ((I & 1) && J == I - 1) {
-            int pb = 0;
-            for (int i = 0; i < I - 1; ++i) pb += tc_row_pairs(i, T);
-            unit = pb + (I - 1) / 2;  // diagonal pair of row I-1, second tile, transposed
-            coff = TC_BM;
-            transposed = true;
-        } else {
-            unit = pairs_before + J / 2;
-            coff = (J & 1) * TC_BM;
-        }
-        const int g = unit < P ? 2 * c : c;
-        const int t0 = unit < P ? unit * 2 * c : 2 * c * P + (unit - P) * c;
-        for (int q = 0; q < g; ++q) {
-            const float* blk = part + (size_t)(t0 + q) * TC_BM * TC_BN;
-            if (!transposed) {
-                const float4 x = __ldg(reinterpret_cast<const float4*>(blk + (size_t)r * TC_BN + coff + c4));
-                v[0] += x.x;
-                v[1] += x.y;
-                v[2] += x.z;
-                v[3] += x.w;
-            } else {
+        const int I2 = I / 2, J2 = J / 2;
+        const int u = I2 * (I2 + 1) / 2 + J2;
+        const int g = c * tc_unit_cost(I2, J2, T) / G;       // partial blocks (task groups) of the unit
+        const int b0 = tc_unit_first_task(u, T, c) / G;
+        const size_t off = (size_t)((I & 1) * TC_BM + r) * TC_BN + (J & 1) * TC_BM + c4;
+        const float* p0 = part + (size_t)b0 * TC_PART + off;
+        int q = 0;
+        for (; q + 4 <= g; q += 4) {  // four loads in flight, added in block order
+            float4 x[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) v[e] += __ldg(blk + (size_t)(c4 + e) * TC_BN + coff + r);
+            for (int e = 0; e < 4; ++e) x[e] = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)(q + e) * TC_PART));
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                v[0] += x[e].x;
+                v[1] += x[e].y;
+                v[2] += x[e].z;
+                v[3] += x[e].w;
             }
+        }
+        for (; q < g; ++q) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)q * TC_PART));
+            v[0] += x.x;
+            v[1] += x.y;
+            v[2] += x.z;
+            v[3] += x.w;
         }
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int64_t gj = (int64_t)J * TC_BM + c4 + e;
         if (gj > gi) continue;
-        double w;
-        if (gi >= n || gj >= n) w = (gi == gj) ? 1.0 : 0.0;
-        else w = v[e] + ((gi == gj) ? lambda : 0.0);
-        W[gi * ldw + gj] = (float)w;
+        float w;
+        if (gi >= n || gj >= n) w = (gi == gj) ? 1.f : 0.f;
+        else w = v[e] + ((gi == gj) ? (float)lambda : 0.f);
+        W[gi * ldw + gj] = w;
     }
 }
 
@@ -436,17 +451,24 @@ GramTcPlan gram_tc_plan(int s_dtype, int kind, int64_t n, int64_t m, int num_sms
     // rows >= 1 MiB too.
     p.packed = (s_dtype == DFS_F32) || ((int64_t)m * 2 >= (1 << 20));
     p.n_tiles = (int)ceil_div(n, TC_BM);
-    int P, Sg;
-    tc_counts(p.n_tiles, P, Sg);
-    p.npairs = P;
-    const int C = 2 * P + Sg;  // cost units (a pair costs two singles)
+    const int T = p.n_tiles, T2 = (T + 1) / 2;
+    p.npairs = T2 * (T2 + 1) / 2;  // quad units
+    int C = 0;                      // tile products per k-step over all units
+    for (int u = 0; u < p.npairs; ++u) {
+        int I2, J2;
+        tc_unit_ij(u, I2, J2);
+        C += tc_unit_cost(I2, J2, T);
+    }
     const int64_t nkb = ceil_div(m, tc_row_elems_kind(kind));
-    // Tasks per cost unit: the smallest c that fills the grid evenly (at most 16 partial blocks
-    // per tile and at least 32 k-blocks per task).
-    int best_c = 1;
+    // Tasks per cost unit: the smallest c that fills the grid evenly (at least 32 k-blocks per
+    // task).
+    // A task's FP32 accumulation chain (its k-blocks) is kept to at most 1024 k-blocks.
+    int c_min = 1;
+    while (c_min < 64 && nkb / c_min > 1024) c_min *= 2;
+    int best_c = c_min;
     double best = -1.0;
-    for (int c = 1; c <= 16; ++c) {
-        if (c > 1 && nkb / (2 * c) < 32) break;
+    for (int c = c_min; c <= 64; ++c) {
+        if (c > c_min && nkb / (4 * c) < 32) break;
         const double tasks = (double)c * C;
         const double eff = tasks / (std::ceil(tasks / num_sms) * num_sms);
         if (eff > best + 0.02) {
@@ -457,7 +479,10 @@ GramTcPlan gram_tc_plan(int s_dtype, int kind, int64_t n, int64_t m, int num_sms
     p.c = best_c;
     p.ntasks = best_c * C;
     p.nkb = nkb;
-    p.partial_bytes = (size_t)p.ntasks * TC_BM * TC_BN * sizeof(float);
+    // a CTA runs `group` consecutive tasks of one unit and adds them into one partial block (every
+    // unit has c * cost tasks, a multiple of the group)
+    p.group = (best_c % 4 == 0) ? 4 : ((best_c % 2 == 0) ? 2 : 1);
+    p.partial_bytes = (size_t)(p.ntasks / p.group) * TC_PART * sizeof(float);
     return p;
 }
 
@@ -486,7 +511,8 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = plan.ntasks < sms ? plan.ntasks : sms;
+    const int ngroups = plan.ntasks / plan.group;
+    const int grid = ngroups < sms ? ngroups : sms;
     const unsigned char* sp = static_cast<const unsigned char*>(Sp);
     float* part = static_cast<float*>(P);
 #define DFS_TC_LAUNCH(K, PK)                                                                                        \
@@ -494,7 +520,7 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
         auto kern = gram_tc_kernel<K, PK>;                                                                          \
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES); \
         if (e != cudaSuccess) return e;                                                                             \
-        kern<<<grid, TC_THREADS, TC_SMEM_BYTES, stream>>>(map, sp, plan.n_tiles, plan.c, plan.npairs, plan.ntasks,  \
+        kern<<<grid, TC_THREADS, TC_SMEM_BYTES, stream>>>(map, sp, plan.n_tiles, plan.c, plan.ntasks, plan.group,    \
                                                           plan.nkb, re, part, st);                                 \
         count_launch();                                                                                             \
     }
@@ -512,7 +538,7 @@ cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64
     const int T = (int)ceil_div(n_out, TC_BM);
     {
         gram_tc_finalize_kernel<<<dim3(T * (T + 1) / 2, TC_BM / 8), 256, 0, stream>>>(
-            static_cast<const float*>(P), plan.n_tiles, plan.c, plan.npairs, n, n_out, lambda,
+            static_cast<const float*>(P), plan.n_tiles, plan.c, plan.group, n, n_out, lambda,
             static_cast<float*>(W), ldw);
         count_launch();
     }

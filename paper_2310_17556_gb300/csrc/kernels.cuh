@@ -20,9 +20,10 @@ struct GramTcPlan {
     int kind;
     int packed;       // operands come from the packed tiles of the S v pass
     int n_tiles;      // T: 128-row blocks of S
-    int npairs;       // P: 128 x 256 units (singles follow)
-    int c;            // tasks per cost unit (pairs get 2c tasks, singles c)
-    int ntasks;       // c * (2P + singles): partial blocks written
+    int npairs;       // quad units (two 128-row blocks x two 128-column blocks)
+    int c;            // tasks per cost unit (a unit of cost k gets c k tasks)
+    int ntasks;       // tasks (k-split pieces of the units)
+    int group;        // tasks per CTA group; ntasks / group partial blocks (256 x 256 FP32)
     int64_t nkb;      // 128-byte k-blocks along m
     size_t partial_bytes;
 };

@@ -26,7 +26,9 @@
 // (one tensor-core k-block of a 128-row tile) as a contiguous 16 KB tile in the 128-byte-swizzled
 // K-major layout the tcgen05 Gram consumes: BF16 (round to nearest even) or TF32 (FP32 rounded to
 // nearest, ties away), or a plain re-layout of BF16 S.  Tiles of rows >= n and columns >= m
-// are zero.  Tile (I, kb) sits at byte offset (I * nkb + kb) * 16384.
+// are zero.  Tile (I, kb) sits at byte offset (kb * T + I) * 16384 (T = row tiles): the tiles of
+// one k-block are contiguous, so the Gram's working set (a few k-blocks, all row tiles) is one
+// contiguous region of L2.
 // Each CTA finally writes its FP64 row sums (and the two per-RHS sums) to partial buffers that
 // pass_reduce adds in a fixed order.
 #include "kernels.cuh"
@@ -129,7 +131,7 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
                 if constexpr (PACK != 0) {
                     if (i < n_rows) {
                         const int r = i & 127;
-                        unsigned char* tile = Sp + (((int64_t)(i >> 7) * nkb + s) << 14) + r * 128;
+                        unsigned char* tile = Sp + (((int64_t)s * (n_rows >> 7) + (i >> 7)) << 14) + r * 128;
                         if constexpr (PACK == 1 && sizeof(TS) == 4) {
                             // 4 floats -> 4 bf16 (8 bytes), half of 16-byte chunk cq / 2
                             const __nv_bfloat162 lo = __floats2bfloat162_rn(sv[u][0], sv[u][1]);
@@ -171,6 +173,145 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
         }
     }
     if (cq == 0) fold_rows<TA, KQ>(Rs64, Rs32, warp * RPW + rr, SWEEP, n);
+    __syncthreads();
+    double* dst = Rpart + (int64_t)blockIdx.x * n * KQ;
+    for (int e = tid; e < n * KQ; e += PASS_THREADS) dst[e] = Rs64[e];
+}
+
+// ------------------------------------------------------------------------------------------
+// R = S V for FP32 S with at most 1024 rows, optionally packing S into BF16 tiles (PACK 1): a
+// streaming form of sv_pack_kernel.  A thread owns rows warp * 2 + rr + 32 t (t < 32) and 16 bytes
+// of every 64-column strip; its row segments stream through a cp.async ring of 4-row sub-stages
+// (6 slots, ~160 KB in flight per SM, each slot refilled by the thread that read it, so no
+// barrier), the per-row partial dot products stay in registers across strips and are reduced over
+// the 16 lanes of a row (shuffles) and folded into FP64 every 32 strips, and the next strip's V is
+// prefetched.  Each 16-byte segment is converted (round to nearest even) and stored as 8 bytes of
+// its swizzled BF16 tile row as it passes.
+constexpr int SVR_TPS = 4;       // rows per thread and sub-stage
+constexpr int SVR_SLOTS = 6;
+constexpr int SVR_MAXNR = 32;    // rows per thread (n_rows <= 1024)
+
+template <int KQ, int PACK>
+__global__ void __launch_bounds__(PASS_THREADS, 1)
+sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds, const float* __restrict__ V,
+               int64_t ldv, int k, double* __restrict__ Rpart, unsigned char* __restrict__ Sp, int64_t nkb,
+               const DevStatus* st) {
+    constexpr int LPR = 16, W = 64, SWEEP = PASS_THREADS / LPR, NSUBMAX = SVR_MAXNR / SVR_TPS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint4* ring = reinterpret_cast<uint4*>(smem);
+    double* Rs64 = reinterpret_cast<double*>(smem + (size_t)SVR_SLOTS * SVR_TPS * PASS_THREADS * 16);  // n x KQ
+    if (block_should_exit(st, 0)) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rr = lane / LPR, cq = lane % LPR;
+    const int row0 = warp * 2 + rr;
+    const int NR = (n_rows + SWEEP - 1) / SWEEP;
+    const int nsub = (NR + SVR_TPS - 1) / SVR_TPS;
+    for (int e = tid; e < n * KQ; e += PASS_THREADS) Rs64[e] = 0.0;
+    const int64_t nstrips = ceil_div(m, W);
+    const int64_t my_strips = (int64_t)blockIdx.x < nstrips ? (nstrips - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nitems = my_strips * nsub;
+    auto issue = [&](int64_t g) {
+        if (g < nitems) {
+            const int64_t s = blockIdx.x + (g / nsub) * gridDim.x;
+            const int j = (int)(g % nsub);
+            const int64_t jn = s * W + cq * 4;
+            const int64_t rem = m - jn;
+            const int bytes_col = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+            uint4* slot = ring + (size_t)(g % SVR_SLOTS) * SVR_TPS * PASS_THREADS;
+#pragma unroll
+            for (int tt = 0; tt < SVR_TPS; ++tt) {
+                const int t = j * SVR_TPS + tt;
+                const int i = row0 + t * SWEEP;
+                const int bytes = (i < n && t < NR) ? bytes_col : 0;
+                const float* src = bytes ? S + (int64_t)i * lds + jn : S;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                                 static_cast<uint32_t>(__cvta_generic_to_shared(&slot[tt * PASS_THREADS + tid]))),
+                             "l"(src), "r"(bytes)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto load_v = [&](int64_t s, float (&vv)[KQ][4]) {
+        const int64_t jc = s * W + cq * 4;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) vv[q][e] = (s < nstrips && q < k && jc + e < m) ? V[(int64_t)q * ldv + jc + e] : 0.f;
+    };
+    float acc[KQ][SVR_MAXNR];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q)
+#pragma unroll
+        for (int t = 0; t < SVR_MAXNR; ++t) acc[q][t] = 0.f;
+    auto fold = [&]() {
+#pragma unroll
+        for (int t = 0; t < SVR_MAXNR; ++t) {
+            const int i = row0 + t * SWEEP;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                float a = acc[q][t];
+                a += __shfl_xor_sync(0xffffffffu, a, 1);
+                a += __shfl_xor_sync(0xffffffffu, a, 2);
+                a += __shfl_xor_sync(0xffffffffu, a, 4);
+                a += __shfl_xor_sync(0xffffffffu, a, 8);
+                if (cq == 0 && i < n) Rs64[i * KQ + q] += (double)a;
+                acc[q][t] = 0.f;
+            }
+        }
+    };
+    for (int g = 0; g < SVR_SLOTS - 1; ++g) issue(g);
+    float vv[KQ][4], vn[KQ][4];
+    load_v(blockIdx.x, vn);
+    __syncthreads();  // Rs64 zeroed
+    int64_t g = 0;
+    int since_fold = 0;
+    for (int64_t ls = 0; ls < my_strips; ++ls) {
+        const int64_t s = blockIdx.x + ls * gridDim.x;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) vv[q][e] = vn[q][e];
+        load_v(s + gridDim.x, vn);
+#pragma unroll
+        for (int j = 0; j < NSUBMAX; ++j) {
+            if (j < nsub) {
+                asm volatile("cp.async.wait_group %0;" ::"n"(SVR_SLOTS - 2) : "memory");
+                const uint4* slot = ring + (size_t)(g % SVR_SLOTS) * SVR_TPS * PASS_THREADS;
+#pragma unroll
+                for (int tt = 0; tt < SVR_TPS; ++tt) {
+                    const int t = j * SVR_TPS + tt;
+                    const uint4 w = slot[tt * PASS_THREADS + tid];
+                    const float x0 = __uint_as_float(w.x), x1 = __uint_as_float(w.y), x2 = __uint_as_float(w.z),
+                                x3 = __uint_as_float(w.w);
+#pragma unroll
+                    for (int q = 0; q < KQ; ++q)
+                        acc[q][t] = fmaf(x3, vv[q][3], fmaf(x2, vv[q][2], fmaf(x1, vv[q][1], fmaf(x0, vv[q][0], acc[q][t]))));
+                    if constexpr (PACK == 1) {
+                        const int i = row0 + t * SWEEP;
+                        if (i < n_rows) {
+                            const int r = i & 127;
+                            unsigned char* tile = Sp + (((int64_t)s * (n_rows >> 7) + (i >> 7)) << 14) + r * 128;
+                            const __nv_bfloat162 lo = __floats2bfloat162_rn(x0, x1);
+                            const __nv_bfloat162 hi = __floats2bfloat162_rn(x2, x3);
+                            uint2 o;
+                            o.x = *reinterpret_cast<const uint32_t*>(&lo);
+                            o.y = *reinterpret_cast<const uint32_t*>(&hi);
+                            *reinterpret_cast<uint2*>(tile + ((((cq >> 1) ^ (r & 7)) << 4) | ((cq & 1) << 3))) = o;
+                        }
+                    }
+                }
+                issue(g + SVR_SLOTS - 1);
+                ++g;
+            }
+        }
+        if (++since_fold == kFold) {
+            since_fold = 0;
+            fold();
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    fold();
     __syncthreads();
     double* dst = Rpart + (int64_t)blockIdx.x * n * KQ;
     for (int e = tid; e < n * KQ; e += PASS_THREADS) dst[e] = Rs64[e];
@@ -653,12 +794,35 @@ size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m) {
     return (size_t)ceil_div(n, 128) * (size_t)pack_kblocks(s_dtype, pack, m) * 16384;
 }
 
+template <int KQ, int PACK>
+static cudaError_t launch_sv_ring_t(int grid, const void* S, int n, int n_rows, int64_t m, int64_t lds, const void* V,
+                                    int64_t ldv, int k, double* Rpart, void* Sp, int64_t nkb, const DevStatus* st,
+                                    cudaStream_t stream) {
+    const size_t smem = (size_t)SVR_SLOTS * SVR_TPS * PASS_THREADS * 16 + (size_t)n * KQ * 8;
+    auto kern = sv_ring_kernel<KQ, PACK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, PASS_THREADS, smem, stream>>>(static_cast<const float*>(S), n, n_rows, m, lds,
+                                               static_cast<const float*>(V), ldv, k, Rpart,
+                                               static_cast<unsigned char*>(Sp), nkb, st);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,
                            int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
                            const DevStatus* st, cudaStream_t stream) {
     const int n_rows = pack ? (int)round_up(n, 128) : n;
     const int64_t nkb = pack ? pack_kblocks(s_dtype, pack, m) : 0;
     const int grid = plan.sv_grid;
+    // the streaming form: FP32 S, no packing or BF16 tiles, up to 1024 rows and 2 RHS
+    if (s_dtype == DFS_F32 && pack != 2 && n_rows <= SVR_MAXNR * (PASS_THREADS / 16) && kq <= 2) {
+        if (kq == 1)
+            return pack ? launch_sv_ring_t<1, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream)
+                        : launch_sv_ring_t<1, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream);
+        return pack ? launch_sv_ring_t<2, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream)
+                    : launch_sv_ring_t<2, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream);
+    }
 #define DFS_SV_CASE(KQ)                                                                                           \
     case KQ:                                                                                                      \
         if (s_dtype == DFS_F32) {                                                                                 \
