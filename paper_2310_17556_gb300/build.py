@@ -75,7 +75,7 @@ def build(force: bool = False, debug_bounds: bool = False, verbose: bool = False
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     if verbose:
-        print(f"built {LIB}")
+        print(f"built {LIB}", file=sys.stderr)
     return LIB
 
 

@@ -120,6 +120,40 @@ def svd_structured(n: int, m: int, seed: int, sigma_min: float = 1e-3, device="c
     return S.to(dtype), U, s, V
 
 
+def svd_structured_lowmem(n: int, m: int, seed: int, sigma_min: float = 1e-4, device="cpu",
+                          dtype=torch.float32, chunk: int = 1 << 18) -> torch.Tensor:
+    """S = U diag(sigma) V^T / sqrt(n) with the spectrum of ``svd_structured`` (Haar U, sigma
+    log-spaced 1 .. sigma_min), for sizes where an m x n FP64 factor does not fit or an FP64 QR
+    would take minutes: V comes from CholeskyQR2 of an FP32 Gaussian m x n block (FP32 Gram
+    matrices, formed column chunk by column chunk; Cholesky and inverse in FP64 on the host), so it
+    is orthonormal to FP32 accuracy; the Gaussian block is well conditioned (its condition number
+    tends to (1 + sqrt(n/m)) / (1 - sqrt(n/m))), which is what CholeskyQR needs.  Only S is returned;
+    it is a different draw from ``svd_structured`` with the same seed."""
+    import numpy as np
+
+    assert n <= m
+    g = _gen(seed, device)
+    U = _haar_orthogonal(n, g, device)  # FP64, n x n
+    V = torch.empty((m, n), device=device, dtype=torch.float32)
+    for c0 in range(0, m, chunk):
+        V[c0:c0 + chunk] = _randn((min(chunk, m - c0), n), g, device, torch.float32)
+    for _ in range(2):
+        C = torch.zeros((n, n), device=device, dtype=torch.float32)
+        for c0 in range(0, m, chunk):
+            C.addmm_(V[c0:c0 + chunk].T, V[c0:c0 + chunk])
+        L = np.linalg.cholesky(C.double().cpu().numpy())
+        Rinv = torch.from_numpy(np.ascontiguousarray(np.linalg.inv(L).T)).to(device=device, dtype=torch.float32)
+        for c0 in range(0, m, chunk):
+            V[c0:c0 + chunk] = V[c0:c0 + chunk] @ Rinv
+    sigma = torch.logspace(0.0, math.log10(sigma_min), n, dtype=torch.float64, device=device)
+    B = (U * (sigma / math.sqrt(n))[None, :]).float()  # U diag(sigma) / sqrt(n), n x n
+    S = torch.empty((n, m), device=device, dtype=dtype)
+    for c0 in range(0, m, chunk):
+        S[:, c0:c0 + chunk] = (B @ V[c0:c0 + chunk].T).to(dtype)
+    del V
+    return S
+
+
 def heavy_tailed(n: int, m: int, seed: int, device="cpu", dtype=torch.bfloat16) -> torch.Tensor:
     """Student-t (nu = 3) entries times a per-column log-normal(0, 1) factor, / sqrt(n).
 

@@ -375,3 +375,103 @@ def test_full_size_headline_workload_matches_oracle():
     assert ef["e_rel"] <= 1e-5, ef
     # the error inside the row space of S, where Algorithm 1's S^T y part lives
     assert em["e_range"] <= 1e-5, em
+
+
+# ---------------------------------------------------------------------------- batched
+
+
+def test_solve_batched_ragged():
+    """Independent problems of uneven (n, m, lambda) in one call (the batching workload's shape mix,
+    at sizes the oracle finishes quickly): each matches its own oracle solve; per-problem status."""
+    shapes = wl.ragged_batch_shapes(6, seed=4242, n_lo=64, n_hi=400, m_lo=2e3, m_hi=6e4, lam_lo=1e-3, lam_hi=1e-1)
+    probs, refs = [], []
+    for j, (n, m, lam) in enumerate(shapes):
+        m = (m + 3) // 4 * 4
+        S = wl.gaussian(n, m, seed=500 + j, device=dev())
+        V = wl.rhs(m, 2, seed=600 + j, device=dev())
+        probs.append((S, V, lam))
+        refs.append(solve_ref(S, V, lam))
+    outs, status = dfs.dfs_solve_batched(probs, precision="bf16")
+    assert status == [0] * len(probs)
+    for (S, V, lam), X, ref in zip(probs, outs, refs):
+        assert rel_err(np64(X), ref) <= 1e-6
+
+
+# ---------------------------------------------------------------------------- full-size configurations
+
+
+def _residual_fp64(S, X, V, lam, chunk=1 << 18):
+    """||S^T S x + lam x - v|| / ||v|| per RHS, in FP64 with torch (column chunks of S), as a check
+    independent of the CUDA path: for SPD A = S^T S + lam I, e_rel <= cond(A) res."""
+    n, m = S.shape
+    k = V.shape[0]
+    Sx = torch.zeros((n, k), device=S.device, dtype=torch.float64)
+    for c0 in range(0, m, chunk):
+        Sx += S[:, c0:c0 + chunk].double() @ X[:, c0:c0 + chunk].double().T
+    num = torch.zeros(k, device=S.device, dtype=torch.float64)
+    for c0 in range(0, m, chunk):
+        r = (S[:, c0:c0 + chunk].double().T @ Sx).T + lam * X[:, c0:c0 + chunk].double() - V[:, c0:c0 + chunk].double()
+        num += (r * r).sum(dim=1)
+    return (num.sqrt() / V.double().norm(dim=1)).cpu().numpy()
+
+
+def _sigma_max_sq(S, iters=30, chunk=1 << 18):
+    """Rayleigh-quotient estimate of ||S||_2^2 (a lower bound) by power iteration on S S^T, FP32
+    products over column chunks of S, with torch."""
+    n, m = S.shape
+    g = torch.Generator(device=S.device).manual_seed(7)
+    u = torch.randn(n, device=S.device, dtype=torch.float32, generator=g)
+    u /= u.norm()
+    est = 0.0
+    for _ in range(iters):
+        w = torch.zeros(n, device=S.device, dtype=torch.float32)
+        for c0 in range(0, m, chunk):
+            Sc = S[:, c0:c0 + chunk].float()
+            w += Sc @ (Sc.T @ u)
+        est = float(torch.dot(u, w))
+        u = w / w.norm()
+    return est
+
+
+@pytest.mark.slow
+def test_full_size_n4096_m2p22_k4_mixed():
+    """The precision configuration at its full size: n=4096, m=2^22 (64 GB of FP32 S), k=4,
+    lambda=1e-4, BF16 Gram with refinement, S with log-spaced singular values 1/sqrt(n) .. 1e-4/sqrt(n)
+    (low-memory generator: its SVD factors in FP32).  cond(A) = (1/n + lambda)/lambda ~ 3.4, so the
+    FP64 residual bounds the relative error: e_rel <= cond(A) res <= 1e-6 asks res <= 1e-6/cond(A)."""
+    n, m, k, lam = 4096, 1 << 22, 4, 1e-4
+    S = wl.svd_structured_lowmem(n, m, seed=231017556 + 3, sigma_min=1e-4, device=dev())
+    V = wl.rhs(m, k, seed=231017556 + 10, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="bf16")
+    assert info["status"] == 0 and info["iters"] >= 1, info
+    assert info["rel_correction"] <= 1e-6, info
+    cond = (1.0 / n + lam) / lam * 1.01  # 1 % for the FP32 orthogonality of the generated factors
+    res = _residual_fp64(S, X, V, lam)
+    assert res.max() <= 1e-6 / cond, res
+    del S, V, X
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_full_size_n8192_m2p22_heavy_tailed_bf16():
+    """The stress configuration: n=8192, m=2^22, BF16 S (64 GB) with Student-t entries and log-normal
+    column scales, lambda=1e-5 (near-singular W), k=1.
+
+    x is returned in FP32; its rounding delta_x alone (|delta_x_i| <= 2^-24 |x_i|) adds up to
+    ||A delta_x|| <= ||A||_2 2^-24 ||x|| to the residual of Eq. 1, ||A||_2 = ||S||_2^2 + lambda, which
+    here (||S||_2^2 ~ 1e4, ||x|| ~ ||v||/lambda) is far above 1.  So the check is that the FP64
+    residual stays within twice that storage floor (the factor 2 covers the power-iteration estimate
+    of ||S||_2^2 from below), i.e. that the solver's own error is below it; an unrefined
+    BF16-factor answer misses this floor by orders of magnitude."""
+    n, m, lam = 8192, 1 << 22, 1e-5
+    S = wl.heavy_tailed(n, m, seed=231017556 + 5, device=dev(), dtype=torch.bfloat16)
+    V = wl.rhs(m, 1, seed=231017556 + 12, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="bf16", max_iter=12)
+    assert info["status"] in (0, 3), info  # converged, or stopped at the rounding floor
+    assert torch.isfinite(X).all()
+    res = _residual_fp64(S, X, V, lam)
+    s2 = _sigma_max_sq(S)
+    floor = 2.0 ** -24 * (s2 + lam) * (X.double().norm(dim=1) / V.double().norm(dim=1)).cpu().numpy()
+    assert (res <= 2.0 * floor).all(), (res, floor, s2)
+    del S, V, X
+    torch.cuda.empty_cache()
