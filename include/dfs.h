@@ -65,7 +65,9 @@ typedef enum {
     DFS_PREC_FP32 = 2,   /* plain FP32 path: FP32 FFMA Gram, FP32 solves, no refinement */
     DFS_PREC_BF16 = 3,   /* tcgen05 BF16 Gram (FP32 accumulate) + n-space refinement */
     DFS_PREC_TF32 = 4,   /* tcgen05 TF32 Gram (FP32 accumulate) + n-space refinement */
-    DFS_PREC_BF16X3 = 5  /* tcgen05 split-BF16 (hi/lo, three products) Gram + refinement */
+    DFS_PREC_BF16X3 = 5  /* FP32 S only: S = H + L, H = bf16(S), L = bf16(S - H); tcgen05 BF16 Gram
+                            of W = H H^T + L H^T + (L H^T)^T (L L^T, ~2^-16 relative, dropped): the
+                            work of three BF16 Grams, ~2^-16 relative accuracy; + refinement */
 } dfs_precision;
 
 /* entries of dfs_info.ms and of dfs_step_times' output */

@@ -160,7 +160,7 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     }
     p->pp = pass_make_plan((int)n, kq, s_dtype, h->num_sms, m, h->smem_optin);
     p->pgrid = pass_partial_rows(p->pp);
-    p->pack = (p->tensor && p->tc.packed) ? (p->tc.kind == 1 ? 2 : 1) : 0;
+    p->pack = (p->tensor && p->tc.packed) ? (p->tc.kind == 1 ? 2 : (p->tc.kind == 2 ? 3 : 1)) : 0;
     p->ns = nspace_slots((int)p->n_pad, kq, (int)es, h->smem_optin) >= 2;
     size_t off = 0;
     auto take = [&](size_t bytes) {

@@ -32,7 +32,13 @@
 // Every mbarrier wait is bounded (2 s of wall time); a timeout sets DFS_ERR_TIMEOUT, makes the
 // other roles stop, waits for TMA copies and MMAs in flight and frees TMEM before returning.
 //
-// Kinds: BF16 MMA (kind::f16) on BF16 tiles, TF32 MMA (kind::tf32) on FP32 / TF32 tiles.
+// Kinds: BF16 MMA (kind::f16) on BF16 tiles, TF32 MMA (kind::tf32) on FP32 / TF32 tiles, and
+// BF16x3: FP32 S split as S = H + L (H = bf16(S), L = bf16(S - H), both round to nearest even), so
+// S S^T = H H^T + L H^T + (L H^T)^T + L L^T; the last term (relative size 2^-16) is dropped.  The
+// packed operand is the stacked 2 T_h-block matrix Z = [H; L] (T_h = T rounded up to even, so no
+// super-row mixes H and L blocks) and the kernel runs the units of Gram(Z) with J2 < H2 = T_h / 2:
+// the H H^T triangle and the full L H^T rectangle (3 of the 4 quarters of Z Z^T, the work of three
+// BF16 Grams); gram_tc_finalize_x3 forms W = H H^T + L H^T + (L H^T)^T.
 #include <cudaTypedefs.h>
 
 #include <cstring>
@@ -91,18 +97,38 @@ __host__ __device__ __forceinline__ int tc_unit_cost(int I2, int J2, int T) {
     return a1 ? 3 : 1;
 }
 
+// The unit list: all (I2, J2), J2 <= I2 < T2, in row-major order when H2 = 0; for the stacked
+// BF16x3 operand (H2 > 0, T = 4 H2) the H H^T triangle (I2 < H2, row-major) followed by the L H^T
+// rectangle (I2 >= H2, J2 < H2, row-major).
+__host__ __device__ __forceinline__ int tc_num_units(int T, int H2) {
+    const int T2 = (T + 1) / 2;
+    return H2 ? H2 * (H2 + 1) / 2 + H2 * H2 : T2 * (T2 + 1) / 2;
+}
+__host__ __device__ __forceinline__ void tc_unit_ij2(int u, int H2, int& I2, int& J2) {
+    const int tri = H2 * (H2 + 1) / 2;
+    if (H2 == 0 || u < tri) {
+        tc_unit_ij(u, I2, J2);
+        return;
+    }
+    I2 = H2 + (u - tri) / H2;
+    J2 = (u - tri) % H2;
+}
+__host__ __device__ __forceinline__ int tc_unit_index(int I2, int J2, int H2) {
+    if (H2 == 0 || I2 < H2) return I2 * (I2 + 1) / 2 + J2;
+    return H2 * (H2 + 1) / 2 + (I2 - H2) * H2 + J2;
+}
+
 struct TcTask {
     int I2, J2, slot, stride;
 };
 // Task t -> unit, slot and stride (unit u has c * cost(u) tasks, numbered consecutively).
-__host__ __device__ inline TcTask tc_task(int t, int T, int c) {
-    const int T2 = (T + 1) / 2;
-    const int U = T2 * (T2 + 1) / 2;
+__host__ __device__ inline TcTask tc_task(int t, int T, int c, int H2) {
+    const int U = tc_num_units(T, H2);
     TcTask k{0, 0, 0, 1};
     int before = 0;
     for (int u = 0; u < U; ++u) {
         int I2, J2;
-        tc_unit_ij(u, I2, J2);
+        tc_unit_ij2(u, H2, I2, J2);
         const int g = c * tc_unit_cost(I2, J2, T);
         if (t < before + g) {
             k.I2 = I2;
@@ -115,11 +141,11 @@ __host__ __device__ inline TcTask tc_task(int t, int T, int c) {
     }
     return k;
 }
-__host__ __device__ inline int tc_unit_first_task(int u, int T, int c) {
+__host__ __device__ inline int tc_unit_first_task(int u, int T, int c, int H2) {
     int before = 0;
     for (int v = 0; v < u; ++v) {
         int I2, J2;
-        tc_unit_ij(v, I2, J2);
+        tc_unit_ij2(v, H2, I2, J2);
         before += c * tc_unit_cost(I2, J2, T);
     }
     return before;
@@ -134,7 +160,7 @@ __host__ __device__ __forceinline__ int tc_task_nk(const TcTask& k, int64_t nkb)
 // used when S has short rows and no tile copy was made).
 template <int KIND, int PACKED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ Sp, int T, int c,
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ Sp, int T, int H2, int c,
                int ntasks, int G, int64_t nkb, int row_elems, float* __restrict__ part, DevStatus* st) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* stage_mem =
@@ -174,7 +200,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
             bool ok = true;
             const int ngroups = ntasks / G;
             for (int t = 0, gi = blockIdx.x; ok && gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
-                const TcTask tk = tc_task(gi * G + t, T, c);
+                const TcTask tk = tc_task(gi * G + t, T, c, H2);
                 const int nk = tc_task_nk(tk, nkb);
                 const int i0 = 2 * tk.I2, j0 = 2 * tk.J2;
                 const bool a1 = i0 + 1 < T, diag = tk.J2 == tk.I2;
@@ -236,7 +262,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
             bool ok = true;
             const int ngroups = ntasks / G;
             for (int t = 0, gi = blockIdx.x; ok && gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
-                const TcTask tk = tc_task(gi * G + t, T, c);
+                const TcTask tk = tc_task(gi * G + t, T, c, H2);
                 const int nk = tc_task_nk(tk, nkb);
                 if (nk == 0) continue;  // the epilogue writes zeros for an empty task
                 const bool a1 = 2 * tk.I2 + 1 < T, diag = tk.J2 == tk.I2;
@@ -290,7 +316,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
         uint32_t acc_phase = 0;
         const int ngroups = ntasks / G;
         for (int t = 0, gi = blockIdx.x; gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
-            const TcTask tk = tc_task(gi * G + t, T, c);
+            const TcTask tk = tc_task(gi * G + t, T, c, H2);
             const bool a1 = 2 * tk.I2 + 1 < T, diag = tk.J2 == tk.I2;
             // the group's tasks (separate FP32 accumulation chains) are added into one partial
             // block in task order: the first stores, the others add (read-modify-write)
@@ -359,6 +385,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
 __global__ void __launch_bounds__(256)
 gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int G, int64_t n, int64_t n_out, double lambda,
                         float* __restrict__ W, int64_t ldw) {
+    constexpr int H2 = 0;
     int I, J;
     {
         const int t = blockIdx.x;
@@ -378,9 +405,9 @@ gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int G, int
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (gi < n && I < T) {
         const int I2 = I / 2, J2 = J / 2;
-        const int u = I2 * (I2 + 1) / 2 + J2;
+        const int u = tc_unit_index(I2, J2, H2);
         const int g = c * tc_unit_cost(I2, J2, T) / G;       // partial blocks (task groups) of the unit
-        const int b0 = tc_unit_first_task(u, T, c) / G;
+        const int b0 = tc_unit_first_task(u, T, c, H2) / G;
         const size_t off = (size_t)((I & 1) * TC_BM + r) * TC_BN + (J & 1) * TC_BM + c4;
         const float* p0 = part + (size_t)b0 * TC_PART + off;
         int q = 0;
@@ -415,6 +442,85 @@ gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int G, int
     }
 }
 
+// FP32 sum, in group order, of the partial blocks of unit (I2, J2) at offset `off` of each block.
+__device__ __forceinline__ float4 tc_sum_groups(const float* __restrict__ part, int I2, int J2, int T, int H2, int c,
+                                                int G, size_t off) {
+    const int g = c * tc_unit_cost(I2, J2, T) / G;
+    const int b0 = tc_unit_first_task(tc_unit_index(I2, J2, H2), T, c, H2) / G;
+    const float* p0 = part + (size_t)b0 * TC_PART + off;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < g; ++q) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)q * TC_PART));
+        v.x += x.x;
+        v.y += x.y;
+        v.z += x.z;
+        v.w += x.w;
+    }
+    return v;
+}
+
+// BF16x3 finalize: W[gi][gj] (lower, rows < n_out) = (H H^T)[gi][gj] + (L H^T)[gi][gj] + (L H^T)[gj][gi]
+// plus lambda on the diagonal, from the partial blocks of the stacked Gram (Z block b = H block b,
+// Z block T_h + b = L block b); rows/cols in [n, n_out) get the identity.  One CTA per 32 rows of a
+// 128 x 128 tile (I, J): the transposed term (128 x 32 of Z tile (T_h + J, I)) is summed into
+// shared memory first, then thread (row, 4 x 4 columns) adds the two direct terms.
+__global__ void __launch_bounds__(256)
+gram_tc_finalize_x3_kernel(const float* __restrict__ part, int T, int H2, int c, int G, int64_t n, int64_t n_out,
+                           double lambda, float* __restrict__ W, int64_t ldw) {
+    __shared__ float sT[TC_BM][33];
+    int I, J;
+    {
+        const int t = blockIdx.x;
+        int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((i + 1) * (i + 2) / 2 <= t) ++i;
+        while (i * (i + 1) / 2 > t) --i;
+        I = i;
+        J = t - i * (i + 1) / 2;
+    }
+    const int Th = 2 * H2;
+    const int r0 = blockIdx.y * 32;
+    const int tid = threadIdx.x;
+    const bool live = (int64_t)I * TC_BM < n;  // tiles entirely in the padding only get the identity
+    // (L H^T)[k][i] for k in tile J (128 rows), i in rows r0..r0+31 of tile I
+    for (int e = tid; e < TC_BM * 8; e += 256) {
+        const int kk = e >> 3, i4 = (e & 7) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live) {
+            const int I2 = (Th + J) / 2, J2 = I / 2;
+            const size_t off = (size_t)((J & 1) * TC_BM + kk) * TC_BN + (I & 1) * TC_BM + r0 + i4;
+            v = tc_sum_groups(part, I2, J2, 2 * Th, H2, c, G, off);
+        }
+        sT[kk][i4] = v.x;
+        sT[kk][i4 + 1] = v.y;
+        sT[kk][i4 + 2] = v.z;
+        sT[kk][i4 + 3] = v.w;
+    }
+    __syncthreads();
+    const int rr = tid >> 3;
+    const int64_t gi = (int64_t)I * TC_BM + r0 + rr;
+    if (gi >= n_out) return;
+#pragma unroll 1
+    for (int u = 0; u < 4; ++u) {
+        const int cc = (tid & 7) * 4 + 32 * u;
+        float4 hh = make_float4(0.f, 0.f, 0.f, 0.f), lh = hh;
+        if (live && gi < n) {
+            const size_t off = (size_t)((I & 1) * TC_BM + r0 + rr) * TC_BN + (J & 1) * TC_BM + cc;
+            hh = tc_sum_groups(part, I / 2, J / 2, 2 * Th, H2, c, G, off);
+            lh = tc_sum_groups(part, (Th + I) / 2, J / 2, 2 * Th, H2, c, G, off);
+        }
+        const float a[4] = {hh.x + lh.x, hh.y + lh.y, hh.z + lh.z, hh.w + lh.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t gj = (int64_t)J * TC_BM + cc + e;
+            if (gj > gi) continue;
+            float w;
+            if (gi >= n || gj >= n) w = (gi == gj) ? 1.f : 0.f;
+            else w = (a[e] + sT[cc + e][rr]) + ((gi == gj) ? (float)lambda : 0.f);
+            W[gi * ldw + gj] = w;
+        }
+    }
+}
+
 // ---- host side ------------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -433,15 +539,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // kind 0 = BF16 MMA (FP32 S is packed to BF16 tiles, BF16 S used directly or re-laid out),
-// kind 1 = TF32 MMA (FP32 S, packed to TF32 tiles or read directly).
+// kind 1 = TF32 MMA (FP32 S, packed to TF32 tiles or read directly),
+// kind 2 = BF16x3 (FP32 S packed to stacked H / L BF16 tiles).
 int gram_tc_supported(int s_dtype, int kind) {
-    if (kind == 1) return s_dtype == DFS_F32;
+    if (kind == 1 || kind == 2) return s_dtype == DFS_F32;
     if (kind == 0) return s_dtype == DFS_F32 || s_dtype == DFS_BF16;
     return 0;
 }
 
 // elements per 128-byte k-block row: BF16 MMA -> 64, TF32 MMA -> 32
-static int tc_row_elems_kind(int kind) { return kind == 0 ? 64 : 32; }
+static int tc_row_elems_kind(int kind) { return kind == 1 ? 32 : 64; }
 
 GramTcPlan gram_tc_plan(int s_dtype, int kind, int64_t n, int64_t m, int num_sms) {
     GramTcPlan p{};
@@ -451,12 +558,17 @@ GramTcPlan gram_tc_plan(int s_dtype, int kind, int64_t n, int64_t m, int num_sms
     // rows >= 1 MiB too.
     p.packed = (s_dtype == DFS_F32) || ((int64_t)m * 2 >= (1 << 20));
     p.n_tiles = (int)ceil_div(n, TC_BM);
-    const int T = p.n_tiles, T2 = (T + 1) / 2;
-    p.npairs = T2 * (T2 + 1) / 2;  // quad units
-    int C = 0;                      // tile products per k-step over all units
+    p.h2 = 0;
+    if (kind == 2) {  // stacked [H; L]: T_h = T rounded up to even blocks of each
+        p.h2 = (p.n_tiles + 1) / 2;
+        p.n_tiles = 4 * p.h2;
+    }
+    const int T = p.n_tiles;
+    p.npairs = tc_num_units(T, p.h2);  // quad units
+    int C = 0;                          // tile products per k-step over all units
     for (int u = 0; u < p.npairs; ++u) {
         int I2, J2;
-        tc_unit_ij(u, I2, J2);
+        tc_unit_ij2(u, p.h2, I2, J2);
         C += tc_unit_cost(I2, J2, T);
     }
     const int64_t nkb = ceil_div(m, tc_row_elems_kind(kind));
@@ -520,8 +632,8 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
         auto kern = gram_tc_kernel<K, PK>;                                                                          \
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES); \
         if (e != cudaSuccess) return e;                                                                             \
-        kern<<<grid, TC_THREADS, TC_SMEM_BYTES, stream>>>(map, sp, plan.n_tiles, plan.c, plan.ntasks, plan.group,    \
-                                                          plan.nkb, re, part, st);                                 \
+        kern<<<grid, TC_THREADS, TC_SMEM_BYTES, stream>>>(map, sp, plan.n_tiles, plan.h2, plan.c, plan.ntasks,       \
+                                                          plan.group, plan.nkb, re, part, st);                     \
         count_launch();                                                                                             \
     }
     if (plan.kind == 1) {
@@ -536,7 +648,12 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
 cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64_t n, int64_t n_out, double lambda,
                                     void* W, int64_t ldw, cudaStream_t stream) {
     const int T = (int)ceil_div(n_out, TC_BM);
-    {
+    if (plan.kind == 2) {
+        gram_tc_finalize_x3_kernel<<<dim3(T * (T + 1) / 2, TC_BM / 32), 256, 0, stream>>>(
+            static_cast<const float*>(P), plan.n_tiles, plan.h2, plan.c, plan.group, n, n_out, lambda,
+            static_cast<float*>(W), ldw);
+        count_launch();
+    } else {
         gram_tc_finalize_kernel<<<dim3(T * (T + 1) / 2, TC_BM / 8), 256, 0, stream>>>(
             static_cast<const float*>(P), plan.n_tiles, plan.c, plan.group, n, n_out, lambda,
             static_cast<float*>(W), ldw);

@@ -19,7 +19,8 @@ cudaError_t launch_gram_finalize(int acc_f64, int w_f64, int BM, const void* P, 
 struct GramTcPlan {
     int kind;
     int packed;       // operands come from the packed tiles of the S v pass
-    int n_tiles;      // T: 128-row blocks of S
+    int n_tiles;      // T: 128-row blocks of S (of the stacked [H; L] operand for kind 2)
+    int h2;           // kind 2: T_h / 2 super-rows of H (the units with J2 >= h2 are skipped); else 0
     int npairs;       // quad units (two 128-row blocks x two 128-column blocks)
     int c;            // tasks per cost unit (a unit of cost k gets c k tasks)
     int ntasks;       // tasks (k-split pieces of the units)
@@ -82,7 +83,7 @@ int pass_max_group(int n, int s_dtype, size_t smem_limit);
 int pass_grid(int n, int KQ, int s_dtype, int num_sms, int64_t m);
 PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit);
 int pass_partial_rows(const PassPlan& p);  // rows of the partial buffers (max of both grids)
-// pack: 0 none, 1 BF16 tiles, 2 TF32 tiles (see sv_pack_kernel)
+// pack: 0 none, 1 BF16 tiles, 2 TF32 tiles, 3 stacked BF16 H / L tiles (see sv_pack_kernel)
 int64_t pack_kblocks(int s_dtype, int pack, int64_t m);
 size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m);
 cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,

@@ -54,6 +54,19 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
+// H = bf16(x) and L = bf16(x - H) (both round to nearest even) of four consecutive floats, as
+// two 8-byte groups of BF16 pairs; x - H is exact in FP32.
+__device__ __forceinline__ void split_bf16x4(float x0, float x1, float x2, float x3, uint2& wh, uint2& wl) {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(x0, x1), h23 = __floats2bfloat162_rn(x2, x3);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(x0 - f01.x, x1 - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(x2 - f23.x, x3 - f23.y);
+    wh.x = *reinterpret_cast<const uint32_t*>(&h01);
+    wh.y = *reinterpret_cast<const uint32_t*>(&h23);
+    wl.x = *reinterpret_cast<const uint32_t*>(&l01);
+    wl.y = *reinterpret_cast<const uint32_t*>(&l23);
+}
+
 // Fold the FP32 per-row sums of the rows this thread owns into FP64.
 template <typename TA, int KQ>
 __device__ __forceinline__ void fold_rows(double* Rs64, TA* Rs32, int first, int step, int n) {
@@ -67,7 +80,9 @@ __device__ __forceinline__ void fold_rows(double* Rs64, TA* Rs32, int first, int
 
 // ------------------------------------------------------------------------------------------
 // R = S V, optionally packing S into tensor-core tiles.
-//   PACK 0: none; 1: BF16 tiles (64-column k-blocks); 2: TF32 tiles (32-column k-blocks).
+//   PACK 0: none; 1: BF16 tiles (64-column k-blocks); 2: TF32 tiles (32-column k-blocks);
+//   3 (FP32 S): BF16 H = bf16(s) in row block I and L = bf16(s - H) in row block n_rows / 128 + I,
+//   2 n_rows / 128 tiles per k-block (the stacked operand of the BF16x3 Gram).
 template <typename TS, int KQ, int PACK>
 __global__ void __launch_bounds__(PASS_THREADS)
 sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds,
@@ -75,7 +90,8 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
                unsigned char* __restrict__ Sp, int64_t nkb, const DevStatus* st) {
     using TA = typename PassTypes<TS>::TA;
     constexpr int VEC = Vec16<TS>::N;
-    constexpr int LPR = (PACK == 1 && sizeof(TS) == 4) ? 16 : 8;  // lanes per row
+    constexpr int LPR = ((PACK == 1 || PACK == 3) && sizeof(TS) == 4) ? 16 : 8;  // lanes per row
+    static_assert(PACK != 3 || sizeof(TS) == 4, "the H / L split needs FP32 S");
     constexpr int W = LPR * VEC;
     constexpr int RPW = 32 / LPR;
     constexpr int SWEEP = PASS_WARPS * RPW;
@@ -131,8 +147,15 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
                 if constexpr (PACK != 0) {
                     if (i < n_rows) {
                         const int r = i & 127;
-                        unsigned char* tile = Sp + (((int64_t)s * (n_rows >> 7) + (i >> 7)) << 14) + r * 128;
-                        if constexpr (PACK == 1 && sizeof(TS) == 4) {
+                        constexpr int NTM = PACK == 3 ? 2 : 1;
+                        unsigned char* tile = Sp + (((int64_t)s * (NTM * (n_rows >> 7)) + (i >> 7)) << 14) + r * 128;
+                        if constexpr (PACK == 3) {
+                            uint2 wh, wl;
+                            split_bf16x4(sv[u][0], sv[u][1], sv[u][2], sv[u][3], wh, wl);
+                            const int off = (((cq >> 1) ^ (r & 7)) << 4) | ((cq & 1) << 3);
+                            *reinterpret_cast<uint2*>(tile + off) = wh;
+                            *reinterpret_cast<uint2*>(tile + ((int64_t)(n_rows >> 7) << 14) + off) = wl;
+                        } else if constexpr (PACK == 1 && sizeof(TS) == 4) {
                             // 4 floats -> 4 bf16 (8 bytes), half of 16-byte chunk cq / 2
                             const __nv_bfloat162 lo = __floats2bfloat162_rn(sv[u][0], sv[u][1]);
                             const __nv_bfloat162 hi = __floats2bfloat162_rn(sv[u][2], sv[u][3]);
@@ -287,7 +310,18 @@ sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_
 #pragma unroll
                     for (int q = 0; q < KQ; ++q)
                         acc[q][t] = fmaf(x3, vv[q][3], fmaf(x2, vv[q][2], fmaf(x1, vv[q][1], fmaf(x0, vv[q][0], acc[q][t]))));
-                    if constexpr (PACK == 1) {
+                    if constexpr (PACK == 3) {
+                        const int i = row0 + t * SWEEP;
+                        if (i < n_rows) {
+                            const int r = i & 127;
+                            unsigned char* tile = Sp + (((int64_t)s * (2 * (n_rows >> 7)) + (i >> 7)) << 14) + r * 128;
+                            uint2 wh, wl;
+                            split_bf16x4(x0, x1, x2, x3, wh, wl);
+                            const int off = (((cq >> 1) ^ (r & 7)) << 4) | ((cq & 1) << 3);
+                            *reinterpret_cast<uint2*>(tile + off) = wh;
+                            *reinterpret_cast<uint2*>(tile + ((int64_t)(n_rows >> 7) << 14) + off) = wl;
+                        }
+                    } else if constexpr (PACK == 1) {
                         const int i = row0 + t * SWEEP;
                         if (i < n_rows) {
                             const int r = i & 127;
@@ -789,9 +823,15 @@ int64_t pack_kblocks(int s_dtype, int pack, int64_t m) {
     return ceil_div(m, width);
 }
 
+// 128-row tiles per k-block: T, or 2 T_h (T rounded up to even) for the stacked H / L operand
+static int64_t pack_tiles_per_kblock(int pack, int64_t n) {
+    const int64_t T = ceil_div(n, 128);
+    return pack == 3 ? 2 * round_up(T, 2) : T;
+}
+
 size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m) {
     if (pack == 0) return 0;
-    return (size_t)ceil_div(n, 128) * (size_t)pack_kblocks(s_dtype, pack, m) * 16384;
+    return (size_t)pack_tiles_per_kblock(pack, n) * (size_t)pack_kblocks(s_dtype, pack, m) * 16384;
 }
 
 template <int KQ, int PACK>
@@ -812,16 +852,20 @@ static cudaError_t launch_sv_ring_t(int grid, const void* S, int n, int n_rows, 
 cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,
                            int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
                            const DevStatus* st, cudaStream_t stream) {
-    const int n_rows = pack ? (int)round_up(n, 128) : n;
+    if (pack == 3 && s_dtype != DFS_F32) return cudaErrorInvalidValue;
+    // packed rows: the 128-row blocks of S (for the stacked H / L operand: an even number of them)
+    const int n_rows = pack ? (int)round_up(n, pack == 3 ? 256 : 128) : n;
     const int64_t nkb = pack ? pack_kblocks(s_dtype, pack, m) : 0;
     const int grid = plan.sv_grid;
-    // the streaming form: FP32 S, no packing or BF16 tiles, up to 1024 rows and 2 RHS
+    // the streaming form: FP32 S, no packing or BF16 (H / L) tiles, up to 1024 rows and 2 RHS
     if (s_dtype == DFS_F32 && pack != 2 && n_rows <= SVR_MAXNR * (PASS_THREADS / 16) && kq <= 2) {
-        if (kq == 1)
-            return pack ? launch_sv_ring_t<1, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream)
-                        : launch_sv_ring_t<1, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream);
-        return pack ? launch_sv_ring_t<2, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream)
-                    : launch_sv_ring_t<2, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream);
+#define DFS_SVR(KQ)                                                                                               \
+    return pack == 3   ? launch_sv_ring_t<KQ, 3>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream) \
+           : pack == 1 ? launch_sv_ring_t<KQ, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream) \
+                       : launch_sv_ring_t<KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream);
+        if (kq == 1) DFS_SVR(1)
+        DFS_SVR(2)
+#undef DFS_SVR
     }
 #define DFS_SV_CASE(KQ)                                                                                           \
     case KQ:                                                                                                      \
@@ -831,6 +875,9 @@ cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, 
                                                  stream, s_dtype);                                                \
             if (pack == 2)                                                                                        \
                 return launch_sv_t<float, KQ, 2>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,       \
+                                                 stream, s_dtype);                                                \
+            if (pack == 3)                                                                                        \
+                return launch_sv_t<float, KQ, 3>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,       \
                                                  stream, s_dtype);                                                \
             return launch_sv_t<float, KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream,   \
                                              s_dtype);                                                            \

@@ -220,7 +220,13 @@ def test_bf16_storage_bf16_tensor_path():
     # accumulation errs: at most one unit of 2^-23 (truncating adds) per accumulating MMA step, of
     # which there are at most m / 16, relative to sum |s_i s_j| <= max W  ->  tol = m / 16 * 2^-23
     (torch.bfloat16, "bf16", 600, 33000, 33000 / 16 * 2.0 ** -23),
-    (torch.bfloat16, "bf16", 130, 64, 2e-6), (torch.bfloat16, "bf16", 1153, 3000, 3000 / 16 * 2.0 ** -23)])
+    (torch.bfloat16, "bf16", 130, 64, 2e-6), (torch.bfloat16, "bf16", 1153, 3000, 3000 / 16 * 2.0 ** -23),
+    # BF16x3: s = H + L + E with |s - H| <= 2^-8 |s| and |E| <= 2^-16 |s|; dropping L L^T and E leaves
+    # at most 3 * 2^-16 of sum |s_i s_j| per entry, plus the FP32 accumulation of the three products
+    (torch.float32, "bf16x3", 600, 33000, 3 * 2.0 ** -16 + 3 * 33000 / 16 * 2.0 ** -23),
+    (torch.float32, "bf16x3", 77, 64, 3 * 2.0 ** -16 + 1e-6),
+    (torch.float32, "bf16x3", 1153, 3000, 3 * 2.0 ** -16 + 3 * 3000 / 16 * 2.0 ** -23),
+    (torch.float32, "bf16x3", 2100, 4000, 3 * 2.0 ** -16 + 3 * 4000 / 16 * 2.0 ** -23)])
 def test_gram_step(dtype, prec, n, m, tol):
     lam = 0.25
     S = aligned(wl.gaussian(n, m, seed=31, device=dev(), dtype=dtype))
@@ -230,6 +236,40 @@ def test_gram_step(dtype, prec, n, m, tol):
     err = np.abs(np64(W) - Wr)[lo].max() / np.abs(Wr).max()
     assert err <= tol
     assert np.all(np64(W)[~lo] == 0.0)  # upper triangle untouched (zeros from the caller)
+
+
+@pytest.mark.parametrize("n,m", [(300, 20000), (1024, 8192), (1100, 6000)])
+def test_bf16x3_gram_cross_terms(n, m):
+    """Rows h_i = bf16(g + z_i / 2) share a common component g (so every Gram entry is O(m)) and
+    carry a per-row low part: s_i = h_i (1 + c_i 2^-9), |c_i| < 1, so bf16(s_i) = h_i and the low
+    BF16 part is ~c_i 2^-9 h_i.  Then (L H^T)[i][k] ~ c_i 2^-9 W_ik, and W needs both cross terms,
+    c_i and c_k: a dropped or mis-transposed L H^T term is off by ~1e-3 W_ik, twenty times the
+    tolerance, which covers the dropped L L^T (2^-18) and the FP32 accumulation."""
+    g = torch.Generator(device=dev()).manual_seed(97)
+    base = torch.randn(m, generator=g, device=dev())
+    z = torch.randn(n, m, generator=g, device=dev())
+    h = (base[None, :] + 0.5 * z).to(torch.bfloat16).float()
+    c = (torch.rand(n, generator=g, device=dev()) * 1.8 - 0.9)
+    S = aligned((h * (1.0 + c[:, None] * 2.0 ** -9)).contiguous())
+    lam = 0.5
+    W = dfs.dfs_gram(S, lam, precision="bf16x3")
+    Wr = oracle.gram(np64(S), lam)
+    lo = np.tril(np.ones((n, n), bool))
+    err = np.abs(np64(W) - Wr)[lo].max() / np.abs(Wr).max()
+    assert err <= 5e-5 + m / 1024 * 2.0 ** -23 * 16, err
+    # the same matrix in plain BF16 misses the low parts: its error is of the size the test detects
+    Wb = dfs.dfs_gram(S, lam, precision="bf16")
+    assert np.abs(np64(Wb) - Wr)[lo].max() / np.abs(Wr).max() >= 4e-4
+
+
+@pytest.mark.parametrize("n,m,k,lam", [(1024, 65536, 1, 1e-4), (257, 33336, 3, 1e-3), (100, 5000, 8, 1e-1),
+                                       (2100, 9000, 2, 1e-2)])
+def test_bf16x3_refined_path_matches_oracle(n, m, k, lam):
+    S = aligned(wl.gaussian(n, m, seed=181 + n, device=dev()))
+    V = wl.rhs(m, k, seed=182 + n, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="bf16x3")
+    assert info["status"] == 0 and info["precision"] == "bf16x3", info
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
 
 
 @pytest.mark.parametrize("dtype,n,tol", [(torch.float32, 300, 1e-5), (torch.float64, 200, 1e-12),
