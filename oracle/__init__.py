@@ -17,5 +17,6 @@ from .alg1 import (  # noqa: F401
     solve,
     solve_batched,
     solve_steps,
+    sr_scores,
 )
 from .exact import solve_dense_exact  # noqa: F401

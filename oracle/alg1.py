@@ -47,6 +47,7 @@ __all__ = [
     "apply_operator",
     "residual_n_space",
     "solve_batched",
+    "sr_scores",
     "errors",
 ]
 
@@ -211,6 +212,15 @@ def residual_n_space(S, V, Y, lam: float) -> np.ndarray:
     Y2 = Y2[:, None] if Y2.ndim == 1 else Y2
     r = S @ (V2 - S.T @ Y2) - float(lam) * Y2
     return r[:, 0] if vec else r
+
+
+def sr_scores(O) -> np.ndarray:
+    """Section 4, stochastic reconfiguration: S = (O - O_bar) / sqrt(n), with O the n x m matrix of
+    log-derivatives of the wave function (one row per sample) and O_bar its average over the
+    samples, i.e. the mean of each column over the n rows.  FP64."""
+    O = _as_f64(O)
+    n = O.shape[0]
+    return (O - O.mean(axis=0, keepdims=True)) / np.sqrt(n)
 
 
 def solve_batched(problems) -> list:

@@ -261,6 +261,42 @@ def _pin_dense(solve_fn):
     return rel(solve_fn(S, v, 0.05), dense_solve(S, v, 0.05)) < 1e-10
 
 
+def test_sr_scores_section4_invariants():
+    """Section 4's SR scores S = (O - O_bar) / sqrt(n): rows that all agree give S = 0 (so x = v /
+    lambda); a common offset added to every row changes nothing; every column of S sums to zero;
+    the 1 / sqrt(n) scale is the one of Section 2's S."""
+    rng = np.random.default_rng(5)
+    n, m = 7, 11
+    mu = rng.standard_normal(m)
+    # zero up to the rounding of the column mean (a sum of n equal values divided by n)
+    assert np.abs(oracle.sr_scores(np.tile(mu, (n, 1)))).max() <= 4 * np.finfo(float).eps * np.abs(mu).max()
+    v = rng.standard_normal(m)
+    np.testing.assert_allclose(oracle.solve(oracle.sr_scores(np.tile(mu, (n, 1))), v, 0.3), v / 0.3, rtol=1e-14)
+    O = rng.standard_normal((n, m))
+    S = oracle.sr_scores(O)
+    np.testing.assert_allclose(oracle.sr_scores(O + mu[None, :]), S, atol=1e-14)
+    np.testing.assert_allclose(S.sum(axis=0), 0.0, atol=1e-14)
+    # one sample away from the mean by e_j: S_ij = (1 - 1/n) / sqrt(n) there, -1/(n sqrt(n)) elsewhere
+    E = np.zeros((n, m))
+    E[2, 4] = 1.0
+    Se = oracle.sr_scores(E)
+    assert math.isclose(Se[2, 4], (1 - 1 / n) / math.sqrt(n), rel_tol=1e-14)
+    assert math.isclose(Se[0, 4], -1 / (n * math.sqrt(n)), rel_tol=1e-14)
+
+
+@pytest.mark.parametrize("lam", [1e-3, 0.5])
+def test_sr_two_samples_closed_form(lam):
+    """n = 2: S = [d; -d] / (2 sqrt 2) with d = o_1 - o_2, so S^T S = d d^T / 4 and Eq. 1 has the
+    Sherman-Morrison solution x = v / lambda - d (d . v) / (lambda (4 lambda + ||d||^2))."""
+    rng = np.random.default_rng(6)
+    m = 9
+    O = rng.standard_normal((2, m))
+    v = rng.standard_normal(m)
+    d = O[0] - O[1]
+    x_cf = v / lam - d * (d @ v) / (lam * (4 * lam + d @ d))
+    np.testing.assert_allclose(oracle.solve(oracle.sr_scores(O), v, lam), x_cf, rtol=1e-12, atol=1e-12)
+
+
 def test_planted_mistakes_are_caught(monkeypatch):
     assert _pin_dense(oracle.solve)
 
