@@ -2,8 +2,9 @@
 //
 // Blocked right-looking factorisation of the padded n_pad x n_pad matrix W (row-major, lower
 // triangle) in NB x NB tiles, as ONE persistent cooperative kernel (one CTA per SM, every CTA
-// resident).  Tile t = (i, p), i >= p, t = i (i + 1) / 2 + p, is owned by CTA t mod G for the
-// whole factorisation.  Step j applies column block j to the trailing matrix:
+// resident; two per SM when they fit, so that one CTA's L2 round trips overlap the other's work).
+// Tile t = (i, p), i >= p, t = i (i + 1) / 2 + p, is owned by CTA t mod G for the whole
+// factorisation.  Step j applies column block j to the trailing matrix:
 //   A[i, p] -= P_i P_p^T,   P_i = A[i, j] Linv_j^T   (panel TRSM, recomputed where needed)
 // for all i >= p > j.  The panels A[i, j] stay unscaled while the steps run (so no tile is read
 // after its owner overwrote it) and are scaled in place once every CTA has finished; that last
@@ -11,13 +12,13 @@
 // Dependencies are tracked per tile instead of with grid-wide barriers:
 //   done[t]   tile t = (i, p) has received its last update (after step p - 1);
 //   diag[j]   diagonal block j is factored: L_jj written and Linv_j = L_jj^{-1} published.
-// Within a step a CTA first updates its tiles of column j + 1 (the next panel), the diagonal
-// tile first; the owner of diagonal tile j + 1 factors it right away, so the factor of the
+// Within a step a CTA first updates its tiles of column j + 1 (the next panel); the owner of
+// diagonal tile j + 1 fetches that tile and panel tile (j + 1, j) before diagonal block j is
+// published, then applies the last update and factors block j + 1 at once, so the factor of the
 // next block overlaps the rest of step j's trailing update (look-ahead).
-// Each diagonal block is factored by one warp with the block's rows in registers: column j's
-// pivot, scale and rank-1 update use shuffles only, in the compute type CT (double: the FP64
-// diagonal panel; float: the fast variant).  Its inverse (all 8 warps, 4 columns each) feeds
-// the panel TRSM and the triangular solves.
+// Each diagonal block is factored by one warp with the block's rows in registers, in the
+// compute type CT (double: the FP64 diagonal panel; float: the fast variant).  Its inverse (all
+// 8 warps, 4 columns each) feeds the panel TRSM and the triangular solves.
 // Every wait is bounded (DFS_ERR_TIMEOUT after 2 s) and also ends when another CTA has set an
 // error status: a pivot <= 0 (DFS_ERR_NOT_SPD) or NaN/Inf (DFS_ERR_NONFINITE) with its index.
 #include "kernels.cuh"
@@ -67,11 +68,14 @@ __device__ bool block_wait(const int* f, int target, DevStatus* st, int* s_ok, i
     return *s_ok != 0;
 }
 
-// Make this CTA's global writes visible, then thread 0 sets *f = 1 (release).
+// Publish this CTA's global writes: after the barrier, thread 0 fences (cumulative over the
+// writes the barrier ordered before it) and sets *f = 1 with a release store.
 __device__ __forceinline__ void block_publish(int* f) {
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) st_release_gpu(f, 1);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release_gpu(f, 1);
+    }
 }
 
 __device__ __forceinline__ void tile_ij(int t, int& i, int& p) {
@@ -82,6 +86,7 @@ __device__ __forceinline__ void tile_ij(int t, int& i, int& p) {
     p = t - r * (r + 1) / 2;
 }
 __device__ __forceinline__ int tile_id(int i, int p) { return i * (i + 1) / 2 + p; }
+
 
 // 1/sqrt(d): FP32 hardware estimate, then (FP64) two Newton steps r <- r (3 - d r^2) / 2, each
 // doubling the correct bits (~2^-22 -> 2^-44 -> below FP64 rounding): a short dependent chain.
@@ -97,12 +102,12 @@ __device__ __forceinline__ double rsqrt_ct(double d) {
 }
 __device__ __forceinline__ float rsqrt_ct(float d) { return rsqrtf(d); }
 
-// dst = L^{-1} (NB x NB row-major, zeros above the diagonal) for the lower-triangular L in sF,
+// dst(r, c, v) receives L^{-1} (zeros above the diagonal) for the lower-triangular L in sF,
 // with s_rinv[i] = 1 / L[i][i].  Needs 256 threads: warp w forms columns c = w + 8 u (u < 4) of
 // X = L^{-1} by forward substitution on L x = e_c, lane i holding x_i; the four chains are
 // interleaved.  Arithmetic in T.
-template <typename T, typename CT>
-__device__ __forceinline__ void invert_lower_32(const CT (*sF)[NB + 1], const T* s_rinv, T* dst) {
+template <typename T, typename CT, typename D>
+__device__ __forceinline__ void invert_lower_32(const CT (*sF)[NB + 1], const T* s_rinv, D&& dst) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T x[4];
 #pragma unroll
@@ -121,52 +126,53 @@ __device__ __forceinline__ void invert_lower_32(const CT (*sF)[NB + 1], const T*
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int c = warp + 8 * u;
-        dst[lane * NB + c] = (lane >= c) ? x[u] : (T)0;
+        dst(lane, c, (lane >= c) ? x[u] : (T)0);
     }
 }
 
-// Factor diagonal block kb (all threads of the CTA call it).  Warp 0: lane i holds row i of the
-// block in registers; for each column j the pivot is broadcast, every lane scales its entry and
-// applies the rank-1 update to the entries right of column j with the scaled column shuffled in.
-// Then L_kb goes to W (lower part) and sF, and all 8 warps form Linv_kb (4 columns per warp,
-// forward substitution on L x = e_c with the 4 chains interleaved).  Returns false (uniformly)
-// on a bad pivot, after recording it.
+// Factor diagonal block kb, whose updated entries (lower triangle) are in sF; all threads of the
+// CTA call it.  Warp 0: lane i holds row i in registers; for each column j every lane scales its
+// entry by the broadcast 1/sqrt(pivot), the scaled column goes through a shared-memory vector
+// (double-buffered by column parity, read by all lanes at one address: no bank conflicts, no
+// shuffle latency per entry), and every lane applies the rank-1 update to its entries right of
+// column j.  Lane j + 1 forms the next pivot from its own scaled entry and it is broadcast before
+// the update runs, so the dependent chain per column is one shuffle, one rsqrt and two
+// multiply-adds.  L_kb goes back to sF; then all threads store it to W (coalesced) and form
+// Linv_kb (4 columns per warp, forward substitution on L x = e_c with the 4 chains interleaved)
+// into sX, stored to Linv (coalesced).  Returns false (uniformly) on a bad pivot, after recording it.
 template <typename T, typename CT>
-__device__ __noinline__ bool factor_diag(T* W, int64_t ld, int kb, T* Linv, DevStatus* st, CT (*sF)[NB + 1], T* s_rinv,
-                            int* s_fail) {
+__device__ __noinline__ bool factor_diag(T* W, int64_t ld, int kb, T* Linv, DevStatus* st, CT (*sF)[NB + 1],
+                                         T (*sX)[NB + 1], T* s_rinv, int* s_fail, CT (*sCol)[NB]) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t o = (int64_t)kb * NB;
     if (warp == 0) {
         CT a[NB];
-        const T* row = W + (o + lane) * ld + o;
 #pragma unroll
-        for (int p = 0; p < NB; ++p) a[p] = (p <= lane) ? (CT)__ldcg(row + p) : (CT)0;
+        for (int p = 0; p < NB; ++p) a[p] = (p <= lane) ? sF[lane][p] : (CT)0;
         int fail = -1;
+        CT d = __shfl_sync(0xffffffffu, a[0], 0);
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-            const CT d = __shfl_sync(0xffffffffu, a[j], j);
             if (fail < 0 && (!(d > (CT)0) || !isfinite(d))) fail = isfinite(d) ? j : -2 - j;
             const CT r = rsqrt_ct(d);
             const CT l = a[j] * r;
             a[j] = (lane >= j) ? l : (CT)0;
+            sCol[j & 1][lane] = l;
+            // lane j + 1's pivot after this column (the same multiply-add its own update does),
+            // broadcast before the update
+            if (j + 1 < NB) d = __shfl_sync(0xffffffffu, fma(-l, l, a[j + 1]), j + 1);
+            __syncwarp();
             // constant trip count (fully unrolled, a[] stays in registers); p <= j is skipped
 #pragma unroll
             for (int p = 0; p < NB; ++p) {
-                if (p > j) {
-                    const CT lp = __shfl_sync(0xffffffffu, l, p);
-                    a[p] = (lane >= p) ? fma(-l, lp, a[p]) : a[p];
-                }
+                if (p > j) a[p] = (lane >= p) ? fma(-l, sCol[j & 1][p], a[p]) : a[p];
             }
         }
         if (lane == 0) *s_fail = fail;
         if (fail < 0) {
-            T* wr = W + (o + lane) * ld + o;
 #pragma unroll
-            for (int p = 0; p < NB; ++p) {
-                sF[lane][p] = a[p];
-                if (p <= lane) wr[p] = (T)a[p];
-                if (p == lane) s_rinv[lane] = (T)1 / (T)a[p];
-            }
+            for (int p = 0; p < NB; ++p) sF[lane][p] = a[p];
+            s_rinv[lane] = (T)1 / (T)a[lane];
         }
     }
     __syncthreads();
@@ -179,43 +185,58 @@ __device__ __noinline__ bool factor_diag(T* W, int64_t ld, int kb, T* Linv, DevS
         }
         return false;
     }
-    invert_lower_32<T, CT>(sF, s_rinv, Linv + (int64_t)kb * NB * NB);
-    return true;
-}
-
-// sOut = A[r0.., c0..] Linv^T for one NB x NB tile: sOut[r][c] = sum_q A[r][q] Li[c][q] (Li is
-// lower triangular with zeros above the diagonal).  Thread: row tid / 8, columns tid % 8 + 8 u.
-template <typename T>
-__device__ __forceinline__ void tile_times_linv_t(const T* W, int64_t ld, int64_t r0, int64_t c0,
-                                                  const T (*sLi)[NB + 1], T (*sOut)[NB + 1]) {
-    const int tid = threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
+        const int e = tid + u * CC_THREADS, r = e / NB, c = e % NB;
+        if (c <= r) W[(o + r) * ld + o + c] = (T)sF[r][c];
+    }
+    invert_lower_32<T, CT>(sF, s_rinv, [&](int r, int c, T v) { sX[r][c] = v; });
+    __syncthreads();
+    T* dst = Linv + (int64_t)kb * NB * NB;
 #pragma unroll
     for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
         const int e = tid + u * CC_THREADS;
-        sOut[e / NB][e % NB] = __ldcg(W + (r0 + e / NB) * ld + c0 + e % NB);
+        dst[e] = sX[e / NB][e % NB];
     }
+    return true;
+}
+
+// s = the NB x NB tile of W at (r0, c0) (L2 loads: other CTAs wrote it)
+template <typename T>
+__device__ __forceinline__ void load_tile(const T* W, int64_t ld, int64_t r0, int64_t c0, T (*s)[NB + 1]) {
+#pragma unroll
+    for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
+        const int e = threadIdx.x + u * CC_THREADS;
+        s[e / NB][e % NB] = __ldcg(W + (r0 + e / NB) * ld + c0 + e % NB);
+    }
+}
+
+// sA <- sA Linv^T in place: sA[r][c] = sum_q A[r][q] Li[c][q] (Li lower triangular, zeros above
+// the diagonal).  Thread: row tid / 8, columns tid % 8 + 8 u.  Starts and ends with a barrier.
+template <typename T>
+__device__ __forceinline__ void times_linv_t(T (*sA)[NB + 1], const T (*sLi)[NB + 1]) {
+    const int tid = threadIdx.x;
     __syncthreads();
     const int r = tid >> 3, c = tid & 7;
     T acc[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
-        const T a = sOut[r][q];
+        const T a = sA[r][q];
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u] = fma(a, sLi[c + 8 * u][q], acc[u]);
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 4; ++u) sOut[r][c + 8 * u] = acc[u];
+    for (int u = 0; u < 4; ++u) sA[r][c + 8 * u] = acc[u];
     __syncthreads();
 }
 
 template <typename T>
 __device__ __forceinline__ void load_linv(const T* Linv, int kb, T (*sLi)[NB + 1]) {
-    const T* src = Linv + (int64_t)kb * NB * NB;
 #pragma unroll
     for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
         const int e = threadIdx.x + u * CC_THREADS;
-        sLi[e / NB][e % NB] = __ldcg(src + e);
+        sLi[e / NB][e % NB] = __ldcg(Linv + (int64_t)kb * NB * NB + e);
     }
     __syncthreads();
 }
@@ -227,7 +248,9 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
     __shared__ __align__(16) T sLi[NB][NB + 1];
     __shared__ __align__(16) T sP[NB][NB + 1];
     __shared__ __align__(16) T sQ[NB][NB + 1];
+    __shared__ __align__(16) T sD[NB][NB + 1];  // the next diagonal tile (owner only), before its update
     __shared__ __align__(16) CT sF[NB][NB + 1];
+    __shared__ __align__(16) CT sCol[2][NB];
     __shared__ T s_rinv[NB];
     __shared__ int s_ok, s_fail;
     if (block_should_exit(st, 0)) return;
@@ -238,7 +261,15 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
     int* fin = flags + nb + ntiles;
 
     if (tile_id(0, 0) % G == cta) {
-        if (!factor_diag<T, CT>(W, ld, 0, Linv, st, sF, s_rinv, &s_fail)) return;
+        load_tile<T>(W, ld, 0, 0, sD);
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
+            const int e = tid + u * CC_THREADS;
+            sF[e / NB][e % NB] = (CT)sD[e / NB][e % NB];
+        }
+        __syncthreads();
+        if (!factor_diag<T, CT>(W, ld, 0, Linv, st, sF, sQ, s_rinv, &s_fail, sCol)) return;
         block_publish(&diag[0]);
     }
     int last_p = -1;  // the largest column index among this CTA's tiles: no work after step last_p - 1
@@ -248,6 +279,14 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
         last_p = p > last_p ? p : last_p;
     }
     for (int j = 0; j + 1 < nb && j < last_p; ++j) {
+        // The owner of the next diagonal tile (j + 1, j + 1) is on the critical path: it fetches
+        // that tile and the panel tile (j + 1, j) before it waits for diagonal block j.
+        const bool diag_owner = tile_id(j + 1, j + 1) % G == cta;
+        if (diag_owner) {
+            if (j > 0 && !block_wait(&done[tile_id(j + 1, j)], 1, st, &s_ok, 0)) return;
+            load_tile<T>(W, ld, (int64_t)(j + 1) * NB, (int64_t)j * NB, sP);
+            load_tile<T>(W, ld, (int64_t)(j + 1) * NB, (int64_t)(j + 1) * NB, sD);
+        }
         if (!block_wait(&diag[j], 1, st, &s_ok, 0)) return;
         load_linv<T>(Linv, j, sLi);
         // pass 0: tiles of column j + 1 (diagonal first: it has the smallest id); pass 1: the rest
@@ -256,13 +295,18 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
                 int i, p;
                 tile_ij(t, i, p);
                 if (pass == 0 ? (p != j + 1) : (p <= j + 1)) continue;
-                if (j > 0) {
+                const bool is_next_diag = (i == p) && (p == j + 1);
+                if (j > 0 && !is_next_diag) {
                     if (!block_wait(&done[tile_id(i, j)], 1, st, &s_ok, 0)) return;
                     if (p != i && !block_wait(&done[tile_id(p, j)], 1, st, &s_ok, 0)) return;
                 }
                 const int64_t c0 = (int64_t)j * NB;
-                tile_times_linv_t<T>(W, ld, (int64_t)i * NB, c0, sLi, sP);
-                if (p != i) tile_times_linv_t<T>(W, ld, (int64_t)p * NB, c0, sLi, sQ);
+                if (!is_next_diag) {
+                    load_tile<T>(W, ld, (int64_t)i * NB, c0, sP);
+                    if (p != i) load_tile<T>(W, ld, (int64_t)p * NB, c0, sQ);
+                }
+                times_linv_t<T>(sP, sLi);
+                if (p != i) times_linv_t<T>(sQ, sLi);
                 const T(*pq)[NB + 1] = (p != i) ? sQ : sP;
                 // A[i, p] -= P_i P_p^T; thread: rows ty + 16 a, columns tx + 16 b
                 const int tx = tid & 15, ty = tid >> 4;
@@ -276,6 +320,20 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
                     acc[1][0] = fma(a1, b0, acc[1][0]);
                     acc[1][1] = fma(a1, b1, acc[1][1]);
                 }
+                if (is_next_diag) {
+                    // the updated tile goes straight to the factorisation (W gets L from it)
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            const int r = ty + 16 * a, c = tx + 16 * b;
+                            sF[r][c] = (CT)(sD[r][c] - acc[a][b]);
+                        }
+                    __syncthreads();
+                    if (!factor_diag<T, CT>(W, ld, p, Linv, st, sF, sQ, s_rinv, &s_fail, sCol)) return;
+                    block_publish(&diag[p]);
+                    continue;
+                }
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -285,31 +343,28 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
                         T* w = W + ((int64_t)i * NB + r) * ld + (int64_t)p * NB + c;
                         *w = __ldcg(w) - acc[a][b];
                     }
-                __syncthreads();  // sP / sQ are reused by the next tile
                 if (p == j + 1) {  // the tile's last update
-                    if (i == p) {
-                        __threadfence();
-                        __syncthreads();
-                        if (!factor_diag<T, CT>(W, ld, p, Linv, st, sF, s_rinv, &s_fail)) return;
-                        block_publish(&diag[p]);
-                    } else {
-                        block_publish(&done[t]);
-                    }
+                    block_publish(&done[t]);
+                } else {
+                    __syncthreads();  // sP / sQ are reused by the next tile
                 }
             }
         }
     }
     // every CTA has applied all its steps: scale the panels in place, L[i, p] = A[i, p] Linv_p^T
-    __threadfence();
     __syncthreads();
-    if (tid == 0) atomicAdd(fin, 1);
+    if (tid == 0) {
+        __threadfence();
+        atomicAdd(fin, 1);
+    }
     if (!block_wait(fin, G, st, &s_ok, 64)) return;
     for (int t = cta; t < ntiles; t += G) {
         int i, p;
         tile_ij(t, i, p);
         if (i == p) continue;
         load_linv<T>(Linv, p, sLi);
-        tile_times_linv_t<T>(W, ld, (int64_t)i * NB, (int64_t)p * NB, sLi, sP);
+        load_tile<T>(W, ld, (int64_t)i * NB, (int64_t)p * NB, sP);
+        times_linv_t<T>(sP, sLi);
 #pragma unroll
         for (int u = 0; u < NB * NB / CC_THREADS; ++u) {
             const int e = tid + u * CC_THREADS;
@@ -351,7 +406,8 @@ __global__ void __launch_bounds__(256) diag_inverse_kernel(const T* L, int64_t l
         if (threadIdx.x == 0) set_status(st, DFS_ERR_INVALID_ARG);
         return;
     }
-    invert_lower_32<T, T>(a, rinv, Linv + (int64_t)kb * NB * NB);
+    T* dst = Linv + (int64_t)kb * NB * NB;
+    invert_lower_32<T, T>(a, rinv, [&](int r, int c, T v) { dst[r * NB + c] = v; });
 }
 
 cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
@@ -386,8 +442,9 @@ static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* 
     auto kern = chol_coop_kernel<T, CT>;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CC_THREADS, 0)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // one CTA per SM (two for large n, where the trailing updates dominate); all resident
-    int G = sms * (per_sm >= 2 && ntiles >= 32 * sms ? 2 : 1);
+    // two CTAs per SM where they fit (all resident): a CTA waiting on an L2 round trip leaves the
+    // SM to the other
+    int G = sms * (per_sm >= 2 ? 2 : 1);
     if (G > ntiles) G = ntiles;
     if ((e = cudaMemsetAsync(flags, 0, cholesky_flag_bytes(n_pad), stream)) != cudaSuccess) return e;
     void* args[] = {&W, &ld, &nb, &Linv, &flags, &st};
