@@ -65,9 +65,12 @@ typedef enum {
     DFS_PREC_FP32 = 2,   /* plain FP32 path: FP32 FFMA Gram, FP32 solves, no refinement */
     DFS_PREC_BF16 = 3,   /* tcgen05 BF16 Gram (FP32 accumulate) + n-space refinement */
     DFS_PREC_TF32 = 4,   /* tcgen05 TF32 Gram (FP32 accumulate) + n-space refinement */
-    DFS_PREC_BF16X3 = 5  /* FP32 S only: S = H + L, H = bf16(S), L = bf16(S - H); tcgen05 BF16 Gram
+    DFS_PREC_BF16X3 = 5, /* FP32 S only: S = H + L, H = bf16(S), L = bf16(S - H); tcgen05 BF16 Gram
                             of W = H H^T + L H^T + (L H^T)^T (L L^T, ~2^-16 relative, dropped): the
                             work of three BF16 Grams, ~2^-16 relative accuracy; + refinement */
+    DFS_PREC_FP8 = 6     /* FP32 or BF16 S: each row scaled by a power of two r_i (max |s_ij| / r_i
+                            <= 448) and rounded to e4m3; tcgen05 kind::f8f6f4 Gram, W_ik scaled by
+                            r_i r_k; one extra read of S for the row maxima; + refinement */
 } dfs_precision;
 
 /* entries of dfs_info.ms and of dfs_step_times' output */
@@ -79,6 +82,13 @@ typedef enum {
                                    (FP32 and mixed paths; the FP64 path always does).  Off by
                                    default: GB300's FP64 rate makes each block ~4x slower, and
                                    the trailing updates are FP32 in any case */
+#define DFS_FLAG_CENTER 4       /* stochastic reconfiguration (Section 4): the S argument holds O, the
+                                   log-derivatives of the wave function, and the system solved is
+                                   Eq. 1 with S = (O - O_bar) / sqrt(n), O_bar the mean of O over the
+                                   n rows.  O is never modified or copied: W = P (O O^T / n) P +
+                                   lambda I with P = I - 1 1^T / n, b = P O v / sqrt(n), and each
+                                   pass over O reads P y / sqrt(n) (the triangular solves run on the
+                                   reduce + substitution kernels).  dfs_solve and dfs_solve_host. */
 
 typedef struct {
     int precision;   /* dfs_precision */

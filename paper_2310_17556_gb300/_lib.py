@@ -23,7 +23,7 @@ DFS_ERR_CUDA = 7
 DFS_ERR_UNSUPPORTED = 8
 
 DFS_F64, DFS_F32, DFS_BF16 = 0, 1, 2
-PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "bf16": 3, "tf32": 4, "bf16x3": 5}
+PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "bf16": 3, "tf32": 4, "bf16x3": 5, "fp8": 6}
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 
 # every entry point include/dfs.h declares
@@ -47,6 +47,7 @@ class dfs_info(C.Structure):
 DFS_STEP_TIMES = 8
 DFS_FLAG_STEP_TIMING = 1
 DFS_FLAG_FP64_PANEL = 2
+DFS_FLAG_CENTER = 4
 DFS_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 

@@ -43,9 +43,10 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def _opts(precision, max_iter, tol, timing=False, fp64_panel=False) -> dfs_options:
+def _opts(precision, max_iter, tol, timing=False, fp64_panel=False, center=False) -> dfs_options:
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     flags = (_lib.DFS_FLAG_STEP_TIMING if timing else 0) | (_lib.DFS_FLAG_FP64_PANEL if fp64_panel else 0)
+    flags |= _lib.DFS_FLAG_CENTER if center else 0
     return dfs_options(p, int(max_iter), float(tol), flags)
 
 
@@ -108,8 +109,10 @@ def dfs_reserve(n_max: int, m_max: int, k_max: int, precision="auto", handle: Ha
 
 def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
               max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
-              sync: bool = True, timing: bool = False, fp64_panel: bool = False):
+              sync: bool = True, timing: bool = False, fp64_panel: bool = False, center: bool = False):
     """Solve (S^T S + lam I) X^T = V^T for the k rows of V (Eq. 1, Algorithm 1).
+
+    center=True: S holds O and the system is Eq. 1 with Section 4's SR scores (O - O_bar)/sqrt(n).
 
     Returns (X, info) when sync is True (info = dict of dfs_info), else (X, None) with the work
     queued on the stream (read the status later with dfs_sync_info).
@@ -124,7 +127,7 @@ def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | No
         raise TypeError(f"V must be {vdt} for S of dtype {S.dtype}")
     if X is None:
         X = torch.empty((k, m), device=S.device, dtype=vdt)
-    opt = _opts(precision, max_iter, tol, timing, fp64_panel)
+    opt = _opts(precision, max_iter, tol, timing, fp64_panel, center)
     info = dfs_info()
     st = h.lib.dfs_solve(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k, _rows(V, "V"),
                          float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt), _stream(stream),
@@ -157,14 +160,15 @@ def dfs_step_times(handle: Handle | None = None) -> tuple[list[float], int]:
 
 
 def dfs_solve_host(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
-                   max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None):
+                   max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
+                   center: bool = False):
     """Same solve with S, V, X in host memory (pinned for full copy speed); copies inside the call."""
     h = handle or default_handle()
     n, m = S.shape
     k = V.shape[0]
     if X is None:
         X = torch.empty((k, m), dtype=V.dtype, pin_memory=S.is_pinned())
-    opt = _opts(precision, max_iter, tol)
+    opt = _opts(precision, max_iter, tol, center=center)
     info = dfs_info()
     st = h.lib.dfs_solve_host(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k,
                               _rows(V, "V"), float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt),

@@ -86,7 +86,7 @@ struct Plan {
     int pack = 0;   // tile packing done by the first S v pass: 0 none, 1 BF16, 2 TF32
     bool ns = false;  // n-space steps as one cluster kernel (nspace.cu)
     size_t off_W = 0, off_Linv = 0, off_P = 0, off_Rpart = 0, off_U2part = 0, off_R = 0, off_Z = 0, off_Y = 0,
-           off_U2 = 0, off_V = 0, off_bn2 = 0, off_Sp = 0, off_Cf = 0, total = 0;
+           off_U2 = 0, off_V = 0, off_bn2 = 0, off_Sp = 0, off_Cf = 0, off_Rs = 0, off_Yc = 0, off_Cg = 0, total = 0;
 };
 
 int tc_kind(int prec) {
@@ -94,6 +94,7 @@ int tc_kind(int prec) {
         case DFS_PREC_BF16: return 0;
         case DFS_PREC_TF32: return 1;
         case DFS_PREC_BF16X3: return 2;
+        case DFS_PREC_FP8: return 3;
         default: return -1;
     }
 }
@@ -115,6 +116,7 @@ dfs_status resolve_precision(dfs_handle h, int s_dtype, int prec, int* out) {
         case DFS_PREC_BF16:
         case DFS_PREC_TF32:
         case DFS_PREC_BF16X3:
+        case DFS_PREC_FP8:
             if (!gram_tc_supported(s_dtype, tc_kind(prec)))
                 return fail(h, DFS_ERR_UNSUPPORTED, "tensor-core Gram kind %d not available for S dtype %d",
                             tc_kind(prec), s_dtype);
@@ -160,7 +162,8 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     }
     p->pp = pass_make_plan((int)n, kq, s_dtype, h->num_sms, m, h->smem_optin);
     p->pgrid = pass_partial_rows(p->pp);
-    p->pack = (p->tensor && p->tc.packed) ? (p->tc.kind == 1 ? 2 : (p->tc.kind == 2 ? 3 : 1)) : 0;
+    p->pack = (p->tensor && p->tc.packed) ? (p->tc.kind == 1 ? 2 : (p->tc.kind == 2 ? 3 : (p->tc.kind == 3 ? 4 : 1)))
+                                          : 0;
     p->ns = nspace_slots((int)p->n_pad, kq, (int)es, h->smem_optin) >= 2;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -182,6 +185,9 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     p->off_bn2 = take(8 * 8);
     p->off_Sp = take(pack_bytes(s_dtype, p->pack, n, m));
     p->off_Cf = take(cholesky_flag_bytes(p->n_pad));
+    p->off_Rs = take(p->pack == 4 ? 2 * np * sizeof(float) : 0);
+    p->off_Yc = take(np * kq * 8);  // centred scores: P y / sqrt(n) for the passes
+    p->off_Cg = take(center_gram_scratch_doubles(np) * 8);
     p->total = off;
     return DFS_OK;
 }
@@ -236,11 +242,13 @@ dfs_status run_gram(dfs_handle h, const Plan& p, const void* S, int64_t lds, dou
     void* P = at<void>(h, p.off_P);
     if (p.tensor) {
         void* Sp = p.pack ? at<void>(h, p.off_Sp) : nullptr;
+        float* rs = p.pack == 4 ? at<float>(h, p.off_Rs) : nullptr;  // FP8 row scales, then their inverses
+        if (rs) DFS_CK(launch_row_scale(p.s_dtype, S, (int)p.n, (int)p.n_pad, p.m, lds, rs, h->dstat, stream));
         if (p.pack)
             DFS_CK(launch_sv_pack(p.pp, p.s_dtype, 1, p.pack, S, (int)p.n, p.m, lds, nullptr, p.m, 0,
-                                  at<double>(h, p.off_Rpart), Sp, h->dstat, stream));
+                                  at<double>(h, p.off_Rpart), Sp, h->dstat, stream, rs ? rs + p.n_pad : nullptr));
         DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, Sp, P, h->dstat, stream));
-        DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, n_out, lambda, W, ldw, stream));
+        DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, n_out, lambda, W, ldw, stream, rs));
     } else {
         DFS_CK(launch_gram_simt(p.s_dtype, p.f64, S, p.n, p.m, lds, p.nsplit, p.chunk, P, stream));
         DFS_CK(launch_gram_finalize(p.f64, p.f64, gram_simt_tile(p.f64), P, p.nsplit, p.n, n_out, lambda, W, ldw,
@@ -313,6 +321,10 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
     if ((s = make_plan(h, s_dtype, prec, n, m, (int)k, &p)) != DFS_OK) return s;
     if ((s = ensure_ws(h, p.total, stream)) != DFS_OK) return s;
     h->last_precision = prec;
+    // S = (O - O_bar) / sqrt(n) from the caller's O: n-space centring around unchanged passes over
+    // O (center.cu), on the reduce + triangular-solve kernels
+    const bool center = opt && (opt->flags & DFS_FLAG_CENTER);
+    if (center) p.ns = false;
 
     void* W = at<void>(h, p.off_W);
     void* Linv = at<void>(h, p.off_Linv);
@@ -323,6 +335,8 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
     double* Y = at<double>(h, p.off_Y);
     double* U2 = at<double>(h, p.off_U2);
     double* bn2 = at<double>(h, p.off_bn2);
+    double* Yc = at<double>(h, p.off_Yc);
+    double* Yp = center ? Yc : Y;  // the y the passes read
     const int ni = (int)n, npi = (int)p.n_pad, kq = p.kq;
     const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
 
@@ -354,9 +368,11 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         }
     }
     void* Sp = p.pack ? at<void>(h, p.off_Sp) : nullptr;
+    float* rs = p.pack == 4 ? at<float>(h, p.off_Rs) : nullptr;  // FP8 row scales, then their inverses
 
     DFS_CK(launch_status_reset(h->dstat, stream));
     DFS_CK(mark(0));
+    if (rs) DFS_CK(launch_row_scale(s_dtype, S, (int)ni, (int)p.n_pad, m, lds, rs, h->dstat, stream));
     for (int64_t q0 = 0; q0 < k; q0 += kq) {
         const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
         const void* Vg = static_cast<const char*>(V) + q0 * ldv * vs;
@@ -365,11 +381,13 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         // b = S v; the first group's pass also writes the packed tensor-core tiles of S
         if (q0 == 0) DFS_CK(mark(6));
         DFS_CK(launch_sv_pack(p.pp, s_dtype, kq, q0 == 0 ? p.pack : 0, S, ni, m, lds, Vg, ldv, kg, Rpart, Sp,
-                              h->dstat, stream));
+                              h->dstat, stream, rs ? rs + p.n_pad : nullptr));
         if (q0 == 0) DFS_CK(mark(7));
         if (!p.ns)
             DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.sv_grid, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z,
                                       nullptr, nullptr, h->dstat, 0, stream));
+        if (center)  // b = P (O v) / sqrt(n)
+            DFS_CK(launch_center_vec(p.f64, 0, ni, npi, kq, kg, R, nullptr, 0.0, Z, nullptr, h->dstat, 0, stream));
         if (q0 == 0) {
             // Algorithm 1 steps 1-2: W = S S^T + lambda I~ and its Cholesky factor
             void* P = at<void>(h, p.off_P);
@@ -379,11 +397,13 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
             else
                 DFS_CK(launch_gram_simt(p.s_dtype, p.f64, S, p.n, p.m, lds, p.nsplit, p.chunk, P, stream));
             DFS_CK(mark(2));
+            const double lam_g = center ? 0.0 : lambda;  // centring adds lambda after P G P / n
             if (p.tensor)
-                DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, p.n_pad, lambda, W, p.n_pad, stream));
+                DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, p.n_pad, lam_g, W, p.n_pad, stream, rs));
             else
-                DFS_CK(launch_gram_finalize(p.f64, p.f64, gram_simt_tile(p.f64), P, p.nsplit, p.n, p.n_pad, lambda,
+                DFS_CK(launch_gram_finalize(p.f64, p.f64, gram_simt_tile(p.f64), P, p.nsplit, p.n, p.n_pad, lam_g,
                                             W, p.n_pad, stream));
+            if (center) DFS_CK(launch_center_gram(p.f64, W, p.n_pad, ni, at<double>(h, p.off_Cg), lambda, stream));
             DFS_CK(mark(10));
             DFS_CK(launch_cholesky(p.f64, W, p.n_pad, p.n_pad, Linv, at<int>(h, p.off_Cf), h->dstat, stream,
                                    fp64_panel));
@@ -403,15 +423,18 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         const bool mark_pass = (q0 == 0);
         if (!p.tensor) {
             // x = (v - S^T y) / lambda
+            if (center) DFS_CK(launch_center_vec(p.f64, 1, ni, npi, kq, kg, nullptr, Y, 0.0, nullptr, Yc, h->dstat, 0, stream));
             if (mark_pass) DFS_CK(mark(8));
-            DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr,
+            DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Yp, kq, lambda, Xg, ldx, nullptr,
                                U2part, 0, h->dstat, 0, stream));
             if (mark_pass) DFS_CK(mark(9));
         } else {
             for (int it = 1; it <= max_iter; ++it) {
                 // x_0 = v / lambda for the first pass; afterwards x_{j-1} is read from X itself
+                if (center)
+                    DFS_CK(launch_center_vec(p.f64, 1, ni, npi, kq, kg, nullptr, Y, 0.0, nullptr, Yc, h->dstat, 1, stream));
                 if (mark_pass && it == 1) DFS_CK(mark(8));
-                DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, Rpart,
+                DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Yp, kq, lambda, Xg, ldx, Rpart,
                                    U2part, it == 1 ? 2 : 1, h->dstat, 1, stream));
                 if (mark_pass && it == 1) DFS_CK(mark(9));
                 if (p.ns) {
@@ -420,8 +443,12 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                                          p.pp.nparts, ni, kg, Y, lambda, nullptr, 0, R, Z, kq, U2part, U2,
                                          h->smem_optin, h->dstat, 1, stream));
                 } else {
-                    DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.nparts, ni, npi, kq, kg, Y, kq, lambda, R, kq, Z,
-                                              U2part, U2, h->dstat, 1, stream));
+                    // r = S u - lambda y; centred: P (O u) / sqrt(n) - lambda y
+                    DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.nparts, ni, npi, kq, kg, center ? nullptr : Y, kq,
+                                              lambda, R, kq, Z, U2part, U2, h->dstat, 1, stream));
+                    if (center)
+                        DFS_CK(launch_center_vec(p.f64, 0, ni, npi, kq, kg, R, Y, lambda, Z, nullptr, h->dstat, 1,
+                                                 stream));
                     DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
                     DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
                 }
@@ -429,8 +456,10 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                                              h->dstat, stream));
             }
             if (max_iter == 0) {
+                if (center)
+                    DFS_CK(launch_center_vec(p.f64, 1, ni, npi, kq, kg, nullptr, Y, 0.0, nullptr, Yc, h->dstat, 0, stream));
                 if (mark_pass) DFS_CK(mark(8));
-                DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Y, kq, lambda, Xg, ldx, nullptr,
+                DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Yp, kq, lambda, Xg, ldx, nullptr,
                                    U2part, 0, h->dstat, 0, stream));
                 if (mark_pass) DFS_CK(mark(9));
             }

@@ -1,26 +1,23 @@
 // Algorithm 1's Gram W = S S^T on the 5th-generation tensor cores (lower triangle), the O(n^2 m)
 // contraction that Section 2 of arXiv 2310.17556 names as the dominant cost.
 //
-// Work decomposition.  S (n x m, row-major, K = m contiguous) is cut into T = ceil(n/128) row
-// blocks, paired into T2 = ceil(T/2) super-rows.  The lower triangle of W is covered exactly once by
-// "quad units" (I2; J2), J2 <= I2, each two tcgen05.mma chains that share their B operand:
-//   off-diagonal (J2 < I2):  A0 = block 2 I2,   A1 = block 2 I2 + 1,   B = blocks 2 J2, 2 J2 + 1
-//                            D0 = A0 B^T (M = 128, N = 256),  D1 = A1 B^T (M = 128, N = 256)
-//   diagonal (J2 = I2):      the same blocks, but D0 = A0 A0^T (N = 128: the tile (2 I2, 2 I2 + 1)
-//                            is above the diagonal) and B is read from the A tiles themselves.
-// A super-row with a single block (odd T) drops A1.  One k-step stages A0, A1, B0, B1 (64 KB, or
-// 32 KB on the diagonal) for 8.4 MFLOP: 131 flop per staged byte, 1.5x the single-product unit,
-// which is what bounds this kernel (operand supply from L2, not the tensor pipe).
-// A unit of cost c_u (128 x 128 tile products per k-step: 4 off-diagonal, 3 diagonal, fewer
-// without A1) is split into c c_u tasks; task `slot` of a unit with g tasks takes the k-blocks
-// slot, slot + g, slot + 2g, ..., so every task costs the same and all CTAs advance through m at
-// the same rate (the tiles of a few k-blocks are live in L2 at any time).  Tasks are dealt
-// round-robin, in groups of consecutive tasks of one unit, to a persistent grid of at most one CTA
-// per SM.  A group's tasks keep separate FP32 accumulation chains (at most 1024 k-blocks each) and
-// are added in task order into one FP32 partial block (256 x 256: rows 0..127 from A0, 128..255
-// from A1); gram_tc_finalize sums the groups of each tile in a fixed order and adds lambda.
-// (The finalize reads only the quadrants a unit computes.)
-//
+// Work decomposition.  S (n x m, row-major, K = m contiguous) is cut into T 128-row blocks (T
+// rounded up to even with zero rows), paired into T / 2 super-rows.  The lower triangle of W is
+// covered by "quad units" (I2; J2), J2 <= I2, each two tcgen05.mma chains that share their B
+// operand:  A0 = block 2 I2, A1 = block 2 I2 + 1, B = blocks 2 J2, 2 J2 + 1 (on the diagonal B is
+// [A0 | A1] itself, read from the A tiles), D0 = A0 B^T and D1 = A1 B^T (M = 128, N = 256 each).
+// On the diagonal the tile (2 I2, 2 I2 + 1) of D0 lies above the diagonal and is not stored: every
+// unit then costs the same per k-step (4 tile products), so all tasks run at one rate.
+// One k-step stages A0, A1, B0, B1 (64 KB; 32 KB on the diagonal) for 8.4 MFLOP.
+// Every unit has the same c tasks; task (unit, slot) takes the k-blocks slot, slot + c, slot + 2c,
+// ...  A CTA runs a group of G consecutive slots of one unit and adds them into one FP32 partial
+// block (256 x 256: rows 0..127 from A0, 128..255 from A1).  Groups are numbered slot-group
+// major, gi = (slot / G) U + unit, and dealt round-robin to a persistent grid of at most one CTA
+// per SM: the CTAs of one wave hold every unit of a few slot groups, advance through m together,
+// and so touch a window of at most c k-blocks at a time; each operand tile is fetched from DRAM
+// about once and re-read from L2 by the other units that need it.  (A unit-major order would
+// sweep m once per unit in a wave and re-read every tile from DRAM several times.)
+// gram_tc_finalize sums the c / G partial blocks of each tile in group order and adds lambda.
 // Per CTA (192 threads, warp-specialised):
 //   warp 0     producer: per 128-byte k-block, the unit's 128-row tiles land in a 3-stage ring of
 //              64 KB stages (bulk copies of the packed tiles, or TMA boxes of S, 128-byte swizzle).
@@ -33,6 +30,9 @@
 // other roles stop, waits for TMA copies and MMAs in flight and frees TMEM before returning.
 //
 // Kinds: BF16 MMA (kind::f16) on BF16 tiles, TF32 MMA (kind::tf32) on FP32 / TF32 tiles, and
+// FP8: S scaled per row by a power of two r_i (so that max_j |s_ij| / r_i <= 448, exact) and
+// rounded to e4m3 (round to nearest even) by the S v pass; kind::f8f6f4 MMAs on 128-column
+// k-blocks; the finalize multiplies by r_i r_k (exact) before adding lambda.
 // BF16x3: FP32 S split as S = H + L (H = bf16(S), L = bf16(S - H), both round to nearest even), so
 // S S^T = H H^T + L H^T + (L H^T)^T + L L^T; the last term (relative size 2^-16) is dropped.  The
 // packed operand is the stacked 2 T_h-block matrix Z = [H; L] (T_h = T rounded up to even, so no
@@ -90,12 +90,6 @@ __host__ __device__ __forceinline__ void tc_unit_ij(int u, int& I2, int& J2) {
     I2 = i;
     J2 = u - i * (i + 1) / 2;
 }
-// 128 x 128 tile products per k-step of unit (I2, J2)
-__host__ __device__ __forceinline__ int tc_unit_cost(int I2, int J2, int T) {
-    const bool a1 = 2 * I2 + 1 < T;
-    if (J2 < I2) return a1 ? 4 : 2;
-    return a1 ? 3 : 1;
-}
 
 // The unit list: all (I2, J2), J2 <= I2 < T2, in row-major order when H2 = 0; for the stacked
 // BF16x3 operand (H2 > 0, T = 4 H2) the H H^T triangle (I2 < H2, row-major) followed by the L H^T
@@ -121,47 +115,27 @@ __host__ __device__ __forceinline__ int tc_unit_index(int I2, int J2, int H2) {
 struct TcTask {
     int I2, J2, slot, stride;
 };
-// Task t -> unit, slot and stride (unit u has c * cost(u) tasks, numbered consecutively).
-__host__ __device__ inline TcTask tc_task(int t, int T, int c, int H2) {
-    const int U = tc_num_units(T, H2);
-    TcTask k{0, 0, 0, 1};
-    int before = 0;
-    for (int u = 0; u < U; ++u) {
-        int I2, J2;
-        tc_unit_ij2(u, H2, I2, J2);
-        const int g = c * tc_unit_cost(I2, J2, T);
-        if (t < before + g) {
-            k.I2 = I2;
-            k.J2 = J2;
-            k.slot = t - before;
-            k.stride = g;
-            return k;
-        }
-        before += g;
-    }
+// Group gi -> unit gi mod U and slot group gi / U; its t-th task takes slot (gi / U) G + t, i.e.
+// the k-blocks slot, slot + c, slot + 2c, ...
+__host__ __device__ __forceinline__ TcTask tc_task(int gi, int t, int U, int c, int G, int H2) {
+    TcTask k;
+    tc_unit_ij2(gi % U, H2, k.I2, k.J2);
+    k.slot = (gi / U) * G + t;
+    k.stride = c;
     return k;
-}
-__host__ __device__ inline int tc_unit_first_task(int u, int T, int c, int H2) {
-    int before = 0;
-    for (int v = 0; v < u; ++v) {
-        int I2, J2;
-        tc_unit_ij2(v, H2, I2, J2);
-        before += c * tc_unit_cost(I2, J2, T);
-    }
-    return before;
 }
 
 __host__ __device__ __forceinline__ int tc_task_nk(const TcTask& k, int64_t nkb) {
     return k.slot < nkb ? (int)((nkb - 1 - k.slot) / k.stride + 1) : 0;
 }
 
-// KIND: 1 = TF32 MMA, 0 = BF16 MMA.  PACKED: 1 = operands from the packed 16 KB tiles written by
+// KIND: 1 = TF32 MMA, 0 = BF16 MMA, 2 = FP8 (e4m3) MMA.  PACKED: 1 = operands from the packed 16 KB tiles written by
 // the S v pass (one contiguous bulk copy per tile), 0 = TMA boxes straight from S (row-major,
 // used when S has short rows and no tile copy was made).
 template <int KIND, int PACKED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ Sp, int T, int H2, int c,
-               int ntasks, int G, int64_t nkb, int row_elems, float* __restrict__ part, DevStatus* st) {
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ Sp, int T, int H2, int U,
+               int c, int G, int64_t nkb, int row_elems, float* __restrict__ part, DevStatus* st) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* stage_mem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -198,14 +172,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
             bool issued[TC_STAGES];
             for (int s = 0; s < TC_STAGES; ++s) issued[s] = false;
             bool ok = true;
-            const int ngroups = ntasks / G;
+            const int ngroups = U * (c / G);
             for (int t = 0, gi = blockIdx.x; ok && gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
-                const TcTask tk = tc_task(gi * G + t, T, c, H2);
+                const TcTask tk = tc_task(gi, t, U, c, G, H2);
                 const int nk = tc_task_nk(tk, nkb);
                 const int i0 = 2 * tk.I2, j0 = 2 * tk.J2;
-                const bool a1 = i0 + 1 < T, diag = tk.J2 == tk.I2;
-                // tiles: A0, A1 (if any), and for off-diagonal units B0, B1
-                const uint32_t bytes = (uint32_t)TC_TILE_BYTES * ((a1 ? 2u : 1u) + (diag ? 0u : 2u));
+                const bool diag = tk.J2 == tk.I2;
+                // tiles: A0, A1, and for off-diagonal units B0, B1
+                const uint32_t bytes = (uint32_t)TC_TILE_BYTES * (diag ? 2u : 4u);
                 for (int kt = 0; kt < nk; ++kt) {
                     if (!tc::mbar_wait_bounded(&sm->empty[stage], phase ^ 1u, abort, TC_WAIT_NS)) {
                         ok = false;
@@ -217,8 +191,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
                     const int64_t kb = tk.slot + (int64_t)kt * tk.stride;
                     if (PACKED) {
                         tc::bulk_load(a, Sp + ((kb * T + i0) << 14), TC_TILE_BYTES, &sm->full[stage]);
-                        if (a1) tc::bulk_load(a + TC_TILE_BYTES, Sp + ((kb * T + i0 + 1) << 14), TC_TILE_BYTES,
-                                              &sm->full[stage]);
+                        tc::bulk_load(a + TC_TILE_BYTES, Sp + ((kb * T + i0 + 1) << 14), TC_TILE_BYTES,
+                                      &sm->full[stage]);
                         if (!diag) {
                             tc::bulk_load(b, Sp + ((kb * T + j0) << 14), TC_TILE_BYTES, &sm->full[stage]);
                             tc::bulk_load(b + TC_TILE_BYTES, Sp + ((kb * T + j0 + 1) << 14), TC_TILE_BYTES,
@@ -227,7 +201,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
                     } else {
                         const int32_t x = (int32_t)(kb * row_elems);
                         tc::tma_load_2d(a, &tmap, x, i0 * TC_BM, &sm->full[stage]);
-                        if (a1) tc::tma_load_2d(a + TC_TILE_BYTES, &tmap, x, (i0 + 1) * TC_BM, &sm->full[stage]);
+                        tc::tma_load_2d(a + TC_TILE_BYTES, &tmap, x, (i0 + 1) * TC_BM, &sm->full[stage]);
                         if (!diag) {
                             tc::tma_load_2d(b, &tmap, x, j0 * TC_BM, &sm->full[stage]);
                             tc::tma_load_2d(b + TC_TILE_BYTES, &tmap, x, (j0 + 1) * TC_BM, &sm->full[stage]);
@@ -253,19 +227,18 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            constexpr uint32_t fmt = KIND == 1 ? tc::kFmtTF32 : tc::kFmtBF16;
+            constexpr uint32_t fmt = KIND == 1 ? tc::kFmtTF32 : (KIND == 2 ? tc::kFmtE4M3 : tc::kFmtBF16);
             constexpr uint32_t idesc_wide = tc::instr_desc_f32acc(fmt, TC_BM, TC_BN);
-            constexpr uint32_t idesc_half = tc::instr_desc_f32acc(fmt, TC_BM, TC_BM);
             int stage = 0;
             uint32_t phase = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            const int ngroups = ntasks / G;
+            const int ngroups = U * (c / G);
             for (int t = 0, gi = blockIdx.x; ok && gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
-                const TcTask tk = tc_task(gi * G + t, T, c, H2);
+                const TcTask tk = tc_task(gi, t, U, c, G, H2);
                 const int nk = tc_task_nk(tk, nkb);
                 if (nk == 0) continue;  // the epilogue writes zeros for an empty task
-                const bool a1 = 2 * tk.I2 + 1 < T, diag = tk.J2 == tk.I2;
+                const bool diag = tk.J2 == tk.I2;
                 // the accumulators are free once the epilogue has read the previous task's
                 if (!tc::mbar_wait_bounded(&sm->acce, acc_phase ^ 1u, abort, TC_WAIT_NS)) {
                     ok = false;
@@ -285,13 +258,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
 #pragma unroll
                     for (int kk = 0; kk < TC_ROW_BYTES / 32; ++kk)
                         tc::mma_ss<KIND>(tmem, tc::sw128_kmajor_desc(a0 + kk * 32), tc::sw128_kmajor_desc(bb + kk * 32),
-                                         diag ? idesc_half : idesc_wide, (kt | kk) != 0);
-                    if (a1) {
+                                         idesc_wide, (kt | kk) != 0);
 #pragma unroll
-                        for (int kk = 0; kk < TC_ROW_BYTES / 32; ++kk)
-                            tc::mma_ss<KIND>(tmem + (uint32_t)TC_BN, tc::sw128_kmajor_desc(a1a + kk * 32),
-                                             tc::sw128_kmajor_desc(bb + kk * 32), idesc_wide, (kt | kk) != 0);
-                    }
+                    for (int kk = 0; kk < TC_ROW_BYTES / 32; ++kk)
+                        tc::mma_ss<KIND>(tmem + (uint32_t)TC_BN, tc::sw128_kmajor_desc(a1a + kk * 32),
+                                         tc::sw128_kmajor_desc(bb + kk * 32), idesc_wide, (kt | kk) != 0);
                     tc::mma_commit(&sm->empty[stage]);
                     if (++stage == TC_STAGES) {
                         stage = 0;
@@ -314,10 +285,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
         const int q = warp & 3;  // TMEM lane quarter accessible to this warp
         const int row = q * 32 + lane;
         uint32_t acc_phase = 0;
-        const int ngroups = ntasks / G;
+        const int ngroups = U * (c / G);
         for (int t = 0, gi = blockIdx.x; gi < ngroups; t = (t + 1 == G ? 0 : t + 1), gi += (t == 0 ? gridDim.x : 0)) {
-            const TcTask tk = tc_task(gi * G + t, T, c, H2);
-            const bool a1 = 2 * tk.I2 + 1 < T, diag = tk.J2 == tk.I2;
+            const TcTask tk = tc_task(gi, t, U, c, G, H2);
+            const bool diag = tk.J2 == tk.I2;
             // the group's tasks (separate FP32 accumulation chains) are added into one partial
             // block in task order: the first stores, the others add (read-modify-write)
             const bool first = (t == 0);
@@ -341,8 +312,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
             }
             acc_phase ^= 1u;
             tc::fence_after_sync();
-            for (int h = 0; h < (a1 ? 2 : 1); ++h) {
-                const int ncols = (h == 0 && diag) ? TC_BM : TC_BN;
+            for (int h = 0; h < 2; ++h) {
+                const int ncols = (h == 0 && diag) ? TC_BM : TC_BN;  // D0's right half lies above the diagonal
                 const uint32_t tbase = tmem + (uint32_t)(h * TC_BN) + ((uint32_t)(q * 32) << 16);
                 float* dst = blk + (size_t)(h * TC_BM + row) * TC_BN;
 #pragma unroll 1
@@ -383,8 +354,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
 // is block (I mod 2, J mod 2) of unit (I / 2, J / 2).  One CTA per 8 rows of a 128 x 128 tile;
 // thread = (row, 4 consecutive columns).
 __global__ void __launch_bounds__(256)
-gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int G, int64_t n, int64_t n_out, double lambda,
-                        float* __restrict__ W, int64_t ldw) {
+gram_tc_finalize_kernel(const float* __restrict__ part, int U, int c, int G, int64_t n, int64_t n_out, double lambda,
+                        float* __restrict__ W, int64_t ldw, const float* __restrict__ rscale) {
     constexpr int H2 = 0;
     int I, J;
     {
@@ -403,18 +374,18 @@ gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int G, int
     // accumulation error of a few 1e-6 to 1e-5, adding a handful of them in FP32 changes nothing
     // measurable, and FP64 adds are too slow on GB300 to be worth it here
     float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (gi < n && I < T) {
+    if (gi < n) {
         const int I2 = I / 2, J2 = J / 2;
         const int u = tc_unit_index(I2, J2, H2);
-        const int g = c * tc_unit_cost(I2, J2, T) / G;       // partial blocks (task groups) of the unit
-        const int b0 = tc_unit_first_task(u, T, c, H2) / G;
+        const int g = c / G;  // partial blocks (task groups) of the unit: u, u + U, u + 2U, ...
         const size_t off = (size_t)((I & 1) * TC_BM + r) * TC_BN + (J & 1) * TC_BM + c4;
-        const float* p0 = part + (size_t)b0 * TC_PART + off;
+        const float* p0 = part + (size_t)u * TC_PART + off;
+        const size_t gstride = (size_t)U * TC_PART;
         int q = 0;
         for (; q + 4 <= g; q += 4) {  // four loads in flight, added in block order
             float4 x[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) x[e] = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)(q + e) * TC_PART));
+            for (int e = 0; e < 4; ++e) x[e] = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)(q + e) * gstride));
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 v[0] += x[e].x;
@@ -424,7 +395,7 @@ gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int G, int
             }
         }
         for (; q < g; ++q) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)q * TC_PART));
+            const float4 x = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)q * gstride));
             v[0] += x.x;
             v[1] += x.y;
             v[2] += x.z;
@@ -437,20 +408,19 @@ gram_tc_finalize_kernel(const float* __restrict__ part, int T, int c, int G, int
         if (gj > gi) continue;
         float w;
         if (gi >= n || gj >= n) w = (gi == gj) ? 1.f : 0.f;
-        else w = v[e] + ((gi == gj) ? (float)lambda : 0.f);
+        else w = (rscale ? v[e] * (rscale[gi] * rscale[gj]) : v[e]) + ((gi == gj) ? (float)lambda : 0.f);
         W[gi * ldw + gj] = w;
     }
 }
 
 // FP32 sum, in group order, of the partial blocks of unit (I2, J2) at offset `off` of each block.
-__device__ __forceinline__ float4 tc_sum_groups(const float* __restrict__ part, int I2, int J2, int T, int H2, int c,
+__device__ __forceinline__ float4 tc_sum_groups(const float* __restrict__ part, int I2, int J2, int U, int H2, int c,
                                                 int G, size_t off) {
-    const int g = c * tc_unit_cost(I2, J2, T) / G;
-    const int b0 = tc_unit_first_task(tc_unit_index(I2, J2, H2), T, c, H2) / G;
-    const float* p0 = part + (size_t)b0 * TC_PART + off;
+    const int g = c / G;
+    const float* p0 = part + (size_t)tc_unit_index(I2, J2, H2) * TC_PART + off;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int q = 0; q < g; ++q) {
-        const float4 x = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)q * TC_PART));
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p0 + (size_t)q * U * TC_PART));
         v.x += x.x;
         v.y += x.y;
         v.z += x.z;
@@ -465,7 +435,7 @@ __device__ __forceinline__ float4 tc_sum_groups(const float* __restrict__ part, 
 // 128 x 128 tile (I, J): the transposed term (128 x 32 of Z tile (T_h + J, I)) is summed into
 // shared memory first, then thread (row, 4 x 4 columns) adds the two direct terms.
 __global__ void __launch_bounds__(256)
-gram_tc_finalize_x3_kernel(const float* __restrict__ part, int T, int H2, int c, int G, int64_t n, int64_t n_out,
+gram_tc_finalize_x3_kernel(const float* __restrict__ part, int U, int H2, int c, int G, int64_t n, int64_t n_out,
                            double lambda, float* __restrict__ W, int64_t ldw) {
     __shared__ float sT[TC_BM][33];
     int I, J;
@@ -488,7 +458,7 @@ gram_tc_finalize_x3_kernel(const float* __restrict__ part, int T, int H2, int c,
         if (live) {
             const int I2 = (Th + J) / 2, J2 = I / 2;
             const size_t off = (size_t)((J & 1) * TC_BM + kk) * TC_BN + (I & 1) * TC_BM + r0 + i4;
-            v = tc_sum_groups(part, I2, J2, 2 * Th, H2, c, G, off);
+            v = tc_sum_groups(part, I2, J2, U, H2, c, G, off);
         }
         sT[kk][i4] = v.x;
         sT[kk][i4 + 1] = v.y;
@@ -505,8 +475,8 @@ gram_tc_finalize_x3_kernel(const float* __restrict__ part, int T, int H2, int c,
         float4 hh = make_float4(0.f, 0.f, 0.f, 0.f), lh = hh;
         if (live && gi < n) {
             const size_t off = (size_t)((I & 1) * TC_BM + r0 + rr) * TC_BN + (J & 1) * TC_BM + cc;
-            hh = tc_sum_groups(part, I / 2, J / 2, 2 * Th, H2, c, G, off);
-            lh = tc_sum_groups(part, (Th + I) / 2, J / 2, 2 * Th, H2, c, G, off);
+            hh = tc_sum_groups(part, I / 2, J / 2, U, H2, c, G, off);
+            lh = tc_sum_groups(part, (Th + I) / 2, J / 2, U, H2, c, G, off);
         }
         const float a[4] = {hh.x + lh.x, hh.y + lh.y, hh.z + lh.z, hh.w + lh.w};
 #pragma unroll
@@ -540,15 +510,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // kind 0 = BF16 MMA (FP32 S is packed to BF16 tiles, BF16 S used directly or re-laid out),
 // kind 1 = TF32 MMA (FP32 S, packed to TF32 tiles or read directly),
-// kind 2 = BF16x3 (FP32 S packed to stacked H / L BF16 tiles).
+// kind 2 = BF16x3 (FP32 S packed to stacked H / L BF16 tiles),
+// kind 3 = FP8 (FP32 or BF16 S packed to row-scaled e4m3 tiles).
 int gram_tc_supported(int s_dtype, int kind) {
     if (kind == 1 || kind == 2) return s_dtype == DFS_F32;
+    if (kind == 3) return s_dtype == DFS_F32 || s_dtype == DFS_BF16;
     if (kind == 0) return s_dtype == DFS_F32 || s_dtype == DFS_BF16;
     return 0;
 }
 
 // elements per 128-byte k-block row: BF16 MMA -> 64, TF32 MMA -> 32
-static int tc_row_elems_kind(int kind) { return kind == 1 ? 32 : 64; }
+static int tc_row_elems_kind(int kind) { return kind == 1 ? 32 : (kind == 3 ? 128 : 64); }
 
 GramTcPlan gram_tc_plan(int s_dtype, int kind, int64_t n, int64_t m, int num_sms) {
     GramTcPlan p{};
@@ -556,45 +528,38 @@ GramTcPlan gram_tc_plan(int s_dtype, int kind, int64_t n, int64_t m, int num_sms
     // FP32 S always goes through packed tiles (BF16 needs the conversion; TF32 avoids the
     // address-translation cost of boxes spanning rows that are megabytes apart); BF16 S with
     // rows >= 1 MiB too.
-    p.packed = (s_dtype == DFS_F32) || ((int64_t)m * 2 >= (1 << 20));
-    p.n_tiles = (int)ceil_div(n, TC_BM);
+    p.packed = (s_dtype == DFS_F32) || ((int64_t)m * 2 >= (1 << 20)) || kind == 3;
+    p.n_tiles = (int)round_up(ceil_div(n, TC_BM), 2);  // even: every super-row has A0 and A1
     p.h2 = 0;
     if (kind == 2) {  // stacked [H; L]: T_h = T rounded up to even blocks of each
-        p.h2 = (p.n_tiles + 1) / 2;
+        p.h2 = p.n_tiles / 2;
         p.n_tiles = 4 * p.h2;
     }
-    const int T = p.n_tiles;
-    p.npairs = tc_num_units(T, p.h2);  // quad units
-    int C = 0;                          // tile products per k-step over all units
-    for (int u = 0; u < p.npairs; ++u) {
-        int I2, J2;
-        tc_unit_ij2(u, p.h2, I2, J2);
-        C += tc_unit_cost(I2, J2, T);
-    }
+    const int U = tc_num_units(p.n_tiles, p.h2);
+    p.npairs = U;
     const int64_t nkb = ceil_div(m, tc_row_elems_kind(kind));
-    // Tasks per cost unit: the smallest c that fills the grid evenly (at least 32 k-blocks per
-    // task).
-    // A task's FP32 accumulation chain (its k-blocks) is kept to at most 1024 k-blocks.
-    int c_min = 1;
-    while (c_min < 64 && nkb / c_min > 1024) c_min *= 2;
-    int best_c = c_min;
+    // Slot groups per unit w = c / G: the smallest w whose U w groups fill waves of num_sms CTAs to
+    // >= 95 % (else the best w up to 64).  Then G, the tasks per group, is the smallest that keeps
+    // each task's FP32 accumulation chain (nkb / c k-blocks) at most 1024 k-blocks long.
+    int best_w = 1;
     double best = -1.0;
-    for (int c = c_min; c <= 64; ++c) {
-        if (c > c_min && nkb / (4 * c) < 32) break;
-        const double tasks = (double)c * C;
-        const double eff = tasks / (std::ceil(tasks / num_sms) * num_sms);
-        if (eff > best + 0.02) {
+    for (int w = 1; w <= 64; ++w) {
+        if ((int64_t)w > nkb) break;
+        const double groups = (double)U * w;
+        const double eff = groups / (std::ceil(groups / num_sms) * num_sms);
+        if (eff > best + 1e-9) {
             best = eff;
-            best_c = c;
+            best_w = w;
         }
+        if (eff >= 0.95) break;
     }
-    p.c = best_c;
-    p.ntasks = best_c * C;
+    int G = 1;
+    while ((int64_t)best_w * G * 1024 < nkb) ++G;
+    p.c = best_w * G;
+    p.group = G;
+    p.ntasks = U * p.c;
     p.nkb = nkb;
-    // a CTA runs `group` consecutive tasks of one unit and adds them into one partial block (every
-    // unit has c * cost tasks, a multiple of the group)
-    p.group = (best_c % 4 == 0) ? 4 : ((best_c % 2 == 0) ? 2 : 1);
-    p.partial_bytes = (size_t)(p.ntasks / p.group) * TC_PART * sizeof(float);
+    p.partial_bytes = (size_t)(U * best_w) * TC_PART * sizeof(float);
     return p;
 }
 
@@ -623,7 +588,7 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int ngroups = plan.ntasks / plan.group;
+    const int ngroups = plan.npairs * (plan.c / plan.group);
     const int grid = ngroups < sms ? ngroups : sms;
     const unsigned char* sp = static_cast<const unsigned char*>(Sp);
     float* part = static_cast<float*>(P);
@@ -632,11 +597,14 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
         auto kern = gram_tc_kernel<K, PK>;                                                                          \
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES); \
         if (e != cudaSuccess) return e;                                                                             \
-        kern<<<grid, TC_THREADS, TC_SMEM_BYTES, stream>>>(map, sp, plan.n_tiles, plan.h2, plan.c, plan.ntasks,       \
+        kern<<<grid, TC_THREADS, TC_SMEM_BYTES, stream>>>(map, sp, plan.n_tiles, plan.h2, plan.npairs, plan.c,       \
                                                           plan.group, plan.nkb, re, part, st);                     \
         count_launch();                                                                                             \
     }
-    if (plan.kind == 1) {
+    if (plan.kind == 3) {
+        if (!plan.packed) return cudaErrorNotSupported;
+        DFS_TC_LAUNCH(2, 1)
+    } else if (plan.kind == 1) {
         if (plan.packed) DFS_TC_LAUNCH(1, 1) else DFS_TC_LAUNCH(1, 0)
     } else {
         if (plan.packed) DFS_TC_LAUNCH(0, 1) else DFS_TC_LAUNCH(0, 0)
@@ -646,17 +614,17 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
 }
 
 cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64_t n, int64_t n_out, double lambda,
-                                    void* W, int64_t ldw, cudaStream_t stream) {
+                                    void* W, int64_t ldw, cudaStream_t stream, const float* rscale) {
     const int T = (int)ceil_div(n_out, TC_BM);
     if (plan.kind == 2) {
         gram_tc_finalize_x3_kernel<<<dim3(T * (T + 1) / 2, TC_BM / 32), 256, 0, stream>>>(
-            static_cast<const float*>(P), plan.n_tiles, plan.h2, plan.c, plan.group, n, n_out, lambda,
+            static_cast<const float*>(P), plan.npairs, plan.h2, plan.c, plan.group, n, n_out, lambda,
             static_cast<float*>(W), ldw);
         count_launch();
     } else {
         gram_tc_finalize_kernel<<<dim3(T * (T + 1) / 2, TC_BM / 8), 256, 0, stream>>>(
-            static_cast<const float*>(P), plan.n_tiles, plan.c, plan.group, n, n_out, lambda,
-            static_cast<float*>(W), ldw);
+            static_cast<const float*>(P), plan.npairs, plan.c, plan.group, n, n_out, lambda,
+            static_cast<float*>(W), ldw, rscale);
         count_launch();
     }
     return cudaGetLastError();

@@ -33,7 +33,7 @@ GramTcPlan gram_tc_plan(int s_dtype, int kind, int64_t n, int64_t m, int num_sms
 cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, int64_t n, int64_t m, int64_t lds,
                            const void* Sp, void* P, DevStatus* st, cudaStream_t stream);
 cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64_t n, int64_t n_out, double lambda,
-                                    void* W, int64_t ldw, cudaStream_t stream);
+                                    void* W, int64_t ldw, cudaStream_t stream, const float* rscale = nullptr);
 
 // ---- Cholesky (cholesky.cu) ----
 // fp64_panel: factor the 32 x 32 diagonal blocks in FP64 (else in the storage type).
@@ -83,12 +83,15 @@ int pass_max_group(int n, int s_dtype, size_t smem_limit);
 int pass_grid(int n, int KQ, int s_dtype, int num_sms, int64_t m);
 PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit);
 int pass_partial_rows(const PassPlan& p);  // rows of the partial buffers (max of both grids)
-// pack: 0 none, 1 BF16 tiles, 2 TF32 tiles, 3 stacked BF16 H / L tiles (see sv_pack_kernel)
+// pack: 0 none, 1 BF16 tiles, 2 TF32 tiles, 3 stacked BF16 H / L tiles, 4 row-scaled e4m3 tiles
+// (rinv: the inverse row scales from launch_row_scale) (see sv_pack_kernel)
+cudaError_t launch_row_scale(int s_dtype, const void* S, int n, int n_pad, int64_t m, int64_t lds, float* rs,
+                             const DevStatus* st, cudaStream_t stream);
 int64_t pack_kblocks(int s_dtype, int pack, int64_t m);
 size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m);
 cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,
                            int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
-                           const DevStatus* st, cudaStream_t stream);
+                           const DevStatus* st, cudaStream_t stream, const float* rinv = nullptr);
 // dmode: 0 = no change measurement, 1 = also sum (X_new - X_old)^2 with X_old read from X,
 // 2 = same with X_old = V / lambda.  U2part holds 2 * kq doubles per CTA: sum U^2, sum dX^2.
 cudaError_t launch_pass(const PassPlan& plan, int s_dtype, int kq, const void* S, int n, int64_t m, int64_t lds,
@@ -99,6 +102,18 @@ cudaError_t launch_pass_reduce(int f64, const double* Rpart, int nparts, int n, 
                                const double* Y, int64_t ldy, double lambda, double* R, int64_t ldr, void* Rt,
                                const double* U2part, double* U2, const DevStatus* st, int honor_stop,
                                cudaStream_t stream);
+
+// ---- centred score matrices, S = (O - O_bar) / sqrt(n) (center.cu) ----
+// W (lower, rows < n, holding G = O O^T without lambda) <- P G P / n + lambda I; scratch holds
+// center_gram_scratch_doubles(n) doubles.
+cudaError_t launch_center_gram(int f64, void* W, int64_t ld, int n, double* scratch, double lambda,
+                               cudaStream_t stream);
+size_t center_gram_scratch_doubles(int64_t n);
+// mode 0: R <- P R / sqrt(n) - lambda Y (Y may be null), Z <- R; mode 1: Yc <- P Y / sqrt(n).
+// R, Y, Yc, Z: n_pad x KQ row-major (KQ <= 8).
+cudaError_t launch_center_vec(int f64, int mode, int n, int n_pad, int KQ, int k, double* R, const double* Y,
+                              double lambda, void* Z, double* Yc, const DevStatus* st, int honor_stop,
+                              cudaStream_t stream);
 
 // ---- refinement control and small utilities (refine.cu, util.cu) ----
 cudaError_t launch_status_reset(DevStatus* st, cudaStream_t stream);

@@ -31,6 +31,8 @@
 // contiguous region of L2.
 // Each CTA finally writes its FP64 row sums (and the two per-RHS sums) to partial buffers that
 // pass_reduce adds in a fixed order.
+#include <cuda_fp8.h>
+
 #include "kernels.cuh"
 
 namespace dfs {
@@ -67,6 +69,18 @@ __device__ __forceinline__ void split_bf16x4(float x0, float x1, float x2, float
     wl.y = *reinterpret_cast<const uint32_t*>(&l23);
 }
 
+// Four floats -> four e4m3 bytes (round to nearest even, saturating), lowest column first.
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return (lo & 0xffffu) | (hi << 16);
+}
+// Byte offset, within a 128-row x 128-byte swizzled tile, of `bytes_per_lane` e4m3 values of row
+// r that start at column `col` (a multiple of bytes_per_lane) of the tile's 128 columns.
+__device__ __forceinline__ int fp8_tile_offset(int r, int col) {
+    return r * 128 + ((((col >> 4) ^ (r & 7))) << 4) + (col & 15);
+}
+
 // Fold the FP32 per-row sums of the rows this thread owns into FP64.
 template <typename TA, int KQ>
 __device__ __forceinline__ void fold_rows(double* Rs64, TA* Rs32, int first, int step, int n) {
@@ -79,18 +93,101 @@ __device__ __forceinline__ void fold_rows(double* Rs64, TA* Rs32, int first, int
 }
 
 // ------------------------------------------------------------------------------------------
+// Per-row power-of-two scales of the FP8 Gram operand: r_i = 2^e, the smallest power of two with
+// max_j |s_ij| <= 448 r_i (448 is the largest finite e4m3 value), so s_ij / r_i is exact and never
+// saturates; r_i = 1 for a row of zeros and for the padding rows [n, n_pad); r_i = NaN for a row
+// holding Inf or NaN, so the NaN reaches the Cholesky's check through the Gram.
+// rs[0, n_pad) = r_i, rs[n_pad, 2 n_pad) = 1 / r_i.  One CTA of 256 threads per row.
+template <typename TS>
+__global__ void __launch_bounds__(256)
+row_scale_kernel(const TS* __restrict__ S, int n, int n_pad, int64_t m, int64_t lds, float* __restrict__ rs,
+                 const DevStatus* st) {
+    constexpr int VEC = Vec16<TS>::N;
+    __shared__ float s_max[8];
+    __shared__ int s_bad[8];
+    if (block_should_exit(st, 0)) return;
+    const int i = blockIdx.x, tid = threadIdx.x;
+    if (i >= n) {
+        if (tid == 0) rs[i] = rs[n_pad + i] = 1.f;
+        return;
+    }
+    const TS* row = S + (int64_t)i * lds;
+    float amax = 0.f;
+    int bad = 0;
+    for (int64_t j = (int64_t)tid * VEC; j < m; j += 256 * VEC) {
+        float v[VEC];
+        if (j + VEC <= m) {
+            load16_stream<TS, float>(row + j, v);
+        } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) v[e] = (j + e < m) ? load1<TS, float>(row + j + e) : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const float a = fabsf(v[e]);
+            bad |= !(a <= 3.4028235e38f);
+            amax = fmaxf(amax, a);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((tid & 31) == 0) {
+        s_max[tid >> 5] = amax;
+        s_bad[tid >> 5] = bad;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < 8; ++w) {
+            amax = fmaxf(amax, s_max[w]);
+            bad |= s_bad[w];
+        }
+        float r = 1.f;
+        if (bad) {
+            r = __int_as_float(0x7fc00000);
+        } else if (amax > 0.f) {
+            int e;
+            const float f = frexpf(amax / 448.f, &e);  // amax / 448 = f 2^e, f in [0.5, 1)
+            if (f == 0.5f) --e;
+            r = ldexpf(1.f, e < -126 ? -126 : e);
+        }
+        rs[i] = r;
+        rs[n_pad + i] = 1.f / r;
+    }
+}
+
+cudaError_t launch_row_scale(int s_dtype, const void* S, int n, int n_pad, int64_t m, int64_t lds, float* rs,
+                             const DevStatus* st, cudaStream_t stream) {
+    if (s_dtype == DFS_F32)
+        row_scale_kernel<float><<<n_pad, 256, 0, stream>>>(static_cast<const float*>(S), n, n_pad, m, lds, rs, st);
+    else if (s_dtype == DFS_BF16)
+        row_scale_kernel<__nv_bfloat16>
+            <<<n_pad, 256, 0, stream>>>(static_cast<const __nv_bfloat16*>(S), n, n_pad, m, lds, rs, st);
+    else
+        return cudaErrorInvalidValue;
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
 // R = S V, optionally packing S into tensor-core tiles.
 //   PACK 0: none; 1: BF16 tiles (64-column k-blocks); 2: TF32 tiles (32-column k-blocks);
 //   3 (FP32 S): BF16 H = bf16(s) in row block I and L = bf16(s - H) in row block n_rows / 128 + I,
-//   2 n_rows / 128 tiles per k-block (the stacked operand of the BF16x3 Gram).
+//   2 n_rows / 128 tiles per k-block (the stacked operand of the BF16x3 Gram);
+//   4: e4m3(s / r_i) with the row's power-of-two scale (rinv[i] = 1 / r_i), 128-column k-blocks:
+//   a 64-column strip s fills half (s mod 2) of k-block s / 2, and the strip count is rounded up
+//   to whole k-blocks so the tail half is written with zeros.
 template <typename TS, int KQ, int PACK>
 __global__ void __launch_bounds__(PASS_THREADS)
 sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds,
                const typename PassTypes<TS>::TA* __restrict__ V, int64_t ldv, int k, double* __restrict__ Rpart,
-               unsigned char* __restrict__ Sp, int64_t nkb, const DevStatus* st) {
+               unsigned char* __restrict__ Sp, int64_t nkb, const DevStatus* st, const float* __restrict__ rinv) {
     using TA = typename PassTypes<TS>::TA;
     constexpr int VEC = Vec16<TS>::N;
-    constexpr int LPR = ((PACK == 1 || PACK == 3) && sizeof(TS) == 4) ? 16 : 8;  // lanes per row
+    constexpr int LPR = ((PACK == 1 || PACK == 3 || PACK == 4) && sizeof(TS) == 4) ? 16 : 8;  // lanes per row
+    static_assert(PACK != 4 || sizeof(TS) <= 4, "FP8 tiles from FP32 or BF16 S");
     static_assert(PACK != 3 || sizeof(TS) == 4, "the H / L split needs FP32 S");
     constexpr int W = LPR * VEC;
     constexpr int RPW = 32 / LPR;
@@ -107,7 +204,7 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
         Rs32[e] = (TA)0;
     }
     __syncthreads();
-    const int64_t nstrips = ceil_div(m, W);
+    const int64_t nstrips = PACK == 4 ? 2 * ceil_div(m, 2 * W) : ceil_div(m, W);
     int since_fold = 0;
     for (int64_t s = blockIdx.x; s < nstrips; s += gridDim.x) {
         const int64_t j0 = s * W;
@@ -149,7 +246,20 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
                         const int r = i & 127;
                         constexpr int NTM = PACK == 3 ? 2 : 1;
                         unsigned char* tile = Sp + (((int64_t)s * (NTM * (n_rows >> 7)) + (i >> 7)) << 14) + r * 128;
-                        if constexpr (PACK == 3) {
+                        if constexpr (PACK == 4) {
+                            unsigned char* t8 = Sp + (((int64_t)(s >> 1) * (n_rows >> 7) + (i >> 7)) << 14);
+                            const float q = i < n ? __ldg(rinv + i) : 0.f;
+                            const int col = (int)(s & 1) * 64 + cq * VEC;
+                            if constexpr (VEC == 4) {
+                                *reinterpret_cast<uint32_t*>(t8 + fp8_tile_offset(r, col)) =
+                                    e4m3x4(sv[u][0] * q, sv[u][1] * q, sv[u][2] * q, sv[u][3] * q);
+                            } else {
+                                uint2 w;
+                                w.x = e4m3x4(sv[u][0] * q, sv[u][1] * q, sv[u][2] * q, sv[u][3] * q);
+                                w.y = e4m3x4(sv[u][4] * q, sv[u][5] * q, sv[u][6] * q, sv[u][7] * q);
+                                *reinterpret_cast<uint2*>(t8 + fp8_tile_offset(r, col)) = w;
+                            }
+                        } else if constexpr (PACK == 3) {
                             uint2 wh, wl;
                             split_bf16x4(sv[u][0], sv[u][1], sv[u][2], sv[u][3], wh, wl);
                             const int off = (((cq >> 1) ^ (r & 7)) << 4) | ((cq & 1) << 3);
@@ -218,7 +328,7 @@ template <int KQ, int PACK>
 __global__ void __launch_bounds__(PASS_THREADS, 1)
 sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds, const float* __restrict__ V,
                int64_t ldv, int k, double* __restrict__ Rpart, unsigned char* __restrict__ Sp, int64_t nkb,
-               const DevStatus* st) {
+               const DevStatus* st, const float* __restrict__ rinv) {
     constexpr int LPR = 16, W = 64, SWEEP = PASS_THREADS / LPR, NSUBMAX = SVR_MAXNR / SVR_TPS;
     extern __shared__ __align__(16) unsigned char smem[];
     uint4* ring = reinterpret_cast<uint4*>(smem);
@@ -230,7 +340,7 @@ sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_
     const int NR = (n_rows + SWEEP - 1) / SWEEP;
     const int nsub = (NR + SVR_TPS - 1) / SVR_TPS;
     for (int e = tid; e < n * KQ; e += PASS_THREADS) Rs64[e] = 0.0;
-    const int64_t nstrips = ceil_div(m, W);
+    const int64_t nstrips = PACK == 4 ? 2 * ceil_div(m, 2 * W) : ceil_div(m, W);  // FP8: whole k-blocks
     const int64_t my_strips = (int64_t)blockIdx.x < nstrips ? (nstrips - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t nitems = my_strips * nsub;
     auto issue = [&](int64_t g) {
@@ -310,7 +420,15 @@ sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_
 #pragma unroll
                     for (int q = 0; q < KQ; ++q)
                         acc[q][t] = fmaf(x3, vv[q][3], fmaf(x2, vv[q][2], fmaf(x1, vv[q][1], fmaf(x0, vv[q][0], acc[q][t]))));
-                    if constexpr (PACK == 3) {
+                    if constexpr (PACK == 4) {
+                        const int i = row0 + t * SWEEP;
+                        if (i < n_rows) {
+                            unsigned char* t8 = Sp + (((int64_t)(s >> 1) * (n_rows >> 7) + (i >> 7)) << 14);
+                            const float q = i < n ? __ldg(rinv + i) : 0.f;
+                            *reinterpret_cast<uint32_t*>(t8 + fp8_tile_offset(i & 127, (int)(s & 1) * 64 + cq * 4)) =
+                                e4m3x4(x0 * q, x1 * q, x2 * q, x3 * q);
+                        }
+                    } else if constexpr (PACK == 3) {
                         const int i = row0 + t * SWEEP;
                         if (i < n_rows) {
                             const int r = i & 127;
@@ -805,28 +923,58 @@ cudaError_t launch_pass(const PassPlan& plan, int s_dtype, int kq, const void* S
 template <typename TS, int KQ, int PACK>
 static cudaError_t launch_sv_t(int grid, const void* S, int n, int n_rows, int64_t m, int64_t lds, const void* V,
                                int64_t ldv, int k, double* Rpart, void* Sp, int64_t nkb, const DevStatus* st,
-                               cudaStream_t stream, int s_dtype) {
+                               cudaStream_t stream, int s_dtype, const float* rinv) {
     using TA = typename PassTypes<TS>::TA;
     const size_t smem = sv_smem_bytes(n, KQ, s_dtype);
     auto kern = sv_pack_kernel<TS, KQ, PACK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, PASS_THREADS, smem, stream>>>(static_cast<const TS*>(S), n, n_rows, m, lds, static_cast<const TA*>(V),
-                                               ldv, k, Rpart, static_cast<unsigned char*>(Sp), nkb, st);
+                                               ldv, k, Rpart, static_cast<unsigned char*>(Sp), nkb, st, rinv);
     count_launch();
     return cudaGetLastError();
 }
 
+// S v launches for KQ right-hand sides: every (S dtype, packing) pair that exists
+template <int KQ>
+static cudaError_t launch_sv_kq(int grid, int s_dtype, int pack, const void* S, int n, int n_rows, int64_t m,
+                                int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp, int64_t nkb,
+                                const DevStatus* st, cudaStream_t stream, const float* rinv) {
+#define DFS_SV(TS, PK) \
+    launch_sv_t<TS, KQ, PK>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream, s_dtype, rinv)
+    if (s_dtype == DFS_F32) {
+        switch (pack) {
+            case 0: return DFS_SV(float, 0);
+            case 1: return DFS_SV(float, 1);
+            case 2: return DFS_SV(float, 2);
+            case 3: return DFS_SV(float, 3);
+            case 4: return DFS_SV(float, 4);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (s_dtype == DFS_BF16) {
+        switch (pack) {
+            case 0: return DFS_SV(__nv_bfloat16, 0);
+            case 1: return DFS_SV(__nv_bfloat16, 1);
+            case 4: return DFS_SV(__nv_bfloat16, 4);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (s_dtype == DFS_F64 && pack == 0) return DFS_SV(double, 0);
+#undef DFS_SV
+    return cudaErrorInvalidValue;
+}
+
 int64_t pack_kblocks(int s_dtype, int pack, int64_t m) {
-    const int width = (pack == 2) ? 32 : 64;  // elements per 128-byte tile row (TF32 / BF16)
+    const int width = (pack == 2) ? 32 : (pack == 4 ? 128 : 64);  // elements per 128-byte tile row
     (void)s_dtype;
     return ceil_div(m, width);
 }
 
-// 128-row tiles per k-block: T, or 2 T_h (T rounded up to even) for the stacked H / L operand
+// 128-row tiles per k-block: T rounded up to even, twice that for the stacked H / L operand
 static int64_t pack_tiles_per_kblock(int pack, int64_t n) {
-    const int64_t T = ceil_div(n, 128);
-    return pack == 3 ? 2 * round_up(T, 2) : T;
+    const int64_t T = round_up(ceil_div(n, 128), 2);
+    return pack == 3 ? 2 * T : T;
 }
 
 size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m) {
@@ -837,71 +985,51 @@ size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m) {
 template <int KQ, int PACK>
 static cudaError_t launch_sv_ring_t(int grid, const void* S, int n, int n_rows, int64_t m, int64_t lds, const void* V,
                                     int64_t ldv, int k, double* Rpart, void* Sp, int64_t nkb, const DevStatus* st,
-                                    cudaStream_t stream) {
+                                    cudaStream_t stream, const float* rinv) {
     const size_t smem = (size_t)SVR_SLOTS * SVR_TPS * PASS_THREADS * 16 + (size_t)n * KQ * 8;
     auto kern = sv_ring_kernel<KQ, PACK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, PASS_THREADS, smem, stream>>>(static_cast<const float*>(S), n, n_rows, m, lds,
                                                static_cast<const float*>(V), ldv, k, Rpart,
-                                               static_cast<unsigned char*>(Sp), nkb, st);
+                                               static_cast<unsigned char*>(Sp), nkb, st, rinv);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,
                            int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
-                           const DevStatus* st, cudaStream_t stream) {
+                           const DevStatus* st, cudaStream_t stream, const float* rinv) {
     if (pack == 3 && s_dtype != DFS_F32) return cudaErrorInvalidValue;
-    // packed rows: the 128-row blocks of S (for the stacked H / L operand: an even number of them)
-    const int n_rows = pack ? (int)round_up(n, pack == 3 ? 256 : 128) : n;
+    if (pack == 4 && (rinv == nullptr || s_dtype == DFS_F64)) return cudaErrorInvalidValue;
+    // packed rows: an even number of 128-row blocks (the Gram's units pair blocks), zero past n
+    const int n_rows = pack ? (int)round_up(n, 256) : n;
     const int64_t nkb = pack ? pack_kblocks(s_dtype, pack, m) : 0;
     const int grid = plan.sv_grid;
     // the streaming form: FP32 S, no packing or BF16 (H / L) tiles, up to 1024 rows and 2 RHS
     if (s_dtype == DFS_F32 && pack != 2 && n_rows <= SVR_MAXNR * (PASS_THREADS / 16) && kq <= 2) {
-#define DFS_SVR(KQ)                                                                                               \
-    return pack == 3   ? launch_sv_ring_t<KQ, 3>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream) \
-           : pack == 1 ? launch_sv_ring_t<KQ, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream) \
-                       : launch_sv_ring_t<KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream);
+#define DFS_SVR(KQ)                                                                                      \
+    switch (pack) {                                                                                        \
+        case 4: return launch_sv_ring_t<KQ, 4>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,   \
+                                               stream, rinv);                                              \
+        case 3: return launch_sv_ring_t<KQ, 3>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,   \
+                                               stream, rinv);                                              \
+        case 1: return launch_sv_ring_t<KQ, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,   \
+                                               stream, rinv);                                              \
+        default: return launch_sv_ring_t<KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,  \
+                                                stream, rinv);                                             \
+    }
         if (kq == 1) DFS_SVR(1)
         DFS_SVR(2)
 #undef DFS_SVR
     }
-#define DFS_SV_CASE(KQ)                                                                                           \
-    case KQ:                                                                                                      \
-        if (s_dtype == DFS_F32) {                                                                                 \
-            if (pack == 1)                                                                                        \
-                return launch_sv_t<float, KQ, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,       \
-                                                 stream, s_dtype);                                                \
-            if (pack == 2)                                                                                        \
-                return launch_sv_t<float, KQ, 2>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,       \
-                                                 stream, s_dtype);                                                \
-            if (pack == 3)                                                                                        \
-                return launch_sv_t<float, KQ, 3>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,       \
-                                                 stream, s_dtype);                                                \
-            return launch_sv_t<float, KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream,   \
-                                             s_dtype);                                                            \
-        }                                                                                                         \
-        if (s_dtype == DFS_BF16) {                                                                                \
-            if (pack == 1)                                                                                        \
-                return launch_sv_t<__nv_bfloat16, KQ, 1>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb,   \
-                                                         st, stream, s_dtype);                                    \
-            return launch_sv_t<__nv_bfloat16, KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st,   \
-                                                     stream, s_dtype);                                            \
-        }                                                                                                         \
-        if (s_dtype == DFS_F64 && pack == 0)                                                                      \
-            return launch_sv_t<double, KQ, 0>(grid, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream,  \
-                                              s_dtype);                                                           \
-        return cudaErrorInvalidValue;
-    switch (kq) {
-        DFS_SV_CASE(1)
-        DFS_SV_CASE(2)
-        DFS_SV_CASE(4)
-        DFS_SV_CASE(8)
-        default:
-            return cudaErrorInvalidValue;
+switch (kq) {
+        case 1: return launch_sv_kq<1>(grid, s_dtype, pack, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream, rinv);
+        case 2: return launch_sv_kq<2>(grid, s_dtype, pack, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream, rinv);
+        case 4: return launch_sv_kq<4>(grid, s_dtype, pack, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream, rinv);
+        case 8: return launch_sv_kq<8>(grid, s_dtype, pack, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, nkb, st, stream, rinv);
+        default: return cudaErrorInvalidValue;
     }
-#undef DFS_SV_CASE
 }
 
 cudaError_t launch_pass_reduce(int f64, const double* Rpart, int nparts, int n, int n_out, int KQ, int k,

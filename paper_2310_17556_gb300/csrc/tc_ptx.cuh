@@ -117,12 +117,19 @@ __host__ __device__ constexpr uint32_t instr_desc_f32acc(uint32_t ab_format, uin
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 constexpr uint32_t kFmtF16 = 0, kFmtBF16 = 1, kFmtTF32 = 2;
+constexpr uint32_t kFmtE4M3 = 0;  // operand format field of kind::f8f6f4
 
 // ---- tcgen05 ----------------------------------------------------------------------------------
-template <int KIND>  // 0 = kind::f16 (bf16/f16 inputs), 1 = kind::tf32
+template <int KIND>  // 0 = kind::f16 (bf16/f16 inputs), 1 = kind::tf32, 2 = kind::f8f6f4
 __device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate) {
-    if constexpr (KIND == 1) {
+    if constexpr (KIND == 2) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    } else if constexpr (KIND == 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"

@@ -262,6 +262,99 @@ def test_bf16x3_gram_cross_terms(n, m):
     assert np.abs(np64(Wb) - Wr)[lo].max() / np.abs(Wr).max() >= 4e-4
 
 
+def _fp8_gram_model(S64, lam):
+    """W of the FP8 Gram as the arithmetic defines it, computed independently of the kernels:
+    r_i = the smallest power of two with max_j |s_ij| <= 448 r_i, q = e4m3(s / r_i) (round to
+    nearest even; torch's float8_e4m3fn cast), W = r_i r_k sum_j q_ij q_kj + lam I, in FP64."""
+    amax = np.abs(S64).max(axis=1)
+    f, e = np.frexp(amax / 448.0)
+    e = np.where(f == 0.5, e - 1, e)
+    r = np.where(amax > 0, np.ldexp(1.0, e), 1.0)
+    q = torch.from_numpy(S64 / r[:, None]).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    return (r[:, None] * (q @ q.T)) * r[None, :] + lam * np.eye(S64.shape[0]), q, r
+
+
+@pytest.mark.parametrize("dtype,n,m", [(torch.float32, 300, 20000), (torch.float32, 1024, 8192),
+                                       (torch.float32, 77, 100), (torch.bfloat16, 384, 12000),
+                                       (torch.float32, 1500, 3000)])
+def test_fp8_gram_step_matches_quantisation_model(dtype, n, m):
+    S = wl.gaussian(n, m, seed=201, device=dev(), dtype=torch.float32)
+    S[1] *= 1e-3          # rows of very different scale get their own power of two
+    S[2] *= 37.0
+    S[3] = 0.0            # a zero row: scale 1, zeros in W
+    S = aligned(S.to(dtype))
+    lam = 0.25
+    W = dfs.dfs_gram(S, lam, precision="fp8")
+    S64 = np64(S)
+    Wm, q, r = _fp8_gram_model(S64, lam)
+    lo = np.tril(np.ones((n, n), bool))
+    # the MMAs multiply e4m3 values exactly; the tensor core's FP32 accumulation is the only
+    # difference from the model: at most 2^-23 per accumulating step (K = 32), relative to
+    # r_i r_k sum |q_i q_k|
+    # r_i r_k sum |q_i q_k|, plus the FP32 rounding of W itself (2^-24 |W|: it holds lambda on the
+    # diagonal, which dwarfs the small rows' sums there)
+    ref = (r[:, None] * (np.abs(q) @ np.abs(q).T)) * r[None, :]
+    err = ((np.abs(np64(W) - Wm) - 2.0 ** -24 * np.abs(Wm)) / np.maximum(ref, 1e-300))[lo]
+    assert err.max() <= m / 32 * 2.0 ** -23 + 1e-6, err.max()
+    assert np.all(np64(W)[~lo] == 0.0)
+    # and against the exact Gram, the e4m3 rounding bound: |s - r q| <= 2^-4 |s| + 2^-10 r
+    Wr = oracle.gram(S64, lam)
+    bound = 2 * 2.0 ** -4 + 2.0 ** -8
+    assert np.abs(np64(W) - Wr)[lo].max() <= bound * np.abs(Wr).max()
+
+
+def _sr_inputs(n, m, k, seed, dtype=torch.float32):
+    """O = Gaussian scores plus a per-column offset of the same size as their spread (so the
+    centring matters), V Gaussian."""
+    O = wl.gaussian(n, m, seed=seed, device=dev())
+    g = torch.Generator(device=dev()).manual_seed(seed + 1)
+    O += torch.randn(m, generator=g, device=dev())[None, :] / math.sqrt(n)
+    return aligned(O.to(dtype)), wl.rhs(m, k, seed=seed + 2, device=dev())
+
+
+@pytest.mark.parametrize("prec,n,m,k,lam", [("fp32", 300, 20000, 2, 1e-2), ("bf16", 1024, 65536, 1, 1e-3),
+                                            ("bf16", 129, 5000, 3, 1e-2), ("tf32", 257, 33336, 2, 1e-3),
+                                            ("fp8", 500, 40000, 1, 1e-2), ("bf16x3", 300, 9000, 2, 1e-4),
+                                            ("bf16", 2100, 9000, 2, 1e-2)])
+def test_sr_centred_solve_matches_oracle(prec, n, m, k, lam):
+    """Section 4's SR scores: dfs_solve(O, ..., center=True) solves Eq. 1 for S = (O - O_bar) /
+    sqrt(n), compared with the oracle's solve of its own sr_scores(O).  The plain FP32 path centres
+    its FP32 Gram, which adds rounding of the size of the offset's share of O O^T (about u (1 +
+    mu^2 / sigma^2) relative, mu ~ sigma here): 3x its usual bar."""
+    O, V = _sr_inputs(n, m, k, seed=300 + n)
+    X, info = dfs.dfs_solve(O, V, lam, precision=prec, center=True, max_iter=20)
+    assert info["status"] == 0, info
+    S64 = oracle.sr_scores(np64(O))
+    ref = oracle.solve(S64, np64(V).T, lam).T
+    tol = 3 * fp32_tol(torch.from_numpy(S64), lam) if prec == "fp32" else 1e-6
+    assert rel_err(np64(X), ref) <= tol
+    # without centring the same call solves the uncentred system: a different answer
+    X0, _ = dfs.dfs_solve(O, V, lam, precision=prec, max_iter=20)
+    assert rel_err(np64(X0), ref) > 10 * tol
+
+
+def test_fp8_nonfinite_row_reaches_the_cholesky():
+    n, m = 200, 5000
+    S = wl.gaussian(n, m, seed=203, device=dev())
+    S[17, 123] = float("inf")
+    V = wl.rhs(m, 1, seed=204, device=dev())
+    with pytest.raises(DfsError) as e:
+        dfs.dfs_solve(S, V, 1e-2, precision="fp8")
+    assert e.value.status == 4  # DFS_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("dtype,n,m,k,lam", [(torch.float32, 1024, 65536, 1, 1e-2),
+                                             (torch.float32, 257, 33336, 3, 1e-3),
+                                             (torch.float32, 100, 5000, 8, 1e-1),
+                                             (torch.bfloat16, 384, 40000, 2, 1e-2)])
+def test_fp8_refined_path_matches_oracle(dtype, n, m, k, lam):
+    S = aligned(wl.gaussian(n, m, seed=205 + n, device=dev(), dtype=dtype))
+    V = wl.rhs(m, k, seed=206 + n, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="fp8", max_iter=20)
+    assert info["status"] == 0 and info["precision"] == "fp8", info
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+
+
 @pytest.mark.parametrize("n,m,k,lam", [(1024, 65536, 1, 1e-4), (257, 33336, 3, 1e-3), (100, 5000, 8, 1e-1),
                                        (2100, 9000, 2, 1e-2)])
 def test_bf16x3_refined_path_matches_oracle(n, m, k, lam):
