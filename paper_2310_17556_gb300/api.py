@@ -179,8 +179,10 @@ def dfs_solve_host(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor
 
 
 def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float = 0.0,
-                      handle: Handle | None = None, stream=None, sync: bool = True):
-    """problems: list of (S, V, lam[, X]); returns (list of X, list of per-problem status or None)."""
+                      handle: Handle | None = None, stream=None, sync: bool = True, center: bool = False):
+    """problems: list of (S, V, lam[, X]); returns (list of X, list of per-problem status or None).
+
+    When a problem fails, the DfsError raised carries .outs (every X) and .statuses (per problem)."""
     h = handle or default_handle()
     arr = (dfs_problem * len(problems))()
     outs = []
@@ -194,11 +196,16 @@ def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float
         arr[i] = dfs_problem(S.data_ptr(), S.shape[0], S.shape[1], _rows(S, "S"), V.data_ptr(), V.shape[0],
                              _rows(V, "V"), float(lam), X.data_ptr(), _rows(X, "X"))
         outs.append(X)
-    opt = _opts(precision, max_iter, tol)
+    opt = _opts(precision, max_iter, tol, center=center)
     status = (C.c_int * len(problems))() if sync else None
     st = h.lib.dfs_solve_batched(h.h, arr, len(problems), dt, C.byref(opt), _stream(stream), status)
     if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
-        _check(h.lib, h.h, st)
+        try:
+            _check(h.lib, h.h, st)
+        except DfsError as e:
+            e.outs = outs
+            e.statuses = list(status) if sync else None
+            raise
     return outs, (list(status) if sync else None)
 
 

@@ -430,7 +430,7 @@ cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_
 
 template <typename T, typename CT>
 static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* Linv_, int* flags, DevStatus* st,
-                                     cudaStream_t stream) {
+                                     cudaStream_t stream, int share) {
     T* W = static_cast<T*>(W_);
     T* Linv = static_cast<T*>(Linv_);
     int nb = (int)(n_pad / NB);
@@ -445,6 +445,9 @@ static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* 
     // two CTAs per SM where they fit (all resident): a CTA waiting on an L2 round trip leaves the
     // SM to the other
     int G = sms * (per_sm >= 2 ? 2 : 1);
+    // concurrent factorisations (share > 1) each take 1 / share of that capacity, so all of their
+    // CTAs can be resident together and none waits for another's to leave
+    if (share > 1) G = G / share > 0 ? G / share : 1;
     if (G > ntiles) G = ntiles;
     if ((e = cudaMemsetAsync(flags, 0, cholesky_flag_bytes(n_pad), stream)) != cudaSuccess) return e;
     void* args[] = {&W, &ld, &nb, &Linv, &flags, &st};
@@ -454,11 +457,11 @@ static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* 
 }
 
 cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void* Linv, int* flags, DevStatus* st,
-                            cudaStream_t stream, int fp64_panel) {
+                            cudaStream_t stream, int fp64_panel, int share) {
     if (n_pad % NB != 0) return cudaErrorInvalidValue;
-    if (w_f64) return launch_cholesky_t<double, double>(W, ld, n_pad, Linv, flags, st, stream);
-    return fp64_panel ? launch_cholesky_t<float, double>(W, ld, n_pad, Linv, flags, st, stream)
-                      : launch_cholesky_t<float, float>(W, ld, n_pad, Linv, flags, st, stream);
+    if (w_f64) return launch_cholesky_t<double, double>(W, ld, n_pad, Linv, flags, st, stream, share);
+    return fp64_panel ? launch_cholesky_t<float, double>(W, ld, n_pad, Linv, flags, st, stream, share)
+                      : launch_cholesky_t<float, float>(W, ld, n_pad, Linv, flags, st, stream, share);
 }
 
 }  // namespace dfs

@@ -39,8 +39,9 @@ cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64
 // fp64_panel: factor the 32 x 32 diagonal blocks in FP64 (else in the storage type).
 // flags: cholesky_flag_bytes(n_pad) of device scratch (zeroed by the launcher).
 size_t cholesky_flag_bytes(int64_t n_pad);
+// share > 1: the kernel takes 1 / share of the resident-CTA capacity (concurrent factorisations).
 cudaError_t launch_cholesky(int w_f64, void* W, int64_t ld, int64_t n_pad, void* Linv, int* flags, DevStatus* st,
-                            cudaStream_t stream, int fp64_panel = 1);
+                            cudaStream_t stream, int fp64_panel = 1, int share = 1);
 cudaError_t launch_diag_inverse(int w_f64, const void* L, int64_t ld, int64_t n_pad, void* Linv, DevStatus* st,
                                 cudaStream_t stream);
 

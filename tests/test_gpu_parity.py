@@ -530,6 +530,45 @@ def test_solve_batched_ragged():
         assert rel_err(np64(X), ref) <= 1e-6
 
 
+def _ragged_problems(count, seed, k=2, n_hi=400, m_hi=6e4):
+    shapes = wl.ragged_batch_shapes(count, seed=seed, n_lo=64, n_hi=n_hi, m_lo=2e3, m_hi=m_hi, lam_lo=1e-3,
+                                    lam_hi=1e-1)
+    probs = []
+    for j, (n, m, lam) in enumerate(shapes):
+        m = (m + 3) // 4 * 4
+        probs.append((wl.gaussian(n, m, seed=seed + 10 + j, device=dev()), wl.rhs(m, k, seed=seed + 50 + j, device=dev()),
+                      lam))
+    return probs
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_solve_batched_lanes(prec):
+    """Nine uneven problems: more than the concurrent lanes, so lanes run several problems each,
+    longest first; every problem matches its own oracle solve."""
+    probs = _ragged_problems(9, seed=7000)
+    outs, status = dfs.dfs_solve_batched(probs, precision=prec)
+    assert status == [0] * len(probs)
+    for (S, V, lam), X in zip(probs, outs):
+        tol = fp32_tol(S, lam) if prec == "fp32" else 1e-6
+        assert rel_err(np64(X), solve_ref(S, V, lam)) <= tol
+
+
+def test_solve_batched_failure_stays_in_its_problem():
+    """A NaN in one problem's S fails that problem alone (its lane's status is reset before the
+    next problem); the call reports it by index and every other problem is still solved."""
+    probs = _ragged_problems(7, seed=7100)
+    bad = 3
+    probs[bad][0][5, 17] = float("nan")
+    with pytest.raises(DfsError) as e:
+        dfs.dfs_solve_batched(probs, precision="bf16")
+    assert e.value.status == 4 and f"problem {bad}" in str(e.value)
+    assert [st for j, st in enumerate(e.value.statuses) if j != bad] == [0] * (len(probs) - 1)
+    outs = e.value.outs
+    for j, ((S, V, lam), X) in enumerate(zip(probs, outs)):
+        if j != bad:
+            assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+
+
 # ---------------------------------------------------------------------------- full-size configurations
 
 
