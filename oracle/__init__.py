@@ -20,3 +20,4 @@ from .alg1 import (  # noqa: F401
     sr_scores,
 )
 from .exact import solve_dense_exact  # noqa: F401
+from .complex_sr import real_part_scores, solve_complex  # noqa: F401

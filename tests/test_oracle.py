@@ -297,6 +297,53 @@ def test_sr_two_samples_closed_form(lam):
     np.testing.assert_allclose(oracle.solve(oracle.sr_scores(O), v, lam), x_cf, rtol=1e-12, atol=1e-12)
 
 
+def _complex_case(n, m, seed):
+    rng = np.random.default_rng(seed)
+    S = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(2 * n)
+    v = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    return S, v
+
+
+@pytest.mark.parametrize("n,m,lam", [(5, 17, 0.3), (12, 9, 1e-2), (1, 6, 0.7)])
+def test_complex_solve_matches_dense_hermitian_system(n, m, lam):
+    """Section 4, complex SR: (S^dagger S + lambda I) x = v, checked against a dense complex
+    LAPACK solve of that m x m system (a different algorithm from Algorithm 1)."""
+    S, v = _complex_case(n, m, seed=11 + n)
+    A = np.conj(S.T) @ S + lam * np.eye(m)
+    np.testing.assert_allclose(oracle.solve_complex(S, v, lam), np.linalg.solve(A, v), rtol=1e-11, atol=1e-12)
+
+
+def test_complex_solve_single_row_closed_form():
+    """n = 1: S^dagger S = s^dagger s, so x = (v - s^dagger (s v) / (||s||^2 + lambda)) / lambda."""
+    S, v = _complex_case(1, 8, seed=21)
+    lam = 0.4
+    s = S[0]
+    x_cf = (v - np.conj(s) * (s @ v) / (np.vdot(s, s).real + lam)) / lam
+    np.testing.assert_allclose(oracle.solve_complex(S, v, lam), x_cf, rtol=1e-12, atol=1e-12)
+
+
+def test_complex_solve_with_real_scores_splits_into_two_real_solves():
+    """Real S: the system does not mix Re x and Im x, so each is the real Algorithm 1's answer."""
+    rng = np.random.default_rng(23)
+    S = rng.standard_normal((6, 14))
+    v = rng.standard_normal(14) + 1j * rng.standard_normal(14)
+    x = oracle.solve_complex(S, v, 0.2)
+    np.testing.assert_allclose(x.real, oracle.solve(S, v.real, 0.2), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(x.imag, oracle.solve(S, v.imag, 0.2), rtol=1e-12, atol=1e-12)
+
+
+def test_real_part_scores_give_the_real_part_of_the_fisher_matrix():
+    """Section 4, real-part SR: Concat[Re S, Im S] along n has S^T S = Re[S^dagger S]; the real
+    solve on it matches a dense solve with Re[S^dagger S]."""
+    S, _ = _complex_case(7, 11, seed=25)
+    v = np.random.default_rng(26).standard_normal(11)
+    Sr = oracle.real_part_scores(S)
+    assert Sr.shape == (14, 11)
+    np.testing.assert_allclose(Sr.T @ Sr, (np.conj(S.T) @ S).real, rtol=1e-12, atol=1e-13)
+    A = (np.conj(S.T) @ S).real + 0.3 * np.eye(11)
+    np.testing.assert_allclose(oracle.solve(Sr, v, 0.3), np.linalg.solve(A, v), rtol=1e-11, atol=1e-12)
+
+
 def test_planted_mistakes_are_caught(monkeypatch):
     assert _pin_dense(oracle.solve)
 
