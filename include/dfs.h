@@ -153,6 +153,22 @@ dfs_status dfs_solve_host(dfs_handle handle, const void* S, int s_dtype, int64_t
                           void* X, int64_t ldx, const dfs_options* opt, void* stream,
                           dfs_info* info);
 
+/* Complex stochastic reconfiguration (Section 4, full Fisher matrix F = S^dagger S): solve
+ * (S^dagger S + lambda I) X = V for complex S = S_re + i S_im and k complex right-hand sides.
+ * S_re, S_im: DEVICE planes, n x m row-major with the same lds and dtype (FP32, BF16 or FP64, the
+ * dfs_solve contract); V_re, V_im, X_re, X_im: DEVICE planes of k rows of length m (ldv, ldx),
+ * FP64 for FP64 S, else FP32.  Solved as the real Eq. 1 of the 2n x 2m real representation
+ * [[S_re, -S_im], [S_im, S_re]] with x = [Re x, Im x] (exactly equivalent), which the call forms in
+ * a handle-owned device buffer (twice the bytes of the two planes), so every precision of
+ * dfs_solve applies.  2n <= 65536.  Synchronizes `stream` before returning; info may be NULL.
+ * DFS_FLAG_CENTER is not available here (DFS_ERR_UNSUPPORTED).  The real-part Fisher matrix
+ * F = Re[S^dagger S] needs no entry point: it is dfs_solve on the 2n x m matrix with the rows of
+ * S_re followed by those of S_im. */
+dfs_status dfs_solve_complex(dfs_handle handle, const void* S_re, const void* S_im, int s_dtype,
+                             int64_t n, int64_t m, int64_t lds, const void* V_re, const void* V_im,
+                             int64_t k, int64_t ldv, double lambda, void* X_re, void* X_im,
+                             int64_t ldx, const dfs_options* opt, void* stream, dfs_info* info);
+
 /* Synchronize `stream` and report the device status of the last dfs_solve on this handle. */
 dfs_status dfs_sync_info(dfs_handle handle, void* stream, dfs_info* info);
 

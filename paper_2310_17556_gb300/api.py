@@ -178,6 +178,29 @@ def dfs_solve_host(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor
     return X, _info_dict(info)
 
 
+def dfs_solve_complex(S_re: torch.Tensor, S_im: torch.Tensor, V_re: torch.Tensor, V_im: torch.Tensor, lam: float,
+                      precision="auto", max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None,
+                      stream=None):
+    """Complex SR (Section 4, F = S^dagger S): solve (S^dagger S + lam I) X^T = V^T for S = S_re + i S_im
+    (n x m planes) and the k rows of V = V_re + i V_im; returns (X_re, X_im, info)."""
+    h = handle or default_handle(S_re.device.index)
+    n, m = S_re.shape
+    k = V_re.shape[0]
+    if S_im.shape != S_re.shape or S_im.stride() != S_re.stride() or S_im.dtype != S_re.dtype:
+        raise ValueError("S_re and S_im must share shape, strides and dtype")
+    if V_im.shape != V_re.shape or V_im.stride() != V_re.stride() or V_re.shape[1] != m:
+        raise ValueError("V_re and V_im must both be (k, m) with the same strides")
+    X_re, X_im = torch.empty_like(V_re), torch.empty_like(V_re)
+    opt = _opts(precision, max_iter, tol)
+    info = dfs_info()
+    st = h.lib.dfs_solve_complex(h.h, S_re.data_ptr(), S_im.data_ptr(), _dtype_code(S_re), n, m, _rows(S_re, "S"),
+                                 V_re.data_ptr(), V_im.data_ptr(), k, _rows(V_re, "V"), float(lam), X_re.data_ptr(),
+                                 X_im.data_ptr(), _rows(X_re, "X"), C.byref(opt), _stream(stream), C.byref(info))
+    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
+        _check(h.lib, h.h, st)
+    return X_re, X_im, _info_dict(info)
+
+
 def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float = 0.0,
                       handle: Handle | None = None, stream=None, sync: bool = True, center: bool = False):
     """problems: list of (S, V, lam[, X]); returns (list of X, list of per-problem status or None).

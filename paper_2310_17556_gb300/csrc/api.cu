@@ -26,7 +26,7 @@ struct dfs_handle_s {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     DevStatus* dstat = nullptr;
-    void* hbuf[3] = {nullptr, nullptr, nullptr};  // device staging for dfs_solve_host: S, V, X
+    void* hbuf[3] = {nullptr, nullptr, nullptr};  // device staging (dfs_solve_host, dfs_solve_complex): S, V, X
     int* bstat = nullptr;                          // per-problem device status of dfs_solve_batched
     int bstat_count = 0;
     // dfs_solve_batched runs its problems on up to kMaxLanes concurrent lanes: each a private handle
@@ -614,6 +614,43 @@ dfs_status dfs_solve_host(dfs_handle h, const void* S, int s_dtype, int64_t n, i
                      stream, nullptr);
     if (s != DFS_OK) return s;
     DFS_CK(cudaMemcpy2DAsync(X, ldx * vs, h->hbuf[2], ldx_d * vs, m * vs, k, cudaMemcpyDeviceToHost, stream));
+    return fill_info(h, stream, info);
+}
+
+dfs_status dfs_solve_complex(dfs_handle h, const void* S_re, const void* S_im, int s_dtype, int64_t n, int64_t m,
+                             int64_t lds, const void* V_re, const void* V_im, int64_t k, int64_t ldv, double lambda,
+                             void* X_re, void* X_im, int64_t ldx, const dfs_options* opt, void* stream_,
+                             dfs_info* info) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    dfs_status s;
+    if ((s = check_s(h, S_re, s_dtype, n, m, lds)) != DFS_OK) return s;
+    if ((s = check_s(h, S_im, s_dtype, n, m, lds)) != DFS_OK) return s;
+    if ((s = check_lambda(h, lambda)) != DFS_OK) return s;
+    if (!V_re || !V_im || !X_re || !X_im || k < 1 || ldv < m || ldx < m)
+        return fail(h, DFS_ERR_INVALID_ARG, "bad V/X arguments");
+    if (2 * n > 65536) return fail(h, DFS_ERR_UNSUPPORTED, "2n=%lld above the supported maximum 65536", (long long)(2 * n));
+    if (opt && (opt->flags & DFS_FLAG_CENTER))
+        return fail(h, DFS_ERR_UNSUPPORTED, "centring is not available for complex scores");
+    const size_t es = elem_size(s_dtype);
+    const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
+    // R(S): 2n rows of 2m (row stride a multiple of 16 bytes); [Re v | Re v] rows of 2m
+    const int64_t ldr = round_up(2 * m, 8), ldv2 = round_up(2 * m, 4);
+    if ((s = grow(h, 0, (size_t)(2 * n) * ldr * es)) != DFS_OK) return s;
+    if ((s = grow(h, 1, (size_t)k * ldv2 * vs)) != DFS_OK) return s;
+    if ((s = grow(h, 2, (size_t)k * ldv2 * vs)) != DFS_OK) return s;
+    DFS_CK(launch_complex_embed(s_dtype, S_re, S_im, n, m, lds, h->hbuf[0], ldr, stream));
+    char* v2 = static_cast<char*>(h->hbuf[1]);
+    DFS_CK(cudaMemcpy2DAsync(v2, ldv2 * vs, V_re, ldv * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
+    DFS_CK(cudaMemcpy2DAsync(v2 + m * vs, ldv2 * vs, V_im, ldv * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
+    s = solve_device(h, h->hbuf[0], s_dtype, 2 * n, 2 * m, ldr, h->hbuf[1], k, ldv2, lambda, h->hbuf[2], ldv2, opt,
+                     stream, nullptr);
+    if (s != DFS_OK) return s;
+    const char* x2 = static_cast<const char*>(h->hbuf[2]);
+    DFS_CK(cudaMemcpy2DAsync(X_re, ldx * vs, x2, ldv2 * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
+    DFS_CK(cudaMemcpy2DAsync(X_im, ldx * vs, x2 + m * vs, ldv2 * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
     return fill_info(h, stream, info);
 }
 

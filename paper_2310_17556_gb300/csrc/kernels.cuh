@@ -116,6 +116,10 @@ cudaError_t launch_center_vec(int f64, int mode, int n, int n_pad, int KQ, int k
                               double lambda, void* Z, double* Yc, const DevStatus* st, int honor_stop,
                               cudaStream_t stream);
 
+// ---- complex scores (complex.cu): R = [[A, -B], [B, A]] (2n x 2m, row stride ldr) ----
+cudaError_t launch_complex_embed(int s_dtype, const void* A, const void* B, int64_t n, int64_t m, int64_t lds, void* R,
+                                 int64_t ldr, cudaStream_t stream);
+
 // ---- refinement control and small utilities (refine.cu, util.cu) ----
 cudaError_t launch_status_reset(DevStatus* st, cudaStream_t stream);
 cudaError_t launch_group_reset(DevStatus* st, cudaStream_t stream);

@@ -333,6 +333,49 @@ def test_sr_centred_solve_matches_oracle(prec, n, m, k, lam):
     assert rel_err(np64(X0), ref) > 10 * tol
 
 
+def _complex_inputs(n, m, k, seed, dtype=torch.float32):
+    A = wl.gaussian(n, m, seed=seed, device=dev()) / math.sqrt(2)
+    B = wl.gaussian(n, m, seed=seed + 1, device=dev()) / math.sqrt(2)
+    vdt = torch.float64 if dtype == torch.float64 else torch.float32
+    Vr = wl.rhs(m, k, seed=seed + 2, device=dev()).to(vdt)
+    Vi = wl.rhs(m, k, seed=seed + 3, device=dev()).to(vdt)
+    return aligned(A.to(dtype)), aligned(B.to(dtype)), Vr, Vi
+
+
+@pytest.mark.parametrize("prec,n,m,k,lam,dtype", [("bf16", 512, 40000, 2, 1e-3, torch.float32),
+                                                  ("fp32", 200, 9000, 1, 1e-2, torch.float32),
+                                                  ("fp64", 64, 3000, 2, 1e-2, torch.float64),
+                                                  ("bf16", 300, 20000, 1, 1e-2, torch.bfloat16),
+                                                  ("fp8", 257, 30000, 1, 1e-2, torch.float32)])
+def test_complex_solve_matches_oracle(prec, n, m, k, lam, dtype):
+    """Section 4, complex SR with F = S^dagger S: dfs_solve_complex against the oracle's complex
+    Algorithm 1 (Hermitian conjugates, complex128), on the stored planes."""
+    A, B, Vr, Vi = _complex_inputs(n, m, k, seed=400 + n, dtype=dtype)
+    Xr, Xi, info = dfs.dfs_solve_complex(A, B, Vr, Vi, lam, precision=prec)
+    assert info["status"] == 0, info
+    S = np64(A) + 1j * np64(B)
+    ref = oracle.solve_complex(S, (np64(Vr) + 1j * np64(Vi)).T, lam).T
+    X = np64(Xr) + 1j * np64(Xi)
+    err = float(np.max(np.linalg.norm(X - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+    if prec == "fp32":
+        sv = np.linalg.svd(S, compute_uv=False)
+        tol = 1e-5 * max(1.0, (sv[0] ** 2 + lam) / (sv[-1] ** 2 + lam) / 10)
+    else:
+        tol = 1e-12 if prec == "fp64" else 1e-6
+    assert err <= tol, err
+
+
+def test_complex_real_part_fisher_is_the_stacked_real_solve():
+    """Section 4, real-part SR (F = Re[S^dagger S]): dfs_solve on the rows of Re S followed by those
+    of Im S matches the oracle's real solve of real_part_scores(S)."""
+    A, B, Vr, _ = _complex_inputs(300, 20000, 1, seed=450)
+    Sr = torch.cat([A, B], dim=0)
+    X, info = dfs.dfs_solve(Sr, Vr, 1e-2, precision="bf16")
+    assert info["status"] == 0
+    ref = oracle.solve(oracle.real_part_scores(np64(A) + 1j * np64(B)), np64(Vr).T, 1e-2).T
+    assert rel_err(np64(X), ref) <= 1e-6
+
+
 def test_fp8_nonfinite_row_reaches_the_cholesky():
     n, m = 200, 5000
     S = wl.gaussian(n, m, seed=203, device=dev())
