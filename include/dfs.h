@@ -74,7 +74,7 @@ typedef enum {
 } dfs_precision;
 
 /* entries of dfs_info.ms and of dfs_step_times' output */
-#define DFS_STEP_TIMES 8
+#define DFS_STEP_TIMES 9
 
 /* dfs_options.flags */
 #define DFS_FLAG_STEP_TIMING 1  /* record CUDA events around the steps; dfs_info.ms is filled */
@@ -102,6 +102,8 @@ typedef struct {
     int precision_used;     /* dfs_precision actually run */
     int iters;              /* refinement passes run (0 on the FP32/FP64 paths) */
     int failed_pivot;       /* first non-positive pivot index, -1 if none */
+    int passes;             /* full refinement passes over S (iters, less a final correction read
+                               from the packed BF16 tiles) */
     double rel_correction;  /* estimated relative error left in x (0 if no refinement) */
     double rel_residual_n;  /* last ||r_n|| / ||S v||, r_n = S v - (S S^T + lambda I) y */
     float ms[DFS_STEP_TIMES]; /* with DFS_FLAG_STEP_TIMING (CUDA events on the call's stream):
@@ -109,7 +111,8 @@ typedef struct {
                                solve (S v pass, two triangular solves), [3] the rest (refinement
                                or the x pass), [4] whole call, [5] S v pass kernel alone, [6] first
                                pass over S after the solves (refinement or x pass) alone,
-                               [7] Cholesky kernel alone; zeros otherwise */
+                               [7] Cholesky kernel alone, [8] the correction from the packed BF16
+                               tiles alone (0 when it did not run); zeros otherwise */
 } dfs_info;
 
 typedef struct dfs_handle_s* dfs_handle;

@@ -40,11 +40,11 @@ class dfs_options(C.Structure):
 
 class dfs_info(C.Structure):
     _fields_ = [("status", C.c_int), ("precision_used", C.c_int), ("iters", C.c_int),
-                ("failed_pivot", C.c_int), ("rel_correction", C.c_double), ("rel_residual_n", C.c_double),
-                ("ms", C.c_float * 8)]
+                ("failed_pivot", C.c_int), ("passes", C.c_int), ("rel_correction", C.c_double),
+                ("rel_residual_n", C.c_double), ("ms", C.c_float * 9)]
 
 
-DFS_STEP_TIMES = 8
+DFS_STEP_TIMES = 9
 DFS_FLAG_STEP_TIMING = 1
 DFS_FLAG_FP64_PANEL = 2
 DFS_FLAG_CENTER = 4

@@ -58,7 +58,8 @@ def _check(lib, h, status: int):
 
 def _info_dict(info: dfs_info) -> dict:
     return dict(status=info.status, precision=_lib.PRECISION_NAMES.get(info.precision_used, "?"),
-                iters=info.iters, failed_pivot=info.failed_pivot, rel_correction=info.rel_correction,
+                iters=info.iters, passes=info.passes, failed_pivot=info.failed_pivot,
+                rel_correction=info.rel_correction,
                 rel_residual_n=info.rel_residual_n, ms=[float(x) for x in info.ms])
 
 

@@ -43,7 +43,7 @@ struct dfs_handle_s {
     // Marks: 0 start, 1 Gram kernel start, 2 Gram kernel end, 3 Cholesky end, 4 first n-space
     // solve end, 5 end of the call.
     static constexpr int kTimingSlots = 64;
-    static constexpr int kMarks = 11;
+    static constexpr int kMarks = 13;
     cudaEvent_t ev[kTimingSlots][kMarks] = {};
     int tslot = 0;      // slot of the last timed solve
     int tpending = 0;   // timed solves not yet summarised by dfs_step_times
@@ -184,7 +184,7 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     p->off_Linv = take(np * 32 * es);
     p->off_P = take(gram_bytes);
     p->off_Rpart = take((size_t)p->pgrid * n * kq * 8);
-    p->off_U2part = take((size_t)p->pgrid * 2 * kq * 8);
+    p->off_U2part = take((size_t)std::max(p->pgrid, tile_correct_parts(h->num_sms)) * 2 * kq * 8);
     p->off_R = take(np * kq * 8);
     p->off_Z = take(np * kq * es);
     p->off_Y = take(np * kq * 8);
@@ -279,6 +279,7 @@ void step_ms(cudaEvent_t* e, float* ms) {
     cudaEventElapsedTime(&ms[5], e[6], e[7]);   // S v pass kernel
     cudaEventElapsedTime(&ms[6], e[8], e[9]);   // first refinement (or x) pass kernel
     cudaEventElapsedTime(&ms[7], e[10], e[3]);  // Cholesky kernel
+    cudaEventElapsedTime(&ms[8], e[11], e[12]);  // the correction from the packed tiles (0 if none)
 }
 
 dfs_status fill_info(dfs_handle h, cudaStream_t stream, dfs_info* info) {
@@ -290,6 +291,7 @@ dfs_status fill_info(dfs_handle h, cudaStream_t stream, dfs_info* info) {
         info->precision_used = h->last_precision;
         info->iters = ds.iters;
         info->failed_pivot = ds.failed_pivot;
+        info->passes = ds.passes;
         info->rel_correction = ds.rel_correction;
         info->rel_residual_n = ds.rel_residual;
         for (int i = 0; i < DFS_STEP_TIMES; ++i) info->ms[i] = 0.0f;
@@ -380,6 +382,8 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
 
     DFS_CK(launch_status_reset(h->dstat, stream));
     DFS_CK(mark(0));
+    DFS_CK(mark(11));  // both re-recorded around the tile correction when it runs, else 0 ms apart
+    DFS_CK(mark(12));
     if (rs) DFS_CK(launch_row_scale(s_dtype, S, (int)ni, (int)p.n_pad, m, lds, rs, h->dstat, stream));
     for (int64_t q0 = 0; q0 < k; q0 += kq) {
         const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
@@ -437,31 +441,50 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                                U2part, 0, h->dstat, 0, stream));
             if (mark_pass) DFS_CK(mark(9));
         } else {
+            // The step after the first reads the packed BF16 tiles instead of S when they exist:
+            // x_2 = x_1 - S_bf16^T dy_1 / lambda (the tiles' rounding costs 2^-9 of a correction of
+            // relative size delta_2, which the check adds to its estimate).  If that does not
+            // converge, the full pass of step 2 recomputes x_2 exactly and refinement goes on.
+            const bool fast = p.pack == 1 && !center && max_iter >= 3 && !p.f64 && kq <= 4;
             for (int it = 1; it <= max_iter; ++it) {
-                // x_0 = v / lambda for the first pass; afterwards x_{j-1} is read from X itself
+                const bool corrected = fast && it == 2;
+                if (corrected) {
+                    if (mark_pass) DFS_CK(mark(11));
+                    int cparts = 0;
+                    DFS_CK(launch_tile_correct(kq, Sp, ni, (int)round_up(n, 256), m, pack_kblocks(s_dtype, 1, m),
+                                               static_cast<const float*>(Z), kg, lambda, static_cast<float*>(Xg), ldx,
+                                               U2part, h->dstat, h->num_sms, stream, &cparts));
+                    if (mark_pass) DFS_CK(mark(12));
+                    DFS_CK(launch_refine_check(U2part, cparts, U2, kq, kg, lambda, tol, it, max_iter, 1, h->dstat,
+                                               stream));
+                }
                 if (center)
                     DFS_CK(launch_center_vec(p.f64, 1, ni, npi, kq, kg, nullptr, Y, 0.0, nullptr, Yc, h->dstat, 1, stream));
+                // x_0 = v / lambda for the first pass; afterwards x_{j-1} is read from X itself (no
+                // measurement after a correction: its check already took delta_2)
                 if (mark_pass && it == 1) DFS_CK(mark(8));
                 DFS_CK(launch_pass(p.pp, s_dtype, kq, S, ni, m, lds, Vg, ldv, kg, Yp, kq, lambda, Xg, ldx, Rpart,
-                                   U2part, it == 1 ? 2 : 1, h->dstat, 1, stream));
+                                   U2part, corrected ? 0 : (it == 1 ? 2 : 1), h->dstat, 1, stream));
                 if (mark_pass && it == 1) DFS_CK(mark(9));
+                if (!corrected)
+                    DFS_CK(launch_refine_check(U2part, p.pp.nparts, U2, kq, kg, lambda, tol, it, max_iter, 0,
+                                               h->dstat, stream));
                 if (p.ns) {
                     DFS_CK(launch_nspace(p.f64, kq, W, p.n_pad, npi, Linv,
                                          NS_MODE_REDUCE | NS_MODE_LAMBDA_Y | NS_MODE_FWD | NS_MODE_BWD, Rpart,
-                                         p.pp.nparts, ni, kg, Y, lambda, nullptr, 0, R, Z, kq, U2part, U2,
+                                         p.pp.nparts, ni, kg, Y, lambda, nullptr, 0, R, Z, kq, nullptr, nullptr,
                                          h->smem_optin, h->dstat, 1, stream));
                 } else {
                     // r = S u - lambda y; centred: P (O u) / sqrt(n) - lambda y
                     DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.nparts, ni, npi, kq, kg, center ? nullptr : Y, kq,
-                                              lambda, R, kq, Z, U2part, U2, h->dstat, 1, stream));
+                                              lambda, R, kq, Z, nullptr, nullptr, h->dstat, 1, stream));
                     if (center)
                         DFS_CK(launch_center_vec(p.f64, 0, ni, npi, kq, kg, R, Y, lambda, Z, nullptr, h->dstat, 1,
                                                  stream));
                     DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
                     DFS_CK(launch_trsv(p.f64, 1, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 1, stream));
                 }
-                DFS_CK(launch_refine_control(p.f64, Z, R, npi, kq, kg, Y, U2, bn2, lambda, tol, it, max_iter,
-                                             h->dstat, stream));
+                DFS_CK(launch_refine_update(p.f64, Z, R, npi, kq, kg, Y, bn2, h->dstat, stream));
             }
             if (max_iter == 0) {
                 if (center)

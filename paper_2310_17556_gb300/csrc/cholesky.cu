@@ -162,10 +162,13 @@ __device__ __noinline__ bool factor_diag(T* W, int64_t ld, int kb, T* Linv, DevS
             // broadcast before the update
             if (j + 1 < NB) d = __shfl_sync(0xffffffffu, fma(-l, l, a[j + 1]), j + 1);
             __syncwarp();
-            // constant trip count (fully unrolled, a[] stays in registers); p <= j is skipped
+            // constant trip count (fully unrolled, a[] stays in registers); p <= j is skipped.  The
+            // entries above the diagonal (lane < p) take the update too: they are never read back
+            // (the factor reads p <= lane, W and the inverse only the lower triangle, and a column
+            // broadcast through sCol is read at p > j only), so no mask is needed
 #pragma unroll
             for (int p = 0; p < NB; ++p) {
-                if (p > j) a[p] = (lane >= p) ? fma(-l, sCol[j & 1][p], a[p]) : a[p];
+                if (p > j) a[p] = fma(-l, sCol[j & 1][p], a[p]);
             }
         }
         if (lane == 0) *s_fail = fail;

@@ -26,7 +26,8 @@ struct DevStatus {
     int converged;
     int iters;
     int stop;
-    int pad[3];
+    int passes;  // full passes over S run by the refinement (a tile correction does not count)
+    int pad[2];
     double rel_correction;
     double rel_residual;
     double prev_correction;

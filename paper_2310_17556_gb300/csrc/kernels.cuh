@@ -126,9 +126,20 @@ cudaError_t launch_group_reset(DevStatus* st, cudaStream_t stream);
 cudaError_t launch_status_save(const DevStatus* st, int* dst, cudaStream_t stream);
 cudaError_t launch_refine_init(int f64, const void* Z, int n_pad, int KQ, double* Y, const double* R,
                                double* bnorm2, DevStatus* st, cudaStream_t stream);
-cudaError_t launch_refine_control(int f64, const void* Z, const double* R, int n_pad, int KQ, int k, double* Y,
-                                  const double* U2, const double* bnorm2, double lambda, double tol, int it,
-                                  int max_iter, DevStatus* st, cudaStream_t stream);
+// after a pass (or the tile correction, fast = 1): U2 = sum of U2part, the error estimate and the
+// stop decision (refine.cu)
+cudaError_t launch_refine_check(const double* U2part, int nparts, double* U2, int KQ, int k, double lambda, double tol,
+                                int it, int max_iter, int fast, DevStatus* st, cudaStream_t stream);
+// after the n-space solve of a step that did not stop: y += dy and the n-space residual norm
+cudaError_t launch_refine_update(int f64, const void* Z, const double* R, int n_pad, int KQ, int k, double* Y,
+                                 const double* bnorm2, DevStatus* st, cudaStream_t stream);
+// x -= S^T dy / lambda from the packed BF16 tiles (pass.cu), with the per-part sums of the passes;
+// grid = the SM count; the parts it writes (at most tile_correct_parts(num_sms)) are returned by
+// the launch through *parts
+int tile_correct_parts(int num_sms);
+cudaError_t launch_tile_correct(int kq, const void* Sp, int n, int n_rows, int64_t m, int64_t nkb, const float* Z,
+                                int k, double lambda, float* X, int64_t ldx, double* U2part, const DevStatus* st,
+                                int grid, cudaStream_t stream, int* parts);
 cudaError_t launch_pad_copy_in(int f64, const void* src, int64_t lds, int64_t n, void* dst, int64_t n_pad,
                                cudaStream_t stream);
 cudaError_t launch_copy_lower_out(int f64, const void* src, int64_t n_pad, void* dst, int64_t ldd, int64_t n,

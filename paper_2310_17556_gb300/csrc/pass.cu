@@ -470,6 +470,157 @@ sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_
 }
 
 // ------------------------------------------------------------------------------------------
+// The refinement's last correction read from the packed BF16 tiles instead of S:
+//   x <- x - S_bf16^T dy / lambda
+// (n_rows x 64-column tiles, 128-byte swizzled rows, k-block major as written by the S v pass),
+// and per CTA the sums of the passes' stopping statistics: lambda^2 ||x_new||^2 and
+// ||x_new - x_old||^2 per RHS (U2part, 2 KQ doubles per CTA).  Each warp owns whole k-blocks (64
+// columns): lane (chunk c = lane % 8, row group lane / 8) reads the 16-byte logical chunk c (8
+// columns) of rows lane / 8, + 4, + 8, ... (the four rows of a step are whole 128-byte lines), 8
+// steps in flight; dy sits in shared memory; the four row groups are added with shuffles and lanes
+// 0..7 update their 8 columns of x in place.
+constexpr int TC_CORR_THREADS = 512;
+constexpr int TC_CORR_UNROLL = 8;
+
+template <int KQ>
+__global__ void __launch_bounds__(TC_CORR_THREADS)
+tile_correct_kernel(const unsigned char* __restrict__ Sp, int n, int n_rows, int64_t m, int64_t nkb,
+                    const float* __restrict__ Z, int k, double lambda, float* __restrict__ X, int64_t ldx,
+                    double* __restrict__ U2part, const DevStatus* st) {
+    extern __shared__ float sdy[];  // n_rows x KQ
+    __shared__ double red[TC_CORR_THREADS / 32][2 * KQ];
+    if (block_should_exit(st, 1)) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < n_rows * KQ; e += TC_CORR_THREADS) sdy[e] = (e / KQ < n && e % KQ < k) ? Z[e] : 0.f;
+    __syncthreads();
+    const int c = lane & 7, rg = lane >> 3;
+    const int T = n_rows >> 7;
+    const float inv_l = (float)(1.0 / lambda);
+    double sx2[KQ], sd2[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) sx2[q] = sd2[q] = 0.0;
+    const int wpb = TC_CORR_THREADS / 32;
+    for (int64_t kb = (int64_t)blockIdx.x * wpb + warp; kb < nkb; kb += (int64_t)gridDim.x * wpb) {
+        const unsigned char* base = Sp + ((kb * T) << 14);
+        float acc[KQ][8];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[q][e] = 0.f;
+        for (int r0 = 0; r0 < n_rows; r0 += 4 * TC_CORR_UNROLL) {
+            uint4 w[TC_CORR_UNROLL];
+#pragma unroll
+            for (int u = 0; u < TC_CORR_UNROLL; ++u) {
+                const int r = r0 + 4 * u + rg;
+                w[u] = __ldg(reinterpret_cast<const uint4*>(base + ((r >> 7) << 14) + (r & 127) * 128 +
+                                                             ((c ^ (r & 7)) << 4)));
+            }
+#pragma unroll
+            for (int u = 0; u < TC_CORR_UNROLL; ++u) {
+                const int r = r0 + 4 * u + rg;
+                const uint32_t h[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+                float f[8];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    f[2 * e] = __uint_as_float(h[e] << 16);
+                    f[2 * e + 1] = __uint_as_float(h[e] & 0xffff0000u);
+                }
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) {
+                    const float d = sdy[r * KQ + q];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[q][e] = fmaf(f[e], d, acc[q][e]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < KQ; ++q)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                acc[q][e] += __shfl_xor_sync(0xffffffffu, acc[q][e], 8);
+                acc[q][e] += __shfl_xor_sync(0xffffffffu, acc[q][e], 16);
+            }
+        if (rg == 0) {
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                if (q >= k) continue;
+                float px = 0.f, pd = 0.f;
+                const int64_t j0 = kb * 64 + c * 8;
+                float* xr = X + (int64_t)q * ldx;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if (j0 + e < m) {
+                        const float du = acc[q][e] * inv_l;
+                        const float xn = xr[j0 + e] - du;
+                        xr[j0 + e] = xn;
+                        px = fmaf(xn, xn, px);
+                        pd = fmaf(du, du, pd);
+                    }
+                }
+                sx2[q] += (double)px;
+                sd2[q] += (double)pd;
+            }
+        }
+    }
+    // per-CTA sums, in a fixed order: lanes 0..7 of each warp, then the warps
+#pragma unroll
+    for (int q = 0; q < KQ; ++q)
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            sx2[q] += __shfl_xor_sync(0xffffffffu, sx2[q], o);
+            sd2[q] += __shfl_xor_sync(0xffffffffu, sd2[q], o);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            red[warp][q] = sx2[q] * lambda * lambda;
+            red[warp][KQ + q] = sd2[q];
+        }
+    __syncthreads();
+    if (tid < 2 * KQ) {
+        double t = 0.0;
+        for (int w = 0; w < wpb; ++w) t += red[w][tid];
+        U2part[(int64_t)blockIdx.x * 2 * KQ + tid] = t;
+    }
+}
+
+// grid: the SM count (the launch multiplies it by the resident CTAs per SM); U2part needs
+// tile_correct_parts(num_sms) x 2 kq doubles.
+int tile_correct_parts(int num_sms) { return 4 * num_sms; }
+
+cudaError_t launch_tile_correct(int kq, const void* Sp, int n, int n_rows, int64_t m, int64_t nkb, const float* Z,
+                                int k, double lambda, float* X, int64_t ldx, double* U2part, const DevStatus* st,
+                                int grid, cudaStream_t stream, int* parts) {
+    if (n_rows % (4 * TC_CORR_UNROLL) != 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)n_rows * kq * sizeof(float);
+    const unsigned char* sp = static_cast<const unsigned char*>(Sp);
+    // one wave of resident CTAs (grid = num_sms x CTAs per SM): the k-blocks are dealt statically
+#define DFS_TCC(KQ)                                                                                           \
+    {                                                                                                         \
+        auto kern = tile_correct_kernel<KQ>;                                                                  \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        if (e != cudaSuccess) return e;                                                                       \
+        int per_sm = 0;                                                                                       \
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_CORR_THREADS, smem)) !=      \
+            cudaSuccess)                                                                                      \
+            return e;                                                                                         \
+        int g = grid * (per_sm > 0 ? per_sm : 1);                                                             \
+        if (g > 4 * grid) g = 4 * grid;                                                                       \
+        *parts = g;                                                                                           \
+        kern<<<g, TC_CORR_THREADS, smem, stream>>>(sp, n, n_rows, m, nkb, Z, k, lambda, X, ldx, U2part, st);  \
+        count_launch();                                                                                       \
+        return cudaGetLastError();                                                                            \
+    }
+    switch (kq) {
+        case 1: DFS_TCC(1)
+        case 2: DFS_TCC(2)
+        case 4: DFS_TCC(4)
+        default: return cudaErrorInvalidValue;
+    }
+#undef DFS_TCC
+}
+
+// ------------------------------------------------------------------------------------------
 // X = (V - S^T Y) / lambda and R = S (V - S^T Y) - lambda Y in one read of S.
 template <typename TS, int KQ, int RPT>
 __global__ void __launch_bounds__(PASS_THREADS)

@@ -23,6 +23,7 @@ __global__ void status_reset_kernel(DevStatus* st) {
         st->converged = 0;
         st->iters = 0;
         st->stop = 0;
+        st->passes = 0;
         st->rel_correction = 0.0;
         st->rel_residual = 0.0;
         st->prev_correction = 0.0;
@@ -57,18 +58,73 @@ refine_init_kernel(const T* __restrict__ Z, int n_pad, int KQ, double* __restric
     }
 }
 
+// After pass `it` of the refinement (or the correction from the packed tiles): sum the passes'
+// per-part statistics into U2 (sum u^2 = lambda^2 ||x||^2, sum (x_new - x_old)^2, per RHS), form
+// delta_it and the rate, and decide.  `fast`: x came from the packed BF16 tiles, whose rounding
+// (2^-9 relative, of a correction of relative size delta) adds up to 2^-8 delta to the error
+// estimate; if that run does not converge, nothing else is decided here (the full pass that
+// follows recomputes x exactly and the next check carries on from delta_it).
+__global__ void __launch_bounds__(256)
+refine_check_kernel(const double* __restrict__ U2part, int nparts, double* __restrict__ U2, int KQ, int k,
+                    double lambda, double tol, int it, int max_iter, int fast, DevStatus* st) {
+    if (block_should_exit(st, 1)) return;
+    __shared__ double u2[16];
+    if (threadIdx.x < 2 * KQ) {
+        double u = 0.0;
+        for (int b = 0; b < nparts; ++b) u += U2part[(int64_t)b * 2 * KQ + threadIdx.x];
+        u2[threadIdx.x] = u;
+        U2[threadIdx.x] = u;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double delta = 0.0;
+    bool finite = true;
+    for (int q = 0; q < k && q < KQ; ++q) {
+        // ||x_j - x_{j-1}|| / ||x_j|| with ||x_j|| = ||u|| / lambda
+        const double dq = lambda * sqrt(u2[KQ + q]) / fmax(sqrt(u2[q]), 1e-300);
+        if (!isfinite(dq)) finite = false;
+        delta = fmax(delta, dq);
+    }
+    const double prev = st->prev_correction;
+    double est = delta;
+    bool have_rate = false;
+    double rho = 0.0;
+    if (it > 1 && prev > 0.0) {
+        rho = delta / prev;
+        have_rate = true;
+        est = delta * rho / (1.0 - fmin(rho, 0.99));
+    }
+    if (fast) est += delta * (1.0 / 256.0);
+    st->rel_correction = est;
+    st->iters = it;
+    st->prev_correction = delta;
+    if (!finite) {
+        set_status(st, DFS_ERR_NONFINITE);
+        st->stop = 1;
+    } else if ((have_rate && est <= tol) || (!fast && delta <= 1e-2 * tol)) {
+        st->converged = 1;
+        st->stop = 1;
+        st->passes = fast ? it - 1 : it;
+    } else if (!fast && (it >= max_iter || (have_rate && rho >= 0.9))) {
+        set_status(st, DFS_ERR_NOT_CONVERGED);
+        st->stop = 1;
+        st->passes = it;
+    }
+}
+
+// After the n-space solve of a refinement step that did not stop: y += dy, and the relative
+// n-space residual ||r|| / ||b|| of that step (reported in dfs_info).
 template <typename T>
 __global__ void __launch_bounds__(256)
-refine_control_kernel(const T* __restrict__ Z, const double* __restrict__ R, int n_pad, int KQ, int k,
-                      double* __restrict__ Y, const double* __restrict__ U2, const double* __restrict__ bnorm2,
-                      double lambda, double tol, int it, int max_iter, DevStatus* st) {
+refine_update_kernel(const T* __restrict__ Z, const double* __restrict__ R, int n_pad, int KQ, int k,
+                     double* __restrict__ Y, const double* __restrict__ bnorm2, DevStatus* st) {
     if (block_should_exit(st, 1)) return;
     __shared__ double red[8][8];
-    __shared__ int decision;  // 0 = continue (apply dy), 1 = converged, 2 = give up
     double rr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int e = threadIdx.x; e < n_pad * KQ; e += blockDim.x) {
         const double r = R[e];
         rr[e % KQ] += r * r;
+        Y[e] += (double)Z[e];
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = 0; q < 8; ++q) {
@@ -78,50 +134,13 @@ refine_control_kernel(const T* __restrict__ Z, const double* __restrict__ R, int
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double delta = 0.0, relr = 0.0;
-        bool finite = true;
+        double relr = 0.0;
         for (int q = 0; q < k && q < KQ; ++q) {
             double c = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) c += red[w][q];
-            // ||x_j - x_{j-1}|| / ||x_j|| with ||x_j|| = ||u|| / lambda
-            const double dq = lambda * sqrt(U2[KQ + q]) / fmax(sqrt(U2[q]), 1e-300);
-            const double rn = sqrt(c / fmax(bnorm2[q], 1e-300));
-            if (!isfinite(dq) || !isfinite(rn)) finite = false;
-            delta = fmax(delta, dq);
-            relr = fmax(relr, rn);
+            relr = fmax(relr, sqrt(c / fmax(bnorm2[q], 1e-300)));
         }
-        const double prev = st->prev_correction;
-        double est = delta;
-        bool have_rate = false;
-        double rho = 0.0;
-        if (it > 1 && prev > 0.0) {
-            rho = delta / prev;
-            have_rate = true;
-            est = delta * rho / (1.0 - fmin(rho, 0.99));
-        }
-        st->rel_correction = est;
         st->rel_residual = relr;
-        st->iters = it;
-        st->prev_correction = delta;
-        if (!finite) {
-            set_status(st, DFS_ERR_NONFINITE);
-            st->stop = 1;
-            decision = 2;
-        } else if ((have_rate && est <= tol) || delta <= 1e-2 * tol) {
-            st->converged = 1;
-            st->stop = 1;
-            decision = 1;
-        } else if (it >= max_iter || (have_rate && rho >= 0.9)) {
-            set_status(st, DFS_ERR_NOT_CONVERGED);
-            st->stop = 1;
-            decision = 2;
-        } else {
-            decision = 0;
-        }
-    }
-    __syncthreads();
-    if (decision == 0) {
-        for (int e = threadIdx.x; e < n_pad * KQ; e += blockDim.x) Y[e] += (double)Z[e];
     }
 }
 
@@ -148,21 +167,21 @@ cudaError_t launch_refine_init(int f64, const void* Z, int n_pad, int KQ, double
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_control(int f64, const void* Z, const double* R, int n_pad, int KQ, int k, double* Y,
-                                  const double* U2, const double* bnorm2, double lambda, double tol, int it,
-                                  int max_iter, DevStatus* st, cudaStream_t stream) {
+cudaError_t launch_refine_check(const double* U2part, int nparts, double* U2, int KQ, int k, double lambda, double tol,
+                                int it, int max_iter, int fast, DevStatus* st, cudaStream_t stream) {
+    if (KQ > 8) return cudaErrorInvalidValue;
+    refine_check_kernel<<<1, 32, 0, stream>>>(U2part, nparts, U2, KQ, k, lambda, tol, it, max_iter, fast, st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_update(int f64, const void* Z, const double* R, int n_pad, int KQ, int k, double* Y,
+                                 const double* bnorm2, DevStatus* st, cudaStream_t stream) {
     if (f64)
-        {
-            refine_control_kernel<double><<<1, 256, 0, stream>>>(static_cast<const double*>(Z), R, n_pad, KQ, k, Y, U2,
-                                                                  bnorm2, lambda, tol, it, max_iter, st);
-            count_launch();
-        }
+        refine_update_kernel<double><<<1, 256, 0, stream>>>(static_cast<const double*>(Z), R, n_pad, KQ, k, Y, bnorm2, st);
     else
-        {
-            refine_control_kernel<float><<<1, 256, 0, stream>>>(static_cast<const float*>(Z), R, n_pad, KQ, k, Y, U2,
-                                                                 bnorm2, lambda, tol, it, max_iter, st);
-            count_launch();
-        }
+        refine_update_kernel<float><<<1, 256, 0, stream>>>(static_cast<const float*>(Z), R, n_pad, KQ, k, Y, bnorm2, st);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -333,6 +333,21 @@ def test_sr_centred_solve_matches_oracle(prec, n, m, k, lam):
     assert rel_err(np64(X0), ref) > 10 * tol
 
 
+@pytest.mark.parametrize("lam", [1e-4, 1e-2])
+def test_refinement_final_correction_from_bf16_tiles(lam):
+    """The headline shape at small m: the second refinement step reads the packed BF16 tiles instead
+    of S (one full pass over S in all), and x still meets the mixed path's 1e-6."""
+    n, m = 1024, 65536
+    S, U, sig, Vf = wl.svd_structured(n, m, seed=91, sigma_min=1e-3, device=dev())
+    v = wl.rhs(m, 1, seed=92, device=dev())
+    X, info = dfs.dfs_solve(S, v, lam, precision="bf16")
+    assert info["status"] == 0 and info["iters"] == 2 and info["passes"] == 1, info
+    assert rel_err(np64(X), solve_ref(S, v, lam)) <= 1e-6
+    # without the tiles' correction (TF32 tiles) the same solve runs two full passes
+    X2, info2 = dfs.dfs_solve(S, v, lam, precision="tf32")
+    assert info2["passes"] == info2["iters"] >= 1, info2
+
+
 def _complex_inputs(n, m, k, seed, dtype=torch.float32):
     A = wl.gaussian(n, m, seed=seed, device=dev()) / math.sqrt(2)
     B = wl.gaussian(n, m, seed=seed + 1, device=dev()) / math.sqrt(2)
