@@ -13,6 +13,7 @@ than L2, so no L2 flush is needed between steps).  The plain FP32 path is timed 
 every reported solution is compared with the FP64 oracle's on the full problem.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload precision|batch|stress     (the other configurations, one GPU)
 
 N > 1 runs under torchrun; every rank solves its own independent problem (weak scaling, no
 collective on the data path).  Prints one JSON line on rank 0.
@@ -408,6 +409,157 @@ def run_ours(args):
     return 0
 
 
+def _residual_fp64(torch, S, X, V, lam, chunk=1 << 18):
+    """||S^T S x + lam x - v|| / ||v|| per RHS in FP64 (torch, column chunks of S)."""
+    n, m = S.shape
+    k = V.shape[0]
+    Sx = torch.zeros((n, k), device=S.device, dtype=torch.float64)
+    for c0 in range(0, m, chunk):
+        Sx += S[:, c0:c0 + chunk].double() @ X[:, c0:c0 + chunk].double().T
+    num = torch.zeros(k, device=S.device, dtype=torch.float64)
+    for c0 in range(0, m, chunk):
+        r = (S[:, c0:c0 + chunk].double().T @ Sx).T + lam * X[:, c0:c0 + chunk].double() - V[:, c0:c0 + chunk].double()
+        num += (r * r).sum(dim=1)
+    return (num.sqrt() / V.double().norm(dim=1)).cpu().tolist()
+
+
+def run_workload(args):
+    """The other configurations, on one GPU, one JSON line per path:
+      precision  n=4096, m=2^22, k=4, FP32 S with singular values log-spaced 1/sqrt(n) .. 1e-4/sqrt(n),
+                 lambda=1e-4; BF16 and FP8 Gram.  cond(A) ~ 3.4, so the FP64 residual bounds e_rel.
+      batch      64 independent problems, n ~ U{64..1024}, m log-uniform in [1e4, 5e5], lambda log-uniform
+                 in [1e-5, 1e-1], k=8; dfs_solve_batched against one dfs_solve after another.
+      stress     n=8192, m=2^22, BF16 S with Student-t entries and log-normal column scales,
+                 lambda=1e-5, k=1; the FP64 residual against the FP32-storage floor of x.
+    Each timed region holds the solves only (inputs resident in HBM and larger than L2)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2310_17556_gb300 as dfs
+    from paper_2310_17556_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = 231017556
+    steps, warmup = max(1, min(args.steps, 5)), 3
+
+    def timed(fn, k_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(k_steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k_steps
+
+    def emit(line):
+        line.update({"n_gpus": 1, "steps": steps, "warmup": warmup, "higher_is_better": True, "scaling": "weak",
+                     "vs_baseline": None, "data": "synthetic"})
+        print(json.dumps(line), flush=True)
+
+    if args.workload == "precision":
+        n, m, k, lam = 4096, 1 << 22, 4, 1e-4
+        S = wl.svd_structured_lowmem(n, m, seed=base + 3, sigma_min=1e-4, device=dev)
+        V = wl.rhs(m, k, seed=base + 10, device=dev)
+        cond = (1.0 / n + lam) / lam
+        for prec in ("bf16", "fp8"):
+            X = torch.empty_like(V)
+            fn = lambda: dfs.dfs_solve(S, V, lam, X=X, precision=prec, sync=False, timing=True)
+            for _ in range(warmup):
+                fn()
+            dfs.dfs_step_times()
+            clk = _clock_sampler(0)
+            ms = timed(fn, steps)
+            clocks = _clock_summary(clk)
+            info = dfs.dfs_sync_info()
+            st, _ = dfs.dfs_step_times()
+            res = _residual_fp64(torch, S, X, V, lam)
+            emit({"workload": "precision", "metric": "solves/s, n=4096 m=2^22 k=4", "value": 1e3 / ms,
+                  "unit": "solves/s", "ms_per_step": ms, "dtype": prec, "clocks": clocks,
+                  "config": {"n": n, "m": m, "k": k, "lambda": lam, "S": "FP32, sigma log-spaced 1..1e-4 (/sqrt n)"},
+                  "info": {"status": info["status"], "iters": info["iters"], "full_passes": info["passes"]},
+                  "step_ms": {"gram": st[0], "finalize_cholesky": st[1], "first_solve": st[2], "rest": st[3],
+                              "cholesky_kernel": st[7]},
+                  "accuracy": {"fp64_residual_max": max(res), "bound_e_rel": cond * max(res),
+                               "ok": cond * max(res) <= 1e-6}})
+    elif args.workload == "batch":
+        shapes = wl.ragged_batch_shapes(64, seed=base + 4)
+        probs = []
+        for j, (n, m, lam) in enumerate(shapes):
+            m = (m + 3) // 4 * 4
+            probs.append((wl.gaussian(n, m, seed=base + 400 + j, device=dev), wl.rhs(m, 8, seed=base + 700 + j, device=dev),
+                          lam, None))
+        probs = [(S, V, lam, torch.empty_like(V)) for S, V, lam, _ in probs]
+        batch = lambda: dfs.dfs_solve_batched(probs, precision="bf16", sync=False)
+        loop = lambda: [dfs.dfs_solve(S, V, lam, X=X, precision="bf16", sync=False) for S, V, lam, X in probs]
+        for fn in (batch, loop):
+            for _ in range(warmup):
+                fn()
+        clk = _clock_sampler(0)
+        ms_b = timed(batch, steps)
+        clocks = _clock_summary(clk)
+        ms_l = timed(loop, steps)
+        _, status = dfs.dfs_solve_batched(probs, precision="bf16")
+        import oracle
+
+        small = sorted(range(len(probs)), key=lambda j: probs[j][0].numel())[:4]
+        errs = []
+        for j in small:
+            S, V, lam, X = probs[j]
+            ref = oracle.solve(S.double().cpu().numpy(), V.double().cpu().numpy().T, lam).T
+            x = X.double().cpu().numpy()
+            import numpy as np
+
+            errs.append(float(np.max(np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1))))
+        emit({"workload": "batch", "metric": "problems/s, 64 ragged problems, k=8", "value": 64e3 / ms_b,
+              "unit": "problems/s", "ms_per_step": ms_b, "dtype": "bf16", "clocks": clocks,
+              "sequential": {"value": 64e3 / ms_l, "ms_per_step": ms_l, "api": "one dfs_solve after another"},
+              "config": {"problems": 64, "n": "U{64..1024}", "m": "log-uniform [1e4, 5e5]",
+                         "lambda": "log-uniform [1e-5, 1e-1]", "k": 8,
+                         "S_bytes": sum(p[0].numel() * 4 for p in probs)},
+              "accuracy": {"statuses_ok": all(x == 0 for x in status), "e_rel_4_smallest_vs_oracle": errs,
+                           "ok": all(x == 0 for x in status) and max(errs) <= 1e-6}})
+    elif args.workload == "stress":
+        n, m, lam = 8192, 1 << 22, 1e-5
+        S = wl.heavy_tailed(n, m, seed=base + 5, device=dev, dtype=torch.bfloat16)
+        V = wl.rhs(m, 1, seed=base + 12, device=dev)
+        X = torch.empty_like(V)
+        fn = lambda: dfs.dfs_solve(S, V, lam, X=X, precision="bf16", max_iter=12, sync=False, timing=True)
+        for _ in range(warmup):
+            fn()
+        dfs.dfs_step_times()
+        clk = _clock_sampler(0)
+        ms = timed(fn, steps)
+        clocks = _clock_summary(clk)
+        info = dfs.dfs_sync_info()
+        st, _ = dfs.dfs_step_times()
+        res = _residual_fp64(torch, S, X, V, lam)
+        # ||S||_2^2 by power iteration, for the FP32-storage floor 2^-24 (||S||^2 + lambda) ||x|| / ||v||
+        u = torch.randn(n, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+        u /= u.norm()
+        s2 = 0.0
+        for _ in range(30):
+            w = torch.zeros(n, device=dev)
+            for c0 in range(0, m, 1 << 18):
+                Sc = S[:, c0:c0 + (1 << 18)].float()
+                w += Sc @ (Sc.T @ u)
+            s2 = float(torch.dot(u, w))
+            u = w / w.norm()
+        floor = 2.0 ** -24 * (s2 + lam) * float(X.double().norm() / V.double().norm())
+        emit({"workload": "stress", "metric": "solves/s, n=8192 m=2^22 BF16 S heavy-tailed", "value": 1e3 / ms,
+              "unit": "solves/s", "ms_per_step": ms, "dtype": "bf16", "clocks": clocks,
+              "config": {"n": n, "m": m, "k": 1, "lambda": lam, "S": "BF16, Student-t(3) x log-normal columns / sqrt n"},
+              "info": {"status": info["status"], "iters": info["iters"], "full_passes": info["passes"]},
+              "step_ms": {"gram": st[0], "finalize_cholesky": st[1], "first_solve": st[2], "rest": st[3],
+                          "cholesky_kernel": st[7]},
+              "accuracy": {"fp64_residual": res[0], "fp32_storage_floor": floor, "sigma_max_sq": s2,
+                           "ok": res[0] <= 2 * floor}})
+    return 0
+
+
 def run_profile_solve(args):
     """One small BF16 solve for an ncu capture (--profile-solve M): Gaussian S of 1024 x M
     (seed 1), v seed 2, lambda 1e-4, after --warmup solves.  Prints the device status."""
@@ -437,11 +589,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["headline", "precision", "batch", "stress"], default="headline",
+                    help="headline (default): the metric's workload; the others: one GPU, one line per path")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="M",
                     help="run one small solve (n=1024, m=M) after --warmup solves, for ncu captures")
     args = ap.parse_args()
     if args.profile_solve:
         return run_profile_solve(args)
+    if args.workload != "headline" and args.impl == "ours":
+        return run_workload(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

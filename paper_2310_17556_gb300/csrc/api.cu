@@ -153,7 +153,16 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     p->k = k;
     const int es = p->f64 ? 8 : 4;
     int kq = pow2_at_least(k);
-    const int kq_pass = pass_max_group((int)n, s_dtype, h->smem_optin);
+    int kq_pass = pass_max_group((int)n, s_dtype, h->smem_optin);
+    // the cluster pass (FP32 S, n <= 4096) keeps its rows in registers: it takes up to 4 right-hand
+    // sides whatever the one-CTA-per-strip pass's shared-memory bound is
+    for (int c = 4; c > kq_pass; c >>= 1) {
+        int cs = 0, crpt = 0;
+        if (pass_cluster_plan(s_dtype, (int)n, c, h->num_sms, m, h->smem_optin, &cs, &crpt) > 0) {
+            kq_pass = c;
+            break;
+        }
+    }
     const int kq_trsv = trsv_max_group((int)p->n_pad, es, h->smem_optin);
     if (kq_pass < 1 || kq_trsv < 1)
         return fail(h, DFS_ERR_UNSUPPORTED, "n=%lld too large for the on-chip n-space buffers", (long long)n);
