@@ -156,6 +156,19 @@ dfs_status dfs_solve_host(dfs_handle handle, const void* S, int s_dtype, int64_t
                           void* X, int64_t ldx, const dfs_options* opt, void* stream,
                           dfs_info* info);
 
+/* dfs_solve_host without the wait: the copies and the solve are queued and the call returns.
+ * S and V must be PINNED host memory (pageable memory makes the copies synchronous) and must stay
+ * unchanged, and X must not be read, until `stream` has finished the call's work (dfs_sync_info
+ * or a stream synchronize).  The uploads run on a copy stream of the handle into one of two
+ * device staging slots that alternate between calls, so consecutive calls overlap one call's
+ * host -> device copy with the previous call's solve (the link is the bound of a host-to-host
+ * solve); the solve and the download of X run on `stream` in call order.  A failed pivot or
+ * other device error is reported by the next dfs_sync_info, which describes the last call's
+ * solve only. */
+dfs_status dfs_solve_host_async(dfs_handle handle, const void* S, int s_dtype, int64_t n, int64_t m,
+                                int64_t lds, const void* V, int64_t k, int64_t ldv, double lambda,
+                                void* X, int64_t ldx, const dfs_options* opt, void* stream);
+
 /* Complex stochastic reconfiguration (Section 4, full Fisher matrix F = S^dagger S): solve
  * (S^dagger S + lambda I) X = V for complex S = S_re + i S_im and k complex right-hand sides.
  * S_re, S_im: DEVICE planes, n x m row-major with the same lds and dtype (FP32, BF16 or FP64, the

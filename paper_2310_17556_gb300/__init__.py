@@ -18,6 +18,7 @@ from .api import (  # noqa: F401
     dfs_solve,
     dfs_solve_batched,
     dfs_solve_host,
+    dfs_solve_host_async,
     dfs_solve_complex,
     dfs_step_times,
     dfs_sync_info,

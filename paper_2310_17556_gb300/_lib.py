@@ -29,7 +29,7 @@ PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 # every entry point include/dfs.h declares
 EXPORTS = (
     "dfs_create", "dfs_destroy", "dfs_status_string", "dfs_last_error", "dfs_reserve", "dfs_kernel_launches",
-    "dfs_solve", "dfs_solve_host", "dfs_solve_complex", "dfs_sync_info", "dfs_step_times", "dfs_solve_batched",
+    "dfs_solve", "dfs_solve_host", "dfs_solve_host_async", "dfs_solve_complex", "dfs_sync_info", "dfs_step_times", "dfs_solve_batched",
     "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass", "dfs_fisher_pass_noalloc",
 )
 
@@ -70,6 +70,8 @@ _SIGS = {
                             C.POINTER(dfs_options), _VP, C.POINTER(dfs_info)]),
     "dfs_solve_host": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, C.c_double, _VP, _I64,
                                  C.POINTER(dfs_options), _VP, C.POINTER(dfs_info)]),
+    "dfs_solve_host_async": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, C.c_double, _VP,
+                                       _I64, C.POINTER(dfs_options), _VP]),
     "dfs_solve_complex": (C.c_int, [_VP, _VP, _VP, C.c_int, _I64, _I64, _I64, _VP, _VP, _I64, _I64, C.c_double,
                                     _VP, _VP, _I64, C.POINTER(dfs_options), _VP, C.POINTER(dfs_info)]),
     "dfs_sync_info": (C.c_int, [_VP, _VP, C.POINTER(dfs_info)]),

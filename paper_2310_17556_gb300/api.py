@@ -179,6 +179,25 @@ def dfs_solve_host(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor
     return X, _info_dict(info)
 
 
+def dfs_solve_host_async(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor, precision="auto",
+                         max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
+                         center: bool = False) -> torch.Tensor:
+    """dfs_solve_host queued without waiting (pinned S, V, X): consecutive calls overlap one call's
+    upload with the previous call's solve.  Read X, and the status (dfs_sync_info), after the stream
+    has finished."""
+    h = handle or default_handle()
+    n, m = S.shape
+    k = V.shape[0]
+    if not (S.is_pinned() and V.is_pinned() and X.is_pinned()):
+        raise ValueError("dfs_solve_host_async needs pinned host tensors")
+    opt = _opts(precision, max_iter, tol, center=center)
+    st = h.lib.dfs_solve_host_async(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k,
+                                    _rows(V, "V"), float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt),
+                                    _stream(stream))
+    _check(h.lib, h.h, st)
+    return X
+
+
 def dfs_solve_complex(S_re: torch.Tensor, S_im: torch.Tensor, V_re: torch.Tensor, V_im: torch.Tensor, lam: float,
                       precision="auto", max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None,
                       stream=None):

@@ -37,6 +37,17 @@ struct dfs_handle_s {
     cudaEvent_t lane_done[kMaxLanes] = {};
     cudaEvent_t fork_ev = nullptr;
     int chol_share = 1;  // the cooperative Cholesky takes 1 / chol_share of the resident-CTA capacity
+    // dfs_solve_host_async: two device staging slots for S and V (alternating calls), one for X, a
+    // copy stream for the uploads and the events that order slot reuse
+    void* abuf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    size_t abuf_bytes[2][2] = {{0, 0}, {0, 0}};
+    void* axbuf = nullptr;
+    size_t axbuf_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t slot_free[2] = {nullptr, nullptr};
+    cudaEvent_t slot_copied[2] = {nullptr, nullptr};
+    bool slot_used[2] = {false, false};
+    int aslot = 0;
     size_t hbuf_bytes[3] = {0, 0, 0};
     int last_precision = 0;
     // Step-timing events: a ring of kTimingSlots solves x kMarks marks (DFS_FLAG_STEP_TIMING).
@@ -593,6 +604,14 @@ dfs_status dfs_destroy(dfs_handle h) {
         if (h->lane_done[l]) cudaEventDestroy(h->lane_done[l]);
     }
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    for (int sl = 0; sl < 2; ++sl) {
+        for (int b = 0; b < 2; ++b)
+            if (h->abuf[sl][b]) cudaFree(h->abuf[sl][b]);
+        if (h->slot_free[sl]) cudaEventDestroy(h->slot_free[sl]);
+        if (h->slot_copied[sl]) cudaEventDestroy(h->slot_copied[sl]);
+    }
+    if (h->axbuf) cudaFree(h->axbuf);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete h;
     return DFS_OK;
 }
@@ -647,6 +666,58 @@ dfs_status dfs_solve_host(dfs_handle h, const void* S, int s_dtype, int64_t n, i
     if (s != DFS_OK) return s;
     DFS_CK(cudaMemcpy2DAsync(X, ldx * vs, h->hbuf[2], ldx_d * vs, m * vs, k, cudaMemcpyDeviceToHost, stream));
     return fill_info(h, stream, info);
+}
+
+// Grow a staging buffer; a buffer still in use by queued work is only replaced after the device
+// has finished that work (cudaFree synchronizes).
+static dfs_status grow_staging(dfs_handle h, void** buf, size_t* have, size_t need) {
+    if (need <= *have) return DFS_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, DFS_ERR_NO_MEMORY, "cudaMalloc(%zu) for host-path staging failed", need);
+    }
+    *have = need;
+    return DFS_OK;
+}
+
+dfs_status dfs_solve_host_async(dfs_handle h, const void* S, int s_dtype, int64_t n, int64_t m, int64_t lds,
+                                const void* V, int64_t k, int64_t ldv, double lambda, void* X, int64_t ldx,
+                                const dfs_options* opt, void* stream_) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    dfs_status s;
+    if ((s = check_s(h, S, s_dtype, n, m, lds)) != DFS_OK) return s;
+    if (!V || !X || k < 1 || ldv < m || ldx < m) return fail(h, DFS_ERR_INVALID_ARG, "bad V/X arguments");
+    const size_t es = elem_size(s_dtype);
+    const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
+    const int64_t ldv_d = round_up(m, 4);
+    if (!h->copy_stream) DFS_CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    const int sl = h->aslot;
+    h->aslot ^= 1;
+    if (!h->slot_free[sl]) DFS_CK(cudaEventCreateWithFlags(&h->slot_free[sl], cudaEventDisableTiming));
+    if (!h->slot_copied[sl]) DFS_CK(cudaEventCreateWithFlags(&h->slot_copied[sl], cudaEventDisableTiming));
+    if ((s = grow_staging(h, &h->abuf[sl][0], &h->abuf_bytes[sl][0], (size_t)n * lds * es)) != DFS_OK) return s;
+    if ((s = grow_staging(h, &h->abuf[sl][1], &h->abuf_bytes[sl][1], (size_t)k * ldv_d * vs)) != DFS_OK) return s;
+    if ((s = grow_staging(h, &h->axbuf, &h->axbuf_bytes, (size_t)k * ldv_d * vs)) != DFS_OK) return s;
+    // upload into this slot once the solve that last read it has finished
+    if (h->slot_used[sl]) DFS_CK(cudaStreamWaitEvent(h->copy_stream, h->slot_free[sl], 0));
+    DFS_CK(cudaMemcpyAsync(h->abuf[sl][0], S, (size_t)n * lds * es, cudaMemcpyHostToDevice, h->copy_stream));
+    DFS_CK(cudaMemcpy2DAsync(h->abuf[sl][1], ldv_d * vs, V, ldv * vs, m * vs, k, cudaMemcpyHostToDevice,
+                             h->copy_stream));
+    DFS_CK(cudaEventRecord(h->slot_copied[sl], h->copy_stream));
+    DFS_CK(cudaStreamWaitEvent(stream, h->slot_copied[sl], 0));
+    s = solve_device(h, h->abuf[sl][0], s_dtype, n, m, lds, h->abuf[sl][1], k, ldv_d, lambda, h->axbuf, ldv_d, opt,
+                     stream, nullptr);
+    if (s != DFS_OK) return s;
+    DFS_CK(cudaEventRecord(h->slot_free[sl], stream));
+    h->slot_used[sl] = true;
+    DFS_CK(cudaMemcpy2DAsync(X, ldx * vs, h->axbuf, ldv_d * vs, m * vs, k, cudaMemcpyDeviceToHost, stream));
+    return DFS_OK;
 }
 
 dfs_status dfs_solve_complex(dfs_handle h, const void* S_re, const void* S_im, int s_dtype, int64_t n, int64_t m,

@@ -348,6 +348,28 @@ def test_refinement_final_correction_from_bf16_tiles(lam):
     assert info2["passes"] == info2["iters"] >= 1, info2
 
 
+def test_host_async_pipeline_matches_oracle():
+    """Three queued host-memory solves with different S, V (the staging slots alternate, so the
+    third reuses the first's): each X matches its oracle solve after one synchronize."""
+    probs = []
+    for j in range(3):
+        n, m, lam = 300 + 37 * j, 20000 + 1000 * j, 1e-2
+        S = wl.gaussian(n, m, seed=800 + j)
+        V = wl.rhs(m, 2, seed=810 + j)
+        Sh = torch.empty(S.shape, dtype=S.dtype, pin_memory=True)
+        Sh.copy_(S)
+        Vh = torch.empty(V.shape, dtype=V.dtype, pin_memory=True)
+        Vh.copy_(V)
+        Xh = torch.empty(V.shape, dtype=V.dtype, pin_memory=True)
+        probs.append((Sh, Vh, lam, Xh))
+    for Sh, Vh, lam, Xh in probs:
+        dfs.dfs_solve_host_async(Sh, Vh, lam, Xh, precision="bf16")
+    torch.cuda.synchronize()
+    assert dfs.dfs_sync_info()["status"] == 0
+    for Sh, Vh, lam, Xh in probs:
+        assert rel_err(Xh.double().numpy(), solve_ref(Sh, Vh, lam)) <= 1e-6
+
+
 def _complex_inputs(n, m, k, seed, dtype=torch.float32):
     A = wl.gaussian(n, m, seed=seed, device=dev()) / math.sqrt(2)
     B = wl.gaussian(n, m, seed=seed + 1, device=dev()) / math.sqrt(2)
