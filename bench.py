@@ -66,6 +66,23 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over the ranks (a job's time is its slowest rank's); the value itself
+    when there is no process group."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(world_size: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank solves `steps` problems of its own (weak scaling)."""
+    return world_size * steps / seconds
+
+
 def _clock_sampler(gpu_index: int):
     fields = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -284,11 +301,8 @@ def run_ours(args):
     clocks = _clock_summary(clocks_proc)
     info = dfs.dfs_sync_info()
     step_ms, nsteps_timed = dfs.dfs_step_times()
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = ws * args.steps / (elapsed_ms / 1e3)
+    elapsed_ms = _max_over_ranks(elapsed_ms, dist, dev)
+    value = _job_rate(ws, args.steps, elapsed_ms / 1e3)
     X_mixed = X.clone()
 
     # ---------------- same workload at lambda = 1e-2 ----------------
@@ -338,11 +352,8 @@ def run_ours(args):
     info_e2e = dfs.dfs_sync_info()
     if info_e2e["status"] != 0:
         raise RuntimeError(f"host-path solve failed: {info_e2e}")
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * ke / e2e_s
+    e2e_s = _max_over_ranks(e2e_s, dist, dev)
+    e2e_value = _job_rate(ws, ke, e2e_s)
 
     # ---------------- rooflines from the live per-kernel events ----------------
     peaks, peak_kind = _peaks()
