@@ -52,6 +52,7 @@ def workload_config(lam=LAMBDA):
         "mixed_path": "BF16 tcgen05 Gram on packed tiles, FP32 Cholesky, n-space refinement "
                       "(FP32 passes over S with FP64 accumulation) to est. rel. error <= 1e-7",
         "cache": "inputs larger than L2 (S is 4.3 GB; L2 is 129 MB), no flush between steps",
+        "launch": "one dfs_solve captured into a CUDA graph, replayed once per step",
         "parallelism": "replicas (one independent solve per GPU)",
     }
 
@@ -285,22 +286,40 @@ def run_ours(args):
         dfs.dfs_solve(S, v, lam, X=out, precision=prec, sync=False, timing=timing)
 
     # ---------------- mixed path (headline), per-kernel CUDA events inside the timed region ----
+    # The solve's launch sequence is fixed (no host round trip), so it is captured once into a CUDA
+    # graph and the timed steps replay it: every kernel of the solve runs each step, without the
+    # per-launch host overhead.  The step events are part of the graph.
     for _ in range(args.warmup):
         solve()
     info = dfs.dfs_sync_info()
     if info["status"] != 0:
         raise RuntimeError(f"mixed solve failed: {info}")
-    dfs.dfs_step_times()  # reset the event ring
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(stream)
+    launches_cap0 = dfs.dfs_kernel_launches()
+    with torch.cuda.graph(graph, stream=cap):
+        solve(timing=True)
+    per_solve_launches = dfs.dfs_kernel_launches() - launches_cap0
+    stream.wait_stream(cap)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    info = dfs.dfs_sync_info()
+    if info["status"] != 0:
+        raise RuntimeError(f"mixed solve (graph replay) failed: {info}")
+    # (no dfs_step_times reset here: the captured solve left one timed slot pending, and every
+    # replay re-records that slot's events, so after the timed replays it holds the last one's)
     clocks_proc = _clock_sampler(local)
     time.sleep(0.3)
     barrier()
-    launches0 = dfs.dfs_kernel_launches()
-    elapsed_ms = _timed(torch, stream, lambda: solve(timing=True), args.steps)
+    elapsed_ms = _timed(torch, stream, graph.replay, args.steps)
     barrier()
-    launches = dfs.dfs_kernel_launches() - launches0
+    launches = per_solve_launches * args.steps
     clocks = _clock_summary(clocks_proc)
     info = dfs.dfs_sync_info()
     step_ms, nsteps_timed = dfs.dfs_step_times()
+    nsteps_timed = args.steps  # the graph's events are re-recorded by every replay
     elapsed_ms = _max_over_ranks(elapsed_ms, dist, dev)
     value = _job_rate(ws, args.steps, elapsed_ms / 1e3)
     X_mixed = X.clone()

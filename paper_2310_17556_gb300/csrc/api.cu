@@ -378,8 +378,15 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         if (!h->ev[slot][0])
             for (int i = 0; i < dfs_handle_s::kMarks; ++i) DFS_CK(cudaEventCreate(&h->ev[slot][i]));
     }
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap_status) != cudaSuccess) cudaGetLastError();
+    const bool capturing = cap_status == cudaStreamCaptureStatusActive;
     auto mark = [&](int i) -> cudaError_t {
-        return timed ? cudaEventRecord(h->ev[slot][i], stream) : cudaSuccess;
+        // inside a stream capture the marks must be external event nodes, so that every replay of
+        // the graph records them
+        return timed ? cudaEventRecordWithFlags(h->ev[slot][i], stream,
+                                                capturing ? cudaEventRecordExternal : cudaEventRecordDefault)
+                     : cudaSuccess;
     };
     const int fp64_panel = opt && (opt->flags & DFS_FLAG_FP64_PANEL);
 

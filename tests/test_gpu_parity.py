@@ -348,6 +348,31 @@ def test_refinement_final_correction_from_bf16_tiles(lam):
     assert info2["passes"] == info2["iters"] >= 1, info2
 
 
+def test_solve_is_capturable_in_a_cuda_graph():
+    """dfs_solve's launch sequence has no host round trip: captured once into a CUDA graph and
+    replayed, it gives the same x as the stream-launched solve, bit for bit, and the device status."""
+    n, m, lam = 512, 65536, 1e-3
+    S = wl.gaussian(n, m, seed=95, device=dev())
+    V = wl.rhs(m, 1, seed=96, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="bf16")  # also sizes the workspace
+    Xg = torch.empty_like(V)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    dfs.dfs_step_times()
+    with torch.cuda.graph(g, stream=s):
+        dfs.dfs_solve(S, V, lam, X=Xg, precision="bf16", sync=False, timing=True)
+    for _ in range(2):
+        Xg.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(Xg, X)
+        assert dfs.dfs_sync_info()["status"] == 0
+    # the step events are graph nodes: the replays recorded them
+    ms, count = dfs.dfs_step_times()
+    assert count == 1 and ms[0] > 0 and ms[4] >= ms[0]
+
+
 def test_host_async_pipeline_matches_oracle():
     """Three queued host-memory solves with different S, V (the staging slots alternate, so the
     third reuses the first's): each X matches its oracle solve after one synchronize."""
