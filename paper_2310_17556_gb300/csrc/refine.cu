@@ -64,16 +64,23 @@ refine_init_kernel(const T* __restrict__ Z, int n_pad, int KQ, double* __restric
 // (2^-9 relative, of a correction of relative size delta) adds up to 2^-8 delta to the error
 // estimate; if that run does not converge, nothing else is decided here (the full pass that
 // follows recomputes x exactly and the next check carries on from delta_it).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 refine_check_kernel(const double* __restrict__ U2part, int nparts, double* __restrict__ U2, int KQ, int k,
                     double lambda, double tol, int it, int max_iter, int fast, DevStatus* st) {
     if (block_should_exit(st, 1)) return;
     __shared__ double u2[16];
-    if (threadIdx.x < 2 * KQ) {
+    // one warp per statistic: lanes take the parts lane, lane + 32, ..., then a fixed shuffle tree
+    // (a fixed summation order, so the result does not vary run to run)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 2 * KQ) {
         double u = 0.0;
-        for (int b = 0; b < nparts; ++b) u += U2part[(int64_t)b * 2 * KQ + threadIdx.x];
-        u2[threadIdx.x] = u;
-        U2[threadIdx.x] = u;
+        for (int b = lane; b < nparts; b += 32) u += U2part[(int64_t)b * 2 * KQ + warp];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (lane == 0) {
+            u2[warp] = u;
+            U2[warp] = u;
+        }
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -170,7 +177,7 @@ cudaError_t launch_refine_init(int f64, const void* Z, int n_pad, int KQ, double
 cudaError_t launch_refine_check(const double* U2part, int nparts, double* U2, int KQ, int k, double lambda, double tol,
                                 int it, int max_iter, int fast, DevStatus* st, cudaStream_t stream) {
     if (KQ > 8) return cudaErrorInvalidValue;
-    refine_check_kernel<<<1, 32, 0, stream>>>(U2part, nparts, U2, KQ, k, lambda, tol, it, max_iter, fast, st);
+    refine_check_kernel<<<1, 64 * KQ, 0, stream>>>(U2part, nparts, U2, KQ, k, lambda, tol, it, max_iter, fast, st);
     count_launch();
     return cudaGetLastError();
 }
