@@ -370,15 +370,19 @@ nspace_kernel(const T* __restrict__ W, int64_t ld, int n_pad, const T* __restric
         if (gthread && gpart == 0)
 #pragma unroll
             for (int q = 0; q < KQ; ++q) xs[gr * KQ + q] = acc[q];
-        gsync();  // solved values visible to the GEMV threads (and the broadcasting warps)
-        // warp w sends the block to rank (rank + 1 + w) mod cs, 16 bytes per lane and store
-        if (warp < (int)cs - 1) {
-            const uint32_t peer = (rank + 1 + (uint32_t)warp) % cs;
-            const uint32_t rb = ns_mapa(&bars[dir * nsb + sb], peer);
-            const uint32_t rx = ns_mapa(xs, peer);
+        gsync();  // solved values visible to the GEMV threads, which also broadcast them
+        // GEMV warp w sends the block to ranks (rank + 1 + w + 8 j) mod cs, 16 bytes per lane and
+        // store (only the GEMV warps have passed the barrier above: with a 16-CTA cluster the
+        // other warps must not send)
+        if (gthread) {
             const uint4* src = reinterpret_cast<const uint4*>(xs);
-            for (int ch = lane; ch < (int)(NS_SB * KQ * sizeof(T) / 16); ch += 32)
-                ns_st_async_v4(rx + (uint32_t)ch * 16u, rb, src[ch]);
+            for (int pw = warp; pw < (int)cs - 1; pw += NS_GT / 32) {
+                const uint32_t peer = (rank + 1 + (uint32_t)pw) % cs;
+                const uint32_t rb = ns_mapa(&bars[dir * nsb + sb], peer);
+                const uint32_t rx = ns_mapa(xs, peer);
+                for (int ch = lane; ch < (int)(NS_SB * KQ * sizeof(T) / 16); ch += 32)
+                    ns_st_async_v4(rx + (uint32_t)ch * 16u, rb, src[ch]);
+            }
         }
     };
     const auto owner = [&](int sb) { return sb % (int)cs == (int)rank; };
@@ -442,15 +446,23 @@ static size_t ns_fixed_bytes(int n_pad, int KQ, int elem, int cs) {
 }
 static size_t ns_slot_bytes(int elem) { return (size_t)NS_SB * (NS_SB + 16 / elem) * elem; }
 
-int nspace_cluster_size(int n_pad) {
+static bool ns_fits(int n_pad, int KQ, int elem, int cs, size_t smem_limit) {
+    return ns_fixed_bytes(n_pad, KQ, elem, cs) + 8192 + 2 * ns_slot_bytes(elem) <= smem_limit;
+}
+
+// Cluster size: up to 8 CTAs (portable); 16 (a non-portable cluster, 7 of which fit on a GB300)
+// when the owned diagonal inverses of 8 ranks do not fit in shared memory (n_pad > 4608 in FP32).
+int nspace_cluster_size(int n_pad, int KQ, int elem, size_t smem_limit) {
     const int nsb = n_pad / NS_SB;
-    return nsb < NS_MAX_CS ? nsb : NS_MAX_CS;
+    const int cs = nsb < NS_MAX_CS ? nsb : NS_MAX_CS;
+    if (ns_fits(n_pad, KQ, elem, cs, smem_limit) || nsb < 2 * NS_MAX_CS) return cs;
+    return ns_fits(n_pad, KQ, elem, 2 * NS_MAX_CS, smem_limit) ? 2 * NS_MAX_CS : cs;
 }
 
 // Ring slots that fit (0: the cluster form does not apply).
 int nspace_slots(int n_pad, int KQ, int elem, size_t smem_limit) {
     if (n_pad % NS_SB != 0 || n_pad < NS_SB) return 0;
-    const int cs = nspace_cluster_size(n_pad);
+    const int cs = nspace_cluster_size(n_pad, KQ, elem, smem_limit);
     const size_t fixed = ns_fixed_bytes(n_pad, KQ, elem, cs) + 8192;  // + static shared memory
     if (fixed + 2 * ns_slot_bytes(elem) > smem_limit) return 0;
     size_t s = (smem_limit - fixed) / ns_slot_bytes(elem);
@@ -461,12 +473,14 @@ template <typename T, int KQ>
 static cudaError_t launch_ns_t(const void* W, int64_t ld, int n_pad, const void* Linv, int mode, const double* Rpart,
                                int nparts, int n, int k, const double* Y, double lambda, const void* B, int64_t ldb,
                                double* R, void* Z, int64_t ldz, const double* U2part, double* U2, int nslots,
-                               DevStatus* st, int honor_stop, cudaStream_t stream) {
-    const int cs = nspace_cluster_size(n_pad);
+                               int cs, DevStatus* st, int honor_stop, cudaStream_t stream) {
     const size_t smem = (size_t)nslots * ns_slot_bytes(sizeof(T)) + ns_fixed_bytes(n_pad, KQ, sizeof(T), cs);
     auto kern = nspace_kernel<T, KQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (cs > NS_MAX_CS && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+                              cudaSuccess)
+        return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cs);
     cfg.blockDim = dim3(NS_THREADS);
@@ -492,12 +506,13 @@ cudaError_t launch_nspace(int f64, int kq, const void* W, int64_t ld, int n_pad,
                           size_t smem_limit, DevStatus* st, int honor_stop, cudaStream_t stream) {
     const int nslots = nspace_slots(n_pad, kq, f64 ? 8 : 4, smem_limit);
     if (nslots < 2) return cudaErrorInvalidValue;
+    const int cs = nspace_cluster_size(n_pad, kq, f64 ? 8 : 4, smem_limit);
 #define DFS_NS(KQ)                                                                                                 \
     case KQ:                                                                                                       \
         return f64 ? launch_ns_t<double, KQ>(W, ld, n_pad, Linv, mode, Rpart, nparts, n, k, Y, lambda, B, ldb, R, \
-                                             Z, ldz, U2part, U2, nslots, st, honor_stop, stream)                  \
+                                             Z, ldz, U2part, U2, nslots, cs, st, honor_stop, stream)                  \
                    : launch_ns_t<float, KQ>(W, ld, n_pad, Linv, mode, Rpart, nparts, n, k, Y, lambda, B, ldb, R,  \
-                                            Z, ldz, U2part, U2, nslots, st, honor_stop, stream);
+                                            Z, ldz, U2part, U2, nslots, cs, st, honor_stop, stream);
     switch (kq) {
         DFS_NS(1)
         DFS_NS(2)

@@ -348,6 +348,17 @@ def test_refinement_final_correction_from_bf16_tiles(lam):
     assert info2["passes"] == info2["iters"] >= 1, info2
 
 
+def test_nspace_sixteen_cta_cluster():
+    """n = 5000 (n_pad 5120): eight ranks cannot hold their diagonal inverses in shared memory,
+    so the n-space solves run as a 16-CTA cluster; the solve still matches the oracle."""
+    n, m, lam = 5000, 12000, 1e-2
+    S = wl.gaussian(n, m, seed=97, device=dev())
+    V = wl.rhs(m, 1, seed=98, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="bf16")
+    assert info["status"] == 0, info
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+
+
 def test_solve_is_capturable_in_a_cuda_graph():
     """dfs_solve's launch sequence has no host round trip: captured once into a CUDA graph and
     replayed, it gives the same x as the stream-launched solve, bit for bit, and the device status."""
