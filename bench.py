@@ -532,7 +532,8 @@ def run_workload(args):
                   "config": {"n": n, "m": m, "k": k, "lambda": lam, "S": "FP32, sigma log-spaced 1..1e-4 (/sqrt n)"},
                   "info": {"status": info["status"], "iters": info["iters"], "full_passes": info["passes"]},
                   "step_ms": {"gram": st[0], "finalize_cholesky": st[1], "first_solve": st[2], "rest": st[3],
-                              "cholesky_kernel": st[7]},
+                              "sv_kernel": st[5], "first_refinement_pass_kernel": st[6], "cholesky_kernel": st[7],
+                              "tile_correct_kernel": st[8]},
                   "accuracy": {"fp64_residual_max": max(res), "bound_e_rel": cond * max(res),
                                "ok": cond * max(res) <= 1e-6}})
     elif args.workload == "batch":
@@ -604,7 +605,8 @@ def run_workload(args):
               "config": {"n": n, "m": m, "k": 1, "lambda": lam, "S": "BF16, Student-t(3) x log-normal columns / sqrt n"},
               "info": {"status": info["status"], "iters": info["iters"], "full_passes": info["passes"]},
               "step_ms": {"gram": st[0], "finalize_cholesky": st[1], "first_solve": st[2], "rest": st[3],
-                          "cholesky_kernel": st[7]},
+                          "sv_kernel": st[5], "first_refinement_pass_kernel": st[6], "cholesky_kernel": st[7],
+                          "tile_correct_kernel": st[8]},
               "accuracy": {"fp64_residual": res[0], "fp32_storage_floor": floor, "sigma_max_sq": s2,
                            "ok": res[0] <= 2 * floor}})
     return 0
