@@ -419,11 +419,12 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         DFS_CK(launch_group_reset(h->dstat, stream));
         // b = S v; the first group's pass also writes the packed tensor-core tiles of S
         if (q0 == 0) DFS_CK(mark(6));
+        int sv_parts = p.pp.sv_grid;
         DFS_CK(launch_sv_pack(p.pp, s_dtype, kq, q0 == 0 ? p.pack : 0, S, ni, m, lds, Vg, ldv, kg, Rpart, Sp,
-                              h->dstat, stream, rs ? rs + p.n_pad : nullptr));
+                              h->dstat, stream, rs ? rs + p.n_pad : nullptr, &sv_parts));
         if (q0 == 0) DFS_CK(mark(7));
         if (!p.ns)
-            DFS_CK(launch_pass_reduce(p.f64, Rpart, p.pp.sv_grid, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z,
+            DFS_CK(launch_pass_reduce(p.f64, Rpart, sv_parts, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z,
                                       nullptr, nullptr, h->dstat, 0, stream));
         if (center)  // b = P (O v) / sqrt(n)
             DFS_CK(launch_center_vec(p.f64, 0, ni, npi, kq, kg, R, nullptr, 0.0, Z, nullptr, h->dstat, 0, stream));
@@ -451,7 +452,7 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         // y0 = W^{-1} b by the two triangular solves (with the reduction of b = S v folded in)
         if (p.ns) {
             DFS_CK(launch_nspace(p.f64, kq, W, p.n_pad, npi, Linv, NS_MODE_REDUCE | NS_MODE_FWD | NS_MODE_BWD, Rpart,
-                                 p.pp.sv_grid, ni, kg, nullptr, lambda, nullptr, 0, R, Z, kq, nullptr, nullptr,
+                                 sv_parts, ni, kg, nullptr, lambda, nullptr, 0, R, Z, kq, nullptr, nullptr,
                                  h->smem_optin, h->dstat, 0, stream));
         } else {
             DFS_CK(launch_trsv(p.f64, 0, W, p.n_pad, npi, Linv, Z, kq, kg, kq, h->dstat, 0, stream));

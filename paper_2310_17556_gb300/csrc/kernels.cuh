@@ -92,7 +92,8 @@ int64_t pack_kblocks(int s_dtype, int pack, int64_t m);
 size_t pack_bytes(int s_dtype, int pack, int64_t n, int64_t m);
 cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,
                            int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
-                           const DevStatus* st, cudaStream_t stream, const float* rinv = nullptr);
+                           const DevStatus* st, cudaStream_t stream, const float* rinv = nullptr,
+                           int* parts = nullptr);  // *parts: the partial rows of R written (for the reduce)
 // dmode: 0 = no change measurement, 1 = also sum (X_new - X_old)^2 with X_old read from X,
 // 2 = same with X_old = V / lambda.  U2part holds 2 * kq doubles per CTA: sum U^2, sum dX^2.
 cudaError_t launch_pass(const PassPlan& plan, int s_dtype, int kq, const void* S, int n, int64_t m, int64_t lds,

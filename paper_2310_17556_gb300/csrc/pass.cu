@@ -312,6 +312,130 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
 }
 
 // ------------------------------------------------------------------------------------------
+// R = S V by 128-row blocks, optionally packing S into BF16 tiles (PACK 1), for S whose rows are
+// far apart (FP32 S with more than 1024 rows, BF16 S).  CTA (row block I, column chunk c) walks
+// k-blocks kb0 .. kb1 of its 128 rows only: four threads per row, each with 16 contiguous
+// elements (32 or 64 bytes) of every 64-column k-block, four k-blocks in flight.  A CTA thus
+// streams 128 long row runs, where one CTA per 64-column strip touched every row of S per strip
+// (rows megabytes apart: address translation, not bandwidth, bounded that form).  Row sums in FP32,
+// folded into FP64 every 32 k-blocks, reduced over the row's four threads; part c of Rpart holds
+// chunk c's sums of every row.
+constexpr int SVB_ROWS = 128;
+constexpr int SVB_THREADS = 4 * SVB_ROWS;
+constexpr int SVB_UNROLL = 4;
+
+template <typename TS, int KQ, int PACK>
+__global__ void __launch_bounds__(SVB_THREADS)
+sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds, const float* __restrict__ V,
+               int64_t ldv, int k, double* __restrict__ Rpart, unsigned char* __restrict__ Sp, int nchunks,
+               const DevStatus* st) {
+    constexpr int VEC = Vec16<TS>::N;  // elements per 16-byte load
+    constexpr int LPT = 16 / VEC;      // 16-byte loads per thread and k-block
+    if (block_should_exit(st, 0)) return;
+    const int nblk = n_rows / SVB_ROWS;
+    const int I = blockIdx.x % nblk, chunk = blockIdx.x / nblk;
+    const int tid = threadIdx.x, r = tid >> 2, part = tid & 3;
+    const int i = I * SVB_ROWS + r;
+    const int64_t nkb_all = ceil_div(m, 64);
+    const int64_t per = ceil_div(nkb_all, nchunks);
+    const int64_t kb0 = (int64_t)chunk * per;
+    const int64_t kb1 = kb0 + per < nkb_all ? kb0 + per : nkb_all;
+    const TS* row = S + (int64_t)(i < n ? i : 0) * lds;
+    // V's rows need not be 16-byte aligned (ldv is any value >= m): vector loads only when they are
+    const bool v_vec = ((reinterpret_cast<uintptr_t>(V) | (uintptr_t)(ldv * 4)) & 15) == 0;
+    float acc[KQ];
+    double acc64[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) acc[q] = 0.f, acc64[q] = 0.0;
+    int since = 0;
+    for (int64_t kb = kb0; kb < kb1; kb += SVB_UNROLL) {
+        float sv[SVB_UNROLL][16];
+#pragma unroll
+        for (int u = 0; u < SVB_UNROLL; ++u) {
+            const int64_t col = (kb + u) * 64 + part * 16;
+            if (i < n && kb + u < kb1 && col + 16 <= m) {
+#pragma unroll
+                for (int l = 0; l < LPT; ++l) load16_stream<TS, float>(row + col + l * VEC, &sv[u][l * VEC]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    sv[u][e] = (i < n && kb + u < kb1 && col + e < m) ? load1<TS, float>(row + col + e) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < SVB_UNROLL; ++u) {
+            if (kb + u >= kb1) break;
+            const int64_t col = (kb + u) * 64 + part * 16;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                if (q >= k) break;
+                const float* vq = V + (int64_t)q * ldv + col;
+                float a = 0.f;
+                if (v_vec && col + 16 <= m) {
+#pragma unroll
+                    for (int e = 0; e < 16; e += 4) {
+                        const float4 w = __ldg(reinterpret_cast<const float4*>(vq + e));
+                        a = fmaf(sv[u][e], w.x, fmaf(sv[u][e + 1], w.y, fmaf(sv[u][e + 2], w.z, fmaf(sv[u][e + 3], w.w, a))));
+                    }
+                } else {
+                    for (int e = 0; e < 16; ++e)
+                        if (col + e < m) a = fmaf(sv[u][e], __ldg(vq + e), a);
+                }
+                acc[q] += a;
+            }
+            if constexpr (PACK == 1) {
+                // this thread's 32 bytes of the k-block's 128-byte BF16 row: 16-byte chunks 2 part, 2 part + 1
+                unsigned char* trow = Sp + ((((kb + u) * (int64_t)nblk) + I) << 14) + (r & 127) * 128;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint4 w;
+                    uint32_t* wp = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __nv_bfloat162 b = __floats2bfloat162_rn(sv[u][h * 8 + 2 * e], sv[u][h * 8 + 2 * e + 1]);
+                        wp[e] = *reinterpret_cast<const uint32_t*>(&b);
+                    }
+                    const int c = 2 * part + h;
+                    *reinterpret_cast<uint4*>(trow + ((c ^ (r & 7)) << 4)) = w;
+                }
+            }
+        }
+        if (++since == 32 / SVB_UNROLL) {
+            since = 0;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) acc64[q] += (double)acc[q], acc[q] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        double a = acc64[q] + (double)acc[q];
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        if (part == 0 && i < n) Rpart[((int64_t)chunk * n + i) * KQ + q] = a;
+    }
+}
+
+// column chunks of sv_rows_kernel (at most num_sms: the partial rows of R).  One 512-thread CTA
+// fills an SM's registers, so the nblk * c equal CTAs run in waves of num_sms: take the smallest
+// c >= num_sms / nblk whose last wave is at least 95 % full (the fullest found otherwise).
+static int sv_rows_chunks(int n_rows, int64_t m, int num_sms) {
+    const int64_t nblk = n_rows / SVB_ROWS, nkb = ceil_div(m, 64);
+    int64_t cmax = num_sms < nkb ? num_sms : nkb;
+    if (cmax < 1) cmax = 1;
+    int64_t c0 = ceil_div((int64_t)num_sms, nblk);
+    if (c0 > cmax) c0 = cmax;
+    int best = (int)c0;
+    double best_eff = 0.0;
+    for (int64_t c = c0; c <= cmax; ++c) {
+        const int64_t ctas = nblk * c, waves = ceil_div(ctas, (int64_t)num_sms);
+        const double eff = (double)ctas / (double)(waves * num_sms);
+        if (eff > best_eff + 1e-9) best_eff = eff, best = (int)c;
+        if (eff >= 0.95) break;
+    }
+    return best;
+}
+
+// ------------------------------------------------------------------------------------------
 // R = S V for FP32 S with at most 1024 rows, optionally packing S into BF16 tiles (PACK 1): a
 // streaming form of sv_pack_kernel.  A thread owns rows warp * 2 + rr + 32 t (t < 32) and 16 bytes
 // of every 64-column strip; its row segments stream through a cp.async ring of 4-row sub-stages
@@ -1148,9 +1272,53 @@ static cudaError_t launch_sv_ring_t(int grid, const void* S, int n, int n_rows, 
     return cudaGetLastError();
 }
 
+template <typename TS, int KQ, int PACK>
+static cudaError_t launch_sv_rows_t(int nchunks, const void* S, int n, int n_rows, int64_t m, int64_t lds,
+                                    const void* V, int64_t ldv, int k, double* Rpart, void* Sp, const DevStatus* st,
+                                    cudaStream_t stream) {
+    const int grid = nchunks * (n_rows / SVB_ROWS);
+    sv_rows_kernel<TS, KQ, PACK><<<grid, SVB_THREADS, 0, stream>>>(
+        static_cast<const TS*>(S), n, n_rows, m, lds, static_cast<const float*>(V), ldv, k, Rpart,
+        static_cast<unsigned char*>(Sp), nchunks, st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename TS, int KQ>
+static cudaError_t launch_sv_rows_kq(int pack, int nchunks, const void* S, int n, int n_rows, int64_t m, int64_t lds,
+                                     const void* V, int64_t ldv, int k, double* Rpart, void* Sp, const DevStatus* st,
+                                     cudaStream_t stream) {
+    return pack ? launch_sv_rows_t<TS, KQ, 1>(nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, st, stream)
+                : launch_sv_rows_t<TS, KQ, 0>(nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, st, stream);
+}
+
 cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, const void* S, int n, int64_t m,
                            int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
-                           const DevStatus* st, cudaStream_t stream, const float* rinv) {
+                           const DevStatus* st, cudaStream_t stream, const float* rinv, int* parts) {
+    if (parts) *parts = plan.sv_grid;
+    // rows far apart (FP32 S beyond the streaming form's 1024 rows, or BF16 S), BF16 tiles or none:
+    // the row-blocked form
+    if (pack <= 1 && (s_dtype == DFS_BF16 || (s_dtype == DFS_F32 && round_up(n, 256) > SVR_MAXNR * (PASS_THREADS / 16)))) {
+        const int n_rows = (int)round_up(n, pack ? 256 : SVB_ROWS);
+        const int nchunks = sv_rows_chunks(n_rows, m, plan.sv_grid);
+        if (parts) *parts = nchunks;
+#define DFS_SVB(KQ)                                                                                          \
+    case KQ:                                                                                                 \
+        return s_dtype == DFS_F32                                                                            \
+                   ? launch_sv_rows_kq<float, KQ>(pack, nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, st, \
+                                                  stream)                                                    \
+                   : launch_sv_rows_kq<__nv_bfloat16, KQ>(pack, nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, \
+                                                          Sp, st, stream);
+        switch (kq) {
+            DFS_SVB(1)
+            DFS_SVB(2)
+            DFS_SVB(4)
+            DFS_SVB(8)
+            default:
+                return cudaErrorInvalidValue;
+        }
+#undef DFS_SVB
+    }
     if (pack == 3 && s_dtype != DFS_F32) return cudaErrorInvalidValue;
     if (pack == 4 && (rinv == nullptr || s_dtype == DFS_F64)) return cudaErrorInvalidValue;
     // packed rows: an even number of 128-row blocks (the Gram's units pair blocks), zero past n

@@ -118,6 +118,24 @@ def test_bf16_storage_fp32_path():
     assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-5
 
 
+@pytest.mark.parametrize("dtype,prec,n,m,k,lam", [
+    (torch.bfloat16, "bf16", 1153, 12347, 3, 1e-2),   # ragged rows and columns; V rows not 16-byte aligned
+    (torch.float32, "bf16", 1500, 20001, 2, 1e-2),    # FP32 S beyond 1024 rows, packed
+    (torch.float32, "fp32", 2000, 9001, 1, 1e-2),     # FP32 S beyond 1024 rows, no packing
+    (torch.bfloat16, "fp32", 300, 5003, 4, 1e-2),     # BF16 S, no packing, four RHS
+    (torch.bfloat16, "bf16", 64, 70, 1, 0.3),         # one row block, a ragged second k-block
+])
+def test_row_blocked_sv_solves(dtype, prec, n, m, k, lam):
+    """b = S v by 128-row blocks (BF16 S, and FP32 S beyond 1024 rows), packing the BF16 Gram
+    tiles on the way for the mixed path: solves match the oracle at the path's tolerance."""
+    S = aligned(wl.gaussian(n, m, seed=41 + n, device=dev(), dtype=dtype))
+    V = wl.rhs(m, k, seed=42 + n, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision=prec)
+    assert info["status"] == 0 and info["precision"] == prec
+    tol = 1e-6 if prec == "bf16" else fp32_tol(S, lam)
+    assert rel_err(np64(X), solve_ref(S, V, lam)) <= tol
+
+
 def test_padded_leading_dimension_and_in_place():
     n, m, lam = 70, 1001, 1e-2
     big = wl.gaussian(n, 1024, seed=9, device=dev())
