@@ -312,122 +312,237 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
 }
 
 // ------------------------------------------------------------------------------------------
-// R = S V by 128-row blocks, optionally packing S into BF16 tiles (PACK 1), for S whose rows are
-// far apart (FP32 S with more than 1024 rows, BF16 S).  CTA (row block I, column chunk c) walks
-// k-blocks kb0 .. kb1 of its 128 rows only: four threads per row, each with 16 contiguous
-// elements (32 or 64 bytes) of every 64-column k-block, four k-blocks in flight.  A CTA thus
-// streams 128 long row runs, where one CTA per 64-column strip touched every row of S per strip
-// (rows megabytes apart: address translation, not bandwidth, bounded that form).  Row sums in FP32,
-// folded into FP64 every 32 k-blocks, reduced over the row's four threads; part c of Rpart holds
+// R = S V by blocks of R rows (8; 4 with 8 RHS), optionally packing S into BF16 tiles (PACK 1), for
+// S whose rows are far apart (FP32 S with more than 1024 rows, BF16 S).  The CTA's 512 threads
+// share its rows: at each step thread t takes the 8-column group base + t of every row, so a CTA
+// streams each of its rows as one contiguous front of 4096 columns, and the grid keeps about
+// R * num_sms rows open at once.  (One CTA per column strip opens every row of S at once, one per
+// 128 rows 128 * num_sms rows; rows megabytes apart each sit in pages of their own, and that many
+// open pages hold those forms to address-translation speed, well below HBM bandwidth.)  A
+// thread's V values serve all R rows.  Sums in FP32 per thread, folded every 32 steps into FP64
+// per warp (fixed shuffle order), the warps then added in order; part c of Rpart holds column
 // chunk c's sums of every row.
-constexpr int SVB_ROWS = 128;
-constexpr int SVB_THREADS = 4 * SVB_ROWS;
-constexpr int SVB_UNROLL = 4;
+constexpr int SVB_THREADS = 512;
+constexpr int SVB_WARPS = SVB_THREADS / 32;
+constexpr int SVB_FOLD = 32;
+
+template <int KQ>
+struct SvbRows {
+    static constexpr int R = KQ >= 8 ? 4 : 8;
+};
+
+// 8 consecutive elements of S as raw 16-byte vectors (two for FP32, one for BF16), and back
+template <typename TS>
+__device__ __forceinline__ void svb_pack_raw(const float* f, uint4* raw);
+template <>
+__device__ __forceinline__ void svb_pack_raw<float>(const float* f, uint4* raw) {
+    raw[0] = make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]), __float_as_uint(f[3]));
+    raw[1] = make_uint4(__float_as_uint(f[4]), __float_as_uint(f[5]), __float_as_uint(f[6]), __float_as_uint(f[7]));
+}
+__device__ __forceinline__ uint32_t svb_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <>
+__device__ __forceinline__ void svb_pack_raw<__nv_bfloat16>(const float* f, uint4* raw) {
+    // f holds BF16 values: the conversion is exact
+    raw[0] = make_uint4(svb_bf16x2(f[0], f[1]), svb_bf16x2(f[2], f[3]), svb_bf16x2(f[4], f[5]), svb_bf16x2(f[6], f[7]));
+}
+template <typename TS>
+__device__ __forceinline__ void svb_unpack_raw(const uint4* raw, float* f);
+template <>
+__device__ __forceinline__ void svb_unpack_raw<float>(const uint4* raw, float* f) {
+    f[0] = __uint_as_float(raw[0].x), f[1] = __uint_as_float(raw[0].y);
+    f[2] = __uint_as_float(raw[0].z), f[3] = __uint_as_float(raw[0].w);
+    f[4] = __uint_as_float(raw[1].x), f[5] = __uint_as_float(raw[1].y);
+    f[6] = __uint_as_float(raw[1].z), f[7] = __uint_as_float(raw[1].w);
+}
+template <>
+__device__ __forceinline__ void svb_unpack_raw<__nv_bfloat16>(const uint4* raw, float* f) {
+    const uint32_t w[4] = {raw[0].x, raw[0].y, raw[0].z, raw[0].w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) f[2 * e] = __uint_as_float(w[e] << 16), f[2 * e + 1] = __uint_as_float(w[e] & 0xffff0000u);
+}
+// the BF16 tile chunk of the 8 elements: S's own bits for BF16 S, round-to-nearest for FP32 S
+template <typename TS>
+__device__ __forceinline__ uint4 svb_bf16_chunk(const uint4* raw);
+template <>
+__device__ __forceinline__ uint4 svb_bf16_chunk<__nv_bfloat16>(const uint4* raw) {
+    return raw[0];
+}
+template <>
+__device__ __forceinline__ uint4 svb_bf16_chunk<float>(const uint4* raw) {
+    float f[8];
+    svb_unpack_raw<float>(raw, f);
+    return make_uint4(svb_bf16x2(f[0], f[1]), svb_bf16x2(f[2], f[3]), svb_bf16x2(f[4], f[5]), svb_bf16x2(f[6], f[7]));
+}
 
 template <typename TS, int KQ, int PACK>
-__global__ void __launch_bounds__(SVB_THREADS)
+__global__ void __launch_bounds__(SVB_THREADS, 1)
 sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds, const float* __restrict__ V,
                int64_t ldv, int k, double* __restrict__ Rpart, unsigned char* __restrict__ Sp, int nchunks,
                const DevStatus* st) {
-    constexpr int VEC = Vec16<TS>::N;  // elements per 16-byte load
-    constexpr int LPT = 16 / VEC;      // 16-byte loads per thread and k-block
+    constexpr int R = SvbRows<KQ>::R;
+    constexpr int VEC = Vec16<TS>::N;  // elements per 16-byte load: 4 (FP32) or 8 (BF16)
+    constexpr int LPG = 8 / VEC;       // 16-byte loads per row and 8-column group
+    // steps in flight: 2 for BF16 S with one RHS (256 bytes per thread, as FP32 S keeps with one step);
+    // more RHS leave no registers for it
+    constexpr int U = (LPG == 1 && KQ == 1) ? 2 : 1;
+    __shared__ double s_acc[SVB_WARPS][R * KQ];
     if (block_should_exit(st, 0)) return;
-    const int nblk = n_rows / SVB_ROWS;
-    const int I = blockIdx.x % nblk, chunk = blockIdx.x / nblk;
-    const int tid = threadIdx.x, r = tid >> 2, part = tid & 3;
-    const int i = I * SVB_ROWS + r;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nrb = n_rows / R;
+    const int rb = blockIdx.x % nrb, chunk = blockIdx.x / nrb;
+    const int i0 = rb * R;
     const int64_t nkb_all = ceil_div(m, 64);
     const int64_t per = ceil_div(nkb_all, nchunks);
-    const int64_t kb0 = (int64_t)chunk * per;
-    const int64_t kb1 = kb0 + per < nkb_all ? kb0 + per : nkb_all;
-    const TS* row = S + (int64_t)(i < n ? i : 0) * lds;
+    const int64_t g0 = (int64_t)chunk * per * 8;  // this CTA's 8-column groups [g0, g1)
+    const int64_t g1 = g0 + per * 8 < nkb_all * 8 ? g0 + per * 8 : nkb_all * 8;
     // V's rows need not be 16-byte aligned (ldv is any value >= m): vector loads only when they are
     const bool v_vec = ((reinterpret_cast<uintptr_t>(V) | (uintptr_t)(ldv * 4)) & 15) == 0;
-    float acc[KQ];
-    double acc64[KQ];
+    for (int e = tid; e < SVB_WARPS * R * KQ; e += SVB_THREADS) (&s_acc[0][0])[e] = 0.0;
+    __syncthreads();
+    float acc[R][KQ];
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) acc[q] = 0.f, acc64[q] = 0.0;
-    int since = 0;
-    for (int64_t kb = kb0; kb < kb1; kb += SVB_UNROLL) {
-        float sv[SVB_UNROLL][16];
+    for (int j = 0; j < R; ++j)
 #pragma unroll
-        for (int u = 0; u < SVB_UNROLL; ++u) {
-            const int64_t col = (kb + u) * 64 + part * 16;
-            if (i < n && kb + u < kb1 && col + 16 <= m) {
+        for (int q = 0; q < KQ; ++q) acc[j][q] = 0.f;
+    auto fold = [&]() {
 #pragma unroll
-                for (int l = 0; l < LPT; ++l) load16_stream<TS, float>(row + col + l * VEC, &sv[u][l * VEC]);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    sv[u][e] = (i < n && kb + u < kb1 && col + e < m) ? load1<TS, float>(row + col + e) : 0.f;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < SVB_UNROLL; ++u) {
-            if (kb + u >= kb1) break;
-            const int64_t col = (kb + u) * 64 + part * 16;
+        for (int j = 0; j < R; ++j)
 #pragma unroll
             for (int q = 0; q < KQ; ++q) {
                 if (q >= k) break;
-                const float* vq = V + (int64_t)q * ldv + col;
-                float a = 0.f;
-                if (v_vec && col + 16 <= m) {
+                double d = (double)acc[j][q];
+                acc[j][q] = 0.f;
 #pragma unroll
-                    for (int e = 0; e < 16; e += 4) {
-                        const float4 w = __ldg(reinterpret_cast<const float4*>(vq + e));
-                        a = fmaf(sv[u][e], w.x, fmaf(sv[u][e + 1], w.y, fmaf(sv[u][e + 2], w.z, fmaf(sv[u][e + 3], w.w, a))));
-                    }
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                if (lane == 0) s_acc[warp][j * KQ + q] += d;
+            }
+    };
+    int since = 0;
+    for (int64_t base = g0; base < g1; base += (int64_t)U * SVB_THREADS) {
+        // all loads of the step first (raw 16-byte vectors: R * U * LPG in flight per thread)
+        uint4 raw[U][R][LPG];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = base + u * SVB_THREADS + tid;
+            const bool gin = g < g1;
+            const int64_t col = g * 8;
+            const bool full = gin && col + 8 <= m;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const bool rin = i0 + j < n;
+                const TS* p = S + (int64_t)(rin ? i0 + j : 0) * lds + (gin ? col : 0);
+                if (rin && full) {
+#pragma unroll
+                    for (int l = 0; l < LPG; ++l) raw[u][j][l] = __ldcs(reinterpret_cast<const uint4*>(p + l * VEC));
                 } else {
-                    for (int e = 0; e < 16; ++e)
-                        if (col + e < m) a = fmaf(sv[u][e], __ldg(vq + e), a);
+                    float f[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) f[e] = (rin && gin && col + e < m) ? load1<TS, float>(p + e) : 0.f;
+                    svb_pack_raw<TS>(f, raw[u][j]);
                 }
-                acc[q] += a;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = base + u * SVB_THREADS + tid;
+            const bool gin = g < g1;
+            const int64_t col = g * 8;
+            const bool full = gin && col + 8 <= m;
+            // V's 8 values per RHS; BF16 S with up to 4 RHS (small raw vectors) holds all of them and
+            // unpacks each row once, otherwise one RHS at a time
+            constexpr bool ROW_OUTER = LPG == 1 && KQ <= 4;
+            constexpr int WQ = ROW_OUTER ? KQ : 1;
+            float w[WQ][8];
+            auto load_w = [&](int q, float* wq) {
+                const float* vq = V + (int64_t)q * ldv + (gin ? col : 0);
+                if (v_vec && full) {
+                    const float4 w0 = __ldg(reinterpret_cast<const float4*>(vq));
+                    const float4 w1 = __ldg(reinterpret_cast<const float4*>(vq + 4));
+                    wq[0] = w0.x, wq[1] = w0.y, wq[2] = w0.z, wq[3] = w0.w;
+                    wq[4] = w1.x, wq[5] = w1.y, wq[6] = w1.z, wq[7] = w1.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) wq[e] = (gin && col + e < m) ? __ldg(vq + e) : 0.f;
+                }
+            };
+            if constexpr (ROW_OUTER) {
+#pragma unroll
+                for (int q = 0; q < KQ; ++q)
+                    if (q < k) load_w(q, w[q]);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    float sv[8];
+                    svb_unpack_raw<TS>(raw[u][j], sv);
+#pragma unroll
+                    for (int q = 0; q < KQ; ++q) {
+                        if (q >= k) break;
+                        float a = acc[j][q];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) a = fmaf(sv[e], w[q][e], a);
+                        acc[j][q] = a;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) {
+                    if (q >= k) break;
+                    load_w(q, w[0]);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        float sv[8];
+                        svb_unpack_raw<TS>(raw[u][j], sv);
+                        float a = acc[j][q];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) a = fmaf(sv[e], w[0][e], a);
+                        acc[j][q] = a;
+                    }
+                }
             }
             if constexpr (PACK == 1) {
-                // this thread's 32 bytes of the k-block's 128-byte BF16 row: 16-byte chunks 2 part, 2 part + 1
-                unsigned char* trow = Sp + ((((kb + u) * (int64_t)nblk) + I) << 14) + (r & 127) * 128;
+                if (gin) {
+                    // 16-byte chunk c = g & 7 of k-block g >> 3 in tile row i & 127 (128-byte swizzle)
+                    const int nblk = n_rows >> 7, c = (int)(g & 7);
+                    unsigned char* tk = Sp + (((g >> 3) * (int64_t)nblk) << 14);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint4 w;
-                    uint32_t* wp = reinterpret_cast<uint32_t*>(&w);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const __nv_bfloat162 b = __floats2bfloat162_rn(sv[u][h * 8 + 2 * e], sv[u][h * 8 + 2 * e + 1]);
-                        wp[e] = *reinterpret_cast<const uint32_t*>(&b);
+                    for (int j = 0; j < R; ++j) {
+                        const int i = i0 + j, r = i & 127;
+                        *reinterpret_cast<uint4*>(tk + ((int64_t)(i >> 7) << 14) + r * 128 + ((c ^ (r & 7)) << 4)) =
+                            svb_bf16_chunk<TS>(raw[u][j]);
                     }
-                    const int c = 2 * part + h;
-                    *reinterpret_cast<uint4*>(trow + ((c ^ (r & 7)) << 4)) = w;
                 }
             }
         }
-        if (++since == 32 / SVB_UNROLL) {
+        if (++since == SVB_FOLD / U) {
             since = 0;
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) acc64[q] += (double)acc[q], acc[q] = 0.f;
+            fold();
         }
     }
-#pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-        double a = acc64[q] + (double)acc[q];
-        a += __shfl_xor_sync(0xffffffffu, a, 1);
-        a += __shfl_xor_sync(0xffffffffu, a, 2);
-        if (part == 0 && i < n) Rpart[((int64_t)chunk * n + i) * KQ + q] = a;
+    fold();
+    __syncthreads();
+    for (int t = tid; t < R * KQ; t += SVB_THREADS) {
+        const int i = i0 + t / KQ;
+        double a = 0.0;
+        for (int w = 0; w < SVB_WARPS; ++w) a += s_acc[w][t];
+        if (i < n) Rpart[((int64_t)chunk * n + i) * KQ + t % KQ] = a;
     }
 }
 
 // column chunks of sv_rows_kernel (at most num_sms: the partial rows of R).  One 512-thread CTA
-// fills an SM's registers, so the nblk * c equal CTAs run in waves of num_sms: take the smallest
-// c >= num_sms / nblk whose last wave is at least 95 % full (the fullest found otherwise).
-static int sv_rows_chunks(int n_rows, int64_t m, int num_sms) {
-    const int64_t nblk = n_rows / SVB_ROWS, nkb = ceil_div(m, 64);
+// fills an SM's registers, so the nrb * c equal CTAs run in waves of num_sms: take the smallest
+// c >= num_sms / nrb whose last wave is at least 95 % full (the fullest found otherwise).
+static int sv_rows_chunks(int nrb, int64_t m, int num_sms) {
+    const int64_t nkb = ceil_div(m, 64);
     int64_t cmax = num_sms < nkb ? num_sms : nkb;
     if (cmax < 1) cmax = 1;
-    int64_t c0 = ceil_div((int64_t)num_sms, nblk);
+    int64_t c0 = ceil_div((int64_t)num_sms, (int64_t)nrb);
     if (c0 > cmax) c0 = cmax;
     int best = (int)c0;
     double best_eff = 0.0;
     for (int64_t c = c0; c <= cmax; ++c) {
-        const int64_t ctas = nblk * c, waves = ceil_div(ctas, (int64_t)num_sms);
+        const int64_t ctas = (int64_t)nrb * c, waves = ceil_div(ctas, (int64_t)num_sms);
         const double eff = (double)ctas / (double)(waves * num_sms);
         if (eff > best_eff + 1e-9) best_eff = eff, best = (int)c;
         if (eff >= 0.95) break;
@@ -1276,8 +1391,8 @@ template <typename TS, int KQ, int PACK>
 static cudaError_t launch_sv_rows_t(int nchunks, const void* S, int n, int n_rows, int64_t m, int64_t lds,
                                     const void* V, int64_t ldv, int k, double* Rpart, void* Sp, const DevStatus* st,
                                     cudaStream_t stream) {
-    const int grid = nchunks * (n_rows / SVB_ROWS);
-    sv_rows_kernel<TS, KQ, PACK><<<grid, SVB_THREADS, 0, stream>>>(
+    const int64_t grid = (int64_t)nchunks * (n_rows / SvbRows<KQ>::R);
+    sv_rows_kernel<TS, KQ, PACK><<<(unsigned)grid, SVB_THREADS, 0, stream>>>(
         static_cast<const TS*>(S), n, n_rows, m, lds, static_cast<const float*>(V), ldv, k, Rpart,
         static_cast<unsigned char*>(Sp), nchunks, st);
     count_launch();
@@ -1299,8 +1414,8 @@ cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, 
     // rows far apart (FP32 S beyond the streaming form's 1024 rows, or BF16 S), BF16 tiles or none:
     // the row-blocked form
     if (pack <= 1 && (s_dtype == DFS_BF16 || (s_dtype == DFS_F32 && round_up(n, 256) > SVR_MAXNR * (PASS_THREADS / 16)))) {
-        const int n_rows = (int)round_up(n, pack ? 256 : SVB_ROWS);
-        const int nchunks = sv_rows_chunks(n_rows, m, plan.sv_grid);
+        const int n_rows = (int)round_up(n, pack ? 256 : 8);
+        const int nchunks = sv_rows_chunks(n_rows / (kq >= 8 ? SvbRows<8>::R : SvbRows<1>::R), m, plan.sv_grid);
         if (parts) *parts = nchunks;
 #define DFS_SVB(KQ)                                                                                          \
     case KQ:                                                                                                 \
