@@ -613,8 +613,9 @@ def run_workload(args):
 
 
 def run_profile_solve(args):
-    """One small BF16 solve for an ncu capture (--profile-solve M): Gaussian S of 1024 x M
-    (seed 1), v seed 2, lambda 1e-4, after --warmup solves.  Prints the device status."""
+    """One small BF16 solve for an ncu capture (--profile-solve M): Gaussian S of n x M
+    (--profile-n, default 1024; FP32, or BF16 with --profile-bf16; seed 1), v seed 2, lambda 1e-4,
+    after --warmup solves.  Prints the device status."""
     import torch
 
     import __graft_entry__
@@ -624,13 +625,16 @@ def run_profile_solve(args):
     from paper_2310_17556_gb300 import workloads as wl
 
     torch.cuda.set_device(0)
-    S = wl.gaussian(N_SAMPLES, args.profile_solve, seed=1, device="cuda")
+    n = args.profile_n or N_SAMPLES
+    S = wl.gaussian(n, args.profile_solve, seed=1, device="cuda",
+                    dtype=torch.bfloat16 if args.profile_bf16 else torch.float32)
     v = wl.rhs(args.profile_solve, 1, seed=2, device="cuda")
     X = torch.empty_like(v)
     for _ in range(args.warmup + 1):
         dfs.dfs_solve(S, v, LAMBDA, X=X, precision=PRECISION, sync=False)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_solve": {"n": N_SAMPLES, "m": args.profile_solve, **dfs.dfs_sync_info()}}))
+    print(json.dumps({"profile_solve": {"n": n, "m": args.profile_solve, "s_dtype": str(S.dtype),
+                                        **dfs.dfs_sync_info()}}))
     return 0
 
 
@@ -645,6 +649,8 @@ def main():
                     help="headline (default): the metric's workload; the others: one GPU, one line per path")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="M",
                     help="run one small solve (n=1024, m=M) after --warmup solves, for ncu captures")
+    ap.add_argument("--profile-n", type=int, default=0, metavar="N", help="rows of S for --profile-solve")
+    ap.add_argument("--profile-bf16", action="store_true", help="BF16 S for --profile-solve")
     args = ap.parse_args()
     if args.profile_solve:
         return run_profile_solve(args)

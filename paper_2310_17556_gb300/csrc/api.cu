@@ -495,7 +495,7 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                                    U2part, corrected ? 0 : (it == 1 ? 2 : 1), h->dstat, 1, stream));
                 if (mark_pass && it == 1) DFS_CK(mark(9));
                 if (!corrected)
-                    DFS_CK(launch_refine_check(U2part, p.pp.nparts, U2, kq, kg, lambda, tol, it, max_iter, 0,
+                    DFS_CK(launch_refine_check(U2part, p.pp.uparts, U2, kq, kg, lambda, tol, it, max_iter, 0,
                                                h->dstat, stream));
                 if (p.ns) {
                     DFS_CK(launch_nspace(p.f64, kq, W, p.n_pad, npi, Linv,
@@ -897,13 +897,12 @@ dfs_status dfs_fisher_pass(dfs_handle h, const void* S, int s_dtype, int64_t n, 
     const int kmax = pass_max_group((int)n, s_dtype, h->smem_optin);
     if (kmax < 1) return fail(h, DFS_ERR_UNSUPPORTED, "n too large for the pass kernel");
     if (kq > kmax) kq = kmax;
-    const PassPlan pp = pass_make_plan((int)n, kq, s_dtype, h->num_sms, m, h->smem_optin);
-    const int grid = pass_partial_rows(pp);
+    const PassPlan pp = pass_make_plan((int)n, kq, s_dtype, h->num_sms, m, h->smem_optin, X != nullptr);
+    const int grid = std::max(pass_partial_rows(pp), pp.uparts);
     const size_t oR = 0, oU = align_up((size_t)grid * n * kq * 8), oU2 = oU + align_up((size_t)grid * 2 * kq * 8);
     if ((s = ensure_ws(h, oU2 + 128, stream)) != DFS_OK) return s;
     double* Rpart = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oR);
     double* U2part = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oU);
-    double* U2 = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oU2);
     const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
     DFS_CK(launch_status_reset(h->dstat, stream));
     for (int64_t q0 = 0; q0 < k; q0 += kq) {
@@ -915,7 +914,7 @@ dfs_status dfs_fisher_pass(dfs_handle h, const void* S, int s_dtype, int64_t n, 
                            R ? Rpart : nullptr, U2part, 0, h->dstat, 0, stream));
         if (R)
             DFS_CK(launch_pass_reduce(0, Rpart, pp.nparts, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
-                                      U2part, U2, h->dstat, 0, stream));
+                                      nullptr, nullptr, h->dstat, 0, stream));
     }
     return DFS_OK;
 }

@@ -71,7 +71,9 @@ struct PassPlan {
     int cs;       // > 0: the refinement pass runs as clusters of cs CTAs (pass_cluster.cu)
     int crpt;     // rows per thread of the cluster form
     int ncl;      // clusters
-    int nparts;   // partial rows (Rpart / U2part) the refinement pass writes
+    int nparts;   // partial rows of R (Rpart) the refinement pass writes
+    int uparts;   // partial rows of the U^2 / dX^2 sums (U2part) it writes
+    int two;      // 1: the pass runs as sty_cols_kernel (X) then sv_rows_kernel (R) (large n)
 };
 int pass_cluster_plan(int s_dtype, int n, int KQ, int num_sms, int64_t m, size_t smem_limit, int* cs_out,
                       int* rpt_out);
@@ -82,7 +84,8 @@ cudaError_t launch_pass_cluster(int ncl, int cs, int rpt, int kq, const void* S,
 size_t pass_smem_bytes(int n, int KQ, int s_dtype);
 int pass_max_group(int n, int s_dtype, size_t smem_limit);
 int pass_grid(int n, int KQ, int s_dtype, int num_sms, int64_t m);
-PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit);
+// allow_two = 0: keep the one-kernel pass (the two-kernel form needs an X output to carry U)
+PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit, int allow_two = 1);
 int pass_partial_rows(const PassPlan& p);  // rows of the partial buffers (max of both grids)
 // pack: 0 none, 1 BF16 tiles, 2 TF32 tiles, 3 stacked BF16 H / L tiles, 4 row-scaled e4m3 tiles
 // (rinv: the inverse row scales from launch_row_scale) (see sv_pack_kernel)

@@ -14,6 +14,7 @@
 // All calls on one device share the one array: two calls whose work overlaps on the device (on
 // different streams without ordering between them, or from several host threads) race on it and
 // give wrong results.  Order such calls on one stream or with events.
+#include <algorithm>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -119,18 +120,17 @@ extern "C" dfs_status dfs_fisher_pass_noalloc(const void* S, int s_dtype, int64_
     // Right-hand sides per pass: as dfs_fisher_pass, halved while the partials do not fit.
     int kq = pow2_ceil(k);
     if (kq > kmax) kq = kmax;
-    PassPlan pp = pass_make_plan((int)n, kq, s_dtype, d.num_sms, m, d.smem_optin);
-    Layout lay = layout_for(pp.nparts, n, kq, R != nullptr);
+    PassPlan pp = pass_make_plan((int)n, kq, s_dtype, d.num_sms, m, d.smem_optin, X != nullptr);
+    Layout lay = layout_for(std::max(pp.nparts, pp.uparts), n, kq, R != nullptr);
     while (lay.total > DFS_NOALLOC_SCRATCH_BYTES && kq > 1) {
         kq >>= 1;
-        pp = pass_make_plan((int)n, kq, s_dtype, d.num_sms, m, d.smem_optin);
-        lay = layout_for(pp.nparts, n, kq, R != nullptr);
+        pp = pass_make_plan((int)n, kq, s_dtype, d.num_sms, m, d.smem_optin, X != nullptr);
+        lay = layout_for(std::max(pp.nparts, pp.uparts), n, kq, R != nullptr);
     }
     if (scratch_bytes) *scratch_bytes = (int64_t)lay.total;
     if (lay.total > DFS_NOALLOC_SCRATCH_BYTES) return DFS_ERR_NO_MEMORY;
 
     DevStatus* st = reinterpret_cast<DevStatus*>(d.scratch);
-    double* U2 = reinterpret_cast<double*>(d.scratch + lay.off_u2);
     double* U2part = reinterpret_cast<double*>(d.scratch + lay.off_u2part);
     double* Rpart = R ? reinterpret_cast<double*>(d.scratch + lay.off_rpart) : nullptr;
     const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
@@ -146,7 +146,7 @@ extern "C" dfs_status dfs_fisher_pass_noalloc(const void* S, int s_dtype, int64_
                         U2part, 0, st, 0, stream) != cudaSuccess)
             return DFS_ERR_CUDA;
         if (R && launch_pass_reduce(0, Rpart, pp.nparts, (int)n, (int)n, kq, kg, Yg, ldy, lambda, R + q0, ldr, nullptr,
-                                    U2part, U2, st, 0, stream) != cudaSuccess)
+                                    nullptr, nullptr, st, 0, stream) != cudaSuccess)
             return DFS_ERR_CUDA;
     }
     return DFS_OK;

@@ -321,7 +321,7 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
 // open pages hold those forms to address-translation speed, well below HBM bandwidth.)  A
 // thread's V values serve all R rows.  Sums in FP32 per thread, folded every 32 steps into FP64
 // per warp (fixed shuffle order), the warps then added in order; part c of Rpart holds column
-// chunk c's sums of every row.
+// chunk c's sums of every row, times scale (lambda when V is the pass's X = U / lambda).
 constexpr int SVB_THREADS = 512;
 constexpr int SVB_WARPS = SVB_THREADS / 32;
 constexpr int SVB_FOLD = 32;
@@ -381,7 +381,7 @@ template <typename TS, int KQ, int PACK>
 __global__ void __launch_bounds__(SVB_THREADS, 1)
 sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds, const float* __restrict__ V,
                int64_t ldv, int k, double* __restrict__ Rpart, unsigned char* __restrict__ Sp, int nchunks,
-               const DevStatus* st) {
+               const DevStatus* st, double scale, int honor_stop) {
     constexpr int R = SvbRows<KQ>::R;
     constexpr int VEC = Vec16<TS>::N;  // elements per 16-byte load: 4 (FP32) or 8 (BF16)
     constexpr int LPG = 8 / VEC;       // 16-byte loads per row and 8-column group
@@ -389,7 +389,7 @@ sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
     // more RHS leave no registers for it
     constexpr int U = (LPG == 1 && KQ == 1) ? 2 : 1;
     __shared__ double s_acc[SVB_WARPS][R * KQ];
-    if (block_should_exit(st, 0)) return;
+    if (block_should_exit(st, honor_stop)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nrb = n_rows / R;
     const int rb = blockIdx.x % nrb, chunk = blockIdx.x / nrb;
@@ -526,7 +526,7 @@ sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
         const int i = i0 + t / KQ;
         double a = 0.0;
         for (int w = 0; w < SVB_WARPS; ++w) a += s_acc[w][t];
-        if (i < n) Rpart[((int64_t)chunk * n + i) * KQ + t % KQ] = a;
+        if (i < n) Rpart[((int64_t)chunk * n + i) * KQ + t % KQ] = scale * a;
     }
 }
 
@@ -548,6 +548,172 @@ static int sv_rows_chunks(int nrb, int64_t m, int num_sms) {
         if (eff >= 0.95) break;
     }
     return best;
+}
+
+template <typename TS, int KQ, int PACK>
+static cudaError_t launch_sv_rows_t(int nchunks, const void* S, int n, int n_rows, int64_t m, int64_t lds,
+                                    const void* V, int64_t ldv, int k, double* Rpart, void* Sp, const DevStatus* st,
+                                    cudaStream_t stream, double scale = 1.0, int honor_stop = 0) {
+    const int64_t grid = (int64_t)nchunks * (n_rows / SvbRows<KQ>::R);
+    sv_rows_kernel<TS, KQ, PACK><<<(unsigned)grid, SVB_THREADS, 0, stream>>>(
+        static_cast<const TS*>(S), n, n_rows, m, lds, static_cast<const float*>(V), ldv, k, Rpart,
+        static_cast<unsigned char*>(Sp), nchunks, st, scale, honor_stop);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// X = (V - S^T Y) / lambda for S whose rows are far apart (n > 2048): the first kernel of the
+// refinement pass as two (the second, R = S U - lambda Y, is sv_rows_kernel on X with scale
+// lambda).  fisher_pass_kernel's strips span all n rows at once; here a CTA takes 4096-column
+// chunks (round-robin over a one-CTA-per-SM grid) down all n rows, its 512 threads sharing each
+// row, so the grid keeps about RB rows per SM open.  Thread t holds 8 columns of the chunk: 8
+// contiguous BF16, or two runs of 4 FP32 128 columns apart, so that every warp load is 512
+// contiguous bytes.  Column sums in FP32 over panels of 256 rows, the panels added in FP64 in
+// shared memory (a thread owns its columns outright: no cross-thread step; its registers keep 256
+// bytes of S in flight); then, as fisher_pass_kernel, U = V - S^T Y, X = U / lambda and the sums
+// of U^2 and of the change of X (dmode).
+constexpr int STY_COLS = SVB_THREADS * 8;
+
+template <typename TS, int KQ>
+struct StyRows {  // rows in flight per thread: up to 256 bytes of S, as the KQ accumulators allow
+    static constexpr int R = sizeof(TS) == 2 ? (KQ == 1 ? 16 : (KQ == 2 ? 10 : 12)) : (KQ <= 2 ? 8 : 6);
+};
+// dynamic shared memory of sty_cols_kernel: a thread's FP64 column sums (8 columns x KQ), then its
+// FP64 sums of U^2 and dX^2 (KQ each)
+constexpr size_t sty_smem_bytes(int KQ) { return (size_t)KQ * 10 * SVB_THREADS * sizeof(double); }
+
+template <typename TS, int KQ>
+__global__ void __launch_bounds__(SVB_THREADS, 1)
+sty_cols_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds, const float* __restrict__ V, int64_t ldv,
+                int k, const double* __restrict__ Y, int64_t ldy, double lambda, float* __restrict__ X,
+                int64_t ldx, double* __restrict__ U2part, int dmode, const DevStatus* st, int honor_stop) {
+    constexpr int VEC = Vec16<TS>::N;  // 4 (FP32) or 8 (BF16)
+    constexpr int LPG = 8 / VEC;       // 16-byte loads per row: 2 (FP32) or 1 (BF16)
+    constexpr int RB = StyRows<TS, KQ>::R;
+    constexpr bool Y_AHEAD = RB * KQ <= 16;  // the step's y values fit registers beside S
+    constexpr int PANEL = 256;
+    extern __shared__ double tot[];  // [(q * 8 + e) * SVB_THREADS + tid]
+    double* uds = tot + KQ * 8 * SVB_THREADS;  // [q * SVB_THREADS + tid]: U^2, then dX^2 at + KQ
+    __shared__ double red[SVB_WARPS][16];
+    if (block_should_exit(st, honor_stop)) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float inv_lambda = (float)(1.0 / lambda);
+    const int64_t nchunks = ceil_div(m, (int64_t)STY_COLS);
+#pragma unroll
+    for (int q = 0; q < 2 * KQ; ++q) uds[q * SVB_THREADS + tid] = 0.0;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        // column of element e: cb + (e / VEC) * (256 / LPG) + e % VEC
+        const int64_t cb = c * STY_COLS + warp * 256 + lane * VEC;
+#pragma unroll
+        for (int qe = 0; qe < KQ * 8; ++qe) tot[qe * SVB_THREADS + tid] = 0.0;
+        if (Y != nullptr) {
+            float acc[KQ][8];
+#pragma unroll
+            for (int q = 0; q < KQ; ++q)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc[q][e] = 0.f;
+            int rows = 0;
+            for (int i0 = 0; i0 < n; i0 += RB) {
+                uint4 raw[RB][LPG];
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    const int i = i0 + j;
+                    const TS* row = S + (int64_t)(i < n ? i : 0) * lds;
+#pragma unroll
+                    for (int l = 0; l < LPG; ++l) {
+                        const int64_t cl = cb + l * (256 / LPG);
+                        if (i < n && cl + VEC <= m) {
+                            raw[j][l] = __ldcs(reinterpret_cast<const uint4*>(row + cl));
+                        } else {
+                            float f[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) f[e] = 0.f;
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e)
+                                if (i < n && cl + e < m) f[e] = load1<TS, float>(row + cl + e);
+                            uint4 two[2];
+                            svb_pack_raw<TS>(f, two);
+                            raw[j][l] = two[0];
+                        }
+                    }
+                }
+                auto y_at = [&](int j, int q) -> float {
+                    return (i0 + j < n && q < k) ? (float)__ldg(Y + (int64_t)(i0 + j) * ldy + q) : 0.f;
+                };
+                float ya[Y_AHEAD ? RB : 1][KQ];
+                if constexpr (Y_AHEAD) {
+#pragma unroll
+                    for (int j = 0; j < RB; ++j)
+#pragma unroll
+                        for (int q = 0; q < KQ; ++q) ya[j][q] = y_at(j, q);
+                }
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    float yv[KQ];
+#pragma unroll
+                    for (int q = 0; q < KQ; ++q) yv[q] = Y_AHEAD ? ya[Y_AHEAD ? j : 0][q] : y_at(j, q);
+                    float sv[8];
+                    svb_unpack_raw<TS>(raw[j], sv);
+#pragma unroll
+                    for (int q = 0; q < KQ; ++q)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) acc[q][e] = fmaf(sv[e], yv[q], acc[q][e]);
+                }
+                if ((rows += RB) >= PANEL || i0 + RB >= n) {
+                    rows = 0;
+#pragma unroll
+                    for (int q = 0; q < KQ; ++q)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) tot[(q * 8 + e) * SVB_THREADS + tid] += (double)acc[q][e], acc[q][e] = 0.f;
+                }
+            }
+        }
+        // U = V - S^T Y, X = U / lambda, and the stopping rule's sums
+        float u2f[KQ], d2f[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) u2f[q] = d2f[q] = 0.f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t col = cb + (e / VEC) * (256 / LPG) + e % VEC;
+            if (col >= m) continue;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                if (q >= k) break;
+                const float v = V[(int64_t)q * ldv + col];
+                const float u = (float)((double)v - tot[(q * 8 + e) * SVB_THREADS + tid]);
+                const float xn = u * inv_lambda;
+                float dx = 0.f;
+                if (dmode == 1) dx = xn - X[(int64_t)q * ldx + col];
+                else if (dmode == 2) dx = (u - v) * inv_lambda;
+                X[(int64_t)q * ldx + col] = xn;
+                u2f[q] += u * u;
+                d2f[q] += dx * dx;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            uds[q * SVB_THREADS + tid] += (double)u2f[q];
+            uds[(KQ + q) * SVB_THREADS + tid] += (double)d2f[q];
+        }
+    }
+    // per-RHS sums over the CTA, in a fixed order (the U2part layout of fisher_pass_kernel)
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        double v = uds[q * SVB_THREADS + tid], w = uds[(KQ + q) * SVB_THREADS + tid];
+        for (int o = 16; o > 0; o >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        if (lane == 0) red[warp][q] = v, red[warp][8 + q] = w;
+    }
+    __syncthreads();
+    if (tid < KQ) {
+        double v = 0.0, w = 0.0;
+        for (int wp = 0; wp < SVB_WARPS; ++wp) v += red[wp][tid], w += red[wp][8 + tid];
+        U2part[(int64_t)blockIdx.x * 2 * KQ + tid] = v;
+        U2part[(int64_t)blockIdx.x * 2 * KQ + KQ + tid] = w;
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1211,7 +1377,7 @@ static int pass_rpt(int n, int KQ, int s_dtype) {
     return rpt;
 }
 
-PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit) {
+PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size_t smem_limit, int allow_two) {
     PassPlan p{};
     p.rpt = pass_rpt(n, KQ, s_dtype);
     // register-resident strips: one 512-thread CTA per SM; otherwise up to four
@@ -1232,6 +1398,18 @@ PassPlan pass_make_plan(int n, int KQ, int s_dtype, int num_sms, int64_t m, size
     p.ncl = smem_limit ? pass_cluster_plan(s_dtype, n, KQ, num_sms, m, smem_limit, &p.cs, &p.crpt) : 0;
     if (p.ncl == 0) p.cs = p.crpt = 0;
     p.nparts = p.cs > 0 ? p.ncl : p.grid;
+    p.uparts = p.nparts;
+    p.two = 0;
+    // n > 2048 rows (FP32 or BF16 S, up to 4 RHS) with a 4096-column chunk for every SM: the pass
+    // as sty_cols_kernel then sv_rows_kernel, two reads of S by rows shared across each CTA, in
+    // place of one read by strips that span all n rows (which address translation holds to a
+    // fraction of HBM bandwidth at this n)
+    if (allow_two && (s_dtype == DFS_F32 || s_dtype == DFS_BF16) && KQ <= 4 && n > 2048 &&
+        ceil_div(m, (int64_t)STY_COLS) >= num_sms) {
+        p.two = 1;
+        p.uparts = num_sms;
+        p.nparts = sv_rows_chunks((int)round_up(n, 8) / SvbRows<1>::R, m, p.sv_grid);
+    }
     return p;
 }
 
@@ -1283,6 +1461,51 @@ cudaError_t launch_pass(const PassPlan& plan, int s_dtype, int kq, const void* S
                         const void* V, int64_t ldv, int k, const double* Y, int64_t ldy, double lambda, void* X,
                         int64_t ldx, double* Rpart, double* U2part, int dmode, const DevStatus* st, int honor_stop,
                         cudaStream_t stream) {
+    if (plan.two && X != nullptr && (s_dtype == DFS_F32 || s_dtype == DFS_BF16) && kq <= 4) {
+        // X = (V - S^T Y) / lambda, then the partial rows of R = S U (the reduce subtracts lambda Y)
+        cudaError_t e = cudaSuccess;
+#define DFS_STY(TS, KQ)                                                                                          \
+    if ((e = cudaFuncSetAttribute(sty_cols_kernel<TS, KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                  (int)sty_smem_bytes(KQ))) != cudaSuccess)                                        \
+        return e;                                                                                                 \
+    sty_cols_kernel<TS, KQ><<<plan.uparts, SVB_THREADS, sty_smem_bytes(KQ), stream>>>(                           \
+        static_cast<const TS*>(S), n, m, lds, static_cast<const float*>(V), ldv, k, Y, ldy, lambda,               \
+        static_cast<float*>(X), ldx, U2part, dmode, st, honor_stop)
+#define DFS_STY_KQ(TS)                  \
+    switch (kq) {                       \
+        case 1: DFS_STY(TS, 1); break;  \
+        case 2: DFS_STY(TS, 2); break;  \
+        default: DFS_STY(TS, 4); break; \
+    }
+        if (s_dtype == DFS_F32) {
+            DFS_STY_KQ(float)
+        } else {
+            DFS_STY_KQ(__nv_bfloat16)
+        }
+#undef DFS_STY_KQ
+#undef DFS_STY
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess || Rpart == nullptr) return e;
+        // X = U * fl(1 / lambda) in FP32, so U = X / fl(1 / lambda) up to X's own rounding
+        const int n_rows = (int)round_up(n, 8);
+        const double scale = 1.0 / (double)(float)(1.0 / lambda);
+#define DFS_SVR2(TS, KQ)                                                                                         \
+    launch_sv_rows_t<TS, KQ, 0>(plan.nparts, S, n, n_rows, m, lds, X, ldx, k, Rpart, nullptr, st, stream, scale, \
+                                honor_stop)
+        if (s_dtype == DFS_F32) {
+            switch (kq) {
+                case 1: return DFS_SVR2(float, 1);
+                case 2: return DFS_SVR2(float, 2);
+                default: return DFS_SVR2(float, 4);
+            }
+        }
+        switch (kq) {
+            case 1: return DFS_SVR2(__nv_bfloat16, 1);
+            case 2: return DFS_SVR2(__nv_bfloat16, 2);
+            default: return DFS_SVR2(__nv_bfloat16, 4);
+        }
+#undef DFS_SVR2
+    }
     if (plan.cs > 0 && s_dtype == DFS_F32)
         return launch_pass_cluster(plan.ncl, plan.cs, plan.crpt, kq, S, n, m, lds, V, ldv, k, Y, ldy, lambda, X, ldx,
                                    Rpart, U2part, dmode, st, honor_stop, stream);
@@ -1383,18 +1606,6 @@ static cudaError_t launch_sv_ring_t(int grid, const void* S, int n, int n_rows, 
     kern<<<grid, PASS_THREADS, smem, stream>>>(static_cast<const float*>(S), n, n_rows, m, lds,
                                                static_cast<const float*>(V), ldv, k, Rpart,
                                                static_cast<unsigned char*>(Sp), nkb, st, rinv);
-    count_launch();
-    return cudaGetLastError();
-}
-
-template <typename TS, int KQ, int PACK>
-static cudaError_t launch_sv_rows_t(int nchunks, const void* S, int n, int n_rows, int64_t m, int64_t lds,
-                                    const void* V, int64_t ldv, int k, double* Rpart, void* Sp, const DevStatus* st,
-                                    cudaStream_t stream) {
-    const int64_t grid = (int64_t)nchunks * (n_rows / SvbRows<KQ>::R);
-    sv_rows_kernel<TS, KQ, PACK><<<(unsigned)grid, SVB_THREADS, 0, stream>>>(
-        static_cast<const TS*>(S), n, n_rows, m, lds, static_cast<const float*>(V), ldv, k, Rpart,
-        static_cast<unsigned char*>(Sp), nchunks, st);
     count_launch();
     return cudaGetLastError();
 }

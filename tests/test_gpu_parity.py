@@ -559,6 +559,37 @@ def test_trsm_step(dtype, tol, trans):
     assert np.abs(np64(out) - ref).max() / np.abs(ref).max() <= tol
 
 
+@pytest.mark.parametrize("dtype,n,extra,k", [
+    (torch.bfloat16, 2100, 1234, 3),   # ragged rows, odd m (X rows not 16-byte aligned), 3 of 4 RHS
+    (torch.float32, 2049, 0, 2),       # one row past the threshold, whole 4096-column chunks
+    (torch.float32, 2056, 4095, 1),    # a 4095-column last chunk
+])
+def test_fisher_pass_two_kernel_form(dtype, n, extra, k):
+    """n > 2048 with a 4096-column chunk per SM: the pass runs as X = (V - S^T Y)/lambda by column
+    chunks, then R = S U - lambda Y by 8-row blocks.  The reference goes by column blocks b, since
+    u_b depends only on b's columns: X_b = (v_b - S_b^T y)/lambda and R = sum_b r_b + (B - 1) lambda y
+    with r_b the oracle's n-space residual of block b."""
+    sms = torch.cuda.get_device_properties(dev()).multi_processor_count
+    m, lam = 4096 * sms + extra, 1e-2
+    S = aligned(wl.gaussian(n, m, seed=63, device=dev(), dtype=dtype))
+    V = wl.rhs(m, k, seed=64, device=dev())
+    Y = torch.randn(n, k, device=dev(), dtype=torch.float64) * (0.3 / math.sqrt(n / 150))
+    X, R = dfs.dfs_fisher_pass(S, V, lam, Y)
+    y = np64(Y)
+    x_ref = np.empty((k, m))
+    r_ref = np.zeros((n, k))
+    blocks = 0
+    for c0 in range(0, m, 65536):
+        c1 = min(m, c0 + 65536)
+        s, v = np64(S[:, c0:c1]), np64(V[:, c0:c1]).T
+        x_ref[:, c0:c1] = ((v - s.T @ y) / lam).T
+        r_ref += oracle.residual_n_space(s, v, y, lam)
+        blocks += 1
+    r_ref += (blocks - 1) * lam * y
+    assert rel_err(np64(X), x_ref) <= 2e-6
+    assert np.abs(np64(R) - r_ref).max() / np.abs(r_ref).max() <= 1e-5
+
+
 @pytest.mark.parametrize("dtype,n,m,k", [
     (torch.float32, 150, 12345, 3), (torch.bfloat16, 150, 12345, 3), (torch.float64, 150, 12345, 3),
     (torch.float32, 1024, 40000, 8),   # RHS beyond the cluster form's 4 per pass: classic kernel
