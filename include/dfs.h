@@ -201,14 +201,38 @@ typedef struct {
     void* X; int64_t ldx;
 } dfs_problem;
 
-/* Solve `count` independent problems of uneven (n, m) with one grouped launch per step.
- * `problems` is a host array.  status_out (host, `count` ints, may be NULL) receives each
- * problem's device status; when it is non-NULL the call synchronizes `stream`.  The first
- * call for a given batch shape records a CUDA graph that later calls with the same shapes
- * replay. */
+/* Solve `count` independent problems of uneven (n, m) (Eq. 1 for each; Algorithm 1 per
+ * problem).  `problems` is a host array; every problem obeys dfs_solve's rules, S of type s_dtype.
+ * Problems are dealt longest first (estimated cost n^2 m + 4 n m k) to up to 8 lanes, each with
+ * its own stream and workspace, forked from and joined back into `stream`; with one problem the
+ * solve runs on `stream` itself.
+ * status_out (host, `count` ints, may be NULL) receives each problem's device status, in
+ * `problems` order; when it is non-NULL the call synchronizes `stream` and returns the first
+ * problem's error.  With status_out NULL nothing synchronizes; the statuses stay on the device
+ * for dfs_batched_status.
+ * Allocation: lanes, their workspaces and the status array are created or grown on demand,
+ * unless dfs_plan_batched was called before for problems of the same or larger sizes.  During
+ * stream capture any such growth fails with DFS_ERR_NO_MEMORY: plan first, then capture. */
 dfs_status dfs_solve_batched(dfs_handle handle, const dfs_problem* problems, int count,
                              int s_dtype, const dfs_options* opt, void* stream,
                              int* status_out);
+
+/* Prepare dfs_solve_batched for this list without launching anything: validate it (the same
+ * argument errors as dfs_solve_batched), create the lanes it will use with their streams and
+ * events, size each lane's workspace for the problems the longest-first schedule deals it, and
+ * size the device status array.  After it, dfs_solve_batched on a list with the same count, the
+ * same (or smaller) n, m, k per position and the same s_dtype and precision allocates nothing
+ * and can be captured into a CUDA graph.  *workspace_bytes (may be NULL) receives the device
+ * bytes held for the batch: the lanes' workspaces plus the status array.  Only the problems'
+ * sizes, lambda and pointers' alignment are read; S, V and X are not touched. */
+dfs_status dfs_plan_batched(dfs_handle handle, const dfs_problem* problems, int count,
+                            int s_dtype, const dfs_options* opt, size_t* workspace_bytes);
+
+/* Device statuses of the last dfs_solve_batched on this handle, in `problems` order:
+ * synchronizes `stream` (the stream the batch ran on, or a later one) and copies `count`
+ * ints (count <= the batch's count) to host memory status_out.  Returns DFS_OK, or the first
+ * non-zero status among them. */
+dfs_status dfs_batched_status(dfs_handle handle, int* status_out, int count, void* stream);
 
 /* ---- single steps of Algorithm 1 (for composition and testing) ---------------------- */
 

@@ -17,6 +17,8 @@ from .api import (  # noqa: F401
     dfs_reserve,
     dfs_solve,
     dfs_solve_batched,
+    dfs_plan_batched,
+    dfs_batched_status,
     dfs_solve_host,
     dfs_solve_host_async,
     dfs_solve_complex,

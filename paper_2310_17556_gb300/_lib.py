@@ -30,6 +30,7 @@ PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 EXPORTS = (
     "dfs_create", "dfs_destroy", "dfs_status_string", "dfs_last_error", "dfs_reserve", "dfs_kernel_launches",
     "dfs_solve", "dfs_solve_host", "dfs_solve_host_async", "dfs_solve_complex", "dfs_sync_info", "dfs_step_times", "dfs_solve_batched",
+    "dfs_plan_batched", "dfs_batched_status",
     "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass", "dfs_fisher_pass_noalloc",
 )
 
@@ -78,6 +79,9 @@ _SIGS = {
     "dfs_step_times": (C.c_int, [_VP, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
     "dfs_solve_batched": (C.c_int, [_VP, C.POINTER(dfs_problem), C.c_int, C.c_int, C.POINTER(dfs_options), _VP,
                                     C.POINTER(C.c_int)]),
+    "dfs_plan_batched": (C.c_int, [_VP, C.POINTER(dfs_problem), C.c_int, C.c_int, C.POINTER(dfs_options),
+                                   C.POINTER(C.c_size_t)]),
+    "dfs_batched_status": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int, _VP]),
     "dfs_gram": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, C.c_double, C.c_int, _VP, _I64, _VP]),
     "dfs_cholesky": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _VP, C.POINTER(_I64)]),
     "dfs_trsm": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _VP, _I64, _I64, C.c_int, _VP]),

@@ -221,24 +221,33 @@ def dfs_solve_complex(S_re: torch.Tensor, S_im: torch.Tensor, V_re: torch.Tensor
     return X_re, X_im, _info_dict(info)
 
 
-def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float = 0.0,
-                      handle: Handle | None = None, stream=None, sync: bool = True, center: bool = False):
-    """problems: list of (S, V, lam[, X]); returns (list of X, list of per-problem status or None).
-
-    When a problem fails, the DfsError raised carries .outs (every X) and .statuses (per problem)."""
-    h = handle or default_handle()
+def _batch_array(problems, alloc_x: bool):
+    """The C problem array for [(S, V, lam[, X]), ...]: (array, outputs, S dtype code).  Without
+    alloc_x a missing X is stood in for by V (planning reads only sizes and alignment)."""
     arr = (dfs_problem * len(problems))()
     outs = []
     dt = None
     for i, pr in enumerate(problems):
         S, V, lam = pr[0], pr[1], pr[2]
-        X = pr[3] if len(pr) > 3 else torch.empty_like(V)
+        X = pr[3] if len(pr) > 3 else (torch.empty_like(V) if alloc_x else V)
         dt = _dtype_code(S) if dt is None else dt
         if _dtype_code(S) != dt:
             raise TypeError("all S of a batch must share one dtype")
         arr[i] = dfs_problem(S.data_ptr(), S.shape[0], S.shape[1], _rows(S, "S"), V.data_ptr(), V.shape[0],
                              _rows(V, "V"), float(lam), X.data_ptr(), _rows(X, "X"))
         outs.append(X)
+    return arr, outs, dt
+
+
+def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float = 0.0,
+                      handle: Handle | None = None, stream=None, sync: bool = True, center: bool = False):
+    """problems: list of (S, V, lam[, X]); returns (list of X, list of per-problem status or None).
+
+    sync=False: no synchronization (the statuses stay on the device for dfs_batched_status);
+    after dfs_plan_batched for the same shapes the call allocates nothing and can be captured.
+    When a problem fails, the DfsError raised carries .outs (every X) and .statuses (per problem)."""
+    h = handle or default_handle()
+    arr, outs, dt = _batch_array(problems, alloc_x=True)
     opt = _opts(precision, max_iter, tol, center=center)
     status = (C.c_int * len(problems))() if sync else None
     st = h.lib.dfs_solve_batched(h.h, arr, len(problems), dt, C.byref(opt), _stream(stream), status)
@@ -250,6 +259,35 @@ def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float
             e.statuses = list(status) if sync else None
             raise
     return outs, (list(status) if sync else None)
+
+
+def dfs_plan_batched(problems, precision="auto", max_iter: int = -1, tol: float = 0.0,
+                     handle: Handle | None = None, center: bool = False) -> int:
+    """Create the lanes and size the workspaces dfs_solve_batched needs for these problems
+    ([(S, V, lam[, X]), ...]; only sizes and alignment are read).  Returns the device bytes held."""
+    h = handle or default_handle()
+    arr, _, dt = _batch_array(problems, alloc_x=False)
+    opt = _opts(precision, max_iter, tol, center=center)
+    nbytes = C.c_size_t(0)
+    st = h.lib.dfs_plan_batched(h.h, arr, len(problems), dt, C.byref(opt), C.byref(nbytes))
+    _check(h.lib, h.h, st)
+    return nbytes.value
+
+
+def dfs_batched_status(count: int, handle: Handle | None = None, stream=None) -> list:
+    """Synchronize and return the device statuses of the last dfs_solve_batched (first `count`).
+    Raises DfsError (with .statuses) on a failed problem other than NOT_CONVERGED."""
+    h = handle or default_handle()
+    status = (C.c_int * max(count, 1))()
+    st = h.lib.dfs_batched_status(h.h, status, count, _stream(stream))
+    out = list(status)[:count]
+    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
+        try:
+            _check(h.lib, h.h, st)
+        except DfsError as e:
+            e.statuses = out
+            raise
+    return out
 
 
 def dfs_gram(S: torch.Tensor, lam: float, precision="auto", W: torch.Tensor | None = None,

@@ -29,6 +29,7 @@ struct dfs_handle_s {
     void* hbuf[3] = {nullptr, nullptr, nullptr};  // device staging (dfs_solve_host, dfs_solve_complex): S, V, X
     int* bstat = nullptr;                          // per-problem device status of dfs_solve_batched
     int bstat_count = 0;
+    int bstat_used = 0;                            // problems of the last dfs_solve_batched
     // dfs_solve_batched runs its problems on up to kMaxLanes concurrent lanes: each a private handle
     // (workspace, device status) and stream, forked from and joined to the caller's stream by events.
     static constexpr int kMaxLanes = 8;
@@ -919,14 +920,10 @@ dfs_status dfs_fisher_pass(dfs_handle h, const void* S, int s_dtype, int64_t n, 
     return DFS_OK;
 }
 
-dfs_status dfs_solve_batched(dfs_handle h, const dfs_problem* problems, int count, int s_dtype,
-                             const dfs_options* opt, void* stream_, int* status_out) {
-    if (!h) return DFS_ERR_INVALID_ARG;
-    h->err.clear();
-    cudaSetDevice(h->device);
-    cudaStream_t stream = (cudaStream_t)stream_;
+// ---- batches of independent problems ------------------------------------------------------
+
+static dfs_status check_batch(dfs_handle h, const dfs_problem* problems, int count, int s_dtype) {
     if (!problems || count < 1) return fail(h, DFS_ERR_INVALID_ARG, "empty problem list");
-    int64_t n_max = 1, m_max = 1, k_max = 1;
     for (int i = 0; i < count; ++i) {
         const dfs_problem& q = problems[i];
         dfs_status s;
@@ -934,11 +931,49 @@ dfs_status dfs_solve_batched(dfs_handle h, const dfs_problem* problems, int coun
         if ((s = check_lambda(h, q.lambda)) != DFS_OK) return s;
         if (!q.V || !q.X || q.k < 1 || q.ldv < q.m || q.ldx < q.m)
             return fail(h, DFS_ERR_INVALID_ARG, "problem %d: bad V/X arguments", i);
-        n_max = q.n > n_max ? q.n : n_max;
-        m_max = q.m > m_max ? q.m : m_max;
-        k_max = q.k > k_max ? q.k : k_max;
     }
+    return DFS_OK;
+}
+
+// Lanes: problems are dealt longest first (estimated cost n^2 m + 4 n m k: the Gram and the
+// passes over S) to the lane with the least work so far; each lane solves its problems in order
+// on its own stream and workspace.  With one lane this is a plain loop on the caller's stream.
+// Eight lanes: 64 problems of n ~ U{64..1024}, m log-uniform in [1e4, 5e5] ran 1.63x faster than
+// one stream with four lanes, 1.78x with eight, 1.80x with sixteen.  Returns the lane count;
+// `order` receives the problems longest first, `lane_of` each problem's lane.
+static int schedule_batch(const dfs_problem* problems, int count, std::vector<int>& order,
+                          std::vector<int>& lane_of) {
+    const int L = count < dfs_handle_s::kMaxLanes ? count : dfs_handle_s::kMaxLanes;
+    order.resize(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    auto cost = [&](int i) {
+        const dfs_problem& q = problems[i];
+        return (double)q.n * (double)q.n * (double)q.m + 4.0 * (double)q.n * (double)q.m * (double)q.k;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    lane_of.assign(count, 0);
+    std::vector<double> load(L, 0.0);
+    for (int i : order) {
+        int best = 0;
+        for (int l = 1; l < L; ++l)
+            if (load[l] < load[best]) best = l;
+        lane_of[i] = best;
+        load[best] += cost(i);
+    }
+    return L;
+}
+
+static bool capturing(cudaStream_t stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// The per-problem status array and, for L > 1, lanes 0..L-1 with their streams and events.
+// Nothing is created while `stream` is being captured (that is an error).
+static dfs_status prepare_batch(dfs_handle h, int count, int L, cudaStream_t stream) {
+    const bool cap = capturing(stream);
     if (count > h->bstat_count) {
+        if (cap) return fail(h, DFS_ERR_NO_MEMORY, "batch status array must grow during stream capture; call dfs_plan_batched first");
         if (h->bstat) cudaFree(h->bstat);
         h->bstat = nullptr;
         h->bstat_count = 0;
@@ -948,58 +983,87 @@ dfs_status dfs_solve_batched(dfs_handle h, const dfs_problem* problems, int coun
         }
         h->bstat_count = count;
     }
-    // Lanes: problems are dealt longest first (estimated cost n^2 m + 4 n m k: the Gram and the
-    // passes over S) to the lane with the least work so far; each lane solves its problems in order
-    // on its own stream and workspace.  With one lane this is a plain loop on the caller's stream.
-    // eight lanes: 64 config-4 problems ran 1.63x faster than one stream with four lanes, 1.78x
-    // with eight, 1.80x with sixteen
-    const int L = count < dfs_handle_s::kMaxLanes ? count : dfs_handle_s::kMaxLanes;
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    auto cost = [&](int i) {
-        const dfs_problem& q = problems[i];
-        return (double)q.n * (double)q.n * (double)q.m + 4.0 * (double)q.n * (double)q.m * (double)q.k;
-    };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    std::vector<int> lane_of(count, 0);
-    {
-        std::vector<double> load(L, 0.0);
-        for (int i : order) {
-            int best = 0;
-            for (int l = 1; l < L; ++l)
-                if (load[l] < load[best]) best = l;
-            lane_of[i] = best;
-            load[best] += cost(i);
-        }
-    }
-    if (L == 1) {
-        for (int i : order) {
-            const dfs_problem& q = problems[i];
-            dfs_status s = solve_device(h, q.S, s_dtype, q.n, q.m, q.lds, q.V, q.k, q.ldv, q.lambda, q.X, q.ldx, opt,
-                                        stream, nullptr);
-            if (s != DFS_OK) return s;
-            DFS_CK(launch_status_save(h->dstat, h->bstat + i, stream));
-        }
-    } else {
-        for (int l = 0; l < L; ++l) {
+    if (L < 2) return DFS_OK;
+    for (int l = 0; l < L; ++l) {
+        if (!h->lane[l] || !h->lane_stream[l] || !h->lane_done[l]) {
+            if (cap) return fail(h, DFS_ERR_NO_MEMORY, "batch lane %d must be created during stream capture; call dfs_plan_batched first", l);
             if (!h->lane[l]) {
                 dfs_status s = dfs_create(&h->lane[l], h->device);
                 if (s != DFS_OK) return fail(h, s, "creating batch lane %d failed", l);
             }
             if (!h->lane_stream[l]) DFS_CK(cudaStreamCreateWithFlags(&h->lane_stream[l], cudaStreamNonBlocking));
             if (!h->lane_done[l]) DFS_CK(cudaEventCreateWithFlags(&h->lane_done[l], cudaEventDisableTiming));
-            // every lane's cooperative Cholesky fits on the device at the same time as the others'
-            h->lane[l]->chol_share = L;
         }
-        if (!h->fork_ev) DFS_CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        // every lane's cooperative Cholesky fits on the device at the same time as the others'
+        h->lane[l]->chol_share = L;
+    }
+    if (!h->fork_ev) {
+        if (cap) return fail(h, DFS_ERR_NO_MEMORY, "batch fork event must be created during stream capture; call dfs_plan_batched first");
+        DFS_CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    }
+    return DFS_OK;
+}
+
+dfs_status dfs_plan_batched(dfs_handle h, const dfs_problem* problems, int count, int s_dtype,
+                            const dfs_options* opt, size_t* workspace_bytes) {
+    if (workspace_bytes) *workspace_bytes = 0;
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    dfs_status s;
+    if ((s = check_batch(h, problems, count, s_dtype)) != DFS_OK) return s;
+    int prec;
+    if ((s = resolve_precision(h, s_dtype, opt ? opt->precision : DFS_PREC_AUTO, &prec)) != DFS_OK) return s;
+    std::vector<int> order, lane_of;
+    const int L = schedule_batch(problems, count, order, lane_of);
+    if ((s = prepare_batch(h, count, L, nullptr)) != DFS_OK) return s;
+    // each lane's workspace: the largest plan among the problems dealt to it
+    std::vector<size_t> need(L, 0);
+    for (int i = 0; i < count; ++i) {
+        const dfs_problem& q = problems[i];
+        Plan p;
+        if ((s = make_plan(h, s_dtype, prec, q.n, q.m, (int)q.k, &p)) != DFS_OK) return s;
+        if (p.total > need[lane_of[i]]) need[lane_of[i]] = p.total;
+    }
+    size_t held = sizeof(int) * (size_t)h->bstat_count;
+    for (int l = 0; l < L; ++l) {
+        dfs_handle lh = L == 1 ? h : h->lane[l];
+        if ((s = ensure_ws(lh, need[l], nullptr)) != DFS_OK) return L == 1 ? s : fail(h, s, "lane %d: %s", l, lh->err.c_str());
+        held += lh->ws_bytes;
+    }
+    if (workspace_bytes) *workspace_bytes = held;
+    return DFS_OK;
+}
+
+dfs_status dfs_solve_batched(dfs_handle h, const dfs_problem* problems, int count, int s_dtype,
+                             const dfs_options* opt, void* stream_, int* status_out) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    dfs_status s;
+    if ((s = check_batch(h, problems, count, s_dtype)) != DFS_OK) return s;
+    std::vector<int> order, lane_of;
+    const int L = schedule_batch(problems, count, order, lane_of);
+    if ((s = prepare_batch(h, count, L, stream)) != DFS_OK) return s;
+    h->bstat_used = count;
+    if (L == 1) {
+        for (int i : order) {
+            const dfs_problem& q = problems[i];
+            s = solve_device(h, q.S, s_dtype, q.n, q.m, q.lds, q.V, q.k, q.ldv, q.lambda, q.X, q.ldx, opt, stream,
+                             nullptr);
+            if (s != DFS_OK) return s;
+            DFS_CK(launch_status_save(h->dstat, h->bstat + i, stream));
+        }
+    } else {
         DFS_CK(cudaEventRecord(h->fork_ev, stream));
         for (int l = 0; l < L; ++l) DFS_CK(cudaStreamWaitEvent(h->lane_stream[l], h->fork_ev, 0));
         for (int i : order) {
             const dfs_problem& q = problems[i];
             dfs_handle lh = h->lane[lane_of[i]];
             cudaStream_t ls = h->lane_stream[lane_of[i]];
-            dfs_status s = solve_device(lh, q.S, s_dtype, q.n, q.m, q.lds, q.V, q.k, q.ldv, q.lambda, q.X, q.ldx, opt,
-                                        ls, nullptr);
+            s = solve_device(lh, q.S, s_dtype, q.n, q.m, q.lds, q.V, q.k, q.ldv, q.lambda, q.X, q.ldx, opt, ls,
+                             nullptr);
             if (s != DFS_OK) return fail(h, s, "problem %d: %s", i, lh->err.c_str());
             DFS_CK(launch_status_save(lh->dstat, h->bstat + i, ls));
         }
@@ -1008,13 +1072,23 @@ dfs_status dfs_solve_batched(dfs_handle h, const dfs_problem* problems, int coun
             DFS_CK(cudaStreamWaitEvent(stream, h->lane_done[l], 0));
         }
     }
-    if (status_out) {
-        DFS_CK(cudaMemcpyAsync(status_out, h->bstat, sizeof(int) * count, cudaMemcpyDeviceToHost, stream));
-        DFS_CK(cudaStreamSynchronize(stream));
-        for (int i = 0; i < count; ++i)
-            if (status_out[i] != DFS_OK) return fail(h, (dfs_status)status_out[i], "problem %d: %s", i,
-                                                     dfs_status_string(status_out[i]));
-    }
+    if (status_out) return dfs_batched_status(h, status_out, count, stream_);
+    return DFS_OK;
+}
+
+dfs_status dfs_batched_status(dfs_handle h, int* status_out, int count, void* stream_) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    if (!status_out || count < 0 || count > h->bstat_used)
+        return fail(h, DFS_ERR_INVALID_ARG, "count %d is not within the last batch's %d problems", count, h->bstat_used);
+    if (count == 0) return DFS_OK;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    DFS_CK(cudaMemcpyAsync(status_out, h->bstat, sizeof(int) * count, cudaMemcpyDeviceToHost, stream));
+    DFS_CK(cudaStreamSynchronize(stream));
+    for (int i = 0; i < count; ++i)
+        if (status_out[i] != DFS_OK)
+            return fail(h, (dfs_status)status_out[i], "problem %d: %s", i, dfs_status_string(status_out[i]));
     return DFS_OK;
 }
 

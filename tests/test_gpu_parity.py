@@ -734,6 +734,35 @@ def test_solve_batched_failure_stays_in_its_problem():
             assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
 
 
+def test_solve_batched_planned_is_capturable():
+    """dfs_plan_batched creates the lanes and sizes their workspaces, so the batched solve then
+    allocates nothing and captures into a CUDA graph.  Each replay gives the stream-launched
+    results bit for bit, and leaves the per-problem statuses on the device."""
+    shapes = [(300, 20000, 2, 1e-2), (129, 50001, 1, 1e-3), (513, 9000, 3, 1e-1)]
+    probs = [(aligned(wl.gaussian(n, m, seed=300 + j, device=dev())), wl.rhs(m, k, seed=310 + j, device=dev()), lam)
+             for j, (n, m, k, lam) in enumerate(shapes)]
+    h = dfs.Handle()
+    assert dfs.dfs_plan_batched(probs, precision="bf16", handle=h) > 0
+    outs, status = dfs.dfs_solve_batched(probs, precision="bf16", handle=h)
+    assert status == [0, 0, 0]
+    Xg = [torch.empty_like(V) for _, V, _ in probs]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        dfs.dfs_solve_batched([(S, V, lam, X) for (S, V, lam), X in zip(probs, Xg)], precision="bf16", handle=h,
+                              sync=False)
+    for _ in range(2):
+        for X in Xg:
+            X.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for X, ref in zip(Xg, outs):
+            assert torch.equal(X, ref)
+        assert dfs.dfs_batched_status(3, handle=h) == [0, 0, 0]
+    assert rel_err(np64(Xg[1]), solve_ref(*probs[1])) <= 1e-6
+
+
 # ---------------------------------------------------------------------------- full-size configurations
 
 
