@@ -10,7 +10,9 @@
  *   Appendix A   for lambda > 0 the result is the unique solution of Eq. 1.
  *
  * Conventions shared by every entry point
- *   - Every function returns a dfs_status.  The library never aborts and never prints.
+ *   - Every function returns a dfs_status.  The library never aborts.  It prints only when
+ *     the environment variable DFS_LOG is set (to anything but "0"): then each error message
+ *     it records for dfs_last_error also goes to stderr.
  *   - Matrices are row-major with an explicit leading dimension (in elements).
  *     S: n rows of length m, row stride lds >= m (each sample row is contiguous).
  *     V, X: k rows of length m (one right-hand side per row), strides ldv, ldx >= m.

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -71,15 +72,20 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int elem_size(int dt) { return dt == DFS_F64 ? 8 : (dt == DFS_F32 ? 4 : 2); }
 
+// Records the message on the handle; with DFS_LOG set in the environment (to anything but "0")
+// also prints it to stderr.  The library prints nothing otherwise.
 dfs_status fail(dfs_handle h, dfs_status s, const char* fmt, ...) {
-    if (h) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof(buf), fmt, ap);
-        va_end(ap);
-        h->err = buf;
-    }
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    static const bool log = [] {
+        const char* e = std::getenv("DFS_LOG");
+        return e != nullptr && std::strcmp(e, "0") != 0;
+    }();
+    if (log) std::fprintf(stderr, "dfs: %s: %s\n", dfs_status_string(s), buf);
     return s;
 }
 
@@ -575,21 +581,27 @@ dfs_status dfs_create(dfs_handle* out, int device) {
     if (!out) return DFS_ERR_INVALID_ARG;
     *out = nullptr;
     int count = 0;
-    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    const cudaError_t ce = cudaGetDeviceCount(&count);
+    if (ce != cudaSuccess || device < 0 || device >= count) {
         cudaGetLastError();
-        return DFS_ERR_CUDA;
+        return fail(nullptr, DFS_ERR_CUDA, "no CUDA device %d (%d visible: %s)", device, ce == cudaSuccess ? count : 0,
+                    cudaGetErrorString(ce));
     }
     cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DFS_ERR_CUDA;
-    if (prop.major != 10 || prop.minor != 3) return DFS_ERR_UNSUPPORTED;  // built for sm_103a only
-    if (cudaSetDevice(device) != cudaSuccess) return DFS_ERR_CUDA;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+        return fail(nullptr, DFS_ERR_CUDA, "cudaGetDeviceProperties(%d) failed", device);
+    if (prop.major != 10 || prop.minor != 3)  // built for sm_103a only
+        return fail(nullptr, DFS_ERR_UNSUPPORTED, "device %d is sm_%d%d; this build runs on sm_103a only", device,
+                    prop.major, prop.minor);
+    if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, DFS_ERR_CUDA, "cudaSetDevice(%d) failed", device);
     dfs_handle h = new dfs_handle_s();
     h->device = device;
     h->num_sms = prop.multiProcessorCount;
     h->smem_optin = prop.sharedMemPerBlockOptin;
     if (cudaMalloc(&h->dstat, sizeof(DevStatus)) != cudaSuccess) {
         delete h;
-        return DFS_ERR_NO_MEMORY;
+        cudaGetLastError();
+        return fail(nullptr, DFS_ERR_NO_MEMORY, "cudaMalloc for the device status word failed");
     }
     cudaMemset(h->dstat, 0, sizeof(DevStatus));
     *out = h;

@@ -71,3 +71,22 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libdfs.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.load()
+
+
+def test_errors_print_only_with_dfs_log(libpath):
+    """The library prints nothing unless DFS_LOG is set; then each recorded error goes to stderr.
+    A handle for device 999 fails on any machine, before any GPU work."""
+    code = ("import ctypes as C, sys\n"
+            "from paper_2310_17556_gb300 import _lib\n"
+            "h = C.c_void_p()\n"
+            "sys.exit(0 if _lib.load().dfs_create(C.byref(h), 999) == _lib.DFS_ERR_CUDA else 1)\n")
+    runs = {}
+    for log in (None, "0", "1"):
+        env = {k: v for k, v in os.environ.items() if k != "DFS_LOG"}
+        if log is not None:
+            env["DFS_LOG"] = log
+        r = subprocess.run(["python", "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+        assert r.returncode == 0, r.stderr
+        runs[log] = r.stderr
+    assert "dfs:" not in runs[None] and "dfs:" not in runs["0"]
+    assert "dfs: DFS_ERR_CUDA: no CUDA device 999" in runs["1"]
