@@ -49,11 +49,29 @@ def test_ctypes_loads_and_binds(libpath):
     assert lib.dfs_status_string(0) == b"DFS_OK"
 
 
-def test_library_is_built_for_sm103a(libpath):
-    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+def test_every_nvcc_command_targets_sm103a_only(monkeypatch, tmp_path):
+    """The build compiles and links each source for sm_103a alone: the nvcc command lines it
+    issues (captured, not run) carry one -gencode, arch=compute_103a,code=sm_103a."""
+    from paper_2310_17556_gb300 import build
+
+    cmds = []
+
+    class Done:
+        returncode, stdout, stderr = 0, "", ""
+
+    def fake_run(cmd, **kw):
+        cmds.append(list(cmd))
+        open(cmd[cmd.index("-o") + 1], "w").close()
+        return Done()
+
+    monkeypatch.setattr(build.subprocess, "run", fake_run)
+    monkeypatch.setattr(build, "BUILD", str(tmp_path))
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "libdfs.so"))
+    build.build(force=True)
+    assert len(cmds) == len(build._sources()) + 1  # each source, then the link
+    for cmd in cmds:
+        targets = [a for a in cmd if a.startswith(("arch=", "-arch", "--gpu-architecture", "-code", "--gpu-code"))]
+        assert targets == ["arch=compute_103a,code=sm_103a"] and cmd.count("-gencode") == 1, cmd
 
 
 def test_null_handle_is_rejected(libpath):
