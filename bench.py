@@ -556,15 +556,22 @@ def run_workload(args):
         _, status = dfs.dfs_solve_batched(probs, precision="bf16")
         import oracle
 
+        import numpy as np
+
         small = sorted(range(len(probs)), key=lambda j: probs[j][0].numel())[:4]
         errs = []
+        t_oracle = 0.0
         for j in small:
             S, V, lam, X = probs[j]
-            ref = oracle.solve(S.double().cpu().numpy(), V.double().cpu().numpy().T, lam).T
+            s64, v64 = S.double().cpu().numpy(), V.double().cpu().numpy().T
+            t0 = time.perf_counter()
+            ref = oracle.solve(s64, v64, lam).T
+            t_oracle += time.perf_counter() - t0
             x = X.double().cpu().numpy()
-            import numpy as np
-
             errs.append(float(np.max(np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1))))
+        # the oracle's time for the whole batch, scaled from the sample by n^2 m + 4 n m k
+        cost = lambda p: p[0].shape[0] ** 2 * p[0].shape[1] + 4 * p[0].shape[0] * p[0].shape[1] * p[1].shape[0]
+        t_all = t_oracle * sum(cost(p) for p in probs) / sum(cost(probs[j]) for j in small)
         emit({"workload": "batch", "metric": "problems/s, 64 ragged problems, k=8", "value": 64e3 / ms_b,
               "unit": "problems/s", "ms_per_step": ms_b, "dtype": "bf16", "clocks": clocks,
               "sequential": {"value": 64e3 / ms_l, "ms_per_step": ms_l, "api": "one dfs_solve after another"},
@@ -572,7 +579,11 @@ def run_workload(args):
                          "lambda": "log-uniform [1e-5, 1e-1]", "k": 8,
                          "S_bytes": sum(p[0].numel() * 4 for p in probs)},
               "accuracy": {"statuses_ok": all(x == 0 for x in status), "e_rel_4_smallest_vs_oracle": errs,
-                           "ok": all(x == 0 for x in status) and max(errs) <= 1e-6}})
+                           "ok": all(x == 0 for x in status) and max(errs) <= 1e-6},
+              "cpu_baseline": {"value": len(probs) / t_all, "unit": "problems/s", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"FP64 oracle on the {len(small)} smallest problems in {t_oracle:.2f} s, "
+                                         "scaled to all 64 by n^2 m + 4 n m k"}})
     elif args.workload == "stress":
         n, m, lam = 8192, 1 << 22, 1e-5
         S = wl.heavy_tailed(n, m, seed=base + 5, device=dev, dtype=torch.bfloat16)
