@@ -91,6 +91,10 @@ typedef enum {
                                    lambda I with P = I - 1 1^T / n, b = P O v / sqrt(n), and each
                                    pass over O reads P y / sqrt(n) (the triangular solves run on the
                                    reduce + substitution kernels).  dfs_solve and dfs_solve_host. */
+#define DFS_FLAG_TWO_KERNEL_GRAM 8 /* BF16 Gram on FP32 S: run the first pass over S (b = S v and the
+                                   BF16 tiles) and the Gram as two kernels instead of the one fused
+                                   kernel that overlaps them (the default where it applies: n <= 4096
+                                   on 152 SMs, up to 4 right-hand sides per group) */
 
 typedef struct {
     int precision;   /* dfs_precision */

@@ -8,6 +8,7 @@ package is the thin Python binding: same entry-point names, torch tensors in and
 from .api import (  # noqa: F401
     DfsError,
     Handle,
+    NotConvergedError,
     default_handle,
     dfs_cholesky,
     dfs_fisher_pass,

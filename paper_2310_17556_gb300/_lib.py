@@ -49,6 +49,7 @@ DFS_STEP_TIMES = 9
 DFS_FLAG_STEP_TIMING = 1
 DFS_FLAG_FP64_PANEL = 2
 DFS_FLAG_CENTER = 4
+DFS_FLAG_TWO_KERNEL_GRAM = 8
 DFS_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -115,3 +116,8 @@ class DfsError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(message)
         self.status = status
+
+
+class NotConvergedError(DfsError):
+    """Refinement stopped above its tolerance (DFS_ERR_NOT_CONVERGED).  .X (or .outs) holds the
+    best iterate the solve returned and .info its dfs_info fields."""

@@ -14,7 +14,8 @@ import ctypes as C
 import torch
 
 from . import _lib
-from ._lib import DFS_BF16, DFS_F32, DFS_F64, PRECISIONS, DfsError, dfs_info, dfs_options, dfs_problem
+from ._lib import (DFS_BF16, DFS_F32, DFS_F64, PRECISIONS, DfsError, NotConvergedError, dfs_info, dfs_options,
+                   dfs_problem)
 
 _DT = {torch.float64: DFS_F64, torch.float32: DFS_F32, torch.bfloat16: DFS_BF16}
 
@@ -43,11 +44,29 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def _opts(precision, max_iter, tol, timing=False, fp64_panel=False, center=False) -> dfs_options:
+def _opts(precision, max_iter, tol, timing=False, fp64_panel=False, center=False,
+          two_kernel_gram=False) -> dfs_options:
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     flags = (_lib.DFS_FLAG_STEP_TIMING if timing else 0) | (_lib.DFS_FLAG_FP64_PANEL if fp64_panel else 0)
     flags |= _lib.DFS_FLAG_CENTER if center else 0
+    flags |= _lib.DFS_FLAG_TWO_KERNEL_GRAM if two_kernel_gram else 0
     return dfs_options(p, int(max_iter), float(tol), flags)
+
+
+def _settle(lib, h, st: int, allow_not_converged: bool, **result):
+    """Raise on a failed solve.  NOT_CONVERGED raises NotConvergedError (carrying the returned
+    iterate and info) unless the caller allows it."""
+    if st == _lib.DFS_OK:
+        return
+    if st == _lib.DFS_ERR_NOT_CONVERGED:
+        if allow_not_converged:
+            return
+        msg = lib.dfs_last_error(h).decode() if h else ""
+        e = NotConvergedError(st, f"{lib.dfs_status_string(st).decode()}: {msg}")
+        for key, val in result.items():
+            setattr(e, key, val)
+        raise e
+    _check(lib, h, st)
 
 
 def _check(lib, h, status: int):
@@ -110,13 +129,18 @@ def dfs_reserve(n_max: int, m_max: int, k_max: int, precision="auto", handle: Ha
 
 def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
               max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
-              sync: bool = True, timing: bool = False, fp64_panel: bool = False, center: bool = False):
+              sync: bool = True, timing: bool = False, fp64_panel: bool = False, center: bool = False,
+              two_kernel_gram: bool = False, allow_not_converged: bool = False):
     """Solve (S^T S + lam I) X^T = V^T for the k rows of V (Eq. 1, Algorithm 1).
 
     center=True: S holds O and the system is Eq. 1 with Section 4's SR scores (O - O_bar)/sqrt(n).
+    two_kernel_gram=True: the first pass over S and the BF16 Gram as two kernels instead of the
+    fused one (for comparison).
 
     Returns (X, info) when sync is True (info = dict of dfs_info), else (X, None) with the work
-    queued on the stream (read the status later with dfs_sync_info).
+    queued on the stream (read the status later with dfs_sync_info).  A solve whose refinement
+    stops above tolerance raises NotConvergedError (with .X and .info) unless
+    allow_not_converged is set.
     """
     h = handle or default_handle(S.device.index)
     n, m = S.shape
@@ -128,26 +152,26 @@ def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | No
         raise TypeError(f"V must be {vdt} for S of dtype {S.dtype}")
     if X is None:
         X = torch.empty((k, m), device=S.device, dtype=vdt)
-    opt = _opts(precision, max_iter, tol, timing, fp64_panel, center)
+    opt = _opts(precision, max_iter, tol, timing, fp64_panel, center, two_kernel_gram)
     info = dfs_info()
     st = h.lib.dfs_solve(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k, _rows(V, "V"),
                          float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt), _stream(stream),
                          C.byref(info) if sync else None)
     if sync:
-        if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
-            _check(h.lib, h.h, st)
-        return X, _info_dict(info)
+        d = _info_dict(info)
+        _settle(h.lib, h.h, st, allow_not_converged, X=X, info=d)
+        return X, d
     _check(h.lib, h.h, st)
     return X, None
 
 
-def dfs_sync_info(handle: Handle | None = None, stream=None) -> dict:
+def dfs_sync_info(handle: Handle | None = None, stream=None, allow_not_converged: bool = False) -> dict:
     h = handle or default_handle()
     info = dfs_info()
     st = h.lib.dfs_sync_info(h.h, _stream(stream), C.byref(info))
-    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
-        _check(h.lib, h.h, st)
-    return _info_dict(info)
+    d = _info_dict(info)
+    _settle(h.lib, h.h, st, allow_not_converged, info=d)
+    return d
 
 
 def dfs_step_times(handle: Handle | None = None) -> tuple[list[float], int]:
@@ -162,7 +186,7 @@ def dfs_step_times(handle: Handle | None = None) -> tuple[list[float], int]:
 
 def dfs_solve_host(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
                    max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
-                   center: bool = False):
+                   center: bool = False, allow_not_converged: bool = False):
     """Same solve with S, V, X in host memory (pinned for full copy speed); copies inside the call."""
     h = handle or default_handle()
     n, m = S.shape
@@ -174,9 +198,9 @@ def dfs_solve_host(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor
     st = h.lib.dfs_solve_host(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k,
                               _rows(V, "V"), float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt),
                               _stream(stream), C.byref(info))
-    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
-        _check(h.lib, h.h, st)
-    return X, _info_dict(info)
+    d = _info_dict(info)
+    _settle(h.lib, h.h, st, allow_not_converged, X=X, info=d)
+    return X, d
 
 
 def dfs_solve_host_async(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor, precision="auto",
@@ -200,7 +224,7 @@ def dfs_solve_host_async(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.
 
 def dfs_solve_complex(S_re: torch.Tensor, S_im: torch.Tensor, V_re: torch.Tensor, V_im: torch.Tensor, lam: float,
                       precision="auto", max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None,
-                      stream=None):
+                      stream=None, allow_not_converged: bool = False):
     """Complex SR (Section 4, F = S^dagger S): solve (S^dagger S + lam I) X^T = V^T for S = S_re + i S_im
     (n x m planes) and the k rows of V = V_re + i V_im; returns (X_re, X_im, info)."""
     h = handle or default_handle(S_re.device.index)
@@ -216,9 +240,9 @@ def dfs_solve_complex(S_re: torch.Tensor, S_im: torch.Tensor, V_re: torch.Tensor
     st = h.lib.dfs_solve_complex(h.h, S_re.data_ptr(), S_im.data_ptr(), _dtype_code(S_re), n, m, _rows(S_re, "S"),
                                  V_re.data_ptr(), V_im.data_ptr(), k, _rows(V_re, "V"), float(lam), X_re.data_ptr(),
                                  X_im.data_ptr(), _rows(X_re, "X"), C.byref(opt), _stream(stream), C.byref(info))
-    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
-        _check(h.lib, h.h, st)
-    return X_re, X_im, _info_dict(info)
+    d = _info_dict(info)
+    _settle(h.lib, h.h, st, allow_not_converged, X=(X_re, X_im), info=d)
+    return X_re, X_im, d
 
 
 def _batch_array(problems, alloc_x: bool):
@@ -240,7 +264,8 @@ def _batch_array(problems, alloc_x: bool):
 
 
 def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float = 0.0,
-                      handle: Handle | None = None, stream=None, sync: bool = True, center: bool = False):
+                      handle: Handle | None = None, stream=None, sync: bool = True, center: bool = False,
+                      allow_not_converged: bool = False):
     """problems: list of (S, V, lam[, X]); returns (list of X, list of per-problem status or None).
 
     sync=False: no synchronization (the statuses stay on the device for dfs_batched_status);
@@ -251,13 +276,12 @@ def dfs_solve_batched(problems, precision="auto", max_iter: int = -1, tol: float
     opt = _opts(precision, max_iter, tol, center=center)
     status = (C.c_int * len(problems))() if sync else None
     st = h.lib.dfs_solve_batched(h.h, arr, len(problems), dt, C.byref(opt), _stream(stream), status)
-    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
-        try:
-            _check(h.lib, h.h, st)
-        except DfsError as e:
-            e.outs = outs
-            e.statuses = list(status) if sync else None
-            raise
+    try:
+        _settle(h.lib, h.h, st, allow_not_converged)
+    except DfsError as e:
+        e.outs = outs
+        e.statuses = list(status) if sync else None
+        raise
     return outs, (list(status) if sync else None)
 
 
@@ -274,19 +298,20 @@ def dfs_plan_batched(problems, precision="auto", max_iter: int = -1, tol: float 
     return nbytes.value
 
 
-def dfs_batched_status(count: int, handle: Handle | None = None, stream=None) -> list:
+def dfs_batched_status(count: int, handle: Handle | None = None, stream=None,
+                       allow_not_converged: bool = False) -> list:
     """Synchronize and return the device statuses of the last dfs_solve_batched (first `count`).
-    Raises DfsError (with .statuses) on a failed problem other than NOT_CONVERGED."""
+    Raises DfsError (with .statuses) on a failed problem; NOT_CONVERGED only raises
+    (NotConvergedError) unless allow_not_converged is set."""
     h = handle or default_handle()
     status = (C.c_int * max(count, 1))()
     st = h.lib.dfs_batched_status(h.h, status, count, _stream(stream))
     out = list(status)[:count]
-    if st not in (_lib.DFS_OK, _lib.DFS_ERR_NOT_CONVERGED):
-        try:
-            _check(h.lib, h.h, st)
-        except DfsError as e:
-            e.statuses = out
-            raise
+    try:
+        _settle(h.lib, h.h, st, allow_not_converged)
+    except DfsError as e:
+        e.statuses = out
+        raise
     return out
 
 

@@ -39,6 +39,7 @@ struct dfs_handle_s {
     cudaEvent_t lane_done[kMaxLanes] = {};
     cudaEvent_t fork_ev = nullptr;
     int chol_share = 1;  // the cooperative Cholesky takes 1 / chol_share of the resident-CTA capacity
+    bool lane_handle = false;  // a lane of dfs_solve_batched: no whole-GPU fused Gram (lanes run concurrently)
     // dfs_solve_host_async: two device staging slots for S and V (alternating calls), one for X, a
     // copy stream for the uploads and the events that order slot reuse
     void* abuf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -110,9 +111,11 @@ struct Plan {
     PassPlan pp{};
     int pgrid = 1;  // rows of the pass partial buffers
     int pack = 0;   // tile packing done by the first S v pass: 0 none, 1 BF16, 2 TF32
+    bool fused = false;  // b = S v, the BF16 tiles and the Gram in one kernel (gram_fused.cu)
     bool ns = false;  // n-space steps as one cluster kernel (nspace.cu)
     size_t off_W = 0, off_Linv = 0, off_P = 0, off_Rpart = 0, off_U2part = 0, off_R = 0, off_Z = 0, off_Y = 0,
-           off_U2 = 0, off_V = 0, off_bn2 = 0, off_Sp = 0, off_Cf = 0, off_Rs = 0, off_Yc = 0, off_Cg = 0, total = 0;
+           off_U2 = 0, off_V = 0, off_bn2 = 0, off_Sp = 0, off_Cf = 0, off_Rs = 0, off_Yc = 0, off_Cg = 0,
+           off_Rdy = 0, total = 0;
 };
 
 int tc_kind(int prec) {
@@ -160,7 +163,8 @@ int pow2_at_least(int k) {
     return q;
 }
 
-dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, int k, Plan* p) {
+dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, int k, Plan* p,
+                     bool allow_fused = true) {
     p->s_dtype = s_dtype;
     p->prec = prec;
     p->f64 = (prec == DFS_PREC_FP64);
@@ -190,6 +194,12 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     size_t gram_bytes;
     if (p->tensor) {
         p->tc = gram_tc_plan(s_dtype, tc_kind(prec), n, m, h->num_sms);
+        GramTcPlan fp;
+        if (tc_kind(prec) == 0 && allow_fused && !h->lane_handle &&
+            gram_fused_plan(s_dtype, n, m, kq, h->num_sms, h->smem_optin, &fp)) {
+            p->tc = fp;
+            p->fused = true;
+        }
         gram_bytes = p->tc.partial_bytes;
     } else {
         gram_simt_plan(n, m, p->f64, h->num_sms, &p->nsplit, &p->chunk);
@@ -197,6 +207,7 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     }
     p->pp = pass_make_plan((int)n, kq, s_dtype, h->num_sms, m, h->smem_optin);
     p->pgrid = pass_partial_rows(p->pp);
+    if (p->fused && p->pgrid < h->num_sms) p->pgrid = h->num_sms;  // the fused kernel's row sums: one row per CTA
     p->pack = (p->tensor && p->tc.packed) ? (p->tc.kind == 1 ? 2 : (p->tc.kind == 2 ? 3 : (p->tc.kind == 3 ? 4 : 1)))
                                           : 0;
     p->ns = nspace_slots((int)p->n_pad, kq, (int)es, h->smem_optin) >= 2;
@@ -223,6 +234,7 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     p->off_Rs = take(p->pack == 4 ? 2 * np * sizeof(float) : 0);
     p->off_Yc = take(np * kq * 8);  // centred scores: P y / sqrt(n) for the passes
     p->off_Cg = take(center_gram_scratch_doubles(np) * 8);
+    p->off_Rdy = take(p->fused ? gram_fused_ready_bytes(p->tc) : 0);
     p->total = off;
     return DFS_OK;
 }
@@ -279,10 +291,15 @@ dfs_status run_gram(dfs_handle h, const Plan& p, const void* S, int64_t lds, dou
         void* Sp = p.pack ? at<void>(h, p.off_Sp) : nullptr;
         float* rs = p.pack == 4 ? at<float>(h, p.off_Rs) : nullptr;  // FP8 row scales, then their inverses
         if (rs) DFS_CK(launch_row_scale(p.s_dtype, S, (int)p.n, (int)p.n_pad, p.m, lds, rs, h->dstat, stream));
-        if (p.pack)
-            DFS_CK(launch_sv_pack(p.pp, p.s_dtype, 1, p.pack, S, (int)p.n, p.m, lds, nullptr, p.m, 0,
-                                  at<double>(h, p.off_Rpart), Sp, h->dstat, stream, rs ? rs + p.n_pad : nullptr));
-        DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, Sp, P, h->dstat, stream));
+        if (p.fused) {
+            DFS_CK(launch_gram_fused(p.tc, 1, S, p.n, p.m, lds, nullptr, p.m, 0, at<double>(h, p.off_Rpart), Sp, P,
+                                     at<int>(h, p.off_Rdy), h->dstat, h->num_sms, stream, nullptr));
+        } else {
+            if (p.pack)
+                DFS_CK(launch_sv_pack(p.pp, p.s_dtype, 1, p.pack, S, (int)p.n, p.m, lds, nullptr, p.m, 0,
+                                      at<double>(h, p.off_Rpart), Sp, h->dstat, stream, rs ? rs + p.n_pad : nullptr));
+            DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, Sp, P, h->dstat, stream));
+        }
         DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, n_out, lambda, W, ldw, stream, rs));
     } else {
         DFS_CK(launch_gram_simt(p.s_dtype, p.f64, S, p.n, p.m, lds, p.nsplit, p.chunk, P, stream));
@@ -355,7 +372,8 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
     const int max_iter = (opt && opt->max_iter >= 0) ? opt->max_iter : 8;
     const double tol = (opt && opt->tol > 0.0) ? opt->tol : 1e-7;
     Plan p;
-    if ((s = make_plan(h, s_dtype, prec, n, m, (int)k, &p)) != DFS_OK) return s;
+    const bool allow_fused = !(opt && (opt->flags & DFS_FLAG_TWO_KERNEL_GRAM));
+    if ((s = make_plan(h, s_dtype, prec, n, m, (int)k, &p, allow_fused)) != DFS_OK) return s;
     if ((s = ensure_ws(h, p.total, stream)) != DFS_OK) return s;
     h->last_precision = prec;
     // S = (O - O_bar) / sqrt(n) from the caller's O: n-space centring around unchanged passes over
@@ -424,12 +442,20 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         const void* Vg = static_cast<const char*>(V) + q0 * ldv * vs;
         void* Xg = static_cast<char*>(X) + q0 * ldx * vs;
         DFS_CK(launch_group_reset(h->dstat, stream));
-        // b = S v; the first group's pass also writes the packed tensor-core tiles of S
+        // b = S v; the first group's pass also writes the packed tensor-core tiles of S, and in the
+        // fused form computes the Gram partials of Algorithm 1 step 1 in the same kernel
+        const bool fused_now = q0 == 0 && p.fused;
         if (q0 == 0) DFS_CK(mark(6));
+        if (fused_now) DFS_CK(mark(1));
         int sv_parts = p.pp.sv_grid;
-        DFS_CK(launch_sv_pack(p.pp, s_dtype, kq, q0 == 0 ? p.pack : 0, S, ni, m, lds, Vg, ldv, kg, Rpart, Sp,
-                              h->dstat, stream, rs ? rs + p.n_pad : nullptr, &sv_parts));
+        if (fused_now)
+            DFS_CK(launch_gram_fused(p.tc, kq, S, p.n, m, lds, Vg, ldv, kg, Rpart, Sp, at<void>(h, p.off_P),
+                                     at<int>(h, p.off_Rdy), h->dstat, h->num_sms, stream, &sv_parts));
+        else
+            DFS_CK(launch_sv_pack(p.pp, s_dtype, kq, q0 == 0 ? p.pack : 0, S, ni, m, lds, Vg, ldv, kg, Rpart, Sp,
+                                  h->dstat, stream, rs ? rs + p.n_pad : nullptr, &sv_parts));
         if (q0 == 0) DFS_CK(mark(7));
+        if (fused_now) DFS_CK(mark(2));
         if (!p.ns)
             DFS_CK(launch_pass_reduce(p.f64, Rpart, sv_parts, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z,
                                       nullptr, nullptr, h->dstat, 0, stream));
@@ -438,12 +464,14 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         if (q0 == 0) {
             // Algorithm 1 steps 1-2: W = S S^T + lambda I~ and its Cholesky factor
             void* P = at<void>(h, p.off_P);
-            DFS_CK(mark(1));
-            if (p.tensor)
-                DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, Sp, P, h->dstat, stream));
-            else
-                DFS_CK(launch_gram_simt(p.s_dtype, p.f64, S, p.n, p.m, lds, p.nsplit, p.chunk, P, stream));
-            DFS_CK(mark(2));
+            if (!p.fused) {
+                DFS_CK(mark(1));
+                if (p.tensor)
+                    DFS_CK(launch_gram_tc(p.tc, p.s_dtype, S, p.n, p.m, lds, Sp, P, h->dstat, stream));
+                else
+                    DFS_CK(launch_gram_simt(p.s_dtype, p.f64, S, p.n, p.m, lds, p.nsplit, p.chunk, P, stream));
+                DFS_CK(mark(2));
+            }
             const double lam_g = center ? 0.0 : lambda;  // centring adds lambda after P G P / n
             if (p.tensor)
                 DFS_CK(launch_gram_tc_finalize(p.tc, P, p.n, p.n_pad, lam_g, W, p.n_pad, stream, rs));
@@ -1008,6 +1036,7 @@ static dfs_status prepare_batch(dfs_handle h, int count, int L, cudaStream_t str
         }
         // every lane's cooperative Cholesky fits on the device at the same time as the others'
         h->lane[l]->chol_share = L;
+        h->lane[l]->lane_handle = true;
     }
     if (!h->fork_ev) {
         if (cap) return fail(h, DFS_ERR_NO_MEMORY, "batch fork event must be created during stream capture; call dfs_plan_batched first");

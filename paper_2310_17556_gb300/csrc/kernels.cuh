@@ -35,6 +35,17 @@ cudaError_t launch_gram_tc(const GramTcPlan& plan, int s_dtype, const void* S, i
 cudaError_t launch_gram_tc_finalize(const GramTcPlan& plan, const void* P, int64_t n, int64_t n_out, double lambda,
                                     void* W, int64_t ldw, cudaStream_t stream, const float* rscale = nullptr);
 
+// ---- first pass + Gram as one kernel (gram_fused.cu) ----
+// FP32 S, BF16 tiles, kq <= 4 right-hand sides, one-wave schedule; returns 0 where it does not apply.
+int gram_fused_plan(int s_dtype, int64_t n, int64_t m, int kq, int num_sms, size_t smem_optin, GramTcPlan* plan);
+size_t gram_fused_ready_bytes(const GramTcPlan& plan);
+// b = S V into Rpart (num_sms rows of n x kq FP64; *parts = num_sms), the BF16 tiles into Sp, the
+// Gram partial blocks into P (read by launch_gram_tc_finalize); `ready` is per-k-block scratch.
+// k = 0 (V unused): the tiles and the Gram only.
+cudaError_t launch_gram_fused(const GramTcPlan& plan, int kq, const void* S, int64_t n, int64_t m, int64_t lds,
+                              const void* V, int64_t ldv, int k, double* Rpart, void* Sp, void* P, int* ready,
+                              DevStatus* st, int num_sms, cudaStream_t stream, int* parts);
+
 // ---- Cholesky (cholesky.cu) ----
 // fp64_panel: factor the 32 x 32 diagonal blocks in FP64 (else in the storage type).
 // flags: cholesky_flag_bytes(n_pad) of device scratch (zeroed by the launcher).

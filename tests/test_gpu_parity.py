@@ -57,6 +57,46 @@ def fp32_tol(S, lam):
     return 1e-5 * max(1.0, cond / 10.0)
 
 
+def sigma_max_sq(S64):
+    """Largest eigenvalue of S S^T (FP64, from the n x n or m x m Gram)."""
+    G = S64 @ S64.T if S64.shape[0] <= S64.shape[1] else S64.T @ S64
+    return float(np.linalg.eigvalsh(G)[-1])
+
+
+def row_space_amplification(S64, V64, lam):
+    """A = sigma_max (sigma_max^2 + lam) / lam * ||v|| / ||S v||, per right-hand side (V64 is (k, m)).
+
+    For any x with ||x - x*|| <= eps ||x*||, e_range <= A eps: ||S d|| <= sigma_max ||d||, S x* = y*
+    with (S S^T + lam I) y* = S v, so ||y*|| >= ||S v|| / (sigma_max^2 + lam), and ||x*|| <= ||v|| / lam.
+    A is large where sigma_max^2 / lam is (Gaussian scores at small lam); there e_rel, diluted by
+    the v / lam part of x*, says little about the row space and e_range is the sharper check."""
+    s_max = math.sqrt(sigma_max_sq(S64))
+    SV = S64 @ V64.T
+    return s_max * (s_max ** 2 + lam) / lam * np.linalg.norm(V64, axis=1) / np.linalg.norm(SV, axis=0)
+
+
+STOP_TOL = 1e-7  # the solver's default stopping tolerance (estimated relative error of x)
+
+
+def range_bar(S64, V64, lam, base=1e-6):
+    """e_range bar of the refined paths: 1e-6, or the row-space error that twice the stopping
+    tolerance allows through the amplification A (whichever is larger)."""
+    return max(base, 2.0 * STOP_TOL * float(row_space_amplification(S64, V64, lam).max()))
+
+
+def assert_mixed(S, V, lam, X, ref=None, e_rel_tol=1e-6, e_range_tol=1e-6):
+    """Mixed paths after refinement: e_rel <= 1e-6, and the error inside the row space of S (where
+    e_rel is diluted by the v / lam part of x*) within range_bar."""
+    S64, V64, X64 = np64(S), np64(V), np64(X)
+    if ref is None:
+        ref = oracle.solve(S64, V64.T, lam).T
+    e = oracle.errors(S64, V64.T, lam, X64.T, ref.T)
+    assert e["e_rel"] <= e_rel_tol, e
+    bar = range_bar(S64, V64, lam, e_range_tol)
+    assert e["e_range"] <= bar, (e, bar)
+    return e
+
+
 def rel_err(x, ref):
     x = np.asarray(x, np.float64)
     ref = np.asarray(ref, np.float64)
@@ -132,8 +172,10 @@ def test_row_blocked_sv_solves(dtype, prec, n, m, k, lam):
     V = wl.rhs(m, k, seed=42 + n, device=dev())
     X, info = dfs.dfs_solve(S, V, lam, precision=prec)
     assert info["status"] == 0 and info["precision"] == prec
-    tol = 1e-6 if prec == "bf16" else fp32_tol(S, lam)
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= tol
+    if prec == "bf16":
+        assert_mixed(S, V, lam, X)
+    else:
+        assert rel_err(np64(X), solve_ref(S, V, lam)) <= fp32_tol(S, lam)
 
 
 def test_padded_leading_dimension_and_in_place():
@@ -161,7 +203,7 @@ def test_tf32_refined_path_matches_oracle(n, m, k, lam):
     X, info = dfs.dfs_solve(S, V, lam, precision="tf32")
     assert info["status"] == 0 and info["precision"] == "tf32"
     assert info["iters"] >= 1
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+    assert_mixed(S, V, lam, X)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32"])
@@ -171,7 +213,10 @@ def test_fp64_diagonal_panel_variant(prec):
     V = wl.rhs(m, 2, seed=90, device=dev())
     X, info = dfs.dfs_solve(S, V, lam, precision=prec, fp64_panel=True)
     assert info["status"] == 0
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= (fp32_tol(S, lam) if prec == "fp32" else 1e-6)
+    if prec == "fp32":
+        assert rel_err(np64(X), solve_ref(S, V, lam)) <= fp32_tol(S, lam)
+    else:
+        assert_mixed(S, V, lam, X)
 
 
 def test_long_rows_gram():
@@ -192,7 +237,7 @@ def test_long_rows_gram():
     V = wl.rhs(m, 1, seed=92, device=dev())
     X, info = dfs.dfs_solve(S, V, lam, precision="tf32")
     assert info["status"] == 0
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+    assert_mixed(S, V, lam, X)
 
 
 def test_tf32_refined_svd_structured():
@@ -202,17 +247,18 @@ def test_tf32_refined_svd_structured():
     for lam in (1e-2, 1e-4):
         X, info = dfs.dfs_solve(S, v, lam, precision="tf32")
         assert info["status"] == 0
-        assert rel_err(np64(X), solve_ref(S, v, lam)) <= 1e-6
+        assert_mixed(S, v, lam, X)
 
 
 def test_refined_path_in_place():
     n, m, lam = 200, 30000, 1e-3
     S = wl.gaussian(n, m, seed=87, device=dev())
     V = wl.rhs(m, 3, seed=88, device=dev())
+    V0 = V.clone()
     ref = solve_ref(S, V, lam)
     X, info = dfs.dfs_solve(S, V, lam, X=V, precision="tf32")
     assert X.data_ptr() == V.data_ptr() and info["status"] == 0
-    assert rel_err(np64(V), ref) <= 1e-6
+    assert_mixed(S, V0, lam, V, ref=ref)
 
 
 def test_bf16_storage_bf16_tensor_path():
@@ -221,7 +267,7 @@ def test_bf16_storage_bf16_tensor_path():
     V = wl.rhs(m, 2, seed=86, device=dev())
     X, info = dfs.dfs_solve(S, V, lam, precision="bf16")
     assert info["status"] == 0 and info["precision"] == "bf16"
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+    assert_mixed(S, V, lam, X)
 
 
 # ---------------------------------------------------------------------------- single steps
@@ -346,6 +392,9 @@ def test_sr_centred_solve_matches_oracle(prec, n, m, k, lam):
     ref = oracle.solve(S64, np64(V).T, lam).T
     tol = 3 * fp32_tol(torch.from_numpy(S64), lam) if prec == "fp32" else 1e-6
     assert rel_err(np64(X), ref) <= tol
+    if prec != "fp32":
+        e = oracle.errors(S64, np64(V).T, lam, np64(X).T, ref.T)
+        assert e["e_range"] <= range_bar(S64, np64(V), lam), e
     # without centring the same call solves the uncentred system: a different answer
     X0, _ = dfs.dfs_solve(O, V, lam, precision=prec, max_iter=20)
     assert rel_err(np64(X0), ref) > 10 * tol
@@ -360,7 +409,7 @@ def test_refinement_final_correction_from_bf16_tiles(lam):
     v = wl.rhs(m, 1, seed=92, device=dev())
     X, info = dfs.dfs_solve(S, v, lam, precision="bf16")
     assert info["status"] == 0 and info["iters"] == 2 and info["passes"] == 1, info
-    assert rel_err(np64(X), solve_ref(S, v, lam)) <= 1e-6
+    assert_mixed(S, v, lam, X)
     # without the tiles' correction (TF32 tiles) the same solve runs two full passes
     X2, info2 = dfs.dfs_solve(S, v, lam, precision="tf32")
     assert info2["passes"] == info2["iters"] >= 1, info2
@@ -374,7 +423,7 @@ def test_nspace_sixteen_cta_cluster():
     V = wl.rhs(m, 1, seed=98, device=dev())
     X, info = dfs.dfs_solve(S, V, lam, precision="bf16")
     assert info["status"] == 0, info
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+    assert_mixed(S, V, lam, X)
 
 
 def test_solve_is_capturable_in_a_cuda_graph():
@@ -421,7 +470,7 @@ def test_host_async_pipeline_matches_oracle():
     torch.cuda.synchronize()
     assert dfs.dfs_sync_info()["status"] == 0
     for Sh, Vh, lam, Xh in probs:
-        assert rel_err(Xh.double().numpy(), solve_ref(Sh, Vh, lam)) <= 1e-6
+        assert_mixed(Sh, Vh, lam, Xh)
 
 
 def _complex_inputs(n, m, k, seed, dtype=torch.float32):
@@ -463,8 +512,9 @@ def test_complex_real_part_fisher_is_the_stacked_real_solve():
     Sr = torch.cat([A, B], dim=0)
     X, info = dfs.dfs_solve(Sr, Vr, 1e-2, precision="bf16")
     assert info["status"] == 0
-    ref = oracle.solve(oracle.real_part_scores(np64(A) + 1j * np64(B)), np64(Vr).T, 1e-2).T
-    assert rel_err(np64(X), ref) <= 1e-6
+    Sr64 = oracle.real_part_scores(np64(A) + 1j * np64(B))
+    ref = oracle.solve(Sr64, np64(Vr).T, 1e-2).T
+    assert_mixed(torch.from_numpy(Sr64), Vr, 1e-2, X, ref=ref)
 
 
 def test_fp8_nonfinite_row_reaches_the_cholesky():
@@ -486,7 +536,7 @@ def test_fp8_refined_path_matches_oracle(dtype, n, m, k, lam):
     V = wl.rhs(m, k, seed=206 + n, device=dev())
     X, info = dfs.dfs_solve(S, V, lam, precision="fp8", max_iter=20)
     assert info["status"] == 0 and info["precision"] == "fp8", info
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+    assert_mixed(S, V, lam, X)
 
 
 @pytest.mark.parametrize("n,m,k,lam", [(1024, 65536, 1, 1e-4), (257, 33336, 3, 1e-3), (100, 5000, 8, 1e-1),
@@ -496,7 +546,7 @@ def test_bf16x3_refined_path_matches_oracle(n, m, k, lam):
     V = wl.rhs(m, k, seed=182 + n, device=dev())
     X, info = dfs.dfs_solve(S, V, lam, precision="bf16x3")
     assert info["status"] == 0 and info["precision"] == "bf16x3", info
-    assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+    assert_mixed(S, V, lam, X)
 
 
 @pytest.mark.parametrize("dtype,n,tol", [(torch.float32, 300, 1e-5), (torch.float64, 200, 1e-12),
@@ -671,8 +721,10 @@ def test_full_size_headline_workload_matches_oracle():
     ef = oracle.errors(S64, v64, lam, np64(Xf)[0], x_ref)
     assert em["e_rel"] <= 1e-6, em
     assert ef["e_rel"] <= 1e-5, ef
-    # the error inside the row space of S, where Algorithm 1's S^T y part lives
-    assert em["e_range"] <= 1e-5, em
+    # the error inside the row space of S, where Algorithm 1's S^T y part lives (sigma_max^2 / lam
+    # is about 10 here, so x's FP32 storage floor, ~3e-6, is not reached)
+    assert em["e_range"] <= 1e-6, em
+    assert ef["e_range"] <= 1e-5, ef
 
 
 # ---------------------------------------------------------------------------- batched
@@ -714,8 +766,10 @@ def test_solve_batched_lanes(prec):
     outs, status = dfs.dfs_solve_batched(probs, precision=prec)
     assert status == [0] * len(probs)
     for (S, V, lam), X in zip(probs, outs):
-        tol = fp32_tol(S, lam) if prec == "fp32" else 1e-6
-        assert rel_err(np64(X), solve_ref(S, V, lam)) <= tol
+        if prec == "fp32":
+            assert rel_err(np64(X), solve_ref(S, V, lam)) <= fp32_tol(S, lam)
+        else:
+            assert_mixed(S, V, lam, X)
 
 
 def test_solve_batched_failure_stays_in_its_problem():
@@ -731,7 +785,7 @@ def test_solve_batched_failure_stays_in_its_problem():
     outs = e.value.outs
     for j, ((S, V, lam), X) in enumerate(zip(probs, outs)):
         if j != bad:
-            assert rel_err(np64(X), solve_ref(S, V, lam)) <= 1e-6
+            assert_mixed(S, V, lam, X)
 
 
 def test_solve_batched_planned_is_capturable():
@@ -760,7 +814,7 @@ def test_solve_batched_planned_is_capturable():
         for X, ref in zip(Xg, outs):
             assert torch.equal(X, ref)
         assert dfs.dfs_batched_status(3, handle=h) == [0, 0, 0]
-    assert rel_err(np64(Xg[1]), solve_ref(*probs[1])) <= 1e-6
+    assert_mixed(probs[1][0], probs[1][1], probs[1][2], Xg[1])
 
 
 # ---------------------------------------------------------------------------- full-size configurations
@@ -832,7 +886,7 @@ def test_full_size_n8192_m2p22_heavy_tailed_bf16():
     n, m, lam = 8192, 1 << 22, 1e-5
     S = wl.heavy_tailed(n, m, seed=231017556 + 5, device=dev(), dtype=torch.bfloat16)
     V = wl.rhs(m, 1, seed=231017556 + 12, device=dev())
-    X, info = dfs.dfs_solve(S, V, lam, precision="bf16", max_iter=12)
+    X, info = dfs.dfs_solve(S, V, lam, precision="bf16", max_iter=12, allow_not_converged=True)
     assert info["status"] in (0, 3), info  # converged, or stopped at the rounding floor
     assert torch.isfinite(X).all()
     res = _residual_fp64(S, X, V, lam)
