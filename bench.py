@@ -49,8 +49,9 @@ def workload_config(lam=LAMBDA):
         "workload": f"SVD-structured FP32 score matrix n={N_SAMPLES} m={M_PARAMS} k=1 lambda={lam:g} "
                     f"(sigma log-spaced 1..{SIGMA_MIN:g})",
         "n": N_SAMPLES, "m": M_PARAMS, "k": 1, "lambda": lam,
-        "mixed_path": "BF16 tcgen05 Gram on packed tiles, FP32 Cholesky, n-space refinement "
-                      "(FP32 passes over S with FP64 accumulation) to est. rel. error <= 1e-7",
+        "mixed_path": "fused first pass (b = S v, BF16 tiles and the tcgen05 Gram in one kernel), "
+                      "Cholesky, n-space refinement (FP32 passes over S with FP64 accumulation) to "
+                      "est. rel. error <= 1e-7",
         "cache": "inputs larger than L2 (S is 4.3 GB; L2 is 129 MB), no flush between steps",
         "launch": "one dfs_solve captured into a CUDA graph, replayed once per step",
         "parallelism": "replicas (one independent solve per GPU)",
@@ -184,6 +185,52 @@ def _oracle_solve(S64, v64, lam):
     t0 = time.perf_counter()
     x = oracle.solve(S64, v64, lam)
     return x, time.perf_counter() - t0
+
+
+def _cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+_CONFIG1_PROBE = (
+    "import sys, time; sys.path.insert(0, %r); import numpy as np; import oracle\n"
+    "from paper_2310_17556_gb300 import workloads as wl\n"
+    "S = wl.gaussian(256, 16384, seed=231017556, dtype=__import__('torch').float64).numpy()\n"
+    "v = wl.rhs(16384, 1, seed=231017557, dtype=__import__('torch').float64).numpy()[0]\n"
+    "oracle.solve(S, v, 1e-3); t0 = time.perf_counter(); [oracle.solve(S, v, 1e-3) for _ in range(5)]\n"
+    "print((time.perf_counter() - t0) / 5)\n")
+
+
+def _oracle_config1_times():
+    """The oracle's time for the small FP64 configuration (n=256, m=16384, k=1, lambda=1e-3) on all
+    host cores and on one core (BLAS threads pinned to 1), each in a fresh interpreter."""
+    out = {}
+    for label, threads in (("all_cores", None), ("one_core", "1")):
+        env = dict(os.environ)
+        if threads:
+            for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+                env[k] = threads
+        try:
+            r = subprocess.run([sys.executable, "-c", _CONFIG1_PROBE % ROOT], capture_output=True, text=True,
+                               timeout=300, env=env)
+            out[label + "_s"] = float(r.stdout.strip().splitlines()[-1])
+        except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+            out[label + "_s"] = None
+    return out
 
 
 def _errors(S64, v64, lam, x, x_ref):
@@ -375,52 +422,82 @@ def run_ours(args):
     e2e_value = _job_rate(ws, ke, e2e_s)
 
     # ---------------- rooflines from the live per-kernel events ----------------
+    # Algorithmic work is the method's own (Algorithm 1 with Q inlined): S and the vectors it reads
+    # and writes, and the n (n + 1) m flops of the symmetric Gram.  Bytes the design adds (the
+    # BF16 tiles it writes and re-reads) are not counted there; they show in `traffic` (ncu) and
+    # in traffic / algorithmic.  A kernel timed inside a milliseconds-long step takes the burst peaks.
     peaks, peak_kind = _peaks()
     hbm = peaks["hbm_gbs"]
-    bf16_sus = peaks["bf16_tflops_sustained"]
+    bf16 = peaks["bf16_tflops"]
     gram_ms, svp_ms, pass_ms, chol_ms = step_ms[0], step_ms[5], step_ms[6], step_ms[7]
-    n_pad = -(-n // 128) * 128
-    m_pad = -(-m // 64) * 64
+    fused = svp_ms == 0.0  # the fused first pass reports no separate S v pass
     pass_bytes = 4.0 * n * m + 8.0 * m            # S, v read; x written (first refinement pass)
-    svp_bytes = 4.0 * n * m + 4.0 * m + 2.0 * n_pad * m_pad  # S, v read; BF16 tiles written
+    sv_bytes = 4.0 * n * m + 4.0 * m              # S, v read (b = S v; the Gram reads S once with it)
     gram_flop = float(n) * (n + 1) * m            # lower triangle incl. diagonal, 2 flop / MAC
     passes = max(1, info["passes"])  # full passes over S; a final correction reads the BF16 tiles
 
-    def hbm_line(name, nbytes, ms, launches_per_step):
+    def hbm_line(name, nbytes, ms, launches_per_step, extra=None):
         ach = nbytes / (ms / 1e3) / 1e9 if ms > 0 else None
-        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm if ach else None, "traffic": _kernel_traffic(name),
-                "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": ms,
-                "launches_per_step": launches_per_step, "ms_per_step": ms * launches_per_step}
+        traffic = _kernel_traffic(name)
+        d = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+             "frac": ach / hbm if ach else None, "traffic": traffic,
+             "traffic_over_algorithmic": traffic / nbytes if traffic else None,
+             "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": ms,
+             "launches_per_step": launches_per_step, "ms_per_step": ms * launches_per_step}
+        if extra:
+            d.update(extra)
+        return d
 
     pass_line = hbm_line("fisher_pass_cluster_kernel", pass_bytes, pass_ms, passes)
-    # the streaming S v + pack kernel runs for FP32 S with at most 1024 (padded) rows
-    svp_name = "sv_ring_kernel" if n_pad <= 1024 else "sv_pack_kernel"
-    svp_line = hbm_line(svp_name, svp_bytes, svp_ms, 1)
+    kernels = [pass_line]
     gram_tf = gram_flop / (gram_ms / 1e3) / 1e12 if gram_ms > 0 else None
-    gram_line = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": gram_tf, "peak": bf16_sus,
-                 "unit": "TFLOP/s", "frac": gram_tf / bf16_sus if gram_tf else None,
-                 "traffic": _kernel_traffic("gram_tc_kernel"), "algorithmic_flop_per_launch": gram_flop,
-                 "avg_launch_ms": gram_ms, "launches_per_step": 1, "ms_per_step": gram_ms}
-    kernels = [pass_line, gram_line, svp_line]
+    if fused:
+        # one kernel streams S (HBM) and runs the Gram (tensor cores): its bound is the larger of
+        # the two times at peak, 4 n m / HBM against n (n + 1) m / BF16
+        t_hbm, t_tc = sv_bytes / (hbm * 1e9), gram_flop / (bf16 * 1e12)
+        kernels.append(hbm_line("gram_fused_kernel", sv_bytes, gram_ms, 1, {
+            "tensor_achieved_tflops": gram_tf, "tensor_peak_tflops": bf16,
+            "tensor_frac": gram_tf / bf16 if gram_tf else None, "algorithmic_flop_per_launch": gram_flop,
+            "bound_ms_at_peak": max(t_hbm, t_tc), "bound_frac": max(t_hbm, t_tc) * 1e3 / gram_ms if gram_ms else None}))
+    else:
+        svp_name = "sv_ring_kernel" if n <= 1024 else "sv_pack_kernel"
+        kernels.append(hbm_line(svp_name, sv_bytes, svp_ms, 1))
+        kernels.append({"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": gram_tf, "peak": bf16,
+                        "unit": "TFLOP/s", "frac": gram_tf / bf16 if gram_tf else None,
+                        "traffic": _kernel_traffic("gram_tc_kernel"), "algorithmic_flop_per_launch": gram_flop,
+                        "avg_launch_ms": gram_ms, "launches_per_step": 1, "ms_per_step": gram_ms})
     corr_ms = step_ms[8]
     if corr_ms > 0:
-        # x -= S_bf16^T dy / lambda: the BF16 tiles read, x read and written
+        # x -= S_bf16^T dy / lambda: the refinement's last correction, reading the BF16 tiles the
+        # design keeps (2 bytes an entry of S) and x read and written
         n_rows = -(-n // 256) * 256
         corr_bytes = 2.0 * n_rows * (-(-m // 64) * 64) + 8.0 * m
         kernels.append(hbm_line("tile_correct_kernel", corr_bytes, corr_ms, 1))
-    roofline = dict(max(kernels, key=lambda d: d["ms_per_step"]))
-    roofline["peak_source"] = f"{peak_kind} MEASURED_PEAKS ({'hbm_gbs' if roofline['bound'] == 'hbm' else 'bf16_tflops_sustained'})"
+    kernels.append({"kernel": "chol_coop_kernel", "bound": "latency", "avg_launch_ms": chol_ms,
+                    "launches_per_step": 1, "ms_per_step": chol_ms,
+                    "note": "31 dependent 32-wide block steps; n^3/3 = %.2e flop" % (n ** 3 / 3.0)})
+    roofline = dict(max((k for k in kernels if k["bound"] != "latency"), key=lambda d: d["ms_per_step"]))
+    roofline["peak_source"] = f"{peak_kind} MEASURED_PEAKS (hbm_gbs; bf16_tflops burst for the tensor side)"
     roofline["launches_averaged"] = nsteps_timed
+    # the whole step against Algorithm 1's own work: S read twice (Gram + b, then x), v read twice,
+    # x written; the Gram's flops
+    step_s = (elapsed_ms / args.steps) / 1e3
+    alg_bytes = 2 * 4.0 * n * m + 12.0 * m
+    step_roofline = {"algorithmic_bytes": alg_bytes, "algorithmic_flop": gram_flop,
+                     "achieved_gbs": alg_bytes / step_s / 1e9, "frac_hbm": alg_bytes / step_s / 1e9 / hbm,
+                     "achieved_tflops": gram_flop / step_s / 1e12, "frac_tensor": gram_flop / step_s / 1e12 / bf16,
+                     "bound_ms_at_peak": alg_bytes / (hbm * 1e9) * 1e3 + 0.0,
+                     "note": "Algorithm 1 reads S twice; the refinement's extra pass and the tile "
+                             "correction are the design's"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16", "data": "synthetic", "config": workload_config(),
-        "step_ms": {"gram": step_ms[0], "finalize_cholesky": step_ms[1], "first_solve": step_ms[2],
-                    "refinement": step_ms[3], "total": step_ms[4], "sv_kernel": step_ms[5],
-                    "first_refinement_pass_kernel": step_ms[6], "cholesky_kernel": step_ms[7],
-                    "tile_correct_kernel": step_ms[8]},
+        "step_ms": {"gram" if not fused else "fused_first_pass": step_ms[0], "finalize_cholesky": step_ms[1],
+                    "first_solve": step_ms[2], "refinement": step_ms[3], "total": step_ms[4],
+                    "sv_kernel": step_ms[5], "first_refinement_pass_kernel": step_ms[6],
+                    "cholesky_kernel": step_ms[7], "tile_correct_kernel": step_ms[8]},
         "fp32_path": {"value": kf / (fp32_ms / 1e3), "unit": UNIT, "steps": kf, "status": info_f["status"]},
         "lambda_1e-2": {"value": k2 / (alt_ms / 1e3), "unit": UNIT, "iters": info_alt["iters"], "steps": k2},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * m + 4 * m,
@@ -431,6 +508,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roofline,
+        "step_roofline": step_roofline,
         "kernels": kernels,
         "mixed_info": {"iters": info["iters"], "full_passes": info["passes"], "est_rel_err": info["rel_correction"],
                        "status": info["status"]},
@@ -448,9 +526,11 @@ def run_ours(args):
         line["accuracy_vs_fp64_oracle"] = acc
         line["accuracy_ok"] = acc["mixed"]["e_rel"] <= 1e-6 and acc["fp32_path"]["e_rel"] <= 1e-5
         line["cpu_baseline"] = {"value": 1.0 / t_ref, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "cpu_model": _cpu_model(),
                                 "sample": f"one full FP64 oracle solve of this workload (n={n}, m={m}, k=1, "
                                           f"lambda={LAMBDA:g}) in {t_ref:.2f} s, numpy with its default "
-                                          f"BLAS threads on {os.cpu_count()} host cores"}
+                                          f"BLAS threads on {os.cpu_count()} host cores",
+                                "small_config_fp64_n256_m16384": _oracle_config1_times()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

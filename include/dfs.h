@@ -113,9 +113,10 @@ typedef struct {
     double rel_correction;  /* estimated relative error left in x (0 if no refinement) */
     double rel_residual_n;  /* last ||r_n|| / ||S v||, r_n = S v - (S S^T + lambda I) y */
     float ms[DFS_STEP_TIMES]; /* with DFS_FLAG_STEP_TIMING (CUDA events on the call's stream):
-                               [0] Gram kernel, [1] Gram finalize + Cholesky, [2] first n-space
-                               solve (S v pass, two triangular solves), [3] the rest (refinement
-                               or the x pass), [4] whole call, [5] S v pass kernel alone, [6] first
+                               [0] Gram kernel (the fused first-pass kernel when it runs),
+                               [1] Gram finalize + Cholesky, [2] first n-space solve (S v pass,
+                               two triangular solves), [3] the rest (refinement or the x pass),
+                               [4] whole call, [5] S v pass kernel alone (0 in the fused form), [6] first
                                pass over S after the solves (refinement or x pass) alone,
                                [7] Cholesky kernel alone, [8] the correction from the packed BF16
                                tiles alone (0 when it did not run); zeros otherwise */
@@ -272,6 +273,25 @@ dfs_status dfs_fisher_pass(dfs_handle handle, const void* S, int s_dtype, int64_
                            int64_t ldy, double lambda, void* X, int64_t ldx, double* R,
                            int64_t ldr, void* stream);
 
+/* ---- test hook: make one bounded device wait run out ---------------------------------- */
+
+/* Every device-side wait of the library (on a flag, a peer CTA or an mbarrier) gives up after a
+ * limit (2 s by default), records DFS_ERR_TIMEOUT in the call's device status, releases what it
+ * holds and returns; the next call on the handle starts afresh.  This hook lets a test exercise
+ * that path without faulting anything: it sets the limit for the following calls on `handle`
+ * (wait_limit_ns <= 0: back to 2 s) and names one signal that a kernel then withholds (the
+ * waits for it run out):
+ *   DFS_TEST_FAULT_CHOLESKY      the Cholesky never publishes tile (2, 1) as finished (n > 64);
+ *   DFS_TEST_FAULT_CLUSTER_PASS  in a refinement pass run as clusters (FP32 S, n <= 4096), rank 1
+ *                                of the first cluster withholds its first strip's partial sums;
+ *   DFS_TEST_FAULT_FUSED_GRAM    the fused first pass (BF16 Gram, FP32 S) withholds one tile.
+ * DFS_TEST_FAULT_NONE (0) switches it off.  Not for production use. */
+#define DFS_TEST_FAULT_NONE 0
+#define DFS_TEST_FAULT_CHOLESKY 1
+#define DFS_TEST_FAULT_CLUSTER_PASS 2
+#define DFS_TEST_FAULT_FUSED_GRAM 3
+dfs_status dfs_set_test_fault(dfs_handle handle, int fault, int64_t wait_limit_ns);
+
 /* ---- no-allocation variant ---------------------------------------------------------- */
 
 /* Size of the fixed device scratch used by dfs_fisher_pass_noalloc (8 MiB per device). */
@@ -306,6 +326,19 @@ dfs_status dfs_fisher_pass_noalloc(const void* S, int s_dtype, int64_t n, int64_
                                    const void* V, int64_t k, int64_t ldv, const double* Y,
                                    int64_t ldy, double lambda, void* X, int64_t ldx, double* R,
                                    int64_t ldr, void* stream, int64_t* scratch_bytes);
+
+/* The device status of the no-allocation calls queued on `stream`, which the call itself cannot
+ * return without waiting for its work: waits for `stream`, then copies the status word of the
+ * current device's fixed scratch into *status_out (host): DFS_OK, or DFS_ERR_TIMEOUT when a
+ * bounded device wait of the pass ran out (X and R are then incomplete).  Allocates nothing.
+ * The word belongs to the last no-allocation call on the device, whatever its stream.
+ * DFS_ERR_INVALID_ARG if status_out is NULL or no no-allocation call has set up the device;
+ * DFS_ERR_CUDA if the copy fails. */
+dfs_status dfs_fisher_pass_noalloc_status(int* status_out, void* stream);
+
+/* The test hook of dfs_set_test_fault for the no-allocation calls on the current device (the
+ * fault DFS_TEST_FAULT_CLUSTER_PASS applies to them). */
+dfs_status dfs_fisher_pass_noalloc_test_fault(int fault, int64_t wait_limit_ns);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,9 @@ from .api import (  # noqa: F401
     dfs_cholesky,
     dfs_fisher_pass,
     dfs_fisher_pass_noalloc,
+    dfs_fisher_pass_noalloc_status,
+    dfs_fisher_pass_noalloc_test_fault,
+    dfs_set_test_fault,
     dfs_gram,
     dfs_kernel_launches,
     dfs_reserve,

@@ -32,6 +32,7 @@ EXPORTS = (
     "dfs_solve", "dfs_solve_host", "dfs_solve_host_async", "dfs_solve_complex", "dfs_sync_info", "dfs_step_times", "dfs_solve_batched",
     "dfs_plan_batched", "dfs_batched_status",
     "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass", "dfs_fisher_pass_noalloc",
+    "dfs_fisher_pass_noalloc_status", "dfs_fisher_pass_noalloc_test_fault", "dfs_set_test_fault",
 )
 
 
@@ -50,6 +51,10 @@ DFS_FLAG_STEP_TIMING = 1
 DFS_FLAG_FP64_PANEL = 2
 DFS_FLAG_CENTER = 4
 DFS_FLAG_TWO_KERNEL_GRAM = 8
+DFS_TEST_FAULT_NONE = 0
+DFS_TEST_FAULT_CHOLESKY = 1
+DFS_TEST_FAULT_CLUSTER_PASS = 2
+DFS_TEST_FAULT_FUSED_GRAM = 3
 DFS_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -90,6 +95,9 @@ _SIGS = {
                                   _VP, _I64, _VP, _I64, _VP]),
     "dfs_fisher_pass_noalloc": (C.c_int, [_VP, C.c_int, _I64, _I64, _I64, _VP, _I64, _I64, _VP, _I64, C.c_double,
                                           _VP, _I64, _VP, _I64, _VP, C.POINTER(_I64)]),
+    "dfs_fisher_pass_noalloc_status": (C.c_int, [C.POINTER(C.c_int), _VP]),
+    "dfs_fisher_pass_noalloc_test_fault": (C.c_int, [C.c_int, _I64]),
+    "dfs_set_test_fault": (C.c_int, [_VP, C.c_int, _I64]),
 }
 
 _lib = None

@@ -397,3 +397,30 @@ def dfs_fisher_pass_noalloc(S: torch.Tensor, V: torch.Tensor, lam: float, Y: tor
                       f"{_lib.DFS_NOALLOC_SCRATCH_BYTES}")
         raise DfsError(st, lib.dfs_status_string(st).decode() + detail)
     return X, R
+
+
+def dfs_fisher_pass_noalloc_status(stream=None) -> int:
+    """Wait for `stream` and return the device status of the last dfs_fisher_pass_noalloc on the
+    current device (0 = DFS_OK, 5 = DFS_ERR_TIMEOUT, ...).  Allocates nothing."""
+    lib = _lib.load()
+    out = C.c_int(-1)
+    st = lib.dfs_fisher_pass_noalloc_status(C.byref(out), _stream(stream))
+    if st != _lib.DFS_OK:
+        raise DfsError(st, lib.dfs_status_string(st).decode())
+    return int(out.value)
+
+
+def dfs_set_test_fault(fault: int, wait_limit_ns: int = 0, handle: Handle | None = None):
+    """Test hook: following calls on the handle withhold the signal `fault` names
+    (DFS_TEST_FAULT_*), so that the bounded device waits for it run out after wait_limit_ns
+    (<= 0: the 2 s default).  DFS_TEST_FAULT_NONE switches it off."""
+    h = handle or default_handle()
+    _check(h.lib, h.h, h.lib.dfs_set_test_fault(h.h, int(fault), int(wait_limit_ns)))
+
+
+def dfs_fisher_pass_noalloc_test_fault(fault: int, wait_limit_ns: int = 0):
+    """The test hook of dfs_set_test_fault for the no-allocation calls on the current device."""
+    lib = _lib.load()
+    st = lib.dfs_fisher_pass_noalloc_test_fault(int(fault), int(wait_limit_ns))
+    if st != _lib.DFS_OK:
+        raise DfsError(st, lib.dfs_status_string(st).decode())

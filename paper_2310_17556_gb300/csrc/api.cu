@@ -40,6 +40,8 @@ struct dfs_handle_s {
     cudaEvent_t fork_ev = nullptr;
     int chol_share = 1;  // the cooperative Cholesky takes 1 / chol_share of the resident-CTA capacity
     bool lane_handle = false;  // a lane of dfs_solve_batched: no whole-GPU fused Gram (lanes run concurrently)
+    int test_fault = 0;                    // dfs_set_test_fault: DFS_TEST_FAULT_* for the next calls
+    unsigned long long test_wait_ns = 0;   // and the limit of their device waits (0: the default)
     // dfs_solve_host_async: two device staging slots for S and V (alternating calls), one for X, a
     // copy stream for the uploads and the events that order slot reuse
     void* abuf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -432,7 +434,7 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
     void* Sp = p.pack ? at<void>(h, p.off_Sp) : nullptr;
     float* rs = p.pack == 4 ? at<float>(h, p.off_Rs) : nullptr;  // FP8 row scales, then their inverses
 
-    DFS_CK(launch_status_reset(h->dstat, stream));
+    DFS_CK(launch_status_reset(h->dstat, stream, h->test_wait_ns, h->test_fault));
     DFS_CK(mark(0));
     DFS_CK(mark(11));  // both re-recorded around the tile correction when it runs, else 0 ms apart
     DFS_CK(mark(12));
@@ -445,8 +447,12 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         // b = S v; the first group's pass also writes the packed tensor-core tiles of S, and in the
         // fused form computes the Gram partials of Algorithm 1 step 1 in the same kernel
         const bool fused_now = q0 == 0 && p.fused;
+        // (step marks: 6/7 around the S v pass, empty in the fused form; 1/2 around the Gram kernel)
         if (q0 == 0) DFS_CK(mark(6));
-        if (fused_now) DFS_CK(mark(1));
+        if (fused_now) {
+            DFS_CK(mark(7));
+            DFS_CK(mark(1));
+        }
         int sv_parts = p.pp.sv_grid;
         if (fused_now)
             DFS_CK(launch_gram_fused(p.tc, kq, S, p.n, m, lds, Vg, ldv, kg, Rpart, Sp, at<void>(h, p.off_P),
@@ -454,8 +460,8 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
         else
             DFS_CK(launch_sv_pack(p.pp, s_dtype, kq, q0 == 0 ? p.pack : 0, S, ni, m, lds, Vg, ldv, kg, Rpart, Sp,
                                   h->dstat, stream, rs ? rs + p.n_pad : nullptr, &sv_parts));
-        if (q0 == 0) DFS_CK(mark(7));
         if (fused_now) DFS_CK(mark(2));
+        else if (q0 == 0) DFS_CK(mark(7));
         if (!p.ns)
             DFS_CK(launch_pass_reduce(p.f64, Rpart, sv_parts, ni, npi, kq, kg, nullptr, kq, lambda, R, kq, Z,
                                       nullptr, nullptr, h->dstat, 0, stream));
@@ -826,6 +832,15 @@ dfs_status dfs_step_times(dfs_handle h, float* mean_ms, int* count) {
     return DFS_OK;
 }
 
+dfs_status dfs_set_test_fault(dfs_handle h, int fault, int64_t wait_limit_ns) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    if (fault < DFS_TEST_FAULT_NONE || fault > DFS_TEST_FAULT_FUSED_GRAM)
+        return fail(h, DFS_ERR_INVALID_ARG, "unknown test fault %d", fault);
+    h->test_fault = fault;
+    h->test_wait_ns = wait_limit_ns > 0 ? (unsigned long long)wait_limit_ns : 0ull;
+    return DFS_OK;
+}
+
 dfs_status dfs_sync_info(dfs_handle h, void* stream, dfs_info* info) {
     if (!h) return DFS_ERR_INVALID_ARG;
     cudaSetDevice(h->device);
@@ -847,7 +862,7 @@ dfs_status dfs_gram(dfs_handle h, const void* S, int s_dtype, int64_t n, int64_t
     Plan p;
     if ((s = make_plan(h, s_dtype, prec, n, m, 1, &p)) != DFS_OK) return s;
     if ((s = ensure_ws(h, p.total, stream)) != DFS_OK) return s;
-    DFS_CK(launch_status_reset(h->dstat, stream));
+    DFS_CK(launch_status_reset(h->dstat, stream, h->test_wait_ns, h->test_fault));
     return run_gram(h, p, S, lds, lambda, W, ldw, n, stream);
 }
 
@@ -869,7 +884,7 @@ dfs_status dfs_cholesky(dfs_handle h, void* W, int w_dtype, int64_t n, int64_t l
     void* Wp = h->ws;
     void* Linv = static_cast<char*>(h->ws) + oI;
     int* flags = reinterpret_cast<int*>(static_cast<char*>(h->ws) + oF);
-    DFS_CK(launch_status_reset(h->dstat, stream));
+    DFS_CK(launch_status_reset(h->dstat, stream, h->test_wait_ns, h->test_fault));
     DFS_CK(launch_pad_copy_in(f64, W, ldw, n, Wp, n_pad, stream));
     DFS_CK(launch_cholesky(f64, Wp, n_pad, n_pad, Linv, flags, h->dstat, stream));
     DFS_CK(launch_copy_lower_out(f64, Wp, n_pad, W, ldw, n, stream));
@@ -901,7 +916,7 @@ dfs_status dfs_trsm(dfs_handle h, const void* L, int l_dtype, int64_t n, int64_t
     void* Lp = static_cast<char*>(h->ws) + oL;
     void* Linv = static_cast<char*>(h->ws) + oI;
     void* Bp = static_cast<char*>(h->ws) + oB;
-    DFS_CK(launch_status_reset(h->dstat, stream));
+    DFS_CK(launch_status_reset(h->dstat, stream, h->test_wait_ns, h->test_fault));
     DFS_CK(launch_pad_copy_in(f64, L, ldl, n, Lp, n_pad, stream));
     DFS_CK(launch_diag_inverse(f64, Lp, n_pad, n_pad, Linv, h->dstat, stream));
     if (trans) DFS_CK(launch_mirror_lower(f64, Lp, n_pad, (int)n_pad, stream));
@@ -945,7 +960,7 @@ dfs_status dfs_fisher_pass(dfs_handle h, const void* S, int s_dtype, int64_t n, 
     double* Rpart = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oR);
     double* U2part = reinterpret_cast<double*>(static_cast<char*>(h->ws) + oU);
     const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
-    DFS_CK(launch_status_reset(h->dstat, stream));
+    DFS_CK(launch_status_reset(h->dstat, stream, h->test_wait_ns, h->test_fault));
     for (int64_t q0 = 0; q0 < k; q0 += kq) {
         const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
         const void* Vg = static_cast<const char*>(V) + q0 * ldv * vs;

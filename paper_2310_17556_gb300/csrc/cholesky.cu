@@ -28,7 +28,6 @@ namespace dfs {
 
 constexpr int NB = 32;
 constexpr int CC_THREADS = 256;
-constexpr uint64_t kCholWaitNs = 2000000000ull;
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
     int v;
@@ -40,13 +39,14 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
 }
 
 // Thread 0 waits (acquire) until *f >= target.  Block-uniform result: false when the device
-// status is or becomes non-zero, or after kCholWaitNs (then DFS_ERR_TIMEOUT is recorded).
+// status is or becomes non-zero, or after the call's wait limit (then DFS_ERR_TIMEOUT is recorded).
 // Contains a __syncthreads().
 __device__ bool block_wait(const int* f, int target, DevStatus* st, int* s_ok, int sleep_ns) {
     if (threadIdx.x == 0) {
         int ok = 1;
         if (ld_acquire_gpu(f) < target) {
             const volatile int* vs = &st->status;
+            const uint64_t limit_ns = wait_limit(st);
             const uint64_t t0 = tc::globaltimer_ns();
             for (;;) {
                 if (ld_acquire_gpu(f) >= target) break;
@@ -54,7 +54,7 @@ __device__ bool block_wait(const int* f, int target, DevStatus* st, int* s_ok, i
                     ok = 0;
                     break;
                 }
-                if (tc::globaltimer_ns() - t0 > kCholWaitNs) {
+                if (tc::globaltimer_ns() - t0 > limit_ns) {
                     set_status(st, DFS_ERR_TIMEOUT);
                     ok = 0;
                     break;
@@ -347,7 +347,10 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
                         *w = __ldcg(w) - acc[a][b];
                     }
                 if (p == j + 1) {  // the tile's last update
-                    block_publish(&done[t]);
+                    if (test_fault(st) == DFS_TEST_FAULT_CHOLESKY && t == tile_id(2, 1))
+                        __syncthreads();  // test hook: this tile's flag is never set, its waiter times out
+                    else
+                        block_publish(&done[t]);
                 } else {
                     __syncthreads();  // sP / sQ are reused by the next tile
                 }

@@ -27,12 +27,24 @@ struct DevStatus {
     int iters;
     int stop;
     int passes;  // full passes over S run by the refinement (a tile correction does not count)
-    int pad[2];
+    int fault;   // test hook: DFS_TEST_FAULT_* of the call (0 normally), set by the status reset
+    int pad;
     double rel_correction;
     double rel_residual;
     double prev_correction;
-    double pad2;
+    unsigned long long wait_ns;  // limit of every bounded device wait of the call (ns)
 };
+
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;  // 2 s
+
+// The limit of the bounded waits of the call that owns `st` (the default if it was never set).
+__device__ __forceinline__ unsigned long long wait_limit(const DevStatus* st) {
+    const unsigned long long w = *reinterpret_cast<const volatile unsigned long long*>(&st->wait_ns);
+    return w ? w : kDefaultWaitNs;
+}
+__device__ __forceinline__ int test_fault(const DevStatus* st) {
+    return *reinterpret_cast<const volatile int*>(&st->fault);
+}
 
 __device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ float to_f32(double x) { return (float)x; }

@@ -218,6 +218,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
     volatile int* abort = &sm->abort;
     volatile int* never = &sm->never;
     volatile int* gram_tau = &sm->gram_tau;
+    const uint64_t wait_ns = wait_limit(st);
     // Each warpgroup's branch first re-divides the registers (every warp of a warpgroup takes the
     // same step).
     if (warp < FU_FIRST_EPI_WARP) {
@@ -245,7 +246,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                     for (int j = 0; j < nk; ++j) {
                         *gram_tau = t * NK + j;
                         const int64_t kb = slot + (int64_t)j * c;
-                        if (!tc::mbar_wait_bounded(&sm->empty[stage], phase ^ 1u, abort, TC_WAIT_NS)) {
+                        if (!tc::mbar_wait_bounded(&sm->empty[stage], phase ^ 1u, abort, wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -262,7 +263,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                             for (int q = 0; q < FU_FLAG_WINDOW; ++q)
                                 if (cnt == q && v[q] >= T) ++cnt;
                             if (cnt == 0) {
-                                if (!wait_count_bounded(ready + kb, T, st, abort, TC_WAIT_NS)) {
+                                if (!wait_count_bounded(ready + kb, T, st, abort, wait_ns)) {
                                     ok = false;
                                     break;
                                 }
@@ -295,7 +296,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                     set_status(st, DFS_ERR_TIMEOUT);
                 }
                 for (int s = 0; s < TC_STAGES; ++s)
-                    if (issued[s] && !tc::mbar_wait_bounded(&sm->full[s], last_parity[s], never, TC_WAIT_NS))
+                    if (issued[s] && !tc::mbar_wait_bounded(&sm->full[s], last_parity[s], never, kDefaultWaitNs))
                         set_status(st, DFS_ERR_TIMEOUT);
             }
         } else if (warp == kMmaWarp) {
@@ -315,14 +316,14 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                     const int slot = sg + t * w;
                     const int nk = slot < nkb ? (nkb - 1 - slot) / c + 1 : 0;
                     if (nk == 0) continue;  // the epilogue writes zeros for an empty task
-                    if (!tc::mbar_wait_bounded(&sm->acce, acc_phase ^ 1u, abort, TC_WAIT_NS)) {
+                    if (!tc::mbar_wait_bounded(&sm->acce, acc_phase ^ 1u, abort, wait_ns)) {
                         ok = false;
                         break;
                     }
                     acc_phase ^= 1u;
                     tc::fence_after_sync();
                     for (int kt = 0; kt < nk; ++kt) {
-                        if (!tc::mbar_wait_bounded(&sm->full[stage], phase, abort, TC_WAIT_NS)) {
+                        if (!tc::mbar_wait_bounded(&sm->full[stage], phase, abort, wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -352,7 +353,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                     set_status(st, DFS_ERR_TIMEOUT);
                 }
                 tc::mma_commit(&sm->done);
-                if (!tc::mbar_wait_bounded(&sm->done, 0, never, TC_WAIT_NS)) set_status(st, DFS_ERR_TIMEOUT);
+                if (!tc::mbar_wait_bounded(&sm->done, 0, never, kDefaultWaitNs)) set_status(st, DFS_ERR_TIMEOUT);
             }
         } else if (warp == FU_SIG_WARP) {
             // ---------------- signaler ----------------
@@ -371,7 +372,9 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                     cur.advance(Q, w, NK);
                     named_bar_sync(FU_BAR_FULL + (li & 1), FU_HANDSHAKE);
                     if (li + 2 < my_items) named_bar_arrive(FU_BAR_EMPTY + (li & 1), FU_HANDSHAKE);
-                    if (lane == 0 && valid) {
+                    // (test hook: CTA 0 withholds its first tile, so the Gram's waits for it run out)
+                    const bool withhold = test_fault(st) == DFS_TEST_FAULT_FUSED_GRAM && blockIdx.x == 0 && li == 0;
+                    if (lane == 0 && valid && !withhold) {
                         // the converters' stores are ordered before the barrier; this thread's
                         // gpu-scope fence makes them visible before the count it adds
                         fence_proxy_async_global();
@@ -406,7 +409,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                                     make_float4(0.f, 0.f, 0.f, 0.f);
                     continue;
                 }
-                bool ok = tc::mbar_wait_bounded(&sm->accf, acc_phase, abort, TC_WAIT_NS);
+                bool ok = tc::mbar_wait_bounded(&sm->accf, acc_phase, abort, wait_ns);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) {
                     if (lane == 0) {
@@ -517,7 +520,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                         while (*gram_tau < tau - lead) {
                             __nanosleep(64);
                             if (*abort || *reinterpret_cast<const volatile int*>(&st->status) ||
-                                tc::globaltimer_ns() - t0 > TC_WAIT_NS) {
+                                tc::globaltimer_ns() - t0 > wait_ns) {
                                 good = 0;
                                 break;
                             }

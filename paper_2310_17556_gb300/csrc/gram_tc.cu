@@ -83,6 +83,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
     const uint32_t tmem = sm->tmem_base;
     volatile int* abort = &sm->abort;
     volatile int* never = &sm->never;
+    const uint64_t wait_ns = wait_limit(st);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -102,7 +103,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
                 // tiles: A0, A1, and for off-diagonal units B0, B1
                 const uint32_t bytes = (uint32_t)TC_TILE_BYTES * (diag ? 2u : 4u);
                 for (int kt = 0; kt < nk; ++kt) {
-                    if (!tc::mbar_wait_bounded(&sm->empty[stage], phase ^ 1u, abort, TC_WAIT_NS)) {
+                    if (!tc::mbar_wait_bounded(&sm->empty[stage], phase ^ 1u, abort, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -142,7 +143,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
             }
             // Every issued copy must have landed before the CTA may exit.
             for (int s = 0; s < TC_STAGES; ++s)
-                if (issued[s] && !tc::mbar_wait_bounded(&sm->full[s], last_parity[s], never, TC_WAIT_NS))
+                if (issued[s] && !tc::mbar_wait_bounded(&sm->full[s], last_parity[s], never, kDefaultWaitNs))
                     set_status(st, DFS_ERR_TIMEOUT);
         }
     } else if (warp == kMmaWarp) {
@@ -161,14 +162,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
                 if (nk == 0) continue;  // the epilogue writes zeros for an empty task
                 const bool diag = tk.J2 == tk.I2;
                 // the accumulators are free once the epilogue has read the previous task's
-                if (!tc::mbar_wait_bounded(&sm->acce, acc_phase ^ 1u, abort, TC_WAIT_NS)) {
+                if (!tc::mbar_wait_bounded(&sm->acce, acc_phase ^ 1u, abort, wait_ns)) {
                     ok = false;
                     break;
                 }
                 acc_phase ^= 1u;
                 tc::fence_after_sync();
                 for (int kt = 0; kt < nk; ++kt) {
-                    if (!tc::mbar_wait_bounded(&sm->full[stage], phase, abort, TC_WAIT_NS)) {
+                    if (!tc::mbar_wait_bounded(&sm->full[stage], phase, abort, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -199,7 +200,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
             }
             // All MMAs issued by this thread must complete before TMEM is freed.
             tc::mma_commit(&sm->done);
-            if (!tc::mbar_wait_bounded(&sm->done, 0, never, TC_WAIT_NS)) set_status(st, DFS_ERR_TIMEOUT);
+            if (!tc::mbar_wait_bounded(&sm->done, 0, never, kDefaultWaitNs)) set_status(st, DFS_ERR_TIMEOUT);
         }
     } else {
         // ---------------- epilogue (the four warps after the MMA warp) ----------------
@@ -222,7 +223,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
                                 make_float4(0.f, 0.f, 0.f, 0.f);
                 continue;
             }
-            bool ok = tc::mbar_wait_bounded(&sm->accf, acc_phase, abort, TC_WAIT_NS);
+            bool ok = tc::mbar_wait_bounded(&sm->accf, acc_phase, abort, wait_ns);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) {

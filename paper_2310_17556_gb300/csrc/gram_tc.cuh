@@ -15,7 +15,6 @@ constexpr int TC_TILE_BYTES = TC_BM * TC_ROW_BYTES;  // one 128-row tile of one 
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;    // A0, A1, B0, B1
 constexpr int TC_PART = 2 * TC_BM * TC_BN;            // floats per partial block
 constexpr uint32_t TC_TMEM_COLS = 512;
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 
 struct TcSmem {
     uint64_t full[TC_STAGES];

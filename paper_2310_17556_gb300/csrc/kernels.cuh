@@ -136,7 +136,9 @@ cudaError_t launch_complex_embed(int s_dtype, const void* A, const void* B, int6
                                  int64_t ldr, cudaStream_t stream);
 
 // ---- refinement control and small utilities (refine.cu, util.cu) ----
-cudaError_t launch_status_reset(DevStatus* st, cudaStream_t stream);
+// wait_ns: limit of the call's bounded device waits (0: the 2 s default); fault: a test hook's
+// DFS_TEST_FAULT_* (0 normally)
+cudaError_t launch_status_reset(DevStatus* st, cudaStream_t stream, unsigned long long wait_ns = 0, int fault = 0);
 cudaError_t launch_group_reset(DevStatus* st, cudaStream_t stream);
 cudaError_t launch_status_save(const DevStatus* st, int* dst, cudaStream_t stream);
 cudaError_t launch_refine_init(int f64, const void* Z, int n_pad, int KQ, double* Y, const double* R,

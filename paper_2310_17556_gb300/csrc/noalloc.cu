@@ -37,6 +37,9 @@ struct DeviceSetup {
 
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[kMaxDevices];
+// test hook (dfs_fisher_pass_noalloc_test_fault), per device
+int g_test_fault[kMaxDevices] = {};
+unsigned long long g_test_wait_ns[kMaxDevices] = {};
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -136,7 +139,7 @@ extern "C" dfs_status dfs_fisher_pass_noalloc(const void* S, int s_dtype, int64_
     const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
     // The status word must start at zero (the pass kernels skip their work on a non-zero
     // status); the partials need no clearing: every CTA writes all of its own.
-    if (launch_status_reset(st, stream) != cudaSuccess) return DFS_ERR_CUDA;
+    if (launch_status_reset(st, stream, g_test_wait_ns[dev], g_test_fault[dev]) != cudaSuccess) return DFS_ERR_CUDA;
     for (int64_t q0 = 0; q0 < k; q0 += kq) {
         const int kg = (int)((k - q0) < kq ? (k - q0) : kq);
         const void* Vg = static_cast<const char*>(V) + q0 * ldv * vs;
@@ -149,5 +152,42 @@ extern "C" dfs_status dfs_fisher_pass_noalloc(const void* S, int s_dtype, int64_
                                     nullptr, nullptr, st, 0, stream) != cudaSuccess)
             return DFS_ERR_CUDA;
     }
+    return DFS_OK;
+}
+
+extern "C" dfs_status dfs_fisher_pass_noalloc_status(int* status_out, void* stream_) {
+    if (!status_out) return DFS_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return DFS_ERR_CUDA;
+    }
+    unsigned char* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (g_setup[dev].ready) scratch = g_setup[dev].scratch;
+    }
+    if (!scratch) return DFS_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int v = 0;
+    // the status word is the first member of the DevStatus at the start of the scratch
+    if (cudaMemcpyAsync(&v, scratch, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DFS_ERR_CUDA;
+    }
+    *status_out = v;
+    return DFS_OK;
+}
+
+extern "C" dfs_status dfs_fisher_pass_noalloc_test_fault(int fault, int64_t wait_limit_ns) {
+    if (fault < DFS_TEST_FAULT_NONE || fault > DFS_TEST_FAULT_FUSED_GRAM) return DFS_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return DFS_ERR_CUDA;
+    }
+    g_test_fault[dev] = fault;
+    g_test_wait_ns[dev] = wait_limit_ns > 0 ? (unsigned long long)wait_limit_ns : 0ull;
     return DFS_OK;
 }

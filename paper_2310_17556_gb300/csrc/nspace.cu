@@ -34,7 +34,6 @@ constexpr int NS_B = 32;           // Cholesky block (Linv granularity)
 constexpr int NS_MAX_CS = 8;
 constexpr int NS_MAX_SLOTS = 8;
 constexpr int NS_RED_GROUPS = NS_THREADS / NS_SB;  // part groups of the reduction (KQ = 1)
-constexpr uint64_t kNsWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t ns_rank() {
     uint32_t r;
@@ -55,8 +54,8 @@ __device__ __forceinline__ uint32_t ns_mapa(const void* p, uint32_t rank) {
     return r;
 }
 // Bounded wait for phase `parity` of a local mbarrier: spins on try_wait, and only every 1024
-// polls looks at the abort flag and the clock (2 s limit).
-__device__ __forceinline__ bool ns_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// polls looks at the abort flag and the clock (the call's wait limit).
+__device__ __forceinline__ bool ns_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t limit_ns) {
     uint64_t t0 = 0;
     for (uint32_t spins = 1;; ++spins) {
         if (tc::mbar_try_wait(bar, parity)) return true;
@@ -64,7 +63,7 @@ __device__ __forceinline__ bool ns_wait(uint64_t* bar, uint32_t parity, volatile
             if (*abort) return false;
             const uint64_t t = tc::globaltimer_ns();
             if (t0 == 0) t0 = t;
-            else if (t - t0 > kNsWaitNs) return false;
+            else if (t - t0 > limit_ns) return false;
         }
     }
 }
@@ -298,7 +297,7 @@ nspace_kernel(const T* __restrict__ W, int64_t ld, int n_pad, const T* __restric
     // y_sb has landed (the GEMV threads, which read it, wait on the mbarrier themselves)
     auto wait_y = [&](uint64_t* bar) {
         if (gthread && !s_abort) {
-            if (!ns_wait(bar, 0, &s_abort)) {
+            if (!ns_wait(bar, 0, &s_abort, wait_limit(st))) {
                 s_abort = 1;
                 set_status(st, DFS_ERR_TIMEOUT);
             }
@@ -421,7 +420,7 @@ nspace_kernel(const T* __restrict__ W, int64_t ld, int n_pad, const T* __restric
         for (int sb = 0; sb < nsb; ++sb)
             if (sb % (int)cs != (int)rank)
                 for (int d = 0; d < 2; ++d)
-                    if ((d == 0 ? fwd : bwd) && !tc::mbar_wait_bounded(&bars[d * nsb + sb], 0, &s_abort, kNsWaitNs))
+                    if ((d == 0 ? fwd : bwd) && !tc::mbar_wait_bounded(&bars[d * nsb + sb], 0, &s_abort, kDefaultWaitNs))
                         set_status(st, DFS_ERR_TIMEOUT);
     __syncthreads();
     // outputs of the owned rows

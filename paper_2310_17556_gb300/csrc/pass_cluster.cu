@@ -25,7 +25,6 @@
 namespace dfs {
 
 constexpr int CL_THREADS = 512;
-constexpr uint64_t kClWaitNs = 2000000000ull;
 constexpr int CL_WARPS = CL_THREADS / 32;
 constexpr int CL_LPR = 16;               // lanes per row
 constexpr int CL_W = CL_LPR * 4;         // strip width (FP32 columns)
@@ -213,14 +212,17 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
                 for (int w = 0; w < CL_WARPS; ++w) p += ured[(w * CL_W + uc) * KQ + uq];
                 float* slot = pbuf + ((size_t)(par * CL_MAX_CS + rank) * CL_W + uc) * KQ + uq;
                 *slot = p;
+                // (test hook: rank 1 of the first cluster withholds its first strip's partials, so
+                // the other ranks' bounded waits for them run out)
+                const bool withhold = test_fault(st) == DFS_TEST_FAULT_CLUSTER_PASS && cid == 0 && rank == 1 && s == cid;
                 for (uint32_t r = 0; r < cs; ++r)
-                    if (r != rank) st_async_f32(slot, &xbar[par], r, p);
+                    if (r != rank && !withhold) st_async_f32(slot, &xbar[par], r, p);
             }
             __syncthreads();
         }
         // ---- U = V - S^T Y (ranks summed in order), X = U / lambda ----
         if (exch && u_thread) {
-            if (!tc::mbar_wait_bounded(&xbar[par], (xphase >> par) & 1u, &s_abort, kClWaitNs)) {
+            if (!tc::mbar_wait_bounded(&xbar[par], (xphase >> par) & 1u, &s_abort, wait_limit(st))) {
                 s_abort = 1;
                 set_status(const_cast<DevStatus*>(st), DFS_ERR_TIMEOUT);
             }

@@ -16,7 +16,7 @@
 
 namespace dfs {
 
-__global__ void status_reset_kernel(DevStatus* st) {
+__global__ void status_reset_kernel(DevStatus* st, unsigned long long wait_ns, int fault) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         st->status = 0;
         st->failed_pivot = -1;
@@ -27,7 +27,9 @@ __global__ void status_reset_kernel(DevStatus* st) {
         st->rel_correction = 0.0;
         st->rel_residual = 0.0;
         st->prev_correction = 0.0;
-        st->pad2 = 0.0;
+        st->wait_ns = wait_ns;
+        st->fault = fault;
+        st->pad = 0;
     }
 }
 
@@ -151,9 +153,9 @@ refine_update_kernel(const T* __restrict__ Z, const double* __restrict__ R, int 
     }
 }
 
-cudaError_t launch_status_reset(DevStatus* st, cudaStream_t stream) {
+cudaError_t launch_status_reset(DevStatus* st, cudaStream_t stream, unsigned long long wait_ns, int fault) {
     {
-        status_reset_kernel<<<1, 32, 0, stream>>>(st);
+        status_reset_kernel<<<1, 32, 0, stream>>>(st, wait_ns ? wait_ns : kDefaultWaitNs, fault);
         count_launch();
     }
     return cudaGetLastError();

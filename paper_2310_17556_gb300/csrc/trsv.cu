@@ -31,7 +31,6 @@ constexpr int TS_CONS_WARPS = 8;        // consumer warps
 constexpr int TS_THREADS = (TS_CONS_WARPS + 1) * 32;
 constexpr int TS_STAGES = 8;
 constexpr int TS_STAGE_BYTES = 16384;   // 32 rows x 512 bytes
-constexpr uint64_t kTrsvWaitNs = 2000000000ull;
 
 // Items of the stream: for row block i (in solve order), chunks of up to CW columns of the row
 // segment, then Linv_i.  Returned through (ncols of this chunk, c0), or ncols == 0 for Linv.
@@ -102,7 +101,7 @@ trsv_stream_kernel(const __grid_constant__ CUtensorMap tmap, int n_pad, const T*
             for (int c = 0; c <= nch; ++c, ++it) {
                 const int s = (int)(it % nst);
                 const uint32_t ph = (it / nst) & 1u;
-                if (it >= (uint32_t)nst && !tc::mbar_wait_bounded(&empty[s], ph ^ 1u, &s_abort, kTrsvWaitNs)) {
+                if (it >= (uint32_t)nst && !tc::mbar_wait_bounded(&empty[s], ph ^ 1u, &s_abort, wait_limit(st))) {
                     s_abort = 1;
                     set_status(st, DFS_ERR_TIMEOUT);
                     return;
@@ -137,7 +136,7 @@ trsv_stream_kernel(const __grid_constant__ CUtensorMap tmap, int n_pad, const T*
         for (int c = 0; c <= nch; ++c, ++it) {
             const int s = (int)(it % nst);
             const uint32_t ph = (it / nst) & 1u;
-            if (!tc::mbar_wait_bounded(&full[s], ph, &s_abort, kTrsvWaitNs)) {
+            if (!tc::mbar_wait_bounded(&full[s], ph, &s_abort, wait_limit(st))) {
                 if (lane == 0) {
                     s_abort = 1;
                     set_status(st, DFS_ERR_TIMEOUT);

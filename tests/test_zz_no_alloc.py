@@ -1,15 +1,19 @@
-"""dfs_fisher_pass_noalloc (fixed device scratch, no allocation) against dfs_fisher_pass.
+"""dfs_fisher_pass_noalloc (fixed device scratch, no allocation) against the FP64 oracle and
+against dfs_fisher_pass, and its device status.
 
 Collected last on purpose: the no-allocation entry point must give the handle-based pass's
 results both in a fresh process and after every other test has run on the device.
 """
 
+import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2310_17556_gb300 as dfs
 from paper_2310_17556_gb300 import workloads as wl
-from paper_2310_17556_gb300._lib import DFS_ERR_NO_MEMORY, DFS_NOALLOC_SCRATCH_BYTES
+from paper_2310_17556_gb300._lib import (DFS_ERR_NO_MEMORY, DFS_ERR_TIMEOUT, DFS_NOALLOC_SCRATCH_BYTES, DFS_OK,
+                                         DFS_TEST_FAULT_CLUSTER_PASS, DFS_TEST_FAULT_NONE)
 
 pytestmark = pytest.mark.gpu
 
@@ -85,3 +89,89 @@ def test_noalloc_rejects_oversize_partials():
     dfs.dfs_fisher_pass_noalloc(S, V, 1.0, X=X)
     torch.cuda.synchronize()
     assert torch.equal(X, V)
+
+
+def _np64(t):
+    return t.detach().to("cpu").to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("n,m,k,dtype", [(1024, 100_004, 1, torch.float32), (300, 40_000, 3, torch.float32),
+                                         (257, 20_000, 2, torch.float64)])
+def test_noalloc_matches_the_oracle(n, m, k, dtype):
+    """X = (V - S^T Y) / lambda and R = S (V - S^T Y) - lambda Y (Appendix A's n-space residual)
+    against the oracle's FP64 restatement, on the stored values."""
+    S, V, Y = _inputs(n, m, k, dtype, 4300 + n, True)
+    lam = 1e-2
+    X = torch.empty_like(V)
+    R = torch.empty((n, k), device=DEV, dtype=torch.float64)
+    dfs.dfs_fisher_pass_noalloc(S, V, lam, Y=Y, X=X, R=R)
+    assert dfs.dfs_fisher_pass_noalloc_status() == DFS_OK
+    S64, V64, Y64 = _np64(S), _np64(V), _np64(Y)
+    X_ref = (V64.T - S64.T @ Y64).T / lam
+    R_ref = oracle.residual_n_space(S64, V64.T, Y64, lam)
+    tol = 1e-12 if dtype == torch.float64 else 1e-6
+    assert np.abs(_np64(X) - X_ref).max() <= tol * np.abs(X_ref).max()
+    assert np.abs(_np64(R) - R_ref).max() <= 10 * tol * np.abs(R_ref).max()
+
+
+def test_noalloc_two_kernel_form():
+    """n > 2048 with X given and a 4096-column chunk for every SM: the pass runs as its two
+    row-shared kernels (x, then R from x), whose partials are laid out differently.  Against
+    dfs_fisher_pass, and against FP64 sums (torch, column chunks) of the same formulas."""
+    n, m, k, lam = 2056, 622_592, 1, 1e-2
+    S, V, Y = _inputs(n, m, k, torch.bfloat16, 4400, True)
+    X_ref, R_ref = dfs.dfs_fisher_pass(S, V, lam, Y=Y)
+    X = torch.empty_like(V)
+    R = torch.empty((n, k), device=DEV, dtype=torch.float64)
+    for _ in range(2):
+        X.fill_(float("nan"))
+        R.fill_(float("nan"))
+        dfs.dfs_fisher_pass_noalloc(S, V, lam, Y=Y, X=X, R=R)
+        assert dfs.dfs_fisher_pass_noalloc_status() == DFS_OK
+        _close(X, X_ref, 1e-6)
+        _close(R, R_ref, 1e-6)
+    U = torch.empty((k, m), device=DEV, dtype=torch.float64)
+    R64 = -lam * Y.clone()
+    for c0 in range(0, m, 1 << 17):
+        Sc = S[:, c0:c0 + (1 << 17)].double()
+        U[:, c0:c0 + (1 << 17)] = V[:, c0:c0 + (1 << 17)].double() - (Sc.T @ Y).T
+        R64 += Sc @ U[:, c0:c0 + (1 << 17)].T
+    _close(X, U / lam, 1e-6)
+    _close(R, R64, 1e-5)
+
+
+def test_noalloc_allocates_no_device_memory():
+    S, V, Y = _inputs(1024, 200_000, 1, torch.float32, 4500, True)
+    X = torch.empty_like(V)
+    R = torch.empty((1024, 1), device=DEV, dtype=torch.float64)
+    dfs.dfs_fisher_pass_noalloc(S, V, 1e-2, Y=Y, X=X, R=R)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        dfs.dfs_fisher_pass_noalloc(S, V, 1e-2, Y=Y, X=X, R=R)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert dfs.dfs_fisher_pass_noalloc_status() == DFS_OK
+
+
+def test_noalloc_status_reports_a_wait_that_ran_out():
+    """The call cannot return the device's verdict without waiting for its work: the status
+    companion reads it from the fixed scratch.  With rank 1 of the first cluster withholding its
+    partial sums (test hook, 5 ms wait limit) the other ranks' waits run out: DFS_ERR_TIMEOUT.
+    The next call, hook off, is whole again."""
+    n, m, lam = 1024, 100_000, 1e-2
+    S, V, Y = _inputs(n, m, 1, torch.float32, 4600, True)
+    X = torch.empty_like(V)
+    R = torch.empty((n, 1), device=DEV, dtype=torch.float64)
+    try:
+        dfs.dfs_fisher_pass_noalloc_test_fault(DFS_TEST_FAULT_CLUSTER_PASS, 5_000_000)
+        dfs.dfs_fisher_pass_noalloc(S, V, lam, Y=Y, X=X, R=R)
+        assert dfs.dfs_fisher_pass_noalloc_status() == DFS_ERR_TIMEOUT
+    finally:
+        dfs.dfs_fisher_pass_noalloc_test_fault(DFS_TEST_FAULT_NONE, 0)
+    dfs.dfs_fisher_pass_noalloc(S, V, lam, Y=Y, X=X, R=R)
+    assert dfs.dfs_fisher_pass_noalloc_status() == DFS_OK
+    X_ref, R_ref = dfs.dfs_fisher_pass(S, V, lam, Y=Y)
+    _close(X, X_ref, 1e-6)
+    _close(R, R_ref, 1e-6)
