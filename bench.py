@@ -430,7 +430,8 @@ def run_ours(args):
     hbm = peaks["hbm_gbs"]
     bf16 = peaks["bf16_tflops"]
     gram_ms, svp_ms, pass_ms, chol_ms = step_ms[0], step_ms[5], step_ms[6], step_ms[7]
-    fused = svp_ms == 0.0  # the fused first pass reports no separate S v pass
+    # the fused first pass has no separate S v pass: its two marks are adjacent (a few us apart)
+    fused = svp_ms < 0.05 * gram_ms
     pass_bytes = 4.0 * n * m + 8.0 * m            # S, v read; x written (first refinement pass)
     sv_bytes = 4.0 * n * m + 4.0 * m              # S, v read (b = S v; the Gram reads S once with it)
     gram_flop = float(n) * (n + 1) * m            # lower triangle incl. diagonal, 2 flop / MAC

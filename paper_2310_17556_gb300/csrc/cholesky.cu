@@ -258,6 +258,7 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
     __shared__ int s_ok, s_fail;
     if (block_should_exit(st, 0)) return;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int fault = test_fault(st);  // the test hook, read once
     const int ntiles = nb * (nb + 1) / 2;
     int* diag = flags;
     int* done = flags + nb;
@@ -347,7 +348,7 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
                         *w = __ldcg(w) - acc[a][b];
                     }
                 if (p == j + 1) {  // the tile's last update
-                    if (test_fault(st) == DFS_TEST_FAULT_CHOLESKY && t == tile_id(2, 1))
+                    if (fault == DFS_TEST_FAULT_CHOLESKY && t == tile_id(2, 1))
                         __syncthreads();  // test hook: this tile's flag is never set, its waiter times out
                     else
                         block_publish(&done[t]);

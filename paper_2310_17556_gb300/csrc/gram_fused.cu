@@ -219,6 +219,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
     volatile int* never = &sm->never;
     volatile int* gram_tau = &sm->gram_tau;
     const uint64_t wait_ns = wait_limit(st);
+    const int fault = test_fault(st);
     // Each warpgroup's branch first re-divides the registers (every warp of a warpgroup takes the
     // same step).
     if (warp < FU_FIRST_EPI_WARP) {
@@ -373,7 +374,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                     named_bar_sync(FU_BAR_FULL + (li & 1), FU_HANDSHAKE);
                     if (li + 2 < my_items) named_bar_arrive(FU_BAR_EMPTY + (li & 1), FU_HANDSHAKE);
                     // (test hook: CTA 0 withholds its first tile, so the Gram's waits for it run out)
-                    const bool withhold = test_fault(st) == DFS_TEST_FAULT_FUSED_GRAM && blockIdx.x == 0 && li == 0;
+                    const bool withhold = fault == DFS_TEST_FAULT_FUSED_GRAM && blockIdx.x == 0 && li == 0;
                     if (lane == 0 && valid && !withhold) {
                         // the converters' stores are ordered before the barrier; this thread's
                         // gpu-scope fence makes them visible before the count it adds

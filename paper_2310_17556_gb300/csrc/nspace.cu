@@ -139,6 +139,7 @@ nspace_kernel(const T* __restrict__ W, int64_t ld, int n_pad, const T* __restric
     __shared__ double red[NS_RED_GROUPS][NS_SB];
 
     if (block_should_exit(st, honor_stop)) return;  // cluster-uniform: earlier launches write it
+    const uint64_t wait_ns = wait_limit(st);  // the call's wait limit, read once
     const uint32_t cs = ns_size(), rank = ns_rank();
     const int nown = (nsb - (int)rank + (int)cs - 1) / (int)cs;  // owned super-blocks
     const int nown_max = (nsb + (int)cs - 1) / (int)cs;          // same offset in every rank
@@ -297,7 +298,7 @@ nspace_kernel(const T* __restrict__ W, int64_t ld, int n_pad, const T* __restric
     // y_sb has landed (the GEMV threads, which read it, wait on the mbarrier themselves)
     auto wait_y = [&](uint64_t* bar) {
         if (gthread && !s_abort) {
-            if (!ns_wait(bar, 0, &s_abort, wait_limit(st))) {
+            if (!ns_wait(bar, 0, &s_abort, wait_ns)) {
                 s_abort = 1;
                 set_status(st, DFS_ERR_TIMEOUT);
             }

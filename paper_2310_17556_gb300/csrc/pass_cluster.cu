@@ -92,6 +92,9 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
     // every CTA of the launch reads the same status (only earlier launches on this stream
     // write it), so the early exit is cluster-uniform
     if (block_should_exit(st, honor_stop)) return;
+    // the call's wait limit and test hook, read once (not in the strip loop)
+    const uint64_t wait_ns = wait_limit(st);
+    const int fault = test_fault(st);
     const uint32_t cs = cl_size(), rank = cl_rank();
     const int64_t cid = blockIdx.x / cs, ncl = gridDim.x / cs;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -214,7 +217,7 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
                 *slot = p;
                 // (test hook: rank 1 of the first cluster withholds its first strip's partials, so
                 // the other ranks' bounded waits for them run out)
-                const bool withhold = test_fault(st) == DFS_TEST_FAULT_CLUSTER_PASS && cid == 0 && rank == 1 && s == cid;
+                const bool withhold = fault == DFS_TEST_FAULT_CLUSTER_PASS && cid == 0 && rank == 1 && s == cid;
                 for (uint32_t r = 0; r < cs; ++r)
                     if (r != rank && !withhold) st_async_f32(slot, &xbar[par], r, p);
             }
@@ -222,7 +225,7 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         }
         // ---- U = V - S^T Y (ranks summed in order), X = U / lambda ----
         if (exch && u_thread) {
-            if (!tc::mbar_wait_bounded(&xbar[par], (xphase >> par) & 1u, &s_abort, wait_limit(st))) {
+            if (!tc::mbar_wait_bounded(&xbar[par], (xphase >> par) & 1u, &s_abort, wait_ns)) {
                 s_abort = 1;
                 set_status(const_cast<DevStatus*>(st), DFS_ERR_TIMEOUT);
             }

@@ -71,6 +71,7 @@ trsv_stream_kernel(const __grid_constant__ CUtensorMap tmap, int n_pad, const T*
     __shared__ __align__(8) uint64_t full[TS_STAGES], empty[TS_STAGES];
     __shared__ int s_abort;
     if (block_should_exit(st, honor_stop)) return;
+    const uint64_t wait_ns = wait_limit(st);  // the call's wait limit, read once
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Seq seq{n_pad, dir};
     const int nblk = n_pad / TB;
@@ -101,7 +102,7 @@ trsv_stream_kernel(const __grid_constant__ CUtensorMap tmap, int n_pad, const T*
             for (int c = 0; c <= nch; ++c, ++it) {
                 const int s = (int)(it % nst);
                 const uint32_t ph = (it / nst) & 1u;
-                if (it >= (uint32_t)nst && !tc::mbar_wait_bounded(&empty[s], ph ^ 1u, &s_abort, wait_limit(st))) {
+                if (it >= (uint32_t)nst && !tc::mbar_wait_bounded(&empty[s], ph ^ 1u, &s_abort, wait_ns)) {
                     s_abort = 1;
                     set_status(st, DFS_ERR_TIMEOUT);
                     return;
@@ -136,7 +137,7 @@ trsv_stream_kernel(const __grid_constant__ CUtensorMap tmap, int n_pad, const T*
         for (int c = 0; c <= nch; ++c, ++it) {
             const int s = (int)(it % nst);
             const uint32_t ph = (it / nst) & 1u;
-            if (!tc::mbar_wait_bounded(&full[s], ph, &s_abort, wait_limit(st))) {
+            if (!tc::mbar_wait_bounded(&full[s], ph, &s_abort, wait_ns)) {
                 if (lane == 0) {
                     s_abort = 1;
                     set_status(st, DFS_ERR_TIMEOUT);
