@@ -133,6 +133,49 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def _live_peaks(torch, dfs):
+    """Peaks MEASURED_PEAKS.json does not carry, measured here: the SIMT fused multiply-add rates
+    (this library's own probe kernels) and cuBLAS TF32 and FP8 GEMM rates (8192^3, best of 3),
+    in TFLOP/s.  None where a probe is not available."""
+    out = {}
+    for kind in ("ffma32", "dfma64"):
+        try:
+            out[kind + "_tflops"] = dfs.dfs_measure_peak(kind) / 1e12
+        except Exception:  # noqa: BLE001 - a probe that cannot run reports nothing
+            out[kind + "_tflops"] = None
+    N = 8192
+
+    def best(fn, flop):
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return flop / (min(t) / 1e3) / 1e12
+
+    try:
+        a = torch.randn((N, N), device="cuda", dtype=torch.float32)
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        out["tf32_tflops_cublas"] = best(lambda: a @ a, 2.0 * N ** 3)
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        a8 = a.to(torch.float8_e4m3fn)
+        one = torch.ones((), device="cuda", dtype=torch.float32)
+        out["fp8_tflops_cublas"] = best(lambda: torch._scaled_mm(a8, a8.t(), scale_a=one, scale_b=one,
+                                                                  out_dtype=torch.bfloat16), 2.0 * N ** 3)
+        del a, a8
+        torch.cuda.empty_cache()
+    except Exception:  # noqa: BLE001
+        out.setdefault("tf32_tflops_cublas", None)
+        out.setdefault("fp8_tflops_cublas", None)
+    return out
+
+
 def _kernel_traffic(kernel: str):
     """DRAM bytes per full-size launch from the committed ncu summary, or None when the kernel's
     sources changed since the counters were taken."""
@@ -382,8 +425,10 @@ def run_ours(args):
     Xf = torch.empty_like(v)
     solve(prec="fp32", out=Xf)
     kf = max(3, args.steps // 10)
-    fp32_ms = _timed(torch, stream, lambda: solve(prec="fp32", out=Xf), kf)
+    dfs.dfs_step_times()
+    fp32_ms = _timed(torch, stream, lambda: solve(prec="fp32", out=Xf, timing=True), kf)
     info_f = dfs.dfs_sync_info()
+    fp32_steps, _ = dfs.dfs_step_times()
 
     # ---------------- end to end through the host-memory entry point ----------------
     S_h = torch.empty(S.shape, dtype=S.dtype, pin_memory=True)
@@ -420,6 +465,8 @@ def run_ours(args):
         raise RuntimeError(f"host-path solve failed: {info_e2e}")
     e2e_s = _max_over_ranks(e2e_s, dist, dev)
     e2e_value = _job_rate(ws, ke, e2e_s)
+
+    peaks_live = _live_peaks(torch, dfs)
 
     # ---------------- rooflines from the live per-kernel events ----------------
     # Algorithmic work is the method's own (Algorithm 1 with Q inlined): S and the vectors it reads
@@ -478,6 +525,13 @@ def run_ours(args):
                     "launches_per_step": 1, "ms_per_step": chol_ms,
                     "note": "31 dependent 32-wide block steps; n^3/3 = %.2e flop" % (n ** 3 / 3.0)})
     roofline = dict(max((k for k in kernels if k["bound"] != "latency"), key=lambda d: d["ms_per_step"]))
+    # the plain FP32 path's Gram (SIMT, FP32 fused multiply-adds) against the measured FFMA rate
+    ffma = peaks_live.get("ffma32_tflops")
+    fp32_gram_tf = gram_flop / (fp32_steps[0] / 1e3) / 1e12 if fp32_steps[0] > 0 else None
+    fp32_gram_line = {"kernel": "gram_simt_kernel (plain FP32 path)", "bound": "ffma", "achieved": fp32_gram_tf,
+                      "peak": ffma, "unit": "TFLOP/s",
+                      "frac": fp32_gram_tf / ffma if (fp32_gram_tf and ffma) else None,
+                      "avg_launch_ms": fp32_steps[0], "peak_source": "live dfs_measure_peak(ffma32)"}
     roofline["peak_source"] = f"{peak_kind} MEASURED_PEAKS (hbm_gbs; bf16_tflops burst for the tensor side)"
     roofline["launches_averaged"] = nsteps_timed
     # the whole step against Algorithm 1's own work: S read twice (Gram + b, then x), v read twice,
@@ -499,7 +553,10 @@ def run_ours(args):
                     "first_solve": step_ms[2], "refinement": step_ms[3], "total": step_ms[4],
                     "sv_kernel": step_ms[5], "first_refinement_pass_kernel": step_ms[6],
                     "cholesky_kernel": step_ms[7], "tile_correct_kernel": step_ms[8]},
-        "fp32_path": {"value": kf / (fp32_ms / 1e3), "unit": UNIT, "steps": kf, "status": info_f["status"]},
+        "fp32_path": {"value": kf / (fp32_ms / 1e3), "unit": UNIT, "steps": kf, "status": info_f["status"],
+                      "gram_roofline": fp32_gram_line,
+                      "mixed_over_fp32": (args.steps / (elapsed_ms / 1e3)) / (kf / (fp32_ms / 1e3))},
+        "peaks_live": peaks_live,
         "lambda_1e-2": {"value": k2 / (alt_ms / 1e3), "unit": UNIT, "iters": info_alt["iters"], "steps": k2},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * m + 4 * m,
                 "d2h_bytes_per_step": 4 * m, "steps": ke,

@@ -82,8 +82,10 @@ typedef enum {
 #define DFS_FLAG_STEP_TIMING 1  /* record CUDA events around the steps; dfs_info.ms is filled */
 #define DFS_FLAG_FP64_PANEL 2   /* factor the 32 x 32 diagonal blocks of the Cholesky in FP64
                                    (FP32 and mixed paths; the FP64 path always does).  Off by
-                                   default: GB300's FP64 rate makes each block ~4x slower, and
-                                   the trailing updates are FP32 in any case */
+                                   default: GB300's FP64 rate (about 1/64 of FP32) makes the
+                                   factorisation ~4.6x slower at n = 1024 (1.42 ms against
+                                   0.31 ms), each block is stored back in FP32, and the
+                                   trailing updates are FP32 in any case */
 #define DFS_FLAG_CENTER 4       /* stochastic reconfiguration (Section 4): the S argument holds O, the
                                    log-derivatives of the wave function, and the system solved is
                                    Eq. 1 with S = (O - O_bar) / sqrt(n), O_bar the mean of O over the
@@ -250,8 +252,9 @@ dfs_status dfs_gram(dfs_handle handle, const void* S, int s_dtype, int64_t n, in
                     int64_t lds, double lambda, int precision, void* W, int64_t ldw,
                     void* stream);
 
-/* Cholesky: in-place lower factor W = L L^T (device, n x n, ldw, w_dtype FP32 or FP64).
- * Blocked right-looking; each 32 x 32 diagonal block is factored in FP64.  Synchronizes
+/* Cholesky of Algorithm 1: in-place lower factor W = L L^T (device, n x n, ldw, w_dtype FP32 or
+ * FP64).  Blocked right-looking, the kernel dfs_solve runs: FP64 W entirely in FP64, FP32 W with
+ * its 32 x 32 diagonal blocks in FP32 (as dfs_solve without DFS_FLAG_FP64_PANEL).  Synchronizes
  * `stream`.  Returns NOT_SPD (and *failed_pivot, may be NULL) on a pivot <= 0 or NaN. */
 dfs_status dfs_cholesky(dfs_handle handle, void* W, int w_dtype, int64_t n, int64_t ldw,
                         void* stream, int64_t* failed_pivot);
@@ -272,6 +275,16 @@ dfs_status dfs_fisher_pass(dfs_handle handle, const void* S, int s_dtype, int64_
                            int64_t lds, const void* V, int64_t k, int64_t ldv, const double* Y,
                            int64_t ldy, double lambda, void* X, int64_t ldx, double* R,
                            int64_t ldr, void* stream);
+
+/* ---- throughput probes --------------------------------------------------------------- */
+
+/* Measured peak rate (flop/s, 2 per fused multiply-add) of the current device's SIMT units, the
+ * roofline denominator of the kernels that run on them (the FP32 path's Gram, the FP64 path):
+ * independent FMA chains on every SM for ~0.1-0.3 s.  Changes no device setting.  Allocates a
+ * small output buffer.  Synchronous. */
+#define DFS_PEAK_FFMA32 1
+#define DFS_PEAK_DFMA64 2
+dfs_status dfs_measure_peak(int kind, double* flops_per_s);
 
 /* ---- test hook: make one bounded device wait run out ---------------------------------- */
 

@@ -17,6 +17,7 @@ from .api import (  # noqa: F401
     dfs_fisher_pass_noalloc_test_fault,
     dfs_set_test_fault,
     dfs_gram,
+    dfs_measure_peak,
     dfs_kernel_launches,
     dfs_reserve,
     dfs_solve,

@@ -33,6 +33,7 @@ EXPORTS = (
     "dfs_plan_batched", "dfs_batched_status",
     "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass", "dfs_fisher_pass_noalloc",
     "dfs_fisher_pass_noalloc_status", "dfs_fisher_pass_noalloc_test_fault", "dfs_set_test_fault",
+    "dfs_measure_peak",
 )
 
 
@@ -51,6 +52,8 @@ DFS_FLAG_STEP_TIMING = 1
 DFS_FLAG_FP64_PANEL = 2
 DFS_FLAG_CENTER = 4
 DFS_FLAG_TWO_KERNEL_GRAM = 8
+DFS_PEAK_FFMA32 = 1
+DFS_PEAK_DFMA64 = 2
 DFS_TEST_FAULT_NONE = 0
 DFS_TEST_FAULT_CHOLESKY = 1
 DFS_TEST_FAULT_CLUSTER_PASS = 2
@@ -98,6 +101,7 @@ _SIGS = {
     "dfs_fisher_pass_noalloc_status": (C.c_int, [C.POINTER(C.c_int), _VP]),
     "dfs_fisher_pass_noalloc_test_fault": (C.c_int, [C.c_int, _I64]),
     "dfs_set_test_fault": (C.c_int, [_VP, C.c_int, _I64]),
+    "dfs_measure_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
 }
 
 _lib = None

@@ -424,3 +424,15 @@ def dfs_fisher_pass_noalloc_test_fault(fault: int, wait_limit_ns: int = 0):
     st = lib.dfs_fisher_pass_noalloc_test_fault(int(fault), int(wait_limit_ns))
     if st != _lib.DFS_OK:
         raise DfsError(st, lib.dfs_status_string(st).decode())
+
+
+def dfs_measure_peak(kind: str) -> float:
+    """Measured peak flop/s of the current device's SIMT fused multiply-add: kind "ffma32" or
+    "dfma64" (the roofline denominators of the FP32-path Gram and of FP64 arithmetic)."""
+    lib = _lib.load()
+    code = {"ffma32": _lib.DFS_PEAK_FFMA32, "dfma64": _lib.DFS_PEAK_DFMA64}[kind]
+    out = C.c_double(0.0)
+    st = lib.dfs_measure_peak(code, C.byref(out))
+    if st != _lib.DFS_OK:
+        raise DfsError(st, lib.dfs_status_string(st).decode())
+    return float(out.value)

@@ -886,7 +886,8 @@ dfs_status dfs_cholesky(dfs_handle h, void* W, int w_dtype, int64_t n, int64_t l
     int* flags = reinterpret_cast<int*>(static_cast<char*>(h->ws) + oF);
     DFS_CK(launch_status_reset(h->dstat, stream, h->test_wait_ns, h->test_fault));
     DFS_CK(launch_pad_copy_in(f64, W, ldw, n, Wp, n_pad, stream));
-    DFS_CK(launch_cholesky(f64, Wp, n_pad, n_pad, Linv, flags, h->dstat, stream));
+    // the factorisation dfs_solve runs: FP32 W with FP32 diagonal blocks, FP64 W in FP64
+    DFS_CK(launch_cholesky(f64, Wp, n_pad, n_pad, Linv, flags, h->dstat, stream, f64));
     DFS_CK(launch_copy_lower_out(f64, Wp, n_pad, W, ldw, n, stream));
     dfs_info info;
     s = fill_info(h, stream, &info);

@@ -173,9 +173,14 @@ __device__ __noinline__ bool factor_diag(T* W, int64_t ld, int kb, T* Linv, DevS
         }
         if (lane == 0) *s_fail = fail;
         if (fail < 0) {
+            // a[lane] by an unrolled select: a dynamic index would move all of a[] to local memory
+            CT dl = (CT)0;
 #pragma unroll
-            for (int p = 0; p < NB; ++p) sF[lane][p] = a[p];
-            s_rinv[lane] = (T)1 / (T)a[lane];
+            for (int p = 0; p < NB; ++p) {
+                sF[lane][p] = a[p];
+                if (p == lane) dl = a[p];
+            }
+            s_rinv[lane] = (T)1 / (T)dl;
         }
     }
     __syncthreads();
