@@ -93,6 +93,11 @@ typedef enum {
                                    lambda I with P = I - 1 1^T / n, b = P O v / sqrt(n), and each
                                    pass over O reads P y / sqrt(n) (the triangular solves run on the
                                    reduce + substitution kernels).  dfs_solve and dfs_solve_host. */
+/* Right-hand sides per group: the solve runs its passes over S on groups of at most g columns of
+ * V (g = 1, 2, 4 or 8).  More per group means fewer passes over S, but each pass does more work
+ * per strip; DFS_FLAG_RHS_GROUP(0) (the default) lets the library choose (the kernels' limit,
+ * or a dfs_autotune choice for the problem's class). */
+#define DFS_FLAG_RHS_GROUP(g) (((g) & 15) << 8)
 #define DFS_FLAG_TWO_KERNEL_GRAM 8 /* BF16 Gram on FP32 S: run the first pass over S (b = S v and the
                                    BF16 tiles) and the Gram as two kernels instead of the one fused
                                    kernel that overlaps them (the default where it applies: n <= 4096
@@ -212,8 +217,8 @@ typedef struct {
 
 /* Solve `count` independent problems of uneven (n, m) (Eq. 1 for each; Algorithm 1 per
  * problem).  `problems` is a host array; every problem obeys dfs_solve's rules, S of type s_dtype.
- * Problems are dealt longest first (estimated cost n^2 m + 4 n m k) to up to 8 lanes, each with
- * its own stream and workspace, forked from and joined back into `stream`; with one problem the
+ * Problems are dealt longest first (estimated cost n^2 m + 4 n m k) to up to 8 lanes (see
+ * dfs_set_batch_lanes), each with its own stream and workspace, forked from and joined back into `stream`; with one problem the
  * solve runs on `stream` itself.
  * status_out (host, `count` ints, may be NULL) receives each problem's device status, in
  * `problems` order; when it is non-NULL the call synchronizes `stream` and returns the first
@@ -242,6 +247,30 @@ dfs_status dfs_plan_batched(dfs_handle handle, const dfs_problem* problems, int 
  * ints (count <= the batch's count) to host memory status_out.  Returns DFS_OK, or the first
  * non-zero status among them. */
 dfs_status dfs_batched_status(dfs_handle handle, int* status_out, int count, void* stream);
+
+/* Concurrency of dfs_solve_batched on this handle: up to `lanes` (1..16) lanes run at once, and
+ * each lane's kernels size their grids for 1/share (share 1..16) of the SMs, so that several
+ * small problems' latency-bound kernels share the GPU instead of queueing behind each other.
+ * The default is 8 lanes, share 1.  Takes effect at the next dfs_plan_batched or
+ * dfs_solve_batched (plan again before capturing a batch into a graph).  DFS_ERR_INVALID_ARG
+ * for values out of range. */
+dfs_status dfs_set_batch_lanes(dfs_handle handle, int lanes, int share);
+dfs_status dfs_get_batch_lanes(dfs_handle handle, int* lanes, int* share);
+
+/* Choose the batch concurrency (lanes, share) for this list of problems by timing it: each of a
+ * fixed set of candidates runs the batch once untimed and twice timed on `stream` (the problems'
+ * X are overwritten; S and V are only read), and the fastest is set on the handle as by
+ * dfs_set_batch_lanes.  cache_path (may be NULL) names a text file of JSON lines
+ *   {"gpu": <device name>, "batch": <key>, "lanes": L, "share": S, "ms": t}
+ * where the key encodes count, s_dtype, the resolved precision and a hash of the sorted (n, m, k)
+ * of the problems: a line for this GPU and key is used without timing (*ms_out = 0), otherwise
+ * the winner is appended.  lanes_out, share_out, ms_out (may be NULL) receive the choice and its
+ * mean batch time in ms.  Synchronizes `stream`; not allowed during stream capture
+ * (DFS_ERR_INVALID_ARG).  Errors of a timed run are returned as dfs_solve_batched's; a problem
+ * that stops above its tolerance does not stop the tuning. */
+dfs_status dfs_autotune_batched(dfs_handle handle, const dfs_problem* problems, int count,
+                                int s_dtype, const dfs_options* opt, const char* cache_path,
+                                void* stream, int* lanes_out, int* share_out, float* ms_out);
 
 /* ---- single steps of Algorithm 1 (for composition and testing) ---------------------- */
 

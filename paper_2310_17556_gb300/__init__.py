@@ -24,6 +24,9 @@ from .api import (  # noqa: F401
     dfs_solve_batched,
     dfs_plan_batched,
     dfs_batched_status,
+    dfs_set_batch_lanes,
+    dfs_get_batch_lanes,
+    dfs_autotune_batched,
     dfs_solve_host,
     dfs_solve_host_async,
     dfs_solve_complex,

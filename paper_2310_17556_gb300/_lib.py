@@ -30,7 +30,7 @@ PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 EXPORTS = (
     "dfs_create", "dfs_destroy", "dfs_status_string", "dfs_last_error", "dfs_reserve", "dfs_kernel_launches",
     "dfs_solve", "dfs_solve_host", "dfs_solve_host_async", "dfs_solve_complex", "dfs_sync_info", "dfs_step_times", "dfs_solve_batched",
-    "dfs_plan_batched", "dfs_batched_status",
+    "dfs_plan_batched", "dfs_batched_status", "dfs_set_batch_lanes", "dfs_get_batch_lanes", "dfs_autotune_batched",
     "dfs_gram", "dfs_cholesky", "dfs_trsm", "dfs_fisher_pass", "dfs_fisher_pass_noalloc",
     "dfs_fisher_pass_noalloc_status", "dfs_fisher_pass_noalloc_test_fault", "dfs_set_test_fault",
     "dfs_measure_peak",
@@ -91,6 +91,10 @@ _SIGS = {
     "dfs_plan_batched": (C.c_int, [_VP, C.POINTER(dfs_problem), C.c_int, C.c_int, C.POINTER(dfs_options),
                                    C.POINTER(C.c_size_t)]),
     "dfs_batched_status": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int, _VP]),
+    "dfs_set_batch_lanes": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "dfs_get_batch_lanes": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "dfs_autotune_batched": (C.c_int, [_VP, C.POINTER(dfs_problem), C.c_int, C.c_int, C.POINTER(dfs_options), C.c_char_p,
+                                       _VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "dfs_gram": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _I64, C.c_double, C.c_int, _VP, _I64, _VP]),
     "dfs_cholesky": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _VP, C.POINTER(_I64)]),
     "dfs_trsm": (C.c_int, [_VP, _VP, C.c_int, _I64, _I64, _VP, _I64, _I64, C.c_int, _VP]),

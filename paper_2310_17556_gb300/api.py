@@ -45,11 +45,14 @@ def _stream(stream) -> int:
 
 
 def _opts(precision, max_iter, tol, timing=False, fp64_panel=False, center=False,
-          two_kernel_gram=False) -> dfs_options:
+          two_kernel_gram=False, rhs_group=0) -> dfs_options:
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     flags = (_lib.DFS_FLAG_STEP_TIMING if timing else 0) | (_lib.DFS_FLAG_FP64_PANEL if fp64_panel else 0)
     flags |= _lib.DFS_FLAG_CENTER if center else 0
     flags |= _lib.DFS_FLAG_TWO_KERNEL_GRAM if two_kernel_gram else 0
+    if rhs_group not in (0, 1, 2, 4, 8):
+        raise ValueError("rhs_group must be 0 (auto), 1, 2, 4 or 8")
+    flags |= (int(rhs_group) & 15) << 8
     return dfs_options(p, int(max_iter), float(tol), flags)
 
 
@@ -130,12 +133,13 @@ def dfs_reserve(n_max: int, m_max: int, k_max: int, precision="auto", handle: Ha
 def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | None = None, precision="auto",
               max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None, stream=None,
               sync: bool = True, timing: bool = False, fp64_panel: bool = False, center: bool = False,
-              two_kernel_gram: bool = False, allow_not_converged: bool = False):
+              two_kernel_gram: bool = False, allow_not_converged: bool = False, rhs_group: int = 0):
     """Solve (S^T S + lam I) X^T = V^T for the k rows of V (Eq. 1, Algorithm 1).
 
     center=True: S holds O and the system is Eq. 1 with Section 4's SR scores (O - O_bar)/sqrt(n).
     two_kernel_gram=True: the first pass over S and the BF16 Gram as two kernels instead of the
-    fused one (for comparison).
+    fused one (for comparison).  rhs_group: right-hand sides per group of passes (0 = the
+    library's choice).
 
     Returns (X, info) when sync is True (info = dict of dfs_info), else (X, None) with the work
     queued on the stream (read the status later with dfs_sync_info).  A solve whose refinement
@@ -152,7 +156,7 @@ def dfs_solve(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.Tensor | No
         raise TypeError(f"V must be {vdt} for S of dtype {S.dtype}")
     if X is None:
         X = torch.empty((k, m), device=S.device, dtype=vdt)
-    opt = _opts(precision, max_iter, tol, timing, fp64_panel, center, two_kernel_gram)
+    opt = _opts(precision, max_iter, tol, timing, fp64_panel, center, two_kernel_gram, rhs_group)
     info = dfs_info()
     st = h.lib.dfs_solve(h.h, S.data_ptr(), _dtype_code(S), n, m, _rows(S, "S"), V.data_ptr(), k, _rows(V, "V"),
                          float(lam), X.data_ptr(), _rows(X, "X"), C.byref(opt), _stream(stream),
@@ -313,6 +317,38 @@ def dfs_batched_status(count: int, handle: Handle | None = None, stream=None,
         e.statuses = out
         raise
     return out
+
+
+def dfs_set_batch_lanes(lanes: int, share: int = 1, handle: Handle | None = None) -> None:
+    """Run dfs_solve_batched on up to `lanes` concurrent lanes, each lane's kernels sized for
+    1/share of the SMs."""
+    h = handle or default_handle()
+    _check(h.lib, h.h, h.lib.dfs_set_batch_lanes(h.h, int(lanes), int(share)))
+
+
+def dfs_get_batch_lanes(handle: Handle | None = None) -> tuple:
+    """(lanes, share) dfs_solve_batched uses on this handle."""
+    h = handle or default_handle()
+    lanes, share = C.c_int(0), C.c_int(0)
+    _check(h.lib, h.h, h.lib.dfs_get_batch_lanes(h.h, C.byref(lanes), C.byref(share)))
+    return lanes.value, share.value
+
+
+def dfs_autotune_batched(problems, precision="auto", max_iter: int = -1, tol: float = 0.0,
+                         handle: Handle | None = None, stream=None, center: bool = False,
+                         cache_path: str | None = None) -> dict:
+    """Time dfs_solve_batched on `problems` ([(S, V, lam, X), ...]; X is overwritten) under each
+    candidate (lanes, share), set the fastest on the handle and return
+    {"lanes", "share", "ms"} (ms 0.0 when cache_path held a choice for this GPU and batch)."""
+    h = handle or default_handle()
+    arr, _, dt = _batch_array(problems, alloc_x=True)
+    opt = _opts(precision, max_iter, tol, center=center)
+    lanes, share, ms = C.c_int(0), C.c_int(0), C.c_float(0.0)
+    path = cache_path.encode() if cache_path else None
+    st = h.lib.dfs_autotune_batched(h.h, arr, len(problems), dt, C.byref(opt), path, _stream(stream),
+                                    C.byref(lanes), C.byref(share), C.byref(ms))
+    _check(h.lib, h.h, st)
+    return {"lanes": lanes.value, "share": share.value, "ms": ms.value}
 
 
 def dfs_gram(S: torch.Tensor, lam: float, precision="auto", W: torch.Tensor | None = None,

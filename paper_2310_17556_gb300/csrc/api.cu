@@ -2,6 +2,7 @@
 // launch sequence of Algorithm 1 (arXiv 2310.17556) with Q inlined (Section 2).
 #include <cmath>
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -33,7 +34,9 @@ struct dfs_handle_s {
     int bstat_used = 0;                            // problems of the last dfs_solve_batched
     // dfs_solve_batched runs its problems on up to kMaxLanes concurrent lanes: each a private handle
     // (workspace, device status) and stream, forked from and joined to the caller's stream by events.
-    static constexpr int kMaxLanes = 8;
+    static constexpr int kMaxLanes = 16;
+    int batch_lanes = 8;  // lanes dfs_solve_batched uses (dfs_autotune_batched may change it)
+    int batch_share = 1;  // each lane's kernels take 1 / batch_share of the SMs (grid sizes)
     dfs_handle lane[kMaxLanes] = {};
     cudaStream_t lane_stream[kMaxLanes] = {};
     cudaEvent_t lane_done[kMaxLanes] = {};
@@ -165,8 +168,10 @@ int pow2_at_least(int k) {
     return q;
 }
 
+// kq_cap > 0: at most that many right-hand sides per group (DFS_FLAG_RHS_GROUP, or the tuner's
+// choice); 0 = as many as the kernels take
 dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, int k, Plan* p,
-                     bool allow_fused = true) {
+                     bool allow_fused = true, int kq_cap = 0) {
     p->s_dtype = s_dtype;
     p->prec = prec;
     p->f64 = (prec == DFS_PREC_FP64);
@@ -177,10 +182,11 @@ dfs_status make_plan(dfs_handle h, int s_dtype, int prec, int64_t n, int64_t m, 
     p->k = k;
     const int es = p->f64 ? 8 : 4;
     int kq = pow2_at_least(k);
+    if (kq_cap > 0 && kq > kq_cap) kq = pow2_at_least(kq_cap);
     int kq_pass = pass_max_group((int)n, s_dtype, h->smem_optin);
-    // the cluster pass (FP32 S, n <= 4096) keeps its rows in registers: it takes up to 4 right-hand
-    // sides whatever the one-CTA-per-strip pass's shared-memory bound is
-    for (int c = 4; c > kq_pass; c >>= 1) {
+    // the cluster pass (FP32 S, n <= 4096) keeps its rows in registers: it takes up to 8 right-hand
+    // sides (n <= 2048) whatever the one-CTA-per-strip pass's shared-memory bound is
+    for (int c = 8; c > kq_pass; c >>= 1) {
         int cs = 0, crpt = 0;
         if (pass_cluster_plan(s_dtype, (int)n, c, h->num_sms, m, h->smem_optin, &cs, &crpt) > 0) {
             kq_pass = c;
@@ -375,7 +381,8 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
     const double tol = (opt && opt->tol > 0.0) ? opt->tol : 1e-7;
     Plan p;
     const bool allow_fused = !(opt && (opt->flags & DFS_FLAG_TWO_KERNEL_GRAM));
-    if ((s = make_plan(h, s_dtype, prec, n, m, (int)k, &p, allow_fused)) != DFS_OK) return s;
+    const int kq_cap = opt ? (opt->flags >> 8) & 15 : 0;
+    if ((s = make_plan(h, s_dtype, prec, n, m, (int)k, &p, allow_fused, kq_cap)) != DFS_OK) return s;
     if ((s = ensure_ws(h, p.total, stream)) != DFS_OK) return s;
     h->last_precision = prec;
     // S = (O - O_bar) / sqrt(n) from the caller's O: n-space centring around unchanged passes over
@@ -514,7 +521,7 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
             // x_2 = x_1 - S_bf16^T dy_1 / lambda (the tiles' rounding costs 2^-9 of a correction of
             // relative size delta_2, which the check adds to its estimate).  If that does not
             // converge, the full pass of step 2 recomputes x_2 exactly and refinement goes on.
-            const bool fast = p.pack == 1 && !center && max_iter >= 3 && !p.f64 && kq <= 4;
+            const bool fast = p.pack == 1 && !center && max_iter >= 3 && !p.f64 && kq <= 8;
             for (int it = 1; it <= max_iter; ++it) {
                 const bool corrected = fast && it == 2;
                 if (corrected) {
@@ -997,9 +1004,9 @@ static dfs_status check_batch(dfs_handle h, const dfs_problem* problems, int cou
 // Eight lanes: 64 problems of n ~ U{64..1024}, m log-uniform in [1e4, 5e5] ran 1.63x faster than
 // one stream with four lanes, 1.78x with eight, 1.80x with sixteen.  Returns the lane count;
 // `order` receives the problems longest first, `lane_of` each problem's lane.
-static int schedule_batch(const dfs_problem* problems, int count, std::vector<int>& order,
+static int schedule_batch(dfs_handle h, const dfs_problem* problems, int count, std::vector<int>& order,
                           std::vector<int>& lane_of) {
-    const int L = count < dfs_handle_s::kMaxLanes ? count : dfs_handle_s::kMaxLanes;
+    const int L = count < h->batch_lanes ? count : h->batch_lanes;
     order.resize(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     auto cost = [&](int i) {
@@ -1053,6 +1060,9 @@ static dfs_status prepare_batch(dfs_handle h, int count, int L, cudaStream_t str
         // every lane's cooperative Cholesky fits on the device at the same time as the others'
         h->lane[l]->chol_share = L;
         h->lane[l]->lane_handle = true;
+        // the lane's other kernels size their grids for its share of the SMs, so that the small
+        // problems' latency-bound kernels leave room for the other lanes'
+        h->lane[l]->num_sms = h->num_sms / h->batch_share > 0 ? h->num_sms / h->batch_share : 1;
     }
     if (!h->fork_ev) {
         if (cap) return fail(h, DFS_ERR_NO_MEMORY, "batch fork event must be created during stream capture; call dfs_plan_batched first");
@@ -1072,14 +1082,18 @@ dfs_status dfs_plan_batched(dfs_handle h, const dfs_problem* problems, int count
     int prec;
     if ((s = resolve_precision(h, s_dtype, opt ? opt->precision : DFS_PREC_AUTO, &prec)) != DFS_OK) return s;
     std::vector<int> order, lane_of;
-    const int L = schedule_batch(problems, count, order, lane_of);
+    const int L = schedule_batch(h, problems, count, order, lane_of);
     if ((s = prepare_batch(h, count, L, nullptr)) != DFS_OK) return s;
-    // each lane's workspace: the largest plan among the problems dealt to it
+    // each lane's workspace: the largest plan among the problems dealt to it (planned on the lane,
+    // with its share of the SMs and the caller's group size)
+    const int kq_cap = opt ? (opt->flags >> 8) & 15 : 0;
     std::vector<size_t> need(L, 0);
     for (int i = 0; i < count; ++i) {
         const dfs_problem& q = problems[i];
         Plan p;
-        if ((s = make_plan(h, s_dtype, prec, q.n, q.m, (int)q.k, &p)) != DFS_OK) return s;
+        if ((s = make_plan(L == 1 ? h : h->lane[lane_of[i]], s_dtype, prec, q.n, q.m, (int)q.k, &p, true, kq_cap)) !=
+            DFS_OK)
+            return s;
         if (p.total > need[lane_of[i]]) need[lane_of[i]] = p.total;
     }
     size_t held = sizeof(int) * (size_t)h->bstat_count;
@@ -1101,7 +1115,7 @@ dfs_status dfs_solve_batched(dfs_handle h, const dfs_problem* problems, int coun
     dfs_status s;
     if ((s = check_batch(h, problems, count, s_dtype)) != DFS_OK) return s;
     std::vector<int> order, lane_of;
-    const int L = schedule_batch(problems, count, order, lane_of);
+    const int L = schedule_batch(h, problems, count, order, lane_of);
     if ((s = prepare_batch(h, count, L, stream)) != DFS_OK) return s;
     h->bstat_used = count;
     if (L == 1) {
@@ -1130,6 +1144,147 @@ dfs_status dfs_solve_batched(dfs_handle h, const dfs_problem* problems, int coun
         }
     }
     if (status_out) return dfs_batched_status(h, status_out, count, stream_);
+    return DFS_OK;
+}
+
+dfs_status dfs_set_batch_lanes(dfs_handle h, int lanes, int share) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    if (lanes < 1 || lanes > dfs_handle_s::kMaxLanes || share < 1 || share > 16)
+        return fail(h, DFS_ERR_INVALID_ARG, "batch lanes %d (1..%d) or share %d (1..16) out of range", lanes,
+                    dfs_handle_s::kMaxLanes, share);
+    h->batch_lanes = lanes;
+    h->batch_share = share;
+    return DFS_OK;
+}
+
+dfs_status dfs_get_batch_lanes(dfs_handle h, int* lanes, int* share) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    if (lanes) *lanes = h->batch_lanes;
+    if (share) *share = h->batch_share;
+    return DFS_OK;
+}
+
+// ---- autotuner of the batched path -----------------------------------------------------------
+// The batch's key: its size, dtype, precision and a hash of its problems' shapes (n, m, k), sorted
+// so that the order of the list does not matter.
+static std::string batch_key(const dfs_problem* problems, int count, int s_dtype, int prec) {
+    std::vector<std::array<int64_t, 3>> shapes(count);
+    for (int i = 0; i < count; ++i) shapes[i] = {problems[i].n, problems[i].m, problems[i].k};
+    std::sort(shapes.begin(), shapes.end());
+    uint64_t hsh = 1469598103934665603ull;  // FNV-1a over the shape words
+    for (const auto& sh : shapes)
+        for (int64_t v : sh)
+            for (int b = 0; b < 8; ++b) {
+                hsh ^= (uint64_t)((v >> (8 * b)) & 0xff);
+                hsh *= 1099511628211ull;
+            }
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), "c%d_d%d_p%d_%016llx", count, s_dtype, prec, (unsigned long long)hsh);
+    return buf;
+}
+
+// Finds `"field": <int>` in a JSON line (a flat object this file writes itself).
+static bool json_int(const std::string& line, const char* field, int* out) {
+    const std::string tag = std::string("\"") + field + "\":";
+    const size_t p = line.find(tag);
+    return p != std::string::npos && std::sscanf(line.c_str() + p + tag.size(), " %d", out) == 1;
+}
+static bool json_str(const std::string& line, const char* field, std::string* out) {
+    const std::string tag = std::string("\"") + field + "\": \"";
+    const size_t p = line.find(tag);
+    if (p == std::string::npos) return false;
+    const size_t e = line.find('"', p + tag.size());
+    if (e == std::string::npos) return false;
+    *out = line.substr(p + tag.size(), e - p - tag.size());
+    return true;
+}
+
+dfs_status dfs_autotune_batched(dfs_handle h, const dfs_problem* problems, int count, int s_dtype,
+                                const dfs_options* opt, const char* cache_path, void* stream_, int* lanes_out,
+                                int* share_out, float* ms_out) {
+    if (!h) return DFS_ERR_INVALID_ARG;
+    h->err.clear();
+    cudaSetDevice(h->device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    dfs_status s;
+    if ((s = check_batch(h, problems, count, s_dtype)) != DFS_OK) return s;
+    if (capturing(stream)) return fail(h, DFS_ERR_INVALID_ARG, "dfs_autotune_batched cannot run under stream capture");
+    int prec;
+    if ((s = resolve_precision(h, s_dtype, opt ? opt->precision : DFS_PREC_AUTO, &prec)) != DFS_OK) return s;
+    cudaDeviceProp prop;
+    DFS_CK(cudaGetDeviceProperties(&prop, h->device));
+    const std::string gpu = prop.name, key = batch_key(problems, count, s_dtype, prec);
+    // a recorded choice for this GPU and batch (the last line for the key wins): use it untimed
+    if (cache_path) {
+        bool hit = false;
+        if (FILE* fp = std::fopen(cache_path, "r")) {
+            char line[512];
+            while (std::fgets(line, sizeof(line), fp)) {
+                const std::string ln = line;
+                std::string g, b;
+                int lanes = 0, share = 0;
+                if (json_str(ln, "gpu", &g) && json_str(ln, "batch", &b) && g == gpu && b == key &&
+                    json_int(ln, "lanes", &lanes) && json_int(ln, "share", &share) && lanes >= 1 &&
+                    lanes <= dfs_handle_s::kMaxLanes && share >= 1 && share <= 16) {
+                    h->batch_lanes = lanes;
+                    h->batch_share = share;
+                    hit = true;
+                }
+            }
+            std::fclose(fp);
+        }
+        if (hit) {
+            if (lanes_out) *lanes_out = h->batch_lanes;
+            if (share_out) *share_out = h->batch_share;
+            if (ms_out) *ms_out = 0.f;  // nothing was timed
+            return DFS_OK;
+        }
+    }
+    static const int cand[][2] = {{8, 1}, {8, 2}, {8, 4}, {8, 8}, {16, 4}, {16, 8}, {4, 1}, {4, 2}};
+    cudaEvent_t e0, e1;
+    DFS_CK(cudaEventCreate(&e0));
+    DFS_CK(cudaEventCreate(&e1));
+    float best = -1.f;
+    int best_l = h->batch_lanes, best_s = h->batch_share;
+    for (const auto& c : cand) {
+        h->batch_lanes = c[0];
+        h->batch_share = c[1];
+        size_t held = 0;
+        if ((s = dfs_plan_batched(h, problems, count, s_dtype, opt, &held)) != DFS_OK) break;
+        if ((s = dfs_solve_batched(h, problems, count, s_dtype, opt, stream, nullptr)) != DFS_OK) break;  // warm-up
+        DFS_CK(cudaEventRecord(e0, stream));
+        for (int r = 0; r < 2 && s == DFS_OK; ++r) s = dfs_solve_batched(h, problems, count, s_dtype, opt, stream, nullptr);
+        if (s != DFS_OK) break;
+        DFS_CK(cudaEventRecord(e1, stream));
+        DFS_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DFS_CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms *= 0.5f;
+        if (best < 0.f || ms < best) {
+            best = ms;
+            best_l = c[0];
+            best_s = c[1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->batch_lanes = best_l;
+    h->batch_share = best_s;
+    if (s != DFS_OK) return s;
+    // the device status of the last timed run (every problem solved)
+    std::vector<int> st(count);
+    if ((s = dfs_batched_status(h, st.data(), count, stream_)) != DFS_OK && s != DFS_ERR_NOT_CONVERGED) return s;
+    if (cache_path) {
+        if (FILE* fp = std::fopen(cache_path, "a")) {
+            std::fprintf(fp, "{\"gpu\": \"%s\", \"batch\": \"%s\", \"lanes\": %d, \"share\": %d, \"ms\": %.4f}\n",
+                         gpu.c_str(), key.c_str(), best_l, best_s, best);
+            std::fclose(fp);
+        }
+    }
+    if (lanes_out) *lanes_out = best_l;
+    if (share_out) *share_out = best_s;
+    if (ms_out) *ms_out = best;
     return DFS_OK;
 }
 

@@ -1020,6 +1020,7 @@ cudaError_t launch_tile_correct(int kq, const void* Sp, int n, int n_rows, int64
         case 1: DFS_TCC(1)
         case 2: DFS_TCC(2)
         case 4: DFS_TCC(4)
+        case 8: DFS_TCC(8)
         default: return cudaErrorInvalidValue;
     }
 #undef DFS_TCC

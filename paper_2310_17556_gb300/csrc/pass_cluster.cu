@@ -155,6 +155,31 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
     __syncthreads();
     cl_sync();  // every CTA of the cluster is running (and its barriers initialised) before any remote store
 
+    // Phase 2's row sums: with few rows and right-hand sides a lane keeps its own partial sums
+    // (its 4 columns of every strip) in registers and the 16 lanes of a row are added only at
+    // each fold, in place of 4 shuffles per row and right-hand side on every strip.
+    constexpr bool kLaneAcc = RPT * KQ <= 32;
+    float racc[kLaneAcc ? RPT : 1][kLaneAcc ? KQ : 1];
+#pragma unroll
+    for (int t = 0; t < (kLaneAcc ? RPT : 1); ++t)
+#pragma unroll
+        for (int q = 0; q < (kLaneAcc ? KQ : 1); ++q) racc[t][q] = 0.f;
+    auto fold_lanes = [&]() {
+#pragma unroll
+        for (int t = 0; t < (kLaneAcc ? RPT : 1); ++t) {
+            const int li = lrow0 + t * CL_SWEEP;
+#pragma unroll
+            for (int q = 0; q < (kLaneAcc ? KQ : 1); ++q) {
+                float a = racc[t][q];
+                a += __shfl_xor_sync(0xffffffffu, a, 1);
+                a += __shfl_xor_sync(0xffffffffu, a, 2);
+                a += __shfl_xor_sync(0xffffffffu, a, 4);
+                a += __shfl_xor_sync(0xffffffffu, a, 8);
+                if (cq == 0) Rs64[li * KQ + q] += (double)a;
+                racc[t][q] = 0.f;
+            }
+        }
+    };
     int since_fold = 0, par = 0;
     for (int64_t s = cid; s < nstrips; s += ncl, par ^= 1) {
         const int64_t j0 = s * CL_W;
@@ -262,26 +287,35 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
                 const int li = lrow0 + t * CL_SWEEP;
 #pragma unroll
                 for (int q = 0; q < KQ; ++q) {
-                    float a = 0.f;
+                    if constexpr (kLaneAcc) {
+                        // this lane's 4 columns only; the 16 lanes of the row are added at the fold
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) a = fmaf(sv[t][e], uu[q][e], a);
-                    a += __shfl_xor_sync(0xffffffffu, a, 1);
-                    a += __shfl_xor_sync(0xffffffffu, a, 2);
-                    a += __shfl_xor_sync(0xffffffffu, a, 4);
-                    a += __shfl_xor_sync(0xffffffffu, a, 8);
-                    if (cq == 0) Rs32[li * KQ + q] += a;
+                        for (int e = 0; e < 4; ++e) racc[t][q] = fmaf(sv[t][e], uu[q][e], racc[t][q]);
+                    } else {
+                        float a = 0.f;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) a = fmaf(sv[t][e], uu[q][e], a);
+                        a += __shfl_xor_sync(0xffffffffu, a, 1);
+                        a += __shfl_xor_sync(0xffffffffu, a, 2);
+                        a += __shfl_xor_sync(0xffffffffu, a, 4);
+                        a += __shfl_xor_sync(0xffffffffu, a, 8);
+                        if (cq == 0) Rs32[li * KQ + q] += a;
+                    }
                 }
             }
         }
         if (++since_fold == CL_FOLD) {
             since_fold = 0;
-            if (wantR && cq == 0)
+            if constexpr (kLaneAcc) {
+                if (wantR) fold_lanes();
+            } else if (wantR && cq == 0) {
                 for (int li = lrow0; li < RC; li += CL_SWEEP)
 #pragma unroll
                     for (int q = 0; q < KQ; ++q) {
                         Rs64[li * KQ + q] += (double)Rs32[li * KQ + q];
                         Rs32[li * KQ + q] = 0.f;
                     }
+            }
 #pragma unroll
             for (int q = 0; q < KQ; ++q) {
                 u2[q] += (double)u2f[q];
@@ -293,10 +327,13 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         // of this CTA reaches after finishing phase 2 here
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-    if (wantR && cq == 0)
+    if constexpr (kLaneAcc) {
+        if (wantR) fold_lanes();
+    } else if (wantR && cq == 0) {
         for (int li = lrow0; li < RC; li += CL_SWEEP)
 #pragma unroll
             for (int q = 0; q < KQ; ++q) Rs64[li * KQ + q] += (double)Rs32[li * KQ + q];
+    }
 #pragma unroll
     for (int q = 0; q < KQ; ++q) {
         u2[q] += (double)u2f[q];
@@ -343,8 +380,11 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
 // Rows per thread for n rows split over cs CTAs of at most 512 rows; 0 if the cluster form does
 // not apply (needs FP32 S, KQ <= 4, n <= 4096).
 static int cluster_rpt(int n, int KQ, int* cs_out) {
-    if (KQ > 4 || n > CL_MAX_CS * 16 * CL_SWEEP) return 0;
-    const int cs = (n + 16 * CL_SWEEP - 1) / (16 * CL_SWEEP);
+    // eight right-hand sides fill all 512 threads with column sums and hold twice the
+    // accumulators: at most 8 rows a thread (256 a CTA), so n <= 2048
+    const int max_rpt = KQ == 8 ? 8 : 16;
+    if (KQ > 8 || n > CL_MAX_CS * max_rpt * CL_SWEEP) return 0;
+    const int cs = (n + max_rpt * CL_SWEEP - 1) / (max_rpt * CL_SWEEP);
     const int per = (n + cs - 1) / cs;
     int rpt = 4;
     while (rpt * CL_SWEEP < per) rpt *= 2;
@@ -392,6 +432,7 @@ static int max_active_clusters(int kq, int rpt, int cs) {
     DFS_CLMAX(1, 4) DFS_CLMAX(1, 8) DFS_CLMAX(1, 16)
     DFS_CLMAX(2, 4) DFS_CLMAX(2, 8) DFS_CLMAX(2, 16)
     DFS_CLMAX(4, 4) DFS_CLMAX(4, 8) DFS_CLMAX(4, 16)
+    DFS_CLMAX(8, 4) DFS_CLMAX(8, 8)
 #undef DFS_CLMAX
     return 0;
 }
@@ -456,6 +497,7 @@ cudaError_t launch_pass_cluster(int ncl, int cs, int rpt, int kq, const void* S,
     DFS_CL(1, 4) DFS_CL(1, 8) DFS_CL(1, 16)
     DFS_CL(2, 4) DFS_CL(2, 8) DFS_CL(2, 16)
     DFS_CL(4, 4) DFS_CL(4, 8) DFS_CL(4, 16)
+    DFS_CL(8, 4) DFS_CL(8, 8)
 #undef DFS_CL
     return cudaErrorInvalidValue;
 }

@@ -7,6 +7,7 @@ FP64).  Tolerances:
   * mixed paths (tensor Gram + refinement): e_rel <= 1e-6.
 """
 
+import json
 import math
 
 import numpy as np
@@ -770,6 +771,66 @@ def test_solve_batched_lanes(prec):
             assert rel_err(np64(X), solve_ref(S, V, lam)) <= fp32_tol(S, lam)
         else:
             assert_mixed(S, V, lam, X)
+
+
+@pytest.mark.parametrize("lanes,share", [(1, 1), (4, 2), (8, 4), (16, 8)])
+def test_solve_batched_lane_counts_and_shares(lanes, share):
+    """The batch's concurrency knobs change only how problems share the GPU: one lane (a plain loop
+    on the caller's stream), and lanes whose kernels size their grids for a fraction of the SMs,
+    each give every problem its oracle solution."""
+    probs = _ragged_problems(9, seed=7050)
+    h = dfs.Handle()
+    try:
+        dfs.dfs_set_batch_lanes(lanes, share, handle=h)
+        assert dfs.dfs_get_batch_lanes(handle=h) == (lanes, share)
+        outs, status = dfs.dfs_solve_batched(probs, precision="bf16", handle=h)
+        assert status == [0] * len(probs)
+        for (S, V, lam), X in zip(probs, outs):
+            assert_mixed(S, V, lam, X)
+    finally:
+        h.close()
+
+
+def test_batch_lanes_out_of_range_are_rejected():
+    h = dfs.Handle()
+    try:
+        for lanes, share in [(0, 1), (17, 1), (8, 0), (8, 17)]:
+            with pytest.raises(DfsError):
+                dfs.dfs_set_batch_lanes(lanes, share, handle=h)
+        assert dfs.dfs_get_batch_lanes(handle=h) == (8, 1)
+    finally:
+        h.close()
+
+
+def test_autotune_batched_picks_a_candidate_and_caches_it(tmp_path):
+    """The tuner times the batch under its candidates, sets the fastest, and appends it to the cache;
+    a second handle reads the choice back without timing; the tuned batch solves correctly."""
+    probs = [(S, V, lam, torch.empty_like(V)) for S, V, lam in _ragged_problems(12, seed=7060)]
+    cache = tmp_path / "batch_tune.jsonl"
+    h1, h2 = dfs.Handle(), dfs.Handle()
+    try:
+        r1 = dfs.dfs_autotune_batched(probs, precision="bf16", handle=h1, cache_path=str(cache))
+        assert r1["ms"] > 0.0
+        assert (r1["lanes"], r1["share"]) in {(8, 1), (8, 2), (8, 4), (8, 8), (16, 4), (16, 8), (4, 1), (4, 2)}
+        assert dfs.dfs_get_batch_lanes(handle=h1) == (r1["lanes"], r1["share"])
+        lines = cache.read_text().splitlines()
+        assert len(lines) == 1
+        rec = json.loads(lines[0])
+        assert rec["gpu"] == torch.cuda.get_device_name(0)
+        assert (rec["lanes"], rec["share"]) == (r1["lanes"], r1["share"])
+        r2 = dfs.dfs_autotune_batched(probs, precision="bf16", handle=h2, cache_path=str(cache))
+        assert r2 == {"lanes": r1["lanes"], "share": r1["share"], "ms": 0.0}
+        assert len(cache.read_text().splitlines()) == 1
+        # another batch has another key: timed and appended
+        r3 = dfs.dfs_autotune_batched(probs[:5], precision="bf16", handle=h2, cache_path=str(cache))
+        assert r3["ms"] > 0.0 and len(cache.read_text().splitlines()) == 2
+        outs, status = dfs.dfs_solve_batched([p[:3] for p in probs], precision="bf16", handle=h1)
+        assert status == [0] * len(probs)
+        for (S, V, lam, _), X in zip(probs, outs):
+            assert_mixed(S, V, lam, X)
+    finally:
+        h1.close()
+        h2.close()
 
 
 def test_solve_batched_failure_stays_in_its_problem():
