@@ -521,7 +521,8 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
             // x_2 = x_1 - S_bf16^T dy_1 / lambda (the tiles' rounding costs 2^-9 of a correction of
             // relative size delta_2, which the check adds to its estimate).  If that does not
             // converge, the full pass of step 2 recomputes x_2 exactly and refinement goes on.
-            const bool fast = p.pack == 1 && !center && max_iter >= 3 && !p.f64 && kq <= 8;
+            const bool fast = p.pack == 1 && !center && max_iter >= 3 && !p.f64 && kq <= 8 &&
+                              tile_correct_fits((int)round_up(n, 256), kq, h->smem_optin);
             for (int it = 1; it <= max_iter; ++it) {
                 const bool corrected = fast && it == 2;
                 if (corrected) {

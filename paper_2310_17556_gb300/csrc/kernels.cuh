@@ -154,6 +154,7 @@ cudaError_t launch_refine_update(int f64, const void* Z, const double* R, int n_
 // grid = the SM count; the parts it writes (at most tile_correct_parts(num_sms)) are returned by
 // the launch through *parts
 int tile_correct_parts(int num_sms);
+bool tile_correct_fits(int n_rows, int kq, size_t smem_limit);
 cudaError_t launch_tile_correct(int kq, const void* Sp, int n, int n_rows, int64_t m, int64_t nkb, const float* Z,
                                 int k, double lambda, float* X, int64_t ldx, double* U2part, const DevStatus* st,
                                 int grid, cudaStream_t stream, int* parts);

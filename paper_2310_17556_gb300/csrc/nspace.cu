@@ -33,7 +33,6 @@ constexpr int NS_SB = 64;          // super-block rows
 constexpr int NS_B = 32;           // Cholesky block (Linv granularity)
 constexpr int NS_MAX_CS = 8;
 constexpr int NS_MAX_SLOTS = 8;
-constexpr int NS_RED_GROUPS = NS_THREADS / NS_SB;  // part groups of the reduction (KQ = 1)
 
 __device__ __forceinline__ uint32_t ns_rank() {
     uint32_t r;
@@ -136,7 +135,7 @@ nspace_kernel(const T* __restrict__ W, int64_t ld, int n_pad, const T* __restric
     T* x = ring + (size_t)nslots * L::TILE;
     T* diag = x + (size_t)n_pad * KQ;
     __shared__ int s_abort;
-    __shared__ double red[NS_RED_GROUPS][NS_SB];
+    __shared__ double red[NS_THREADS / NS_SB][NS_SB];  // the reduction's group sums
 
     if (block_should_exit(st, honor_stop)) return;  // cluster-uniform: earlier launches write it
     const uint64_t wait_ns = wait_limit(st);  // the call's wait limit, read once
@@ -244,51 +243,56 @@ nspace_kernel(const T* __restrict__ W, int64_t ld, int n_pad, const T* __restric
     }
 
     // ---- right-hand side of the owned rows (and the FP64 residual R) ----
+    // Thread (g, r, q) adds the parts b = g, g + NG, ... of entry (row r, RHS q) of each owned
+    // super-block (8 interleaved sums, then their fixed tree); the NG groups are then added in order.
+    constexpr int NE = NS_SB * KQ;          // entries of a super-block
+    constexpr int NG = NS_THREADS / NE;     // part groups (1 with 8 right-hand sides)
+    double* redf = &red[0][0];              // NG x NE
     for (int j = 0; j < nown; ++j) {
         const int sb = (int)rank + j * (int)cs;
-        for (int q = 0; q < KQ; ++q) {
+        const int e = tid % NE, g = tid / NE;
+        const int r = e / KQ, q = e % KQ;
+        const int i = sb * NS_SB + r;
+        if (g < NG) {
             double v = 0.0;
-            const int r = tid % NS_SB, g = tid / NS_SB;
-            const int i = sb * NS_SB + r;
             if ((mode & NS_REDUCE) && i < n && q < k) {
                 const double* p = Rpart + (int64_t)i * KQ + q;
                 const int64_t stride = (int64_t)n * KQ;
                 double a8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
                 int b = g;
-                for (; b + 7 * NS_RED_GROUPS < nparts; b += 8 * NS_RED_GROUPS) {
+                for (; b + 7 * NG < nparts; b += 8 * NG) {
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) a8[u] += p[(int64_t)(b + u * NS_RED_GROUPS) * stride];
+                    for (int u = 0; u < 8; ++u) a8[u] += p[(int64_t)(b + u * NG) * stride];
                 }
-                for (; b < nparts; b += NS_RED_GROUPS) a8[0] += p[(int64_t)b * stride];
+                for (; b < nparts; b += NG) a8[0] += p[(int64_t)b * stride];
                 v = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
             }
-            red[g][r] = v;
-            __syncthreads();
-            if (tid < NS_SB) {
-                const int ii = sb * NS_SB + tid;
+            redf[g * NE + e] = v;
+        }
+        __syncthreads();
+        if (tid < NE) {  // g = 0, e = tid: row sb * 64 + r, RHS q
+            if (mode & NS_REDUCE) {
                 double t = 0.0;
-                if (mode & NS_REDUCE) {
 #pragma unroll
-                    for (int gg = 0; gg < NS_RED_GROUPS; ++gg) t += red[gg][tid];
-                    if (!(ii < n && q < k)) t = 0.0;
-                    if ((mode & NS_LAMBDA_Y) && ii < n && q < k) t -= lambda * Y[(int64_t)ii * KQ + q];
-                    if (R != nullptr) R[(int64_t)ii * KQ + q] = t;
-                    x[ii * KQ + q] = (T)t;
-                } else {
-                    x[ii * KQ + q] = (q < k) ? B[(int64_t)ii * ldb + q] : (T)0;
-                }
+                for (int gg = 0; gg < NG; ++gg) t += redf[gg * NE + tid];
+                if (!(i < n && q < k)) t = 0.0;
+                if ((mode & NS_LAMBDA_Y) && i < n && q < k) t -= lambda * Y[(int64_t)i * KQ + q];
+                if (R != nullptr) R[(int64_t)i * KQ + q] = t;
+                x[i * KQ + q] = (T)t;
+            } else {
+                x[i * KQ + q] = (q < k) ? B[(int64_t)i * ldb + q] : (T)0;
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
-    if (U2 != nullptr && U2part != nullptr && rank == 0 && warp == 0) {
-        for (int q = 0; q < 2 * KQ; ++q) {
-            double v = 0.0;
-            for (int b = lane; b < nparts; b += 32) v += U2part[(int64_t)b * 2 * KQ + q];
+    // the refinement's stopping sums: one warp per entry
+    if (U2 != nullptr && U2part != nullptr && rank == 0 && warp < 2 * KQ) {
+        const int q = warp;
+        double v = 0.0;
+        for (int b = lane; b < nparts; b += 32) v += U2part[(int64_t)b * 2 * KQ + q];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) U2[q] = v;
-        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) U2[q] = v;
     }
     __syncthreads();
     ns_cluster_sync();  // barriers initialised everywhere before any remote store

@@ -882,110 +882,135 @@ sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_
 // ||x_new - x_old||^2 per RHS (U2part, 2 KQ doubles per CTA).  Each warp owns whole k-blocks (64
 // columns): lane (chunk c = lane % 8, row group lane / 8) reads the 16-byte logical chunk c (8
 // columns) of rows lane / 8, + 4, + 8, ... (the four rows of a step are whole 128-byte lines), 8
-// steps in flight; dy sits in shared memory; the four row groups are added with shuffles and lanes
-// 0..7 update their 8 columns of x in place.
+// steps in flight; with 8 right-hand sides 16 lanes of 8 bytes cover a row and a warp has two row
+// groups.  dy sits in shared memory, each value twice, so that one 16-byte load gives the
+// operands of two right-hand sides' paired multiply-adds (each lane of a pair an IEEE fmaf, as in
+// scalar code); the row groups are added with shuffles and the lanes of row group 0 update their
+// columns of x in place.
 constexpr int TC_CORR_THREADS = 512;
-constexpr int TC_CORR_UNROLL = 8;
+constexpr int TC_CORR_ROWS = 32;  // n_rows is a multiple of the rows a warp has in flight
 
 template <int KQ>
 __global__ void __launch_bounds__(TC_CORR_THREADS)
 tile_correct_kernel(const unsigned char* __restrict__ Sp, int n, int n_rows, int64_t m, int64_t nkb,
                     const float* __restrict__ Z, int k, double lambda, float* __restrict__ X, int64_t ldx,
                     double* __restrict__ U2part, const DevStatus* st) {
-    extern __shared__ float sdy[];  // n_rows x KQ
+    // columns per lane: 8 (a 16-byte chunk), or 4 (half a chunk) with 8 right-hand sides, whose
+    // accumulators would not fit otherwise
+    constexpr int CPL = KQ >= 8 ? 4 : 8;
+    constexpr int LPRC = 64 / CPL;  // lanes per row
+    constexpr int RG = 32 / LPRC;   // row groups of a warp
+    constexpr int UNROLL = CPL == 4 ? 16 : 8;  // rows in flight per thread (128 bytes either way)
+    static_assert(RG * UNROLL <= TC_CORR_ROWS && TC_CORR_ROWS % (RG * UNROLL) == 0, "row step");
+    // dy twice per entry, [row][q][2]: the pair operand of the paired multiply-adds
+    extern __shared__ float sdy[];  // n_rows x KQ x 2
     __shared__ double red[TC_CORR_THREADS / 32][2 * KQ];
     if (block_should_exit(st, 1)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int e = tid; e < n_rows * KQ; e += TC_CORR_THREADS) sdy[e] = (e / KQ < n && e % KQ < k) ? Z[e] : 0.f;
+    for (int e = tid; e < n_rows * KQ; e += TC_CORR_THREADS) {
+        const float d = (e / KQ < n && e % KQ < k) ? Z[e] : 0.f;
+        sdy[2 * e] = d;
+        sdy[2 * e + 1] = d;
+    }
+    const int wpb = TC_CORR_THREADS / 32;
+    // the warp's sums of ||x_new||^2 and ||x_new - x_old||^2 per RHS (added by its lane 0)
+    for (int e = tid; e < wpb * 2 * KQ; e += TC_CORR_THREADS) red[e / (2 * KQ)][e % (2 * KQ)] = 0.0;
     __syncthreads();
-    const int c = lane & 7, rg = lane >> 3;
+    const int c = lane % LPRC, rg = lane / LPRC;
     const int T = n_rows >> 7;
     const float inv_l = (float)(1.0 / lambda);
-    double sx2[KQ], sd2[KQ];
-#pragma unroll
-    for (int q = 0; q < KQ; ++q) sx2[q] = sd2[q] = 0.0;
-    const int wpb = TC_CORR_THREADS / 32;
     for (int64_t kb = (int64_t)blockIdx.x * wpb + warp; kb < nkb; kb += (int64_t)gridDim.x * wpb) {
         const unsigned char* base = Sp + ((kb * T) << 14);
-        float acc[KQ][8];
+        float2 acc[KQ][CPL / 2];  // the lane's columns in pairs (0, 1), (2, 3), ...
 #pragma unroll
         for (int q = 0; q < KQ; ++q)
 #pragma unroll
-            for (int e = 0; e < 8; ++e) acc[q][e] = 0.f;
-        for (int r0 = 0; r0 < n_rows; r0 += 4 * TC_CORR_UNROLL) {
-            uint4 w[TC_CORR_UNROLL];
+            for (int e = 0; e < CPL / 2; ++e) acc[q][e] = make_float2(0.f, 0.f);
+        for (int r0 = 0; r0 < n_rows; r0 += RG * UNROLL) {
+            uint32_t w[UNROLL][CPL / 2];
 #pragma unroll
-            for (int u = 0; u < TC_CORR_UNROLL; ++u) {
-                const int r = r0 + 4 * u + rg;
-                w[u] = __ldg(reinterpret_cast<const uint4*>(base + ((r >> 7) << 14) + (r & 127) * 128 +
-                                                             ((c ^ (r & 7)) << 4)));
+            for (int u = 0; u < UNROLL; ++u) {
+                const int r = r0 + RG * u + rg;
+                const unsigned char* row = base + ((r >> 7) << 14) + (r & 127) * 128;
+                if constexpr (CPL == 8) {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + ((c ^ (r & 7)) << 4)));
+                    w[u][0] = v.x, w[u][1] = v.y, w[u][2] = v.z, w[u][3] = v.w;
+                } else {
+                    const uint2 v = __ldg(reinterpret_cast<const uint2*>(row + ((((c >> 1) ^ (r & 7)) << 4) | ((c & 1) << 3))));
+                    w[u][0] = v.x, w[u][1] = v.y;
+                }
             }
 #pragma unroll
-            for (int u = 0; u < TC_CORR_UNROLL; ++u) {
-                const int r = r0 + 4 * u + rg;
-                const uint32_t h[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-                float f[8];
+            for (int u = 0; u < UNROLL; ++u) {
+                const int r = r0 + RG * u + rg;
+                float2 f[CPL / 2];  // the BF16 pair of word e, widened exactly
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    f[2 * e] = __uint_as_float(h[e] << 16);
-                    f[2 * e + 1] = __uint_as_float(h[e] & 0xffff0000u);
-                }
+                for (int e = 0; e < CPL / 2; ++e)
+                    f[e] = make_float2(__uint_as_float(w[u][e] << 16), __uint_as_float(w[u][e] & 0xffff0000u));
+                if constexpr (KQ >= 2) {
 #pragma unroll
-                for (int q = 0; q < KQ; ++q) {
-                    const float d = sdy[r * KQ + q];
+                    for (int q = 0; q < KQ; q += 2) {
+                        const float4 d4 = *reinterpret_cast<const float4*>(&sdy[(r * KQ + q) * 2]);
+                        const float2 da = make_float2(d4.x, d4.y), db = make_float2(d4.z, d4.w);
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) acc[q][e] = fmaf(f[e], d, acc[q][e]);
+                        for (int e = 0; e < CPL / 2; ++e) {
+                            acc[q][e] = __ffma2_rn(f[e], da, acc[q][e]);
+                            acc[q + 1][e] = __ffma2_rn(f[e], db, acc[q + 1][e]);
+                        }
+                    }
+                } else {
+                    const float2 da = *reinterpret_cast<const float2*>(&sdy[r * 2]);
+#pragma unroll
+                    for (int e = 0; e < CPL / 2; ++e) acc[0][e] = __ffma2_rn(f[e], da, acc[0][e]);
                 }
             }
         }
+        // the row groups, in a fixed order
 #pragma unroll
         for (int q = 0; q < KQ; ++q)
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                acc[q][e] += __shfl_xor_sync(0xffffffffu, acc[q][e], 8);
-                acc[q][e] += __shfl_xor_sync(0xffffffffu, acc[q][e], 16);
-            }
-        if (rg == 0) {
+            for (int e = 0; e < CPL / 2; ++e)
 #pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                if (q >= k) continue;
-                float px = 0.f, pd = 0.f;
-                const int64_t j0 = kb * 64 + c * 8;
+                for (int o = LPRC; o < 32; o <<= 1) {
+                    acc[q][e].x += __shfl_xor_sync(0xffffffffu, acc[q][e].x, o);
+                    acc[q][e].y += __shfl_xor_sync(0xffffffffu, acc[q][e].y, o);
+                }
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            if (q >= k) continue;
+            float px = 0.f, pd = 0.f;
+            if (rg == 0) {
+                const int64_t j0 = kb * 64 + c * CPL;
                 float* xr = X + (int64_t)q * ldx;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
+                for (int e = 0; e < CPL; ++e) {
                     if (j0 + e < m) {
-                        const float du = acc[q][e] * inv_l;
+                        const float du = ((e & 1) ? acc[q][e >> 1].y : acc[q][e >> 1].x) * inv_l;
                         const float xn = xr[j0 + e] - du;
                         xr[j0 + e] = xn;
                         px = fmaf(xn, xn, px);
                         pd = fmaf(du, du, pd);
                     }
                 }
-                sx2[q] += (double)px;
-                sd2[q] += (double)pd;
+            }
+            // the lanes of a row in a fixed order, then into the warp's FP64 sums
+#pragma unroll
+            for (int o = 1; o < LPRC; o <<= 1) {
+                px += __shfl_xor_sync(0xffffffffu, px, o);
+                pd += __shfl_xor_sync(0xffffffffu, pd, o);
+            }
+            if (lane == 0) {
+                red[warp][q] += (double)px;
+                red[warp][KQ + q] += (double)pd;
             }
         }
     }
-    // per-CTA sums, in a fixed order: lanes 0..7 of each warp, then the warps
-#pragma unroll
-    for (int q = 0; q < KQ; ++q)
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            sx2[q] += __shfl_xor_sync(0xffffffffu, sx2[q], o);
-            sd2[q] += __shfl_xor_sync(0xffffffffu, sd2[q], o);
-        }
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-            red[warp][q] = sx2[q] * lambda * lambda;
-            red[warp][KQ + q] = sd2[q];
-        }
+    // per-CTA sums: the warps in order
     __syncthreads();
     if (tid < 2 * KQ) {
         double t = 0.0;
         for (int w = 0; w < wpb; ++w) t += red[w][tid];
-        U2part[(int64_t)blockIdx.x * 2 * KQ + tid] = t;
+        U2part[(int64_t)blockIdx.x * 2 * KQ + tid] = tid < KQ ? t * lambda * lambda : t;
     }
 }
 
@@ -993,11 +1018,16 @@ tile_correct_kernel(const unsigned char* __restrict__ Sp, int n, int n_rows, int
 // tile_correct_parts(num_sms) x 2 kq doubles.
 int tile_correct_parts(int num_sms) { return 4 * num_sms; }
 
+// Whether dy (n_rows x kq, stored twice) fits in the shared memory of one CTA.
+bool tile_correct_fits(int n_rows, int kq, size_t smem_limit) {
+    return (size_t)n_rows * kq * 2 * sizeof(float) + 4096 <= smem_limit;
+}
+
 cudaError_t launch_tile_correct(int kq, const void* Sp, int n, int n_rows, int64_t m, int64_t nkb, const float* Z,
                                 int k, double lambda, float* X, int64_t ldx, double* U2part, const DevStatus* st,
                                 int grid, cudaStream_t stream, int* parts) {
-    if (n_rows % (4 * TC_CORR_UNROLL) != 0) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)n_rows * kq * sizeof(float);
+    if (n_rows % TC_CORR_ROWS != 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)n_rows * kq * 2 * sizeof(float);
     const unsigned char* sp = static_cast<const unsigned char*>(Sp);
     // one wave of resident CTAs (grid = num_sms x CTAs per SM): the k-blocks are dealt statically
 #define DFS_TCC(KQ)                                                                                           \

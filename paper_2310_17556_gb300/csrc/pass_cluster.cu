@@ -6,14 +6,18 @@
 // <= 512 rows per CTA reach the copy rate, so here a cluster of cs = ceil(n / RC) CTAs shares
 // one strip of 64 columns (256 bytes per row): CTA `rank` owns rows [rank RC, rank RC + RC)
 // (RC = 32 RPT), keeps its RC x 64 slice in registers (16 lanes x 16 bytes per row, RPT rows per
-// thread) and stages the next strip's slice in shared memory with cp.async meanwhile.
+// thread) and stages the next strips' slices (about 128 KB) in shared memory with cp.async
+// meanwhile.
 // Per strip:
 //   phase 1  column sums of S^T Y over the CTA's rows (shuffle + shared memory), written to every
-//            CTA of the cluster with asynchronous remote stores that complete the transaction count
-//            of the receiver's mbarrier (no fence, so the next strip's loads stay in flight), then
-//            each CTA forms U = V - sum over ranks in rank order (so all ranks hold identical U);
+//            CTA of the cluster with asynchronous 16-byte remote stores that complete the
+//            transaction count of the receiver's mbarrier (no fence, so the next strip's loads stay
+//            in flight), then each CTA forms U = V - sum over ranks in rank order (so all ranks
+//            hold identical U);
 //            rank r writes X (and the stopping-rule sums) for columns c with floor(c cs / 64) = r;
 //   phase 2  per-row dot products with U into FP32 row sums, folded into FP64 every 32 strips.
+// The multiply-adds of both phases run as pairs (__ffma2_rn: two IEEE fmaf results per
+// instruction, the same values as scalar code).
 // Partials are per cluster: Rpart[c] holds all n rows (each rank its own rows), U2part[c] the
 // per-RHS sums (combined over ranks through rank 0).  The exchange buffers and their mbarriers are
 // double-buffered by strip parity: a rank sends strip s + 2's partials (same parity as s) only
@@ -31,6 +35,7 @@ constexpr int CL_W = CL_LPR * 4;         // strip width (FP32 columns)
 constexpr int CL_SWEEP = CL_THREADS / CL_LPR;  // 32 rows per sweep
 constexpr int CL_MAX_CS = 8;
 constexpr int CL_FOLD = 32;
+constexpr bool kPreferLaneAcc = true;  // see cluster_rpt
 
 __device__ __forceinline__ uint32_t cl_rank() {
     uint32_t r;
@@ -52,21 +57,57 @@ __device__ __forceinline__ void st_cluster_f32(const void* local, uint32_t rank,
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(r), "f"(v) : "memory");
 }
-// Asynchronous remote store of a float into CTA `rank`'s copy of `local`, completing 4 bytes of
-// the transaction count of that CTA's copy of mbarrier `bar`.
-__device__ __forceinline__ void st_async_f32(const void* local, const uint64_t* bar, uint32_t rank, float v) {
+// Asynchronous remote store of 16 bytes (4 floats at a 16-byte aligned `local`) into CTA `rank`'s
+// copy of `local`, completing 16 bytes of the transaction count of that CTA's copy of mbarrier
+// `bar`.
+__device__ __forceinline__ void st_async_v4(const void* local, const uint64_t* bar, uint32_t rank, float4 v) {
     uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local)), b = static_cast<uint32_t>(
                  __cvta_generic_to_shared(bar)), ra, rb;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rb) : "r"(b), "r"(rank));
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(ra),
-                 "r"(__float_as_uint(v)), "r"(rb)
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(ra),
+                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+                 "r"(__float_as_uint(v.w)), "r"(rb)
                  : "memory");
 }
 __device__ __forceinline__ void st_cluster_f64(const void* local, uint32_t rank, double v) {
     uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local)), r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(r), "d"(v) : "memory");
+}
+
+// Paired FP32 fused multiply-add: two IEEE fmaf results (round to nearest) in one instruction.
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2dup(float a) { return make_float2(a, a); }
+
+// Shared-memory layouts, chosen so that every access below is contiguous across the lanes that
+// make it (no bank conflicts) and 16 bytes wide where a lane moves several values:
+//   Ys    [row][q][2]        each y twice, the pair operand of phase 1's paired multiply-adds
+//   ured  [warp][q][col]     phase 1's per-warp column sums (float4 stores of 4 columns)
+//   pbuf  [par][rank][q][col] the ranks' column sums
+//   us    u_{col,q} for phase 2: KQ >= 2 as [q / 2][col % 4 / 2][col / 4][col % 2][q % 2], so a lane
+//         reads the (q, q + 1) pairs of its 4 columns as two float4 loads; KQ = 1 as [col]
+template <int KQ>
+__device__ __forceinline__ int us_index(int c, int q) {
+    if constexpr (KQ >= 2)
+        return ((((q >> 1) * 2 + ((c & 3) >> 1)) * (CL_W / 4) + (c >> 2)) * 2 + (c & 1)) * 2 + (q & 1);
+    else
+        return c;
+}
+
+// Shared memory of a CTA beyond its stage ring (row sums, y, the exchange buffers, u).
+constexpr size_t cl_rest_bytes(int rpt, int kq) {
+    return (size_t)rpt * CL_SWEEP * kq * (8 + 4 + 8) + (size_t)CL_WARPS * CL_W * kq * 4 +
+           (size_t)2 * CL_MAX_CS * CL_W * kq * 4 + (size_t)CL_W * kq * 4;
+}
+// Strips in flight in the stage ring: about 128 KB of S per CTA (HBM latency x the SM's share of
+// the bandwidth is ~66 KB), as far as shared memory allows.
+constexpr int cl_depth(int rpt, int kq) {
+    const size_t strip = (size_t)rpt * CL_THREADS * 16;
+    int d = (int)(131072 / strip);
+    d = d > 4 ? 4 : (d < 1 ? 1 : d);
+    while (d > 1 && d * strip + cl_rest_bytes(rpt, kq) > 220 * 1024) d >>= 1;
+    return d;
 }
 
 template <int KQ, int RPT>
@@ -76,15 +117,17 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
                            float* __restrict__ X, int64_t ldx, double* __restrict__ Rpart,
                            double* __restrict__ U2part, int dmode, const DevStatus* st, int honor_stop) {
     constexpr int RC = RPT * CL_SWEEP;  // rows per CTA
+    constexpr int KP = KQ >= 2 ? KQ / 2 : 1;  // right-hand-side pairs of phase 2
+    constexpr int DEPTH = cl_depth(RPT, KQ);  // strips of the stage ring
     extern __shared__ __align__(16) unsigned char smem[];
-    uint4* stage = reinterpret_cast<uint4*>(smem);                                  // RPT x 512 x 16 B
-    double* Rs64 = reinterpret_cast<double*>(smem + (size_t)RPT * CL_THREADS * 16);  // RC x KQ
+    uint4* stage = reinterpret_cast<uint4*>(smem);  // DEPTH x RPT x 512 x 16 B
+    double* Rs64 = reinterpret_cast<double*>(smem + (size_t)DEPTH * RPT * CL_THREADS * 16);  // RC x KQ
     float* Rs32 = reinterpret_cast<float*>(Rs64 + RC * KQ);                         // RC x KQ
-    float* Ys = Rs32 + RC * KQ;                                                      // RC x KQ
-    float* ured = Ys + RC * KQ;                                                      // warps x W x KQ
-    float* pbuf = ured + CL_WARPS * CL_W * KQ;                                       // 2 x MAX_CS x W x KQ
-    float* us = pbuf + 2 * CL_MAX_CS * CL_W * KQ;                                    // W x KQ
-    __shared__ double u2s[CL_WARPS][16];
+    float* Ys = Rs32 + RC * KQ;                                                      // RC x KQ x 2
+    float* ured = Ys + RC * KQ * 2;                                                  // warps x KQ x W
+    float* pbuf = ured + CL_WARPS * KQ * CL_W;                                       // 2 x MAX_CS x KQ x W
+    float* us = pbuf + 2 * CL_MAX_CS * KQ * CL_W;                                    // W x KQ
+    __shared__ double u2s[CL_WARPS][2];
     __shared__ double u2c[CL_MAX_CS][16];
     __shared__ __align__(8) uint64_t xbar[2];  // partials from the other ranks landed (by parity)
     __shared__ int s_abort;
@@ -107,20 +150,25 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         const int i = r0 + e / KQ, q = e % KQ;
         Rs64[e] = 0.0;
         Rs32[e] = 0.f;
-        Ys[e] = (haveY && i < n && q < k) ? (float)Y[(int64_t)i * ldy + q] : 0.f;
+        const float y = (haveY && i < n && q < k) ? (float)Y[(int64_t)i * ldy + q] : 0.f;
+        Ys[2 * e] = y;
+        Ys[2 * e + 1] = y;
     }
     const int64_t nstrips = ceil_div(m, CL_W);
     const int lrow0 = warp * 2 + rr;  // local row of t = 0
-    // The strip's rows arrive in NSUB sub-stages (rows t in [j RPT/NSUB, (j+1) RPT/NSUB) of every
-    // thread); slot j of the ring is refilled with the next strip's sub-stage j as soon as this
-    // thread has moved it into registers, so about one strip stays in flight at all times.
+    // A strip's rows arrive in NSUB sub-stages (rows t in [j RPT/NSUB, (j+1) RPT/NSUB) of every
+    // thread) in ring slot g mod DEPTH (g: the CTA's strip count); sub-stage j of a slot is
+    // refilled with strip g + DEPTH's as soon as this thread has moved it into registers (each
+    // thread copies and reads only its own 16-byte pieces, so no barrier), so about DEPTH strips
+    // stay in flight at all times.
     constexpr int NSUB = RPT >= 4 ? 4 : RPT;
     constexpr int TPS = RPT / NSUB;  // rows per thread per sub-stage
-    auto issue_sub = [&](int64_t sidx, int j) {
+    auto issue_sub = [&](int64_t sidx, int64_t g, int j) {
         if (sidx < nstrips) {
             const int64_t jn = sidx * CL_W + cq * 4;
             const int64_t rem = m - jn;
             const int bytes_col = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+            uint4* slot = stage + (size_t)(g % DEPTH) * RPT * CL_THREADS;
 #pragma unroll
             for (int tt = 0; tt < TPS; ++tt) {
                 const int t = j * TPS + tt;
@@ -128,7 +176,7 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
                 const int bytes = i < n ? bytes_col : 0;
                 const float* src = bytes ? S + (int64_t)i * lds + jn : S;
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
-                                 static_cast<uint32_t>(__cvta_generic_to_shared(&stage[t * CL_THREADS + tid]))),
+                                 static_cast<uint32_t>(__cvta_generic_to_shared(&slot[t * CL_THREADS + tid]))),
                              "l"(src), "r"(bytes)
                              : "memory");
             }
@@ -136,14 +184,18 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         asm volatile("cp.async.commit_group;" ::: "memory");  // (empty past the last strip)
     };
 #pragma unroll
-    for (int j = 0; j < NSUB; ++j) issue_sub(cid, j);
-    float u2f[KQ], d2f[KQ];
-    double u2[KQ], d2[KQ];
+    for (int d = 0; d < DEPTH; ++d)
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) u2f[q] = d2f[q] = 0.f, u2[q] = d2[q] = 0.0;
+        for (int j = 0; j < NSUB; ++j) issue_sub(cid + d * ncl, d, j);
+    // A thread of the first KQ x 64 forms u for column uc and right-hand side uq of every strip
+    // (a warp: 32 consecutive columns of one right-hand side), and keeps that RHS's stopping-rule
+    // sums.
     const bool u_thread = tid < CL_W * KQ;
-    const int uc = tid / KQ, uq = tid % KQ;
+    const int uc = tid % CL_W, uq = tid / CL_W;
     const bool writer = u_thread && (uc * (int)cs) / CL_W == (int)rank;  // ranks split the columns
+    const int us_at = us_index<KQ>(uc, uq);
+    float u2f = 0.f, d2f = 0.f;
+    double u2 = 0.0, d2 = 0.0;
     if (tid == 0) {
         tc::mbar_init(&xbar[0], 1);
         tc::mbar_init(&xbar[1], 1);
@@ -156,32 +208,39 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
     cl_sync();  // every CTA of the cluster is running (and its barriers initialised) before any remote store
 
     // Phase 2's row sums: with few rows and right-hand sides a lane keeps its own partial sums
-    // (its 4 columns of every strip) in registers and the 16 lanes of a row are added only at
-    // each fold, in place of 4 shuffles per row and right-hand side on every strip.
+    // (its 4 columns of every strip) in registers, as (q, q + 1) pairs, and the 16 lanes of a row
+    // are added only at each fold, in place of 4 shuffles per row and right-hand side on every
+    // strip.
     constexpr bool kLaneAcc = RPT * KQ <= 32;
-    float racc[kLaneAcc ? RPT : 1][kLaneAcc ? KQ : 1];
+    constexpr int LR = kLaneAcc ? RPT : 1, LP = kLaneAcc ? KP : 1;
+    float2 racc[LR][LP];
 #pragma unroll
-    for (int t = 0; t < (kLaneAcc ? RPT : 1); ++t)
+    for (int t = 0; t < LR; ++t)
 #pragma unroll
-        for (int q = 0; q < (kLaneAcc ? KQ : 1); ++q) racc[t][q] = 0.f;
+        for (int p = 0; p < LP; ++p) racc[t][p] = make_float2(0.f, 0.f);
     auto fold_lanes = [&]() {
 #pragma unroll
-        for (int t = 0; t < (kLaneAcc ? RPT : 1); ++t) {
+        for (int t = 0; t < LR; ++t) {
             const int li = lrow0 + t * CL_SWEEP;
 #pragma unroll
-            for (int q = 0; q < (kLaneAcc ? KQ : 1); ++q) {
-                float a = racc[t][q];
-                a += __shfl_xor_sync(0xffffffffu, a, 1);
-                a += __shfl_xor_sync(0xffffffffu, a, 2);
-                a += __shfl_xor_sync(0xffffffffu, a, 4);
-                a += __shfl_xor_sync(0xffffffffu, a, 8);
-                if (cq == 0) Rs64[li * KQ + q] += (double)a;
-                racc[t][q] = 0.f;
+            for (int p = 0; p < LP; ++p) {
+                float a = racc[t][p].x, b = racc[t][p].y;
+#pragma unroll
+                for (int o = 1; o < CL_LPR; o <<= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    if constexpr (KQ >= 2) b += __shfl_xor_sync(0xffffffffu, b, o);
+                }
+                if (cq == 0) {
+                    Rs64[li * KQ + (KQ >= 2 ? 2 * p : 0)] += (double)a;
+                    if constexpr (KQ >= 2) Rs64[li * KQ + 2 * p + 1] += (double)b;
+                }
+                racc[t][p] = make_float2(0.f, 0.f);
             }
         }
     };
     int since_fold = 0, par = 0;
-    for (int64_t s = cid; s < nstrips; s += ncl, par ^= 1) {
+    int64_t g = 0;  // strips of this CTA so far
+    for (int64_t s = cid; s < nstrips; s += ncl, par ^= 1, ++g) {
         const int64_t j0 = s * CL_W;
         float sv[RPT][4];
         float v_pre = 0.f, x_pre = 0.f;
@@ -193,31 +252,40 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         // ---- phase 1: this CTA's column sums of S^T Y -> every rank's pbuf[par][rank] ----
         const bool exch = haveY && cs > 1;
         if (exch && tid == 0 && !s_abort) tc::mbar_arrive_expect_tx(&xbar[par], xbytes);
-        float acc[KQ][4];
+        float2 acc[KQ][2];  // columns (0, 1) and (2, 3) of this lane
 #pragma unroll
-        for (int q = 0; q < KQ; ++q)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
+        for (int q = 0; q < KQ; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < NSUB; ++j) {
-            // sub-stage j of strip s is the oldest pending group but NSUB - 1
-            asm volatile("cp.async.wait_group %0;" ::"n"(NSUB - 1) : "memory");
+            // sub-stage j of strip s is the oldest pending group but DEPTH NSUB - 1
+            asm volatile("cp.async.wait_group %0;" ::"n"(DEPTH * NSUB - 1) : "memory");
+            const uint4* slot = stage + (size_t)(g % DEPTH) * RPT * CL_THREADS;
 #pragma unroll
             for (int tt = 0; tt < TPS; ++tt) {
                 const int t = j * TPS + tt;
-                load16_smem<float, float>(reinterpret_cast<const float*>(&stage[t * CL_THREADS + tid]), sv[t]);
+                load16_smem<float, float>(reinterpret_cast<const float*>(&slot[t * CL_THREADS + tid]), sv[t]);
             }
-            issue_sub(s + ncl, j);
+            issue_sub(s + DEPTH * ncl, g + DEPTH, j);
             if (haveY) {
 #pragma unroll
                 for (int tt = 0; tt < TPS; ++tt) {
                     const int t = j * TPS + tt;
                     const int li = lrow0 + t * CL_SWEEP;
+                    const float2 s01 = make_float2(sv[t][0], sv[t][1]), s23 = make_float2(sv[t][2], sv[t][3]);
+                    if constexpr (KQ >= 2) {
 #pragma unroll
-                    for (int q = 0; q < KQ; ++q) {
-                        const float yv = Ys[li * KQ + q];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) acc[q][e] = fmaf(sv[t][e], yv, acc[q][e]);
+                        for (int q = 0; q < KQ; q += 2) {
+                            const float4 y4 = *reinterpret_cast<const float4*>(&Ys[(li * KQ + q) * 2]);
+                            const float2 ya = make_float2(y4.x, y4.y), yb = make_float2(y4.z, y4.w);
+                            acc[q][0] = f2fma(s01, ya, acc[q][0]);
+                            acc[q][1] = f2fma(s23, ya, acc[q][1]);
+                            acc[q + 1][0] = f2fma(s01, yb, acc[q + 1][0]);
+                            acc[q + 1][1] = f2fma(s23, yb, acc[q + 1][1]);
+                        }
+                    } else {
+                        const float2 ya = *reinterpret_cast<const float2*>(&Ys[li * 2]);
+                        acc[0][0] = f2fma(s01, ya, acc[0][0]);
+                        acc[0][1] = f2fma(s23, ya, acc[0][1]);
                     }
                 }
             }
@@ -226,27 +294,36 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
 #pragma unroll
             for (int q = 0; q < KQ; ++q)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[q][e] += __shfl_xor_sync(0xffffffffu, acc[q][e], 16);
+                for (int h = 0; h < 2; ++h) {
+                    acc[q][h].x += __shfl_xor_sync(0xffffffffu, acc[q][h].x, 16);
+                    acc[q][h].y += __shfl_xor_sync(0xffffffffu, acc[q][h].y, 16);
+                }
             if (rr == 0) {
 #pragma unroll
                 for (int q = 0; q < KQ; ++q)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) ured[(warp * CL_W + cq * 4 + e) * KQ + q] = acc[q][e];
+                    *reinterpret_cast<float4*>(&ured[(warp * KQ + q) * CL_W + cq * 4]) =
+                        make_float4(acc[q][0].x, acc[q][0].y, acc[q][1].x, acc[q][1].y);
             }
             __syncthreads();
+            float* qslot = pbuf + ((size_t)(par * CL_MAX_CS + rank) * KQ + uq) * CL_W + (uc & ~3);
             if (u_thread) {
                 float p = 0.f;
 #pragma unroll 4
-                for (int w = 0; w < CL_WARPS; ++w) p += ured[(w * CL_W + uc) * KQ + uq];
-                float* slot = pbuf + ((size_t)(par * CL_MAX_CS + rank) * CL_W + uc) * KQ + uq;
-                *slot = p;
+                for (int w = 0; w < CL_WARPS; ++w) p += ured[(w * KQ + uq) * CL_W + uc];
+                qslot[uc & 3] = p;
+            }
+            __syncwarp();
+            if (u_thread) {
+                // the 4 lanes of a column quad send its 16 bytes to the other ranks, lane j to the
+                // peers j, j + 4 after this rank, one asynchronous remote store each
                 // (test hook: rank 1 of the first cluster withholds its first strip's partials, so
                 // the other ranks' bounded waits for them run out)
                 const bool withhold = fault == DFS_TEST_FAULT_CLUSTER_PASS && cid == 0 && rank == 1 && s == cid;
-                for (uint32_t r = 0; r < cs; ++r)
-                    if (r != rank && !withhold) st_async_f32(slot, &xbar[par], r, p);
+                const float4 v4 = *reinterpret_cast<const float4*>(qslot);
+                for (int pi = uc & 3; pi < (int)cs - 1; pi += 4)
+                    if (!withhold) st_async_v4(qslot, &xbar[par], (rank + 1 + (uint32_t)pi) % cs, v4);
             }
-            __syncthreads();
+            // (ured is rewritten only after the barrier below that ends this strip's u step)
         }
         // ---- U = V - S^T Y (ranks summed in order), X = U / lambda ----
         if (exch && u_thread) {
@@ -259,47 +336,74 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         if (u_thread) {
             float sum = 0.f;
             if (haveY)
-                for (uint32_t r = 0; r < cs; ++r) sum += pbuf[((size_t)(par * CL_MAX_CS + r) * CL_W + uc) * KQ + uq];
+                for (uint32_t r = 0; r < cs; ++r) sum += pbuf[((size_t)(par * CL_MAX_CS + r) * KQ + uq) * CL_W + uc];
             const float u = u_valid ? v_pre - sum : 0.f;
-            us[uc * KQ + uq] = u;
+            us[us_at] = u;
             if (u_valid && writer) {
                 if (X != nullptr) {
                     const float xn = u * inv_lambda;
                     float dx = 0.f;
                     if (dmode == 1) dx = xn - x_pre;
                     else if (dmode == 2) dx = (u - v_pre) * inv_lambda;
-                    d2f[uq] += dx * dx;
+                    d2f += dx * dx;
                     X[(int64_t)uq * ldx + j0 + uc] = xn;
                 }
-                u2f[uq] += u * u;
+                u2f += u * u;
             }
         }
         __syncthreads();
         // ---- phase 2: R_rows += S_strip U_strip ----
         if (wantR) {
-            float uu[KQ][4];
+            if constexpr (KQ >= 2) {
 #pragma unroll
-            for (int q = 0; q < KQ; ++q)
+                for (int p = 0; p < KP; ++p) {
+                    const float4 ua = *reinterpret_cast<const float4*>(&us[((p * 2 + 0) * (CL_W / 4) + cq) * 4]);
+                    const float4 ub = *reinterpret_cast<const float4*>(&us[((p * 2 + 1) * (CL_W / 4) + cq) * 4]);
+                    // (u_{c,2p}, u_{c,2p+1}) for the lane's columns c = 4 cq + e
+                    const float2 up[4] = {make_float2(ua.x, ua.y), make_float2(ua.z, ua.w), make_float2(ub.x, ub.y),
+                                          make_float2(ub.z, ub.w)};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) uu[q][e] = us[(cq * 4 + e) * KQ + q];
+                    for (int t = 0; t < RPT; ++t) {
+                        if constexpr (kLaneAcc) {
+                            // this lane's 4 columns only; the 16 lanes of the row are added at the fold
 #pragma unroll
-            for (int t = 0; t < RPT; ++t) {
-                const int li = lrow0 + t * CL_SWEEP;
+                            for (int e = 0; e < 4; ++e) racc[t][p] = f2fma(f2dup(sv[t][e]), up[e], racc[t][p]);
+                        } else {
+                            float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int q = 0; q < KQ; ++q) {
+                            for (int e = 0; e < 4; ++e) a = f2fma(f2dup(sv[t][e]), up[e], a);
+#pragma unroll
+                            for (int o = 1; o < CL_LPR; o <<= 1) {
+                                a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+                                a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+                            }
+                            if (cq == 0) {
+                                const int li = lrow0 + t * CL_SWEEP;
+                                Rs32[li * KQ + 2 * p] += a.x;
+                                Rs32[li * KQ + 2 * p + 1] += a.y;
+                            }
+                        }
+                    }
+                }
+            } else {
+                const float4 u4 = *reinterpret_cast<const float4*>(&us[cq * 4]);
+#pragma unroll
+                for (int t = 0; t < RPT; ++t) {
                     if constexpr (kLaneAcc) {
-                        // this lane's 4 columns only; the 16 lanes of the row are added at the fold
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) racc[t][q] = fmaf(sv[t][e], uu[q][e], racc[t][q]);
+                        float a = racc[t][0].x;
+                        a = fmaf(sv[t][0], u4.x, a);
+                        a = fmaf(sv[t][1], u4.y, a);
+                        a = fmaf(sv[t][2], u4.z, a);
+                        a = fmaf(sv[t][3], u4.w, a);
+                        racc[t][0].x = a;
                     } else {
-                        float a = 0.f;
+                        float a = sv[t][0] * u4.x;
+                        a = fmaf(sv[t][1], u4.y, a);
+                        a = fmaf(sv[t][2], u4.z, a);
+                        a = fmaf(sv[t][3], u4.w, a);
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) a = fmaf(sv[t][e], uu[q][e], a);
-                        a += __shfl_xor_sync(0xffffffffu, a, 1);
-                        a += __shfl_xor_sync(0xffffffffu, a, 2);
-                        a += __shfl_xor_sync(0xffffffffu, a, 4);
-                        a += __shfl_xor_sync(0xffffffffu, a, 8);
-                        if (cq == 0) Rs32[li * KQ + q] += a;
+                        for (int o = 1; o < CL_LPR; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                        if (cq == 0) Rs32[(lrow0 + t * CL_SWEEP) * KQ] += a;
                     }
                 }
             }
@@ -316,15 +420,12 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
                         Rs32[li * KQ + q] = 0.f;
                     }
             }
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                u2[q] += (double)u2f[q];
-                d2[q] += (double)d2f[q];
-                u2f[q] = d2f[q] = 0.f;
-            }
+            u2 += (double)u2f;
+            d2 += (double)d2f;
+            u2f = d2f = 0.f;
         }
-        // us is rewritten by the next strip only after its cluster barrier, which every thread
-        // of this CTA reaches after finishing phase 2 here
+        // us is rewritten by the next strip only after that strip's first barrier, which every
+        // thread of this CTA reaches after finishing phase 2 here
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     if constexpr (kLaneAcc) {
@@ -334,11 +435,8 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
 #pragma unroll
             for (int q = 0; q < KQ; ++q) Rs64[li * KQ + q] += (double)Rs32[li * KQ + q];
     }
-#pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-        u2[q] += (double)u2f[q];
-        d2[q] += (double)d2f[q];
-    }
+    u2 += (double)u2f;
+    d2 += (double)d2f;
     __syncthreads();
     if (wantR) {
         double* dst = Rpart + cid * (int64_t)n * KQ;
@@ -347,24 +445,24 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
             if (i < n) dst[(int64_t)i * KQ + e % KQ] = Rs64[e];
         }
     }
-    // per-RHS sums of U^2 and dX^2: warps -> CTA -> rank 0 (ranks in order) -> U2part[cid]
+    // per-RHS sums of U^2 and dX^2: lanes -> warp; the two warps of a right-hand side -> CTA;
+    // ranks in order -> rank 0 -> U2part[cid] (u2 for q = 0..KQ-1, then dX^2)
+    {
+        double v = u2, w = d2;
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-        double v = u2[q], w = d2[q];
         for (int o = 16; o > 0; o >>= 1) {
             v += __shfl_xor_sync(0xffffffffu, v, o);
             w += __shfl_xor_sync(0xffffffffu, w, o);
         }
         if (lane == 0) {
-            u2s[warp][q] = v;
-            u2s[warp][8 + q] = w;
+            u2s[warp][0] = v;
+            u2s[warp][1] = w;
         }
     }
     __syncthreads();
     if (tid < 2 * KQ) {
-        const int slot = tid < KQ ? tid : 8 + (tid - KQ);
-        double v = 0.0;
-        for (int wp = 0; wp < CL_WARPS; ++wp) v += u2s[wp][slot];
+        const int q = tid % KQ, which = tid / KQ;
+        const double v = u2s[2 * q][which] + u2s[2 * q + 1][which];
         st_cluster_f64(&u2c[rank][tid], 0, v);
     }
     cl_sync();
@@ -378,12 +476,16 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
 // ---- host side ------------------------------------------------------------------------------
 
 // Rows per thread for n rows split over cs CTAs of at most 512 rows; 0 if the cluster form does
-// not apply (needs FP32 S, KQ <= 4, n <= 4096).
+// not apply (needs FP32 S, KQ <= 8, n <= 4096; n <= 2048 for KQ = 8).  Where n fits in 8 CTAs
+// whose lanes can keep their row sums in registers (RPT KQ <= 32), those are used.
 static int cluster_rpt(int n, int KQ, int* cs_out) {
+    if (KQ > 8) return 0;
+    const int lane_rpt = KQ >= 2 ? 32 / KQ < 16 ? 32 / KQ : 16 : 16;
     // eight right-hand sides fill all 512 threads with column sums and hold twice the
     // accumulators: at most 8 rows a thread (256 a CTA), so n <= 2048
-    const int max_rpt = KQ == 8 ? 8 : 16;
-    if (KQ > 8 || n > CL_MAX_CS * max_rpt * CL_SWEEP) return 0;
+    int max_rpt = KQ == 8 ? 8 : 16;
+    if (kPreferLaneAcc && n <= CL_MAX_CS * lane_rpt * CL_SWEEP) max_rpt = lane_rpt;
+    if (n > CL_MAX_CS * max_rpt * CL_SWEEP) return 0;
     const int cs = (n + max_rpt * CL_SWEEP - 1) / (max_rpt * CL_SWEEP);
     const int per = (n + cs - 1) / cs;
     int rpt = 4;
@@ -393,9 +495,7 @@ static int cluster_rpt(int n, int KQ, int* cs_out) {
 }
 
 static size_t cluster_smem_bytes(int rpt, int KQ) {
-    const size_t rc = (size_t)rpt * CL_SWEEP;
-    return (size_t)rpt * CL_THREADS * 16 + rc * KQ * (8 + 4 + 4) + (size_t)CL_WARPS * CL_W * KQ * 4 +
-           (size_t)2 * CL_MAX_CS * CL_W * KQ * 4 + (size_t)CL_W * KQ * 4;
+    return (size_t)cl_depth(rpt, KQ) * rpt * CL_THREADS * 16 + cl_rest_bytes(rpt, KQ);
 }
 
 template <int KQ, int RPT>
