@@ -13,7 +13,7 @@ than L2, so no L2 flush is needed between steps).  The plain FP32 path is timed 
 every reported solution is compared with the FP64 oracle's on the full problem.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --workload precision|batch|stress     (the other configurations, one GPU)
+    python bench.py --workload precision|batch|stress|complex     (the other configurations, one GPU)
 
 N > 1 runs under torchrun; every rank solves its own independent problem (weak scaling, no
 collective on the data path).  Prints one JSON line on rank 0.
@@ -616,7 +616,10 @@ def run_workload(args):
       precision  n=4096, m=2^22, k=4, FP32 S with singular values log-spaced 1/sqrt(n) .. 1e-4/sqrt(n),
                  lambda=1e-4; BF16 and FP8 Gram.  cond(A) ~ 3.4, so the FP64 residual bounds e_rel.
       batch      64 independent problems, n ~ U{64..1024}, m log-uniform in [1e4, 5e5], lambda log-uniform
-                 in [1e-5, 1e-1], k=8; dfs_solve_batched against one dfs_solve after another.
+                 in [1e-5, 1e-1], k=8; dfs_solve_batched (concurrency from dfs_autotune_batched) against
+                 one dfs_solve after another and against the plain FP32 path on the same batch.
+      complex    n=512, m=2^18, k=1 complex SR: dfs_solve_complex on stacked planes against dfs_solve on
+                 the real 2n x 2m representation of the same problem.
       stress     n=8192, m=2^22, BF16 S with Student-t entries and log-normal column scales,
                  lambda=1e-5, k=1; the FP64 residual against the FP32-storage floor of x.
     Each timed region holds the solves only (inputs resident in HBM and larger than L2)."""
@@ -679,9 +682,11 @@ def run_workload(args):
         probs = []
         for j, (n, m, lam) in enumerate(shapes):
             m = (m + 3) // 4 * 4
-            probs.append((wl.gaussian(n, m, seed=base + 400 + j, device=dev), wl.rhs(m, 8, seed=base + 700 + j, device=dev),
-                          lam, None))
-        probs = [(S, V, lam, torch.empty_like(V)) for S, V, lam, _ in probs]
+            S = wl.gaussian(n, m, seed=base + 400 + j, device=dev)
+            V = wl.rhs(m, 8, seed=base + 700 + j, device=dev)
+            probs.append((S, V, lam, torch.empty_like(V)))
+        # concurrency chosen by the library's autotuner on this batch (lanes x SM share)
+        tune = dfs.dfs_autotune_batched(probs, precision="bf16")
         batch = lambda: dfs.dfs_solve_batched(probs, precision="bf16", sync=False)
         loop = lambda: [dfs.dfs_solve(S, V, lam, X=X, precision="bf16", sync=False) for S, V, lam, X in probs]
         for fn in (batch, loop):
@@ -692,36 +697,96 @@ def run_workload(args):
         clocks = _clock_summary(clk)
         ms_l = timed(loop, steps)
         _, status = dfs.dfs_solve_batched(probs, precision="bf16")
+        X_mixed = [X.clone() for _, _, _, X in probs]
+        # the plain FP32 path (SIMT Gram, no refinement) on the same batch
+        fp32 = lambda: dfs.dfs_solve_batched(probs, precision="fp32", sync=False)
+        fp32()
+        ms_f = timed(fp32, max(1, min(steps, 3)))
+        _, status_f = dfs.dfs_solve_batched(probs, precision="fp32")
+        X_fp32 = [X.clone() for _, _, _, X in probs]
         import oracle
 
         import numpy as np
 
-        small = sorted(range(len(probs)), key=lambda j: probs[j][0].numel())[:4]
-        errs = []
-        t_oracle = 0.0
-        for j in small:
-            S, V, lam, X = probs[j]
+        # the oracle on a spread of the batch: the smallest, the median and the largest problem by
+        # cost n^2 m + 4 n m k; the batch's CPU time from a fit t = a + b cost over the three
+        cost = lambda p: p[0].shape[0] ** 2 * p[0].shape[1] + 4 * p[0].shape[0] * p[0].shape[1] * p[1].shape[0]
+        by_cost = sorted(range(len(probs)), key=lambda j: cost(probs[j]))
+        sample = [by_cost[0], by_cost[len(by_cost) // 2], by_cost[-1]]
+        samples, err_mixed, err_fp32 = [], [], []
+        for j in sample:
+            S, V, lam, _ = probs[j]
             s64, v64 = S.double().cpu().numpy(), V.double().cpu().numpy().T
             t0 = time.perf_counter()
             ref = oracle.solve(s64, v64, lam).T
-            t_oracle += time.perf_counter() - t0
-            x = X.double().cpu().numpy()
-            errs.append(float(np.max(np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1))))
-        # the oracle's time for the whole batch, scaled from the sample by n^2 m + 4 n m k
-        cost = lambda p: p[0].shape[0] ** 2 * p[0].shape[1] + 4 * p[0].shape[0] * p[0].shape[1] * p[1].shape[0]
-        t_all = t_oracle * sum(cost(p) for p in probs) / sum(cost(probs[j]) for j in small)
+            dt = time.perf_counter() - t0
+            rel = lambda X: float(np.max(np.linalg.norm(X.double().cpu().numpy() - ref, axis=1) /
+                                         np.linalg.norm(ref, axis=1)))
+            err_mixed.append(rel(X_mixed[j]))
+            err_fp32.append(rel(X_fp32[j]))
+            samples.append({"n": S.shape[0], "m": S.shape[1], "k": V.shape[0], "s": round(dt, 3)})
+            del s64, v64, ref
+        cs = np.array([float(cost(probs[j])) for j in sample])
+        ts = np.array([x["s"] for x in samples])
+        b_fit, a_fit = np.polyfit(cs, ts, 1)
+        a_fit = max(float(a_fit), 0.0)
+        t_all = sum(a_fit + float(b_fit) * cost(p) for p in probs)
+        ok = all(x == 0 for x in status) and max(err_mixed) <= 1e-6
         emit({"workload": "batch", "metric": "problems/s, 64 ragged problems, k=8", "value": 64e3 / ms_b,
               "unit": "problems/s", "ms_per_step": ms_b, "dtype": "bf16", "clocks": clocks,
+              "autotune": {"lanes": tune["lanes"], "share": tune["share"], "ms": tune["ms"]},
               "sequential": {"value": 64e3 / ms_l, "ms_per_step": ms_l, "api": "one dfs_solve after another"},
+              "fp32_path": {"value": 64e3 / ms_f, "ms_per_step": ms_f, "statuses_ok": all(x == 0 for x in status_f),
+                            "e_rel_sampled_vs_oracle": err_fp32,
+                            "note": "the plain FP32 path (FFMA Gram, no refinement) on the same batch"},
               "config": {"problems": 64, "n": "U{64..1024}", "m": "log-uniform [1e4, 5e5]",
                          "lambda": "log-uniform [1e-5, 1e-1]", "k": 8,
                          "S_bytes": sum(p[0].numel() * 4 for p in probs)},
-              "accuracy": {"statuses_ok": all(x == 0 for x in status), "e_rel_4_smallest_vs_oracle": errs,
-                           "ok": all(x == 0 for x in status) and max(errs) <= 1e-6},
+              "accuracy": {"statuses_ok": all(x == 0 for x in status), "e_rel_sampled_vs_oracle": err_mixed,
+                           "ok": ok},
               "cpu_baseline": {"value": len(probs) / t_all, "unit": "problems/s", "cores": os.cpu_count(),
-                               "kind": "oracle",
-                               "sample": f"FP64 oracle on the {len(small)} smallest problems in {t_oracle:.2f} s, "
-                                         "scaled to all 64 by n^2 m + 4 n m k"}})
+                               "kind": "oracle", "samples": samples,
+                               "fit": {"a_s": a_fit, "b_s_per_cost": float(b_fit)},
+                               "sample": "FP64 oracle on the smallest, median and largest problem by cost "
+                                         "n^2 m + 4 n m k; batch time from the fit t = a + b cost"}})
+    elif args.workload == "complex":
+        # complex SR (Section 4): the native route on the stacked planes against the real 2n x 2m
+        # representation [[A, -B], [B, A]] solved by dfs_solve (the same Eq. 1), n=512, m=2^18
+        n, m, k, lam = 512, 1 << 18, 1, 1e-3
+        Z = torch.cat([wl.gaussian(n, m, seed=base + 20, device=dev), wl.gaussian(n, m, seed=base + 21, device=dev)],
+                      dim=0) / 2 ** 0.5
+        A, B = Z[:n], Z[n:]
+        Vr, Vi = wl.rhs(m, k, seed=base + 22, device=dev), wl.rhs(m, k, seed=base + 23, device=dev)
+        RS = torch.cat([torch.cat([A, -B], dim=1), torch.cat([B, A], dim=1)], dim=0)
+        V2 = torch.cat([Vr, Vi], dim=1)
+        native = lambda: dfs.dfs_solve_complex(A, B, Vr, Vi, lam, precision="bf16")
+        real2 = lambda: dfs.dfs_solve(RS, V2, lam, precision="bf16")
+        for fn in (native, real2):
+            for _ in range(warmup):
+                fn()
+        clk = _clock_sampler(0)
+        ms_c = timed(native, steps)
+        clocks = _clock_summary(clk)
+        ms_r = timed(real2, steps)
+        Xr, Xi, info = native()
+        X2, _ = real2()
+        import oracle
+
+        import numpy as np
+
+        S64 = (A.double() + 1j * B.double()).cpu().numpy()
+        ref = oracle.solve_complex(S64, (Vr.double() + 1j * Vi.double()).cpu().numpy().T, lam).T
+        rel = lambda X: float(np.max(np.linalg.norm(X - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        e_native = rel((Xr.double() + 1j * Xi.double()).cpu().numpy())
+        x2 = X2.double().cpu().numpy()
+        e_real2 = rel(x2[:, :m] + 1j * x2[:, m:])
+        emit({"workload": "complex", "metric": "complex solves/s, n=512 m=2^18 k=1", "value": 1e3 / ms_c,
+              "unit": "solves/s", "ms_per_step": ms_c, "dtype": "bf16", "clocks": clocks,
+              "real_representation": {"ms_per_step": ms_r, "ratio_native_over_real": ms_c / ms_r,
+                                      "api": "dfs_solve on [[A, -B], [B, A]] (2n x 2m, formed beforehand)"},
+              "config": {"n": n, "m": m, "k": k, "lambda": lam, "S": "complex Gaussian, planes stacked in one array"},
+              "accuracy": {"status": info["status"], "e_rel_native_vs_oracle": e_native,
+                           "e_rel_real_representation_vs_oracle": e_real2, "ok": e_native <= 1e-6}})
     elif args.workload == "stress":
         n, m, lam = 8192, 1 << 22, 1e-5
         S = wl.heavy_tailed(n, m, seed=base + 5, device=dev, dtype=torch.bfloat16)
@@ -794,7 +859,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "precision", "batch", "stress"], default="headline",
+    ap.add_argument("--workload", choices=["headline", "precision", "batch", "stress", "complex"], default="headline",
                     help="headline (default): the metric's workload; the others: one GPU, one line per path")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="M",
                     help="run one small solve (n=1024, m=M) after --warmup solves, for ncu captures")

@@ -187,10 +187,14 @@ dfs_status dfs_solve_host_async(dfs_handle handle, const void* S, int s_dtype, i
  * (S^dagger S + lambda I) X = V for complex S = S_re + i S_im and k complex right-hand sides.
  * S_re, S_im: DEVICE planes, n x m row-major with the same lds and dtype (FP32, BF16 or FP64, the
  * dfs_solve contract); V_re, V_im, X_re, X_im: DEVICE planes of k rows of length m (ldv, ldx),
- * FP64 for FP64 S, else FP32.  Solved as the real Eq. 1 of the 2n x 2m real representation
- * [[S_re, -S_im], [S_im, S_re]] with x = [Re x, Im x] (exactly equivalent), which the call forms in
- * a handle-owned device buffer (twice the bytes of the two planes), so every precision of
- * dfs_solve applies.  2n <= 65536.  Synchronizes `stream` before returning; info may be NULL.
+ * FP64 for FP64 S, else FP32.  Algorithm 1 with Hermitian conjugates, on the stacked real matrix
+ * Z = [S_re; S_im] (2n x m): the Gram is Z Z^T (Re W and Im W are sums and differences of its
+ * blocks), every pass over S reads Z once with two real right-hand sides per complex one, and the
+ * n-space steps factor and solve the real 2n system [[Re W, -Im W], [Im W, Re W]].  When S_im is
+ * row n of the same allocation as S_re (S_im == S_re + n lds elements) Z is used in place;
+ * otherwise the call stacks the planes in a handle-owned buffer (the bytes of the two planes).
+ * Every precision of dfs_solve applies; up to 4 complex right-hand sides share a pass (larger k
+ * runs in groups).  2n <= 65536.  Synchronizes `stream` before returning; info may be NULL.
  * DFS_FLAG_CENTER is not available here (DFS_ERR_UNSUPPORTED).  The real-part Fisher matrix
  * F = Re[S^dagger S] needs no entry point: it is dfs_solve on the 2n x m matrix with the rows of
  * S_re followed by those of S_im. */

@@ -596,6 +596,138 @@ dfs_status grow(dfs_handle h, int i, size_t bytes) {
     return DFS_OK;
 }
 
+// Complex S = A + iB (Section 4, complex SR) natively on Z = [A; B] (2n x m, row stride lds; Zs
+// is its first row), by the real kernels with the glue of complex.cu: the S v pass and the
+// refinement passes read Z with two real right-hand sides per complex one, the Gram is Z Z^T, and
+// the n-space steps solve the real 2n system R(W).  V and X are staged per group of kc complex
+// right-hand sides as 2 kc real rows (the real parts, then the imaginary parts).
+dfs_status solve_complex_device(dfs_handle h, const void* Zs, int s_dtype, int64_t n, int64_t m, int64_t lds,
+                                const void* V_re, const void* V_im, int64_t k, int64_t ldv, double lambda, void* X_re,
+                                void* X_im, int64_t ldx, const dfs_options* opt, cudaStream_t stream) {
+    dfs_status s;
+    int prec;
+    if ((s = resolve_precision(h, s_dtype, opt ? opt->precision : DFS_PREC_AUTO, &prec)) != DFS_OK) return s;
+    const int max_iter = (opt && opt->max_iter >= 0) ? opt->max_iter : 8;
+    const double tol = (opt && opt->tol > 0.0) ? opt->tol : 1e-7;
+    const int64_t n2 = 2 * n;
+    // two pass columns per complex right-hand side, at most 8 (4 complex) per group
+    const int kc_want = (int)(k < 4 ? k : 4);
+    Plan p;
+    if ((s = make_plan(h, s_dtype, prec, n2, m, 2 * kc_want, &p, false)) != DFS_OK) return s;
+    const int KQP = p.kq;
+    const int kc = KQP / 2 < kc_want ? KQP / 2 : kc_want;
+    if (kc < 1)
+        return fail(h, DFS_ERR_UNSUPPORTED, "2n=%lld: the passes take fewer than two right-hand sides", (long long)n2);
+    const int KQN = pow2_at_least(kc);
+    // beyond the real plan: R(W) and the folded stopping sums
+    const size_t es = p.f64 ? 8 : 4;
+    const size_t np = (size_t)p.n_pad;
+    const size_t off_Wc = align_up(p.total);
+    const size_t off_U2c = align_up(off_Wc + np * np * es);
+    const size_t total = align_up(off_U2c + (size_t)std::max(p.pgrid, tile_correct_parts(h->num_sms)) * 2 * KQP * 8);
+    if ((s = ensure_ws(h, total, stream)) != DFS_OK) return s;
+    const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
+    const int64_t ldc = round_up(m, 4);
+    if ((s = grow(h, 1, (size_t)2 * k * ldc * vs)) != DFS_OK) return s;
+    if ((s = grow(h, 2, (size_t)2 * kc * ldc * vs)) != DFS_OK) return s;
+    char* Vall = static_cast<char*>(h->hbuf[1]);  // every group's rows, staged before X is written
+    char* Xp = static_cast<char*>(h->hbuf[2]);
+    h->last_precision = prec;
+    h->timed = false;
+    void* G = at<void>(h, p.off_W);
+    void* Wc = at<void>(h, off_Wc);
+    void* Linv = at<void>(h, p.off_Linv);
+    double* Rpart = at<double>(h, p.off_Rpart);
+    double* U2part = at<double>(h, p.off_U2part);
+    double* U2c = at<double>(h, off_U2c);
+    double* R = at<double>(h, p.off_R);
+    void* Zv = at<void>(h, p.off_Z);
+    double* Y = at<double>(h, p.off_Y);
+    double* Yp = at<double>(h, p.off_Yc);  // the pass's y columns (2n x KQP)
+    double* U2 = at<double>(h, p.off_U2);
+    double* bn2 = at<double>(h, p.off_bn2);
+    void* Sp = p.pack ? at<void>(h, p.off_Sp) : nullptr;
+    float* rs = p.pack == 4 ? at<float>(h, p.off_Rs) : nullptr;
+    const int n2i = (int)n2, npi = (int)p.n_pad, ni = (int)n;
+    const int fp64_panel = opt && (opt->flags & DFS_FLAG_FP64_PANEL);
+    const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+
+    // V staged per group: rows Re v_c0.., then Im v_c0.. (2 kg rows at row 2 c0)
+    for (int64_t c0 = 0; c0 < k; c0 += kc) {
+        const int kg = (int)(k - c0 < kc ? k - c0 : kc);
+        char* Vg = Vall + 2 * c0 * ldc * vs;
+        DFS_CK(cudaMemcpy2DAsync(Vg, ldc * vs, static_cast<const char*>(V_re) + c0 * ldv * vs, ldv * vs, m * vs, kg,
+                                 d2d, stream));
+        DFS_CK(cudaMemcpy2DAsync(Vg + kg * ldc * vs, ldc * vs, static_cast<const char*>(V_im) + c0 * ldv * vs,
+                                 ldv * vs, m * vs, kg, d2d, stream));
+    }
+    DFS_CK(launch_status_reset(h->dstat, stream, h->test_wait_ns, h->test_fault));
+    if (rs) DFS_CK(launch_row_scale(s_dtype, Zs, n2i, npi, m, lds, rs, h->dstat, stream));
+    for (int64_t c0 = 0; c0 < k; c0 += kc) {
+        const int kg = (int)(k - c0 < kc ? k - c0 : kc);  // complex right-hand sides of this group
+        const char* Vp = Vall + 2 * c0 * ldc * vs;
+        DFS_CK(launch_group_reset(h->dstat, stream));
+        // b = S v from the S v pass over Z (the first group also writes Z's tensor-core tiles)
+        int sv_parts = p.pp.sv_grid;
+        DFS_CK(launch_sv_pack(p.pp, s_dtype, KQP, c0 == 0 ? p.pack : 0, Zs, n2i, m, lds, Vp, ldc, 2 * kg, Rpart, Sp,
+                              h->dstat, stream, rs ? rs + p.n_pad : nullptr, &sv_parts));
+        DFS_CK(launch_complex_combine(p.f64, Rpart, sv_parts, ni, kg, KQP, nullptr, lambda, R, Zv, KQN, npi, nullptr, 0,
+                                      nullptr, h->dstat, 0, stream));
+        if (c0 == 0) {
+            // W = S S^dagger + lambda I~ as R(W) from G = Z Z^T, and its Cholesky factor
+            void* P = at<void>(h, p.off_P);
+            if (p.tensor) {
+                DFS_CK(launch_gram_tc(p.tc, s_dtype, Zs, n2, m, lds, Sp, P, h->dstat, stream));
+                DFS_CK(launch_gram_tc_finalize(p.tc, P, n2, p.n_pad, 0.0, G, p.n_pad, stream, rs));
+            } else {
+                DFS_CK(launch_gram_simt(s_dtype, p.f64, Zs, n2, m, lds, p.nsplit, p.chunk, P, stream));
+                DFS_CK(launch_gram_finalize(p.f64, p.f64, gram_simt_tile(p.f64), P, p.nsplit, n2, p.n_pad, 0.0, G,
+                                            p.n_pad, stream));
+            }
+            DFS_CK(launch_complex_assemble(p.f64, G, p.n_pad, ni, npi, lambda, Wc, stream));
+            DFS_CK(launch_cholesky(p.f64, Wc, p.n_pad, p.n_pad, Linv, at<int>(h, p.off_Cf), h->dstat, stream,
+                                   fp64_panel, h->chol_share));
+        }
+        // z = R(W)^{-1} (the combined right-hand side in Zv), in place
+        auto nspace_solve = [&](int honor) -> dfs_status {
+            if (p.ns) {
+                DFS_CK(launch_nspace(p.f64, KQN, Wc, p.n_pad, npi, Linv, NS_MODE_FWD | NS_MODE_BWD, nullptr, 0, n2i,
+                                     kg, nullptr, lambda, Zv, KQN, nullptr, Zv, KQN, nullptr, nullptr, h->smem_optin,
+                                     h->dstat, honor, stream));
+            } else {
+                DFS_CK(launch_trsv(p.f64, 0, Wc, p.n_pad, npi, Linv, Zv, KQN, kg, KQN, h->dstat, honor, stream));
+                DFS_CK(launch_trsv(p.f64, 1, Wc, p.n_pad, npi, Linv, Zv, KQN, kg, KQN, h->dstat, honor, stream));
+            }
+            return DFS_OK;
+        };
+        if ((s = nspace_solve(0)) != DFS_OK) return s;
+        DFS_CK(launch_refine_init(p.f64, Zv, npi, KQN, Y, R, bn2, h->dstat, stream));
+        if (!p.tensor || max_iter == 0) {
+            // x = (v - S^dagger y) / lambda
+            DFS_CK(launch_complex_yexp(Y, KQN, ni, kg, KQP, Yp, h->dstat, 0, stream));
+            DFS_CK(launch_pass(p.pp, s_dtype, KQP, Zs, n2i, m, lds, Vp, ldc, 2 * kg, Yp, KQP, lambda, Xp, ldc, nullptr,
+                               U2part, 0, h->dstat, 0, stream));
+        } else {
+            for (int it = 1; it <= max_iter; ++it) {
+                DFS_CK(launch_complex_yexp(Y, KQN, ni, kg, KQP, Yp, h->dstat, 1, stream));
+                DFS_CK(launch_pass(p.pp, s_dtype, KQP, Zs, n2i, m, lds, Vp, ldc, 2 * kg, Yp, KQP, lambda, Xp, ldc,
+                                   Rpart, U2part, it == 1 ? 2 : 1, h->dstat, 1, stream));
+                DFS_CK(launch_complex_combine(p.f64, Rpart, p.pp.nparts, ni, kg, KQP, Y, lambda, R, Zv, KQN, npi,
+                                              U2part, p.pp.uparts, U2c, h->dstat, 1, stream));
+                DFS_CK(launch_refine_check(U2c, p.pp.uparts, U2, KQN, kg, lambda, tol, it, max_iter, 0, h->dstat,
+                                           stream));
+                if ((s = nspace_solve(1)) != DFS_OK) return s;
+                DFS_CK(launch_refine_update(p.f64, Zv, R, npi, KQN, kg, Y, bn2, h->dstat, stream));
+            }
+        }
+        DFS_CK(cudaMemcpy2DAsync(static_cast<char*>(X_re) + c0 * ldx * vs, ldx * vs, Xp, ldc * vs, m * vs, kg, d2d,
+                                 stream));
+        DFS_CK(cudaMemcpy2DAsync(static_cast<char*>(X_im) + c0 * ldx * vs, ldx * vs, Xp + kg * ldc * vs, ldc * vs,
+                                 m * vs, kg, d2d, stream));
+    }
+    return DFS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -800,23 +932,20 @@ dfs_status dfs_solve_complex(dfs_handle h, const void* S_re, const void* S_im, i
     if (2 * n > 65536) return fail(h, DFS_ERR_UNSUPPORTED, "2n=%lld above the supported maximum 65536", (long long)(2 * n));
     if (opt && (opt->flags & DFS_FLAG_CENTER))
         return fail(h, DFS_ERR_UNSUPPORTED, "centring is not available for complex scores");
+    // Z = [Re S; Im S]: the planes themselves when Im S follows Re S in one allocation (row n of
+    // a 2n-row array), else a stacked copy
     const size_t es = elem_size(s_dtype);
-    const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
-    // R(S): 2n rows of 2m (row stride a multiple of 16 bytes); [Re v | Re v] rows of 2m
-    const int64_t ldr = round_up(2 * m, 8), ldv2 = round_up(2 * m, 4);
-    if ((s = grow(h, 0, (size_t)(2 * n) * ldr * es)) != DFS_OK) return s;
-    if ((s = grow(h, 1, (size_t)k * ldv2 * vs)) != DFS_OK) return s;
-    if ((s = grow(h, 2, (size_t)k * ldv2 * vs)) != DFS_OK) return s;
-    DFS_CK(launch_complex_embed(s_dtype, S_re, S_im, n, m, lds, h->hbuf[0], ldr, stream));
-    char* v2 = static_cast<char*>(h->hbuf[1]);
-    DFS_CK(cudaMemcpy2DAsync(v2, ldv2 * vs, V_re, ldv * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
-    DFS_CK(cudaMemcpy2DAsync(v2 + m * vs, ldv2 * vs, V_im, ldv * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
-    s = solve_device(h, h->hbuf[0], s_dtype, 2 * n, 2 * m, ldr, h->hbuf[1], k, ldv2, lambda, h->hbuf[2], ldv2, opt,
-                     stream, nullptr);
+    const void* Zs = S_re;
+    if (static_cast<const char*>(S_im) != static_cast<const char*>(S_re) + (size_t)n * lds * es) {
+        if ((s = grow(h, 0, (size_t)(2 * n) * lds * es)) != DFS_OK) return s;
+        char* z = static_cast<char*>(h->hbuf[0]);
+        DFS_CK(cudaMemcpy2DAsync(z, lds * es, S_re, lds * es, m * es, n, cudaMemcpyDeviceToDevice, stream));
+        DFS_CK(cudaMemcpy2DAsync(z + (size_t)n * lds * es, lds * es, S_im, lds * es, m * es, n,
+                                 cudaMemcpyDeviceToDevice, stream));
+        Zs = z;
+    }
+    s = solve_complex_device(h, Zs, s_dtype, n, m, lds, V_re, V_im, k, ldv, lambda, X_re, X_im, ldx, opt, stream);
     if (s != DFS_OK) return s;
-    const char* x2 = static_cast<const char*>(h->hbuf[2]);
-    DFS_CK(cudaMemcpy2DAsync(X_re, ldx * vs, x2, ldv2 * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
-    DFS_CK(cudaMemcpy2DAsync(X_im, ldx * vs, x2 + m * vs, ldv2 * vs, m * vs, k, cudaMemcpyDeviceToDevice, stream));
     return fill_info(h, stream, info);
 }
 

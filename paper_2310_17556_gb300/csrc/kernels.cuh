@@ -131,9 +131,19 @@ cudaError_t launch_center_vec(int f64, int mode, int n, int n_pad, int KQ, int k
                               double lambda, void* Z, double* Yc, const DevStatus* st, int honor_stop,
                               cudaStream_t stream);
 
-// ---- complex scores (complex.cu): R = [[A, -B], [B, A]] (2n x 2m, row stride ldr) ----
-cudaError_t launch_complex_embed(int s_dtype, const void* A, const void* B, int64_t n, int64_t m, int64_t lds, void* R,
-                                 int64_t ldr, cudaStream_t stream);
+// ---- complex scores (complex.cu): the glue of the native complex solve on Z = [Re S; Im S] ----
+// r = R(S) u - lambda y (or b = S v without Y) from the pass partials over Z (KQP columns, the
+// complex RHS q in columns q and kc + q) into R (FP64) and Zb (solve type), n_pad x KQN; folds the
+// per-part stopping sums U2part (uparts x 2 KQP) into U2c (uparts x 2 KQN) when U2part is given
+cudaError_t launch_complex_combine(int f64, const double* P, int nparts, int n, int kc, int KQP, const double* Y,
+                                   double lambda, double* R, void* Zb, int KQN, int n_pad, const double* U2part,
+                                   int uparts, double* U2c, const DevStatus* st, int honor_stop, cudaStream_t stream);
+// the pass's y (2n x KQP, FP64) from the real n-space y (rows 0..2n-1, stride KQN)
+cudaError_t launch_complex_yexp(const double* Y, int KQN, int n, int kc, int KQP, double* Yp, const DevStatus* st,
+                                int honor_stop, cudaStream_t stream);
+// R(W) + lambda I~ (lower, n_pad x n_pad, ld) from the stacked Gram G = Z Z^T (lower, same shape)
+cudaError_t launch_complex_assemble(int f64, const void* G, int64_t ld, int n, int n_pad, double lambda, void* W,
+                                    cudaStream_t stream);
 
 // ---- refinement control and small utilities (refine.cu, util.cu) ----
 // wait_ns: limit of the call's bounded device waits (0: the 2 s default); fault: a test hook's

@@ -506,6 +506,36 @@ def test_complex_solve_matches_oracle(prec, n, m, k, lam, dtype):
     assert err <= tol, err
 
 
+@pytest.mark.parametrize("prec,n,m,k,lam,dtype", [("bf16", 300, 20004, 6, 1e-2, torch.float32),  # groups of 4 + 2
+                                                  ("bf16", 1100, 30000, 3, 1e-2, torch.float32),  # 2n > 2048: 2 + 1
+                                                  ("fp32", 129, 5000, 3, 1e-2, torch.float32),
+                                                  ("fp64", 100, 2000, 5, 1e-2, torch.float64),
+                                                  ("bf16", 64, 64, 1, 0.3, torch.bfloat16)])
+def test_complex_solve_on_stacked_planes(prec, n, m, k, lam, dtype):
+    """The planes as rows 0..n-1 and n..2n-1 of one array (used in place, no stacking copy), with
+    more complex right-hand sides than one pass takes (groups), ragged n and 2n beyond the
+    8-right-hand-side pass; against the oracle's complex Algorithm 1."""
+    A, B, Vr, Vi = _complex_inputs(n, m, k, seed=470 + n, dtype=dtype)
+    Z = torch.cat([A, B], dim=0)
+    Ar, Bi = Z[:n], Z[n:]
+    assert Bi.data_ptr() == Ar.data_ptr() + n * Ar.stride(0) * Ar.element_size()
+    Xr, Xi, info = dfs.dfs_solve_complex(Ar, Bi, Vr, Vi, lam, precision=prec)
+    assert info["status"] == 0, info
+    S = np64(A) + 1j * np64(B)
+    ref = oracle.solve_complex(S, (np64(Vr) + 1j * np64(Vi)).T, lam).T
+    X = np64(Xr) + 1j * np64(Xi)
+    err = float(np.max(np.linalg.norm(X - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+    if prec == "fp32":
+        sv = np.linalg.svd(S, compute_uv=False)
+        tol = 1e-5 * max(1.0, (sv[0] ** 2 + lam) / (sv[-1] ** 2 + lam) / 10)
+    else:
+        tol = 1e-12 if prec == "fp64" else 1e-6
+    assert err <= tol, err
+    # the separate-plane call (stacked by the library) gives the same x bit for bit
+    Xr2, Xi2, _ = dfs.dfs_solve_complex(A, B, Vr, Vi, lam, precision=prec)
+    assert torch.equal(Xr, Xr2) and torch.equal(Xi, Xi2)
+
+
 def test_complex_real_part_fisher_is_the_stacked_real_solve():
     """Section 4, real-part SR (F = Re[S^dagger S]): dfs_solve on the rows of Re S followed by those
     of Im S matches the oracle's real solve of real_part_scores(S)."""
