@@ -228,7 +228,7 @@ def dfs_solve_host_async(S: torch.Tensor, V: torch.Tensor, lam: float, X: torch.
 
 def dfs_solve_complex(S_re: torch.Tensor, S_im: torch.Tensor, V_re: torch.Tensor, V_im: torch.Tensor, lam: float,
                       precision="auto", max_iter: int = -1, tol: float = 0.0, handle: Handle | None = None,
-                      stream=None, allow_not_converged: bool = False):
+                      stream=None, allow_not_converged: bool = False, two_kernel_gram: bool = False):
     """Complex SR (Section 4, F = S^dagger S): solve (S^dagger S + lam I) X^T = V^T for S = S_re + i S_im
     (n x m planes) and the k rows of V = V_re + i V_im; returns (X_re, X_im, info)."""
     h = handle or default_handle(S_re.device.index)
@@ -239,7 +239,7 @@ def dfs_solve_complex(S_re: torch.Tensor, S_im: torch.Tensor, V_re: torch.Tensor
     if V_im.shape != V_re.shape or V_im.stride() != V_re.stride() or V_re.shape[1] != m:
         raise ValueError("V_re and V_im must both be (k, m) with the same strides")
     X_re, X_im = torch.empty_like(V_re), torch.empty_like(V_re)
-    opt = _opts(precision, max_iter, tol)
+    opt = _opts(precision, max_iter, tol, two_kernel_gram=two_kernel_gram)
     info = dfs_info()
     st = h.lib.dfs_solve_complex(h.h, S_re.data_ptr(), S_im.data_ptr(), _dtype_code(S_re), n, m, _rows(S_re, "S"),
                                  V_re.data_ptr(), V_im.data_ptr(), k, _rows(V_re, "V"), float(lam), X_re.data_ptr(),

@@ -613,7 +613,8 @@ dfs_status solve_complex_device(dfs_handle h, const void* Zs, int s_dtype, int64
     // two pass columns per complex right-hand side, at most 8 (4 complex) per group
     const int kc_want = (int)(k < 4 ? k : 4);
     Plan p;
-    if ((s = make_plan(h, s_dtype, prec, n2, m, 2 * kc_want, &p, false)) != DFS_OK) return s;
+    const bool allow_fused = !(opt && (opt->flags & DFS_FLAG_TWO_KERNEL_GRAM));
+    if ((s = make_plan(h, s_dtype, prec, n2, m, 2 * kc_want, &p, allow_fused)) != DFS_OK) return s;
     const int KQP = p.kq;
     const int kc = KQP / 2 < kc_want ? KQP / 2 : kc_want;
     if (kc < 1)
@@ -624,7 +625,9 @@ dfs_status solve_complex_device(dfs_handle h, const void* Zs, int s_dtype, int64
     const size_t np = (size_t)p.n_pad;
     const size_t off_Wc = align_up(p.total);
     const size_t off_U2c = align_up(off_Wc + np * np * es);
-    const size_t total = align_up(off_U2c + (size_t)std::max(p.pgrid, tile_correct_parts(h->num_sms)) * 2 * KQP * 8);
+    const size_t off_dy = align_up(off_U2c + (size_t)std::max(p.pgrid, tile_correct_parts(h->num_sms)) * 2 * KQP * 8);
+    const int n_rows_t = (int)round_up(n2, 256);  // rows of the packed tiles
+    const size_t total = align_up(off_dy + (size_t)n_rows_t * KQP * sizeof(float));
     if ((s = ensure_ws(h, total, stream)) != DFS_OK) return s;
     const size_t vs = s_dtype == DFS_F64 ? 8 : 4;
     const int64_t ldc = round_up(m, 4);
@@ -640,6 +643,7 @@ dfs_status solve_complex_device(dfs_handle h, const void* Zs, int s_dtype, int64
     double* Rpart = at<double>(h, p.off_Rpart);
     double* U2part = at<double>(h, p.off_U2part);
     double* U2c = at<double>(h, off_U2c);
+    float* dy = at<float>(h, off_dy);  // the packed-tile correction's dy columns
     double* R = at<double>(h, p.off_R);
     void* Zv = at<void>(h, p.off_Z);
     double* Y = at<double>(h, p.off_Y);
@@ -667,17 +671,23 @@ dfs_status solve_complex_device(dfs_handle h, const void* Zs, int s_dtype, int64
         const int kg = (int)(k - c0 < kc ? k - c0 : kc);  // complex right-hand sides of this group
         const char* Vp = Vall + 2 * c0 * ldc * vs;
         DFS_CK(launch_group_reset(h->dstat, stream));
-        // b = S v from the S v pass over Z (the first group also writes Z's tensor-core tiles)
+        // b = S v from the S v pass over Z (the first group also writes Z's tensor-core tiles, and in
+        // the fused form computes the Gram partials in the same kernel)
         int sv_parts = p.pp.sv_grid;
-        DFS_CK(launch_sv_pack(p.pp, s_dtype, KQP, c0 == 0 ? p.pack : 0, Zs, n2i, m, lds, Vp, ldc, 2 * kg, Rpart, Sp,
-                              h->dstat, stream, rs ? rs + p.n_pad : nullptr, &sv_parts));
+        const bool fused_now = c0 == 0 && p.fused;
+        if (fused_now)
+            DFS_CK(launch_gram_fused(p.tc, KQP, Zs, n2, m, lds, Vp, ldc, 2 * kg, Rpart, Sp, at<void>(h, p.off_P),
+                                     at<int>(h, p.off_Rdy), h->dstat, h->num_sms, stream, &sv_parts));
+        else
+            DFS_CK(launch_sv_pack(p.pp, s_dtype, KQP, c0 == 0 ? p.pack : 0, Zs, n2i, m, lds, Vp, ldc, 2 * kg, Rpart,
+                                  Sp, h->dstat, stream, rs ? rs + p.n_pad : nullptr, &sv_parts));
         DFS_CK(launch_complex_combine(p.f64, Rpart, sv_parts, ni, kg, KQP, nullptr, lambda, R, Zv, KQN, npi, nullptr, 0,
                                       nullptr, h->dstat, 0, stream));
         if (c0 == 0) {
             // W = S S^dagger + lambda I~ as R(W) from G = Z Z^T, and its Cholesky factor
             void* P = at<void>(h, p.off_P);
             if (p.tensor) {
-                DFS_CK(launch_gram_tc(p.tc, s_dtype, Zs, n2, m, lds, Sp, P, h->dstat, stream));
+                if (!p.fused) DFS_CK(launch_gram_tc(p.tc, s_dtype, Zs, n2, m, lds, Sp, P, h->dstat, stream));
                 DFS_CK(launch_gram_tc_finalize(p.tc, P, n2, p.n_pad, 0.0, G, p.n_pad, stream, rs));
             } else {
                 DFS_CK(launch_gram_simt(s_dtype, p.f64, Zs, n2, m, lds, p.nsplit, p.chunk, P, stream));
@@ -708,14 +718,31 @@ dfs_status solve_complex_device(dfs_handle h, const void* Zs, int s_dtype, int64
             DFS_CK(launch_pass(p.pp, s_dtype, KQP, Zs, n2i, m, lds, Vp, ldc, 2 * kg, Yp, KQP, lambda, Xp, ldc, nullptr,
                                U2part, 0, h->dstat, 0, stream));
         } else {
+            // as the real path: the step after the first takes x_2 = x_1 - S_bf16^dagger dy_1 / lambda from
+            // Z's packed BF16 tiles; if that does not converge, the full pass of step 2 recomputes x_2
+            const bool fast = p.pack == 1 && max_iter >= 3 && !p.f64 && tile_correct_fits(n_rows_t, KQP, h->smem_optin);
             for (int it = 1; it <= max_iter; ++it) {
+                const bool corrected = fast && it == 2;
+                if (corrected) {
+                    DFS_CK(launch_complex_dyexp(static_cast<const float*>(Zv), KQN, ni, kg, KQP, dy, n_rows_t, h->dstat,
+                                                1, stream));
+                    int cparts = 0;
+                    DFS_CK(launch_tile_correct(KQP, Sp, n2i, n_rows_t, m, pack_kblocks(s_dtype, 1, m), dy, 2 * kg,
+                                               lambda, reinterpret_cast<float*>(Xp), ldc, U2part, h->dstat,
+                                               h->num_sms, stream, &cparts));
+                    DFS_CK(launch_complex_combine(p.f64, nullptr, 0, ni, kg, KQP, nullptr, lambda, nullptr, nullptr, KQN,
+                                                  npi, U2part, cparts, U2c, h->dstat, 1, stream));
+                    DFS_CK(launch_refine_check(U2c, cparts, U2, KQN, kg, lambda, tol, it, max_iter, 1, h->dstat,
+                                               stream));
+                }
                 DFS_CK(launch_complex_yexp(Y, KQN, ni, kg, KQP, Yp, h->dstat, 1, stream));
                 DFS_CK(launch_pass(p.pp, s_dtype, KQP, Zs, n2i, m, lds, Vp, ldc, 2 * kg, Yp, KQP, lambda, Xp, ldc,
-                                   Rpart, U2part, it == 1 ? 2 : 1, h->dstat, 1, stream));
+                                   Rpart, U2part, corrected ? 0 : (it == 1 ? 2 : 1), h->dstat, 1, stream));
                 DFS_CK(launch_complex_combine(p.f64, Rpart, p.pp.nparts, ni, kg, KQP, Y, lambda, R, Zv, KQN, npi,
-                                              U2part, p.pp.uparts, U2c, h->dstat, 1, stream));
-                DFS_CK(launch_refine_check(U2c, p.pp.uparts, U2, KQN, kg, lambda, tol, it, max_iter, 0, h->dstat,
-                                           stream));
+                                              corrected ? nullptr : U2part, p.pp.uparts, U2c, h->dstat, 1, stream));
+                if (!corrected)
+                    DFS_CK(launch_refine_check(U2c, p.pp.uparts, U2, KQN, kg, lambda, tol, it, max_iter, 0, h->dstat,
+                                               stream));
                 if ((s = nspace_solve(1)) != DFS_OK) return s;
                 DFS_CK(launch_refine_update(p.f64, Zv, R, npi, KQN, kg, Y, bn2, h->dstat, stream));
             }

@@ -26,7 +26,8 @@ namespace {
 // (without y: b = S v from the S v pass).  Parts are added in order (a fixed summation order).
 // Writes R (FP64) and Zb (the solve type) with row stride KQN, zero in padding rows and columns.
 // Also folds the pass's per-part stopping sums (U2part, parts x 2 KQP) into one pair per complex
-// right-hand side (U2c, parts x 2 KQN): |u|^2 = |u_r|^2 + |u_i|^2, the same for dx.
+// right-hand side (U2c, parts x 2 KQN): |u|^2 = |u_r|^2 + |u_i|^2, the same for dx.  With P null
+// only the fold runs (after the correction from the packed tiles).
 template <typename T>
 __global__ void __launch_bounds__(256)
 complex_combine_kernel(const double* __restrict__ P, int nparts, int n, int kc, int KQP,
@@ -36,7 +37,7 @@ complex_combine_kernel(const double* __restrict__ P, int nparts, int n, int kc, 
     if (block_should_exit(st, honor_stop)) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n2 = 2 * (int64_t)n;
-    if (t < (int64_t)n_pad * KQN) {
+    if (P != nullptr && t < (int64_t)n_pad * KQN) {
         const int64_t row = t / KQN;
         const int q = (int)(t % KQN);
         double v = 0.0;
@@ -74,24 +75,28 @@ complex_combine_kernel(const double* __restrict__ P, int nparts, int n, int kc, 
 
 // The pass's y columns from the real n-space y (rows 0..2n-1, stride KQN):
 //   Yp[row][q] = y_real[row][q],  Yp[row][kc+q] = row < n ? y_real[n+row][q] : -y_real[row-n][q]
-// (Z^T of the second column is Im(S^dagger y)); other columns zero.
+// (Z^T of the second column is Im(S^dagger y)); other columns, and rows 2n..rows_out-1, zero.
+// FP64 for the passes' y, FP32 for the packed-tile correction's dy.
+template <typename TI, typename TO>
 __global__ void __launch_bounds__(256)
-complex_yexp_kernel(const double* __restrict__ Y, int KQN, int n, int kc, int KQP, double* __restrict__ Yp,
+complex_yexp_kernel(const TI* __restrict__ Y, int KQN, int n, int kc, int KQP, TO* __restrict__ Yp, int rows_out,
                     const DevStatus* st, int honor_stop) {
     if (block_should_exit(st, honor_stop)) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n2 = 2 * (int64_t)n;
-    if (t >= n2 * KQP) return;
+    if (t >= (int64_t)rows_out * KQP) return;
     const int64_t row = t / KQP;
     const int c = (int)(t % KQP);
     double v = 0.0;
-    if (c < kc) {
-        v = Y[row * KQN + c];
-    } else if (c < 2 * kc) {
-        const int q = c - kc;
-        v = row < n ? Y[(row + n) * KQN + q] : -Y[(row - n) * KQN + q];
+    if (row < n2) {
+        if (c < kc) {
+            v = (double)Y[row * KQN + c];
+        } else if (c < 2 * kc) {
+            const int q = c - kc;
+            v = row < n ? (double)Y[(row + n) * KQN + q] : -(double)Y[(row - n) * KQN + q];
+        }
     }
-    Yp[t] = v;
+    Yp[t] = (TO)v;
 }
 
 // W_real (lower triangle, n_pad x n_pad, ld) = R(W) from G = Z Z^T (lower, same size, ld), with
@@ -147,7 +152,17 @@ cudaError_t launch_complex_combine(int f64, const double* P, int nparts, int n, 
 cudaError_t launch_complex_yexp(const double* Y, int KQN, int n, int kc, int KQP, double* Yp, const DevStatus* st,
                                 int honor_stop, cudaStream_t stream) {
     const int64_t total = 2 * (int64_t)n * KQP;
-    complex_yexp_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(Y, KQN, n, kc, KQP, Yp, st, honor_stop);
+    complex_yexp_kernel<double, double><<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(Y, KQN, n, kc, KQP, Yp,
+                                                                                            2 * n, st, honor_stop);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_complex_dyexp(const float* Z, int KQN, int n, int kc, int KQP, float* dy, int rows_out,
+                                 const DevStatus* st, int honor_stop, cudaStream_t stream) {
+    const int64_t total = (int64_t)rows_out * KQP;
+    complex_yexp_kernel<float, float><<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(Z, KQN, n, kc, KQP, dy,
+                                                                                          rows_out, st, honor_stop);
     count_launch();
     return cudaGetLastError();
 }

@@ -141,6 +141,9 @@ cudaError_t launch_complex_combine(int f64, const double* P, int nparts, int n, 
 // the pass's y (2n x KQP, FP64) from the real n-space y (rows 0..2n-1, stride KQN)
 cudaError_t launch_complex_yexp(const double* Y, int KQN, int n, int kc, int KQP, double* Yp, const DevStatus* st,
                                 int honor_stop, cudaStream_t stream);
+// the same from an FP32 n-space correction into rows_out x KQP FP32 (the packed-tile correction's dy)
+cudaError_t launch_complex_dyexp(const float* Z, int KQN, int n, int kc, int KQP, float* dy, int rows_out,
+                                 const DevStatus* st, int honor_stop, cudaStream_t stream);
 // R(W) + lambda I~ (lower, n_pad x n_pad, ld) from the stacked Gram G = Z Z^T (lower, same shape)
 cudaError_t launch_complex_assemble(int f64, const void* G, int64_t ld, int n, int n_pad, double lambda, void* W,
                                     cudaStream_t stream);

@@ -510,7 +510,9 @@ def test_complex_solve_matches_oracle(prec, n, m, k, lam, dtype):
                                                   ("bf16", 1100, 30000, 3, 1e-2, torch.float32),  # 2n > 2048: 2 + 1
                                                   ("fp32", 129, 5000, 3, 1e-2, torch.float32),
                                                   ("fp64", 100, 2000, 5, 1e-2, torch.float64),
-                                                  ("bf16", 64, 64, 1, 0.3, torch.bfloat16)])
+                                                  ("bf16", 64, 64, 1, 0.3, torch.bfloat16),
+                                                  ("bf16", 512, 65536, 1, 1e-3, torch.float32),  # fused first pass
+                                                  ("bf16", 257, 33336, 2, 1e-3, torch.float32)])
 def test_complex_solve_on_stacked_planes(prec, n, m, k, lam, dtype):
     """The planes as rows 0..n-1 and n..2n-1 of one array (used in place, no stacking copy), with
     more complex right-hand sides than one pass takes (groups), ragged n and 2n beyond the
@@ -534,6 +536,12 @@ def test_complex_solve_on_stacked_planes(prec, n, m, k, lam, dtype):
     # the separate-plane call (stacked by the library) gives the same x bit for bit
     Xr2, Xi2, _ = dfs.dfs_solve_complex(A, B, Vr, Vi, lam, precision=prec)
     assert torch.equal(Xr, Xr2) and torch.equal(Xi, Xi2)
+    if prec == "bf16" and dtype == torch.float32 and k <= 2:
+        # b = S v, the tiles and the Gram of the first group as one kernel or as two: the same solve
+        Xr3, Xi3, info3 = dfs.dfs_solve_complex(Ar, Bi, Vr, Vi, lam, precision=prec, two_kernel_gram=True)
+        assert info3["status"] == 0, info3
+        X3 = np64(Xr3) + 1j * np64(Xi3)
+        assert float(np.max(np.linalg.norm(X3 - ref, axis=1) / np.linalg.norm(ref, axis=1))) <= 1e-6
 
 
 def test_complex_real_part_fisher_is_the_stacked_real_solve():
