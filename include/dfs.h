@@ -51,7 +51,10 @@ typedef enum {
     DFS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
     DFS_ERR_NO_MEMORY = 6,     /* workspace allocation failed */
     DFS_ERR_CUDA = 7,          /* a CUDA runtime call failed (text in dfs_last_error) */
-    DFS_ERR_UNSUPPORTED = 8    /* valid request this build cannot serve (e.g. no sm_103a device) */
+    DFS_ERR_UNSUPPORTED = 8,   /* valid request this build cannot serve (e.g. no sm_103a device) */
+    DFS_ERR_BOUNDS = 9         /* debug build only (libdfs_debug.so, -DDFS_DEBUG_BOUNDS): a device
+                                  index check failed and its access was skipped; dfs_last_error
+                                  names the site */
 } dfs_status;
 
 typedef enum {

@@ -10,6 +10,7 @@ import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libdfs.so")
+LIB_DEBUG_PATH = os.path.join(PKG, "libdfs_debug.so")  # device index checks (-DDFS_DEBUG_BOUNDS)
 
 # enums of include/dfs.h
 DFS_OK = 0
@@ -21,6 +22,7 @@ DFS_ERR_TIMEOUT = 5
 DFS_ERR_NO_MEMORY = 6
 DFS_ERR_CUDA = 7
 DFS_ERR_UNSUPPORTED = 8
+DFS_ERR_BOUNDS = 9
 
 DFS_F64, DFS_F32, DFS_BF16 = 0, 1, 2
 PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "bf16": 3, "tf32": 4, "bf16x3": 5, "fp8": 6}
@@ -111,15 +113,22 @@ _SIGS = {
 _lib = None
 
 
+def lib_path() -> str:
+    """The library this process uses: libdfs_debug.so when DFS_DEBUG_BOUNDS=1, else libdfs.so."""
+    return LIB_DEBUG_PATH if os.environ.get("DFS_DEBUG_BOUNDS", "0") == "1" else LIB_PATH
+
+
 def load() -> C.CDLL:
-    """Load libdfs.so from the package folder (RuntimeError if it was never built)."""
+    """Load the library from the package folder (RuntimeError if it was never built)."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2310_17556_gb300.build` "
+    path = lib_path()
+    if not os.path.exists(path):
+        flag = " --debug-bounds" if path == LIB_DEBUG_PATH else ""
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2310_17556_gb300.build{flag}` "
                            "(the CUDA path has no CPU fallback)")
-    lib = C.CDLL(LIB_PATH)
+    lib = C.CDLL(path)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)
         fn.restype = res

@@ -1,7 +1,10 @@
 """Build libdfs.so in-tree with nvcc for sm_103a (GB300).
 
 Every .cu file under csrc/ is compiled to an object in parallel, then linked into
-``paper_2310_17556_gb300/libdfs.so``.  No CMake, no torch extension machinery: the C ABI
+``paper_2310_17556_gb300/libdfs.so``.  ``--debug-bounds`` builds the same sources with
+-DDFS_DEBUG_BOUNDS (device index checks that record DFS_ERR_BOUNDS instead of faulting) into
+``libdfs_debug.so``, in its own object folder; the binding loads it when the environment variable
+DFS_DEBUG_BOUNDS is set to 1.  No CMake, no torch extension machinery: the C ABI
 in include/dfs.h is the boundary, and the Python binding loads the library with ctypes.
 
     python -m paper_2310_17556_gb300.build [--force] [--debug-bounds]
@@ -22,6 +25,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdfs.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libdfs_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -49,8 +54,8 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -59,24 +64,26 @@ def _compile(src: str, extra) -> str:
 
 
 def build(force: bool = False, debug_bounds: bool = False, verbose: bool = False) -> str:
-    """Compile every CUDA source and link libdfs.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+    """Compile every CUDA source and link libdfs.so (libdfs_debug.so with debug_bounds); returns
+    the library path."""
+    lib, build_dir = (LIB_DEBUG, BUILD_DEBUG) if debug_bounds else (LIB, BUILD)
+    os.makedirs(build_dir, exist_ok=True)
     deps = _deps() + [os.path.abspath(__file__)]
-    if not force and not _stale(LIB, deps):
-        return LIB
+    if not force and not _stale(lib, deps):
+        return lib
     extra = ["-DDFS_DEBUG_BOUNDS"] if debug_bounds else []
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}", file=sys.stderr)
-    return LIB
+        print(f"built {lib}", file=sys.stderr)
+    return lib
 
 
 if __name__ == "__main__":

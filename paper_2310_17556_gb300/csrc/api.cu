@@ -350,6 +350,9 @@ dfs_status fill_info(dfs_handle h, cudaStream_t stream, dfs_info* info) {
         if (h->timed) step_ms(h->ev[h->tslot], info->ms);
     }
     if (ds.status != 0) {
+        if (ds.status == DFS_ERR_BOUNDS)
+            return fail(h, DFS_ERR_BOUNDS, "device index check failed at source %d, line %d", ds.bounds_site / 100000,
+                        ds.bounds_site % 100000);
         if (ds.status == DFS_ERR_NOT_SPD || ds.status == DFS_ERR_NONFINITE)
             return fail(h, (dfs_status)ds.status, "device reported %s at pivot %d", dfs_status_string(ds.status),
                         ds.failed_pivot);
@@ -770,6 +773,7 @@ const char* dfs_status_string(int status) {
         case DFS_ERR_NO_MEMORY: return "DFS_ERR_NO_MEMORY";
         case DFS_ERR_CUDA: return "DFS_ERR_CUDA";
         case DFS_ERR_UNSUPPORTED: return "DFS_ERR_UNSUPPORTED";
+        case DFS_ERR_BOUNDS: return "DFS_ERR_BOUNDS";
         default: return "DFS_ERR_UNKNOWN";
     }
 }

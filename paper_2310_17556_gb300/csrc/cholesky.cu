@@ -21,6 +21,7 @@
 // 8 warps, 4 columns each) feeds the panel TRSM and the triangular solves.
 // Every wait is bounded (DFS_ERR_TIMEOUT after 2 s) and also ends when another CTA has set an
 // error status: a pivot <= 0 (DFS_ERR_NOT_SPD) or NaN/Inf (DFS_ERR_NONFINITE) with its index.
+#define DFS_SRC_ID 5
 #include "kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -262,6 +263,9 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
     __shared__ T s_rinv[NB];
     __shared__ int s_ok, s_fail;
     if (block_should_exit(st, 0)) return;
+    // every tile of the nb x nb block grid lies inside W's rows of ld elements (uniform over the
+    // grid: all CTAs return alike)
+    if (!DFS_IN_BOUNDS(st, ld >= (int64_t)nb * NB)) return;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int fault = test_fault(st);  // the test hook, read once
     const int ntiles = nb * (nb + 1) / 2;
@@ -349,6 +353,7 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
                     for (int b = 0; b < 2; ++b) {
                         const int r = ty + 16 * a, c = tx + 16 * b;
                         if (i == p && c > r) continue;
+                        if (!DFS_IN_BOUNDS(st, i < nb && p <= i)) continue;
                         T* w = W + ((int64_t)i * NB + r) * ld + (int64_t)p * NB + c;
                         *w = __ldcg(w) - acc[a][b];
                     }
@@ -374,6 +379,7 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
         int i, p;
         tile_ij(t, i, p);
         if (i == p) continue;
+        if (!DFS_IN_BOUNDS(st, i < nb && p < i)) continue;  // (uniform over the CTA)
         load_linv<T>(Linv, p, sLi);
         load_tile<T>(W, ld, (int64_t)i * NB, (int64_t)p * NB, sP);
         times_linv_t<T>(sP, sLi);

@@ -28,7 +28,7 @@ struct DevStatus {
     int stop;
     int passes;  // full passes over S run by the refinement (a tile correction does not count)
     int fault;   // test hook: DFS_TEST_FAULT_* of the call (0 normally), set by the status reset
-    int pad;
+    int bounds_site;  // debug build: site of the first failed index check (file id * 100000 + line)
     double rel_correction;
     double rel_residual;
     double prev_correction;
@@ -163,6 +163,30 @@ __host__ __device__ constexpr int64_t round_up(int64_t a, int64_t b) { return ce
 __device__ __forceinline__ void set_status(DevStatus* st, int code) {
     atomicCAS(&st->status, 0, code);
 }
+
+// ---- index checks of the debug build ----
+// Built with -DDFS_DEBUG_BOUNDS (build.py --debug-bounds, a separate libdfs_debug.so),
+// DFS_IN_BOUNDS(st, cond) tests the index condition of a global memory access: when it fails,
+// the first failure records DFS_ERR_BOUNDS and its site (DFS_SRC_ID * 100000 + line) in the
+// device status and the caller skips the access (a copy that others wait for aborts its loop,
+// so their bounded waits end).  Nothing traps.  In other builds every check is the constant true.
+// A source file defines DFS_SRC_ID before its includes.
+#ifndef DFS_SRC_ID
+#define DFS_SRC_ID 0
+#endif
+#ifdef DFS_DEBUG_BOUNDS
+static __device__ __noinline__ bool dfs_bounds_fail(const DevStatus* st, int site) {
+    if (st != nullptr) {
+        DevStatus* s = const_cast<DevStatus*>(st);
+        atomicCAS(&s->bounds_site, 0, site);
+        atomicCAS(&s->status, 0, (int)DFS_ERR_BOUNDS);
+    }
+    return false;
+}
+#define DFS_IN_BOUNDS(st, cond) ((cond) || ::dfs::dfs_bounds_fail((st), DFS_SRC_ID * 100000 + __LINE__))
+#else
+#define DFS_IN_BOUNDS(st, cond) true
+#endif
 
 // Block-uniform early exit: thread 0 reads the device status once (another CTA may change it
 // while this one runs), all threads see the same answer.  Contains a __syncthreads().

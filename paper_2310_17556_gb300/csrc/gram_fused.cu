@@ -49,6 +49,7 @@
 // b: converter CTA (I, q) writes rows I * 128 ... of partial q of Rpart (Q partials of n x KQ
 // FP64, each row added in a fixed order by one thread), which pass_reduce / the n-space kernel sum
 // in partial order, so b is deterministic.
+#define DFS_SRC_ID 4
 #include <climits>
 
 #include "gram_tc.cuh"
@@ -273,6 +274,11 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                             known = j + cnt;
                         }
                         fence_proxy_async_global();
+                        if (!DFS_IN_BOUNDS(st, kb < nkb && i0 + 1 < T && (diag || j0 + 1 < T))) {
+                            *abort = 1;
+                            ok = false;
+                            break;
+                        }
                         unsigned char* a = stage_mem + stage * TC_STAGE_BYTES;
                         unsigned char* b = a + 2 * TC_TILE_BYTES;
                         tc::mbar_arrive_expect_tx(&sm->full[stage], bytes);
@@ -607,6 +613,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                         }
                     }
                 unsigned char* tile = Sp + (((int64_t)dkb * T + I) << 14);
+                const bool tile_ok = DFS_IN_BOUNDS(st, dkb < nkb && I < T);
 #pragma unroll
                 for (int e = 0; e < FU_RPT; ++e) {
 #pragma unroll
@@ -622,7 +629,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                         uint2 o;
                         o.x = *reinterpret_cast<const uint32_t*>(&lo);
                         o.y = *reinterpret_cast<const uint32_t*>(&hi);
-                        *reinterpret_cast<uint2*>(tile + soff[e][h]) = o;
+                        if (tile_ok) *reinterpret_cast<uint2*>(tile + soff[e][h]) = o;
                     }
                 }
             };
@@ -672,7 +679,7 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                 for (int e = 0; e < FU_RPT; ++e) {
                     const int r = cw * 4 + rg + FU_ROW_STEP * e;
                     const int i = I * TC_BM + r;
-                    if (i < n)
+                    if (i < n && DFS_IN_BOUNDS(st, q0 < Q))
 #pragma unroll
                         for (int q = 0; q < KQ; ++q) Rpart[((size_t)q0 * n + i) * KQ + q] = rsum[r * KQ + q];
                 }

@@ -39,6 +39,7 @@
 // super-row mixes H and L blocks) and the kernel runs the units of Gram(Z) with J2 < H2 = T_h / 2:
 // the H H^T triangle and the full L H^T rectangle (3 of the 4 quarters of Z Z^T, the work of three
 // BF16 Grams); gram_tc_finalize_x3 forms W = H H^T + L H^T + (L H^T)^T.
+#define DFS_SRC_ID 3
 #include <cudaTypedefs.h>
 
 #include <cstring>
@@ -107,10 +108,15 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const unsigned char* __
                         ok = false;
                         break;
                     }
+                    const int64_t kb = tk.slot + (int64_t)kt * tk.stride;
+                    if (!DFS_IN_BOUNDS(st, kb < nkb && i0 + 1 < T && (diag || j0 + 1 < T))) {
+                        *abort = 1;
+                        ok = false;
+                        break;
+                    }
                     unsigned char* a = stage_mem + stage * TC_STAGE_BYTES;
                     unsigned char* b = a + 2 * TC_TILE_BYTES;
                     tc::mbar_arrive_expect_tx(&sm->full[stage], bytes);
-                    const int64_t kb = tk.slot + (int64_t)kt * tk.stride;
                     if (PACKED) {
                         tc::bulk_load(a, Sp + ((kb * T + i0) << 14), TC_TILE_BYTES, &sm->full[stage]);
                         tc::bulk_load(a + TC_TILE_BYTES, Sp + ((kb * T + i0 + 1) << 14), TC_TILE_BYTES,

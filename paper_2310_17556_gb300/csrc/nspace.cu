@@ -21,6 +21,7 @@
 // Products and sums in T (FP32 on the FP32 / mixed paths, FP64 on the FP64 path); the reduction in
 // FP64.  Every wait is bounded (DFS_ERR_TIMEOUT); with `stop` set (refinement converged) the kernel
 // returns at once.
+#define DFS_SRC_ID 6
 #include "kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -187,6 +188,10 @@ nspace_kernel(const T* __restrict__ W, int64_t ld, int n_pad, const T* __restric
         if (!gthread) return;
         if (idx < ntiles) {
             const int I = tseq[idx] >> 16, sb = tseq[idx] & 0xffff;
+            if (!DFS_IN_BOUNDS(st, I < nsb && sb < nsb && (I + 1) * NS_SB <= n_pad)) {
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                return;
+            }
             T* dst = ring + (size_t)(idx % nslots) * L::TILE + gr * L::RS + gpart * 16;
             const T* src = W + ((int64_t)I * NS_SB + gr) * ld + (int64_t)sb * NS_SB + gpart * 16;
 #pragma unroll

@@ -33,6 +33,7 @@
 // pass_reduce adds in a fixed order.
 #include <cuda_fp8.h>
 
+#define DFS_SRC_ID 2
 #include "kernels.cuh"
 
 namespace dfs {
@@ -267,6 +268,7 @@ sv_pack_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
                             *reinterpret_cast<uint2*>(tile + ((int64_t)(n_rows >> 7) << 14) + off) = wl;
                         } else if constexpr (PACK == 1 && sizeof(TS) == 4) {
                             // 4 floats -> 4 bf16 (8 bytes), half of 16-byte chunk cq / 2
+                            if (!DFS_IN_BOUNDS(st, s < nkb)) continue;
                             const __nv_bfloat162 lo = __floats2bfloat162_rn(sv[u][0], sv[u][1]);
                             const __nv_bfloat162 hi = __floats2bfloat162_rn(sv[u][2], sv[u][3]);
                             uint2 w;
@@ -846,7 +848,7 @@ sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_
                         }
                     } else if constexpr (PACK == 1) {
                         const int i = row0 + t * SWEEP;
-                        if (i < n_rows) {
+                        if (i < n_rows && DFS_IN_BOUNDS(st, s < nkb)) {
                             const int r = i & 127;
                             unsigned char* tile = Sp + (((int64_t)s * (n_rows >> 7) + (i >> 7)) << 14) + r * 128;
                             const __nv_bfloat162 lo = __floats2bfloat162_rn(x0, x1);
@@ -932,6 +934,11 @@ tile_correct_kernel(const unsigned char* __restrict__ Sp, int n, int n_rows, int
             for (int u = 0; u < UNROLL; ++u) {
                 const int r = r0 + RG * u + rg;
                 const unsigned char* row = base + ((r >> 7) << 14) + (r & 127) * 128;
+                if (!DFS_IN_BOUNDS(st, r < n_rows && kb < nkb)) {
+#pragma unroll
+                    for (int e = 0; e < CPL / 2; ++e) w[u][e] = 0u;
+                    continue;
+                }
                 if constexpr (CPL == 8) {
                     const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + ((c ^ (r & 7)) << 4)));
                     w[u][0] = v.x, w[u][1] = v.y, w[u][2] = v.z, w[u][3] = v.w;
@@ -984,7 +991,7 @@ tile_correct_kernel(const unsigned char* __restrict__ Sp, int n, int n_rows, int
                 float* xr = X + (int64_t)q * ldx;
 #pragma unroll
                 for (int e = 0; e < CPL; ++e) {
-                    if (j0 + e < m) {
+                    if (j0 + e < m && DFS_IN_BOUNDS(st, j0 + e < ldx)) {
                         const float du = ((e & 1) ? acc[q][e >> 1].y : acc[q][e >> 1].x) * inv_l;
                         const float xn = xr[j0 + e] - du;
                         xr[j0 + e] = xn;

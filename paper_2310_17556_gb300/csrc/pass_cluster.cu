@@ -23,6 +23,7 @@
 // double-buffered by strip parity: a rank sends strip s + 2's partials (same parity as s) only
 // after it has received strip s + 1's from every rank, which each rank sends only after its own
 // reads of strip s's buffer, so no buffer is overwritten while it is read.
+#define DFS_SRC_ID 1
 #include "kernels.cuh"
 #include "tc_ptx.cuh"
 
@@ -150,7 +151,7 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         const int i = r0 + e / KQ, q = e % KQ;
         Rs64[e] = 0.0;
         Rs32[e] = 0.f;
-        const float y = (haveY && i < n && q < k) ? (float)Y[(int64_t)i * ldy + q] : 0.f;
+        const float y = (haveY && i < n && q < k && DFS_IN_BOUNDS(st, q < ldy)) ? (float)Y[(int64_t)i * ldy + q] : 0.f;
         Ys[2 * e] = y;
         Ys[2 * e + 1] = y;
     }
@@ -173,7 +174,8 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
             for (int tt = 0; tt < TPS; ++tt) {
                 const int t = j * TPS + tt;
                 const int i = r0 + lrow0 + t * CL_SWEEP;
-                const int bytes = i < n ? bytes_col : 0;
+                int bytes = i < n ? bytes_col : 0;
+                if (bytes && !DFS_IN_BOUNDS(st, jn + bytes / 4 <= m && jn + bytes / 4 <= lds)) bytes = 0;
                 const float* src = bytes ? S + (int64_t)i * lds + jn : S;
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
                                  static_cast<uint32_t>(__cvta_generic_to_shared(&slot[t * CL_THREADS + tid]))),
@@ -244,7 +246,8 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         const int64_t j0 = s * CL_W;
         float sv[RPT][4];
         float v_pre = 0.f, x_pre = 0.f;
-        const bool u_valid = u_thread && (j0 + uc < m) && (uq < k);
+        const bool u_valid = u_thread && (j0 + uc < m) && (uq < k) &&
+                             DFS_IN_BOUNDS(st, j0 + uc < ldv && (X == nullptr || j0 + uc < ldx));
         if (u_valid) {
             v_pre = V[(int64_t)uq * ldv + j0 + uc];
             if (writer && X != nullptr && dmode == 1) x_pre = X[(int64_t)uq * ldx + j0 + uc];
@@ -442,7 +445,7 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
         double* dst = Rpart + cid * (int64_t)n * KQ;
         for (int e = tid; e < RC * KQ; e += CL_THREADS) {
             const int i = r0 + e / KQ;
-            if (i < n) dst[(int64_t)i * KQ + e % KQ] = Rs64[e];
+            if (i < n && DFS_IN_BOUNDS(st, cid < ncl)) dst[(int64_t)i * KQ + e % KQ] = Rs64[e];
         }
     }
     // per-RHS sums of U^2 and dX^2: lanes -> warp; the two warps of a right-hand side -> CTA;
@@ -469,7 +472,7 @@ fisher_pass_cluster_kernel(const float* __restrict__ S, int n, int64_t m, int64_
     if (rank == 0 && tid < 2 * KQ) {
         double v = 0.0;
         for (uint32_t r = 0; r < cs; ++r) v += u2c[r][tid];
-        U2part[cid * 2 * KQ + tid] = v;
+        if (DFS_IN_BOUNDS(st, cid < ncl)) U2part[cid * 2 * KQ + tid] = v;
     }
 }
 

@@ -29,7 +29,7 @@ __global__ void status_reset_kernel(DevStatus* st, unsigned long long wait_ns, i
         st->prev_correction = 0.0;
         st->wait_ns = wait_ns;
         st->fault = fault;
-        st->pad = 0;
+        st->bounds_site = 0;
     }
 }
 

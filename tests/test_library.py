@@ -74,6 +74,63 @@ def test_every_nvcc_command_targets_sm103a_only(monkeypatch, tmp_path):
         assert targets == ["arch=compute_103a,code=sm_103a"] and cmd.count("-gencode") == 1, cmd
 
 
+def test_debug_build_has_its_own_flag_objects_and_library(monkeypatch, tmp_path):
+    """--debug-bounds compiles every source with -DDFS_DEBUG_BOUNDS into its own object folder and
+    links libdfs_debug.so; the release build carries no such define (commands captured, not run)."""
+    from paper_2310_17556_gb300 import build
+
+    cmds = []
+
+    class Done:
+        returncode, stdout, stderr = 0, "", ""
+
+    def fake_run(cmd, **kw):
+        cmds.append(list(cmd))
+        open(cmd[cmd.index("-o") + 1], "w").close()
+        return Done()
+
+    monkeypatch.setattr(build.subprocess, "run", fake_run)
+    monkeypatch.setattr(build, "BUILD", str(tmp_path / "rel"))
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "libdfs.so"))
+    monkeypatch.setattr(build, "BUILD_DEBUG", str(tmp_path / "dbg"))
+    monkeypatch.setattr(build, "LIB_DEBUG", str(tmp_path / "libdfs_debug.so"))
+    assert build.build(force=True, debug_bounds=True) == str(tmp_path / "libdfs_debug.so")
+    compiles, link = cmds[:-1], cmds[-1]
+    assert len(compiles) == len(build._sources())
+    for cmd in compiles:
+        assert "-DDFS_DEBUG_BOUNDS" in cmd and cmd[cmd.index("-o") + 1].startswith(str(tmp_path / "dbg")), cmd
+    assert link[link.index("-o") + 1].startswith(str(tmp_path / "libdfs_debug.so"))
+    cmds.clear()
+    build.build(force=True)
+    assert all("-DDFS_DEBUG_BOUNDS" not in cmd for cmd in cmds)
+
+
+def test_debug_checks_guard_the_hot_kernels():
+    """Each kernel source the debug build instruments holds index checks, under its own source id."""
+    csrc = os.path.join(ROOT, "paper_2310_17556_gb300", "csrc")
+    total = 0
+    for name, sid in (("pass_cluster.cu", 1), ("pass.cu", 2), ("gram_tc.cu", 3), ("gram_fused.cu", 4),
+                      ("cholesky.cu", 5), ("nspace.cu", 6)):
+        text = open(os.path.join(csrc, name)).read()
+        assert f"#define DFS_SRC_ID {sid}\n" in text, name
+        assert text.count("DFS_IN_BOUNDS(") >= 1, name
+        total += text.count("DFS_IN_BOUNDS(")
+    assert total >= 15
+
+
+def test_debug_library_is_selected_by_the_environment(monkeypatch, tmp_path):
+    from paper_2310_17556_gb300 import _lib
+
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_DEBUG_PATH", str(tmp_path / "libdfs_debug.so"))
+    monkeypatch.setenv("DFS_DEBUG_BOUNDS", "1")
+    assert _lib.lib_path() == str(tmp_path / "libdfs_debug.so")
+    with pytest.raises(RuntimeError, match="--debug-bounds"):
+        _lib.load()
+    monkeypatch.setenv("DFS_DEBUG_BOUNDS", "0")
+    assert _lib.lib_path() == _lib.LIB_PATH
+
+
 def test_null_handle_is_rejected(libpath):
     from paper_2310_17556_gb300 import _lib
 
