@@ -506,7 +506,7 @@ def run_ours(args):
         kernels.append(hbm_line("gram_fused_kernel", sv_bytes, gram_ms, 1, {
             "tensor_achieved_tflops": gram_tf, "tensor_peak_tflops": bf16,
             "tensor_frac": gram_tf / bf16 if gram_tf else None, "algorithmic_flop_per_launch": gram_flop,
-            "bound_ms_at_peak": max(t_hbm, t_tc), "bound_frac": max(t_hbm, t_tc) * 1e3 / gram_ms if gram_ms else None}))
+            "bound_ms_at_peak": max(t_hbm, t_tc) * 1e3, "bound_frac": max(t_hbm, t_tc) * 1e3 / gram_ms if gram_ms else None}))
     else:
         svp_name = "sv_ring_kernel" if n <= 1024 else "sv_pack_kernel"
         kernels.append(hbm_line(svp_name, sv_bytes, svp_ms, 1))

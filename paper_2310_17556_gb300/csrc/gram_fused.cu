@@ -21,7 +21,8 @@
 //               layout, the layout the MMA descriptors read), and add each row's dot products with
 //               V to FP32 row sums held in registers.  After an item's stores they arrive at a
 //               named barrier the signaler waits on (barriers do not wait for loads in flight), in
-//               two alternating slots, each freed again by the signaler.  A prefetch to L2 runs a
+//               FU_SLOTS rotating slots, each freed again by the signaler.  The signaler publishes
+//               the items in groups of FU_PUB, one fence per group.  A prefetch to L2 runs a
 //               few items ahead of their loads.
 // The kernel is launched at 128 registers a thread and the warpgroups re-divide them
 // (setmaxnreg): the converters take 184, enough for three items of loads in flight.
@@ -41,9 +42,9 @@
 //
 // Progress.  All CTAs are co-resident (cooperative launch).  A producer waiting at step tau needs
 // only items of step tau, and a converter is held back only while it is more than `lead` steps
-// ahead of a producer that has work left, with none of the items whose loads it holds needed
-// before then; so the item of the smallest unfinished step can always be converted, and every
-// wait ends.  Every wait is still bounded (2 s); on a timeout the CTA records DFS_ERR_TIMEOUT,
+// ahead of a producer that has work left, with none of the items whose loads it holds (or that
+// it wrote and whose publication group is still open) needed before then; so the item of the
+// smallest unfinished step can always be converted and published, and every wait ends.  Every wait is still bounded (2 s); on a timeout the CTA records DFS_ERR_TIMEOUT,
 // stops its roles, waits for its copies and MMAs in flight and frees TMEM.
 //
 // b: converter CTA (I, q) writes rows I * 128 ... of partial q of Rpart (Q partials of n x KQ
@@ -74,9 +75,14 @@ constexpr int FU_LAUNCH_REGS = 128;
 constexpr int FU_REGS_WG0 = 64, FU_REGS_EPI = 80, FU_REGS_CONV = 184;
 static_assert(128 * (FU_REGS_WG0 + FU_REGS_EPI) + FU_CONV_THREADS * FU_REGS_CONV <= FU_THREADS * FU_LAUNCH_REGS,
               "the register split must fit the launch's registers");
-// named barriers: 1 = converters' start; 2, 3 = item written (converters arrive, the signaler
-// waits); 4, 5 = slot free again (the signaler arrives, converters wait)
-constexpr int FU_BAR_START = 1, FU_BAR_FULL = 2, FU_BAR_EMPTY = 4;
+// Items the signaler publishes per gpu-scope fence (a fence waits for the stores it covers to
+// reach L2; one fence per item held the converters back: 1.456 -> 1.442 ms at n=1024, m=2^20).
+constexpr int FU_PUB = 4;
+constexpr int FU_SLOTS = FU_PUB > 2 ? FU_PUB : 2;        // items a converter may run ahead of the signaler
+// named barriers: 1 = converters' start; 2 .. 2 + FU_SLOTS - 1 = item written (converters arrive,
+// the signaler waits); the next FU_SLOTS = slot free again (the signaler arrives, converters wait)
+constexpr int FU_BAR_START = 1, FU_BAR_FULL = 2, FU_BAR_EMPTY = 2 + FU_SLOTS;
+static_assert(FU_BAR_EMPTY + FU_SLOTS <= 16, "named barrier ids");
 constexpr bool kVAtIssue(int kq) { return kq == 1; }  // V loaded with the item (else when converted)
 constexpr int FU_HANDSHAKE = FU_CONV_THREADS + 32;
 constexpr int FU_FLAG_WINDOW = 8;  // ready counts the producer reads ahead at once
@@ -120,6 +126,7 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
+
 __device__ __forceinline__ void red_relaxed_gpu_add(int* p, int v) {
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -365,28 +372,39 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
         } else if (warp == FU_SIG_WARP) {
             // ---------------- signaler ----------------
             // For every item of this CTA, in order: wait until the converters have written it (slot
-            // li % 2), free the slot for item li + 2, and publish the tile.  The barrier sequence is
-            // the converters' exactly (every item, whatever its validity), so neither side can wait
-            // for an arrival that never comes.
+            // li % FU_SLOTS) and free the slot for item li + FU_SLOTS; after each group of FU_PUB
+            // items, one fence and the group's ready counts.  The barrier sequence is the
+            // converters' exactly (every item, whatever its validity), so neither side can wait for
+            // an arrival that never comes.
             if (conv) {
                 FuCursor cur;
                 cur.init(q0, w, NK);
-                if (my_items > 0) named_bar_arrive(FU_BAR_EMPTY + 0, FU_HANDSHAKE);
-                if (my_items > 1) named_bar_arrive(FU_BAR_EMPTY + 1, FU_HANDSHAKE);
-                for (int li = 0; li < my_items; ++li) {
-                    const int kb = cur.kb(w, c);
-                    const bool valid = kb < nkb;
-                    cur.advance(Q, w, NK);
-                    named_bar_sync(FU_BAR_FULL + (li & 1), FU_HANDSHAKE);
-                    if (li + 2 < my_items) named_bar_arrive(FU_BAR_EMPTY + (li & 1), FU_HANDSHAKE);
-                    // (test hook: CTA 0 withholds its first tile, so the Gram's waits for it run out)
-                    const bool withhold = fault == DFS_TEST_FAULT_FUSED_GRAM && blockIdx.x == 0 && li == 0;
-                    if (lane == 0 && valid && !withhold) {
-                        // the converters' stores are ordered before the barrier; this thread's
-                        // gpu-scope fence makes them visible before the count it adds
+                for (int sl = 0; sl < FU_SLOTS && sl < my_items; ++sl)
+                    named_bar_arrive(FU_BAR_EMPTY + sl, FU_HANDSHAKE);
+                for (int g0 = 0; g0 < my_items; g0 += FU_PUB) {
+                    int kbs[FU_PUB];
+#pragma unroll
+                    for (int d = 0; d < FU_PUB; ++d) {
+                        const int li = g0 + d;
+                        kbs[d] = -1;
+                        if (li < my_items) {
+                            const int kb = cur.kb(w, c);
+                            cur.advance(Q, w, NK);
+                            named_bar_sync(FU_BAR_FULL + li % FU_SLOTS, FU_HANDSHAKE);
+                            if (li + FU_SLOTS < my_items) named_bar_arrive(FU_BAR_EMPTY + li % FU_SLOTS, FU_HANDSHAKE);
+                            // (test hook: CTA 0 withholds its first tile, so the Gram's waits for it run out)
+                            const bool withhold = fault == DFS_TEST_FAULT_FUSED_GRAM && blockIdx.x == 0 && li == 0;
+                            if (kb < nkb && !withhold) kbs[d] = kb;
+                        }
+                    }
+                    if (lane == 0) {
+                        // the converters' stores are ordered before the barriers; this thread's
+                        // gpu-scope fence makes them visible before the counts it adds
                         fence_proxy_async_global();
                         fence_acq_rel_gpu();
-                        red_relaxed_gpu_add(ready + kb, 1);
+#pragma unroll
+                        for (int d = 0; d < FU_PUB; ++d)
+                            if (kbs[d] >= 0) red_relaxed_gpu_add(ready + kbs[d], 1);
                     }
                 }
             }
@@ -662,8 +680,8 @@ gram_fused_kernel(const float* __restrict__ S, int n, int64_t m, int64_t lds, co
                     if (li < my_items) {
                         process(buf[d], desc[d], vbuf[d]);
                         // hand the item to the signaler: wait until its slot is free, then arrive
-                        named_bar_sync(FU_BAR_EMPTY + (li & 1), FU_HANDSHAKE);
-                        named_bar_arrive(FU_BAR_FULL + (li & 1), FU_HANDSHAKE);
+                        named_bar_sync(FU_BAR_EMPTY + li % FU_SLOTS, FU_HANDSHAKE);
+                        named_bar_arrive(FU_BAR_FULL + li % FU_SLOTS, FU_HANDSHAKE);
                         if (++since_fold == kFoldItems) {
                             since_fold = 0;
                             fold();
@@ -770,11 +788,12 @@ cudaError_t launch_gram_fused(const GramTcPlan& plan, int kq, const void* S, int
     int ni = (int)n;
     int nkb = (int)plan.nkb;
     // A converter holds the loads of fu_depth - 1 items it has not yet written while it waits to
-    // issue the next; its consecutive items are Q / w steps apart, so those items lie at most
+    // issue the next, and up to FU_PUB - 1 written items may still wait for the rest of their
+    // publication group; its consecutive items are Q / w steps apart, so those items lie at most
     // `span` steps behind it.  With lead >= span an item the producer waits for is never one held
     // back that way (the progress argument above).
     const int Q = num_sms / T;
-    const int span = (int)ceil_div((int64_t)(fu_depth(kq) - 1) * Q, w) + 1;
+    const int span = (int)ceil_div((int64_t)(fu_depth(kq) - 1 + FU_PUB - 1) * Q, w) + 1;
     int lead = kLead + span;
     void* args[] = {(void*)&s,  (void*)&ni, (void*)&m,   (void*)&lds, (void*)&v,    (void*)&ldv,
                     (void*)&k,  (void*)&v_vec, (void*)&Rpart, (void*)&sp, (void*)&T,  (void*)&U,
