@@ -520,21 +520,24 @@ dfs_status solve_device(dfs_handle h, const void* S, int s_dtype, int64_t n, int
                                U2part, 0, h->dstat, 0, stream));
             if (mark_pass) DFS_CK(mark(9));
         } else {
-            // The step after the first reads the packed BF16 tiles instead of S when they exist:
-            // x_2 = x_1 - S_bf16^T dy_1 / lambda (the tiles' rounding costs 2^-9 of a correction of
-            // relative size delta_2, which the check adds to its estimate).  If that does not
-            // converge, the full pass of step 2 recomputes x_2 exactly and refinement goes on.
+            // Steps 2 and 3 first read the packed BF16 tiles instead of S when they exist:
+            // x_j = x_{j-1} - S_bf16^T dy_{j-1} / lambda (the tiles' rounding costs 2^-9 of a
+            // correction of relative size delta_j, which the check adds to its estimate).  If that
+            // does not converge, the full pass of step j recomputes x_j exactly and refinement goes
+            // on; a step-3 correction then usually ends it (its delta_3 is a small multiple of
+            // delta_2) one full pass earlier.  The last allowed step is always a full pass, so the
+            // iteration budget is still decided on exact x.
             const bool fast = p.pack == 1 && !center && max_iter >= 3 && !p.f64 && kq <= 8 &&
                               tile_correct_fits((int)round_up(n, 256), kq, h->smem_optin);
             for (int it = 1; it <= max_iter; ++it) {
-                const bool corrected = fast && it == 2;
+                const bool corrected = fast && (it == 2 || it == 3) && it < max_iter;
                 if (corrected) {
-                    if (mark_pass) DFS_CK(mark(11));
+                    if (mark_pass && it == 2) DFS_CK(mark(11));
                     int cparts = 0;
                     DFS_CK(launch_tile_correct(kq, Sp, ni, (int)round_up(n, 256), m, pack_kblocks(s_dtype, 1, m),
                                                static_cast<const float*>(Z), kg, lambda, static_cast<float*>(Xg), ldx,
                                                U2part, h->dstat, h->num_sms, stream, &cparts));
-                    if (mark_pass) DFS_CK(mark(12));
+                    if (mark_pass && it == 2) DFS_CK(mark(12));
                     DFS_CK(launch_refine_check(U2part, cparts, U2, kq, kg, lambda, tol, it, max_iter, 1, h->dstat,
                                                stream));
                 }
@@ -721,11 +724,11 @@ dfs_status solve_complex_device(dfs_handle h, const void* Zs, int s_dtype, int64
             DFS_CK(launch_pass(p.pp, s_dtype, KQP, Zs, n2i, m, lds, Vp, ldc, 2 * kg, Yp, KQP, lambda, Xp, ldc, nullptr,
                                U2part, 0, h->dstat, 0, stream));
         } else {
-            // as the real path: the step after the first takes x_2 = x_1 - S_bf16^dagger dy_1 / lambda from
-            // Z's packed BF16 tiles; if that does not converge, the full pass of step 2 recomputes x_2
+            // as the real path: steps 2 and 3 first take x_j = x_{j-1} - S_bf16^dagger dy_{j-1} / lambda
+            // from Z's packed BF16 tiles; if that does not converge, the full pass of step j recomputes x_j
             const bool fast = p.pack == 1 && max_iter >= 3 && !p.f64 && tile_correct_fits(n_rows_t, KQP, h->smem_optin);
             for (int it = 1; it <= max_iter; ++it) {
-                const bool corrected = fast && it == 2;
+                const bool corrected = fast && (it == 2 || it == 3) && it < max_iter;
                 if (corrected) {
                     DFS_CK(launch_complex_dyexp(static_cast<const float*>(Zv), KQN, ni, kg, KQP, dy, n_rows_t, h->dstat,
                                                 1, stream));

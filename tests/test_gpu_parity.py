@@ -416,6 +416,18 @@ def test_refinement_final_correction_from_bf16_tiles(lam):
     assert info2["passes"] == info2["iters"] >= 1, info2
 
 
+def test_refinement_step3_correction_from_bf16_tiles():
+    """A batch-like problem (m/n near 70, eight right-hand sides) whose step-2 correction from the
+    tiles misses the tolerance: the full pass recomputes x_2, and step 3 then ends on a correction
+    from the tiles again instead of a third full pass.  x still meets the mixed path's 1e-6."""
+    n, m, lam = 900, 62776, 0.0156
+    S = wl.gaussian(n, m, seed=94, device=dev())
+    V = wl.rhs(m, 8, seed=95, device=dev())
+    X, info = dfs.dfs_solve(S, V, lam, precision="bf16")
+    assert info["status"] == 0 and info["passes"] < info["iters"], info
+    assert_mixed(S, V, lam, X)
+
+
 def test_nspace_sixteen_cta_cluster():
     """n = 5000 (n_pad 5120): eight ranks cannot hold their diagonal inverses in shared memory,
     so the n-space solves run as a 16-CTA cluster; the solve still matches the oracle."""
