@@ -409,18 +409,25 @@ sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
     for (int j = 0; j < R; ++j)
 #pragma unroll
         for (int q = 0; q < KQ; ++q) acc[j][q] = 0.f;
+    // FP32 row sums -> the warp's FP64 sums: each (row, RHS) value is added over the warp's lanes
+    // in FP32 (a butterfly: every lane ends with the total), then lane j KQ + q adds value (j, q)
+    // to FP64, so that a fold costs each warp two FP64 instructions (on GB300 an FP64 warp
+    // instruction occupies its sub-partition's FP64 unit for about 64 cycles, whatever the lanes).
+    static_assert(R * KQ <= 32, "one lane per (row, RHS) value");
     auto fold = [&]() {
+        float mine = 0.f;
 #pragma unroll
         for (int j = 0; j < R; ++j)
 #pragma unroll
             for (int q = 0; q < KQ; ++q) {
                 if (q >= k) break;
-                double d = (double)acc[j][q];
+                float a = acc[j][q];
                 acc[j][q] = 0.f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                if (lane == 0) s_acc[warp][j * KQ + q] += d;
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == j * KQ + q) mine = a;
             }
+        if (lane < R * KQ) s_acc[warp][lane] += (double)mine;
     };
     int since = 0;
     for (int64_t base = g0; base < g1; base += (int64_t)U * SVB_THREADS) {
@@ -593,8 +600,13 @@ sty_cols_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds, const f
     constexpr int VEC = Vec16<TS>::N;  // 4 (FP32) or 8 (BF16)
     constexpr int LPG = 8 / VEC;       // 16-byte loads per row: 2 (FP32) or 1 (BF16)
     constexpr int RB = StyRows<TS, KQ>::R;
-    constexpr bool Y_AHEAD = RB * KQ <= 16;  // the step's y values fit registers beside S
     constexpr int PANEL = 256;
+    // y in FP32, YB rows at a time (a multiple of the rows of a step), converted once per CTA and
+    // read from shared memory: converting it from FP64 in the row loop (KQ conversions a row and
+    // thread) made the loop FP64-bound with several right-hand sides, as FP64 instructions are
+    // slow on this GPU.  The values are the same FP32 roundings of y as before.
+    constexpr int YB = RB * ((PANEL + RB - 1) / RB);
+    __shared__ __align__(16) float ys[YB * KQ];
     extern __shared__ double tot[];  // [(q * 8 + e) * SVB_THREADS + tid]
     double* uds = tot + KQ * 8 * SVB_THREADS;  // [q * SVB_THREADS + tid]: U^2, then dX^2 at + KQ
     __shared__ double red[SVB_WARPS][16];
@@ -615,8 +627,17 @@ sty_cols_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds, const f
             for (int q = 0; q < KQ; ++q)
 #pragma unroll
                 for (int e = 0; e < 8; ++e) acc[q][e] = 0.f;
-            int rows = 0;
+            int rows = 0, yb0 = 0;
             for (int i0 = 0; i0 < n; i0 += RB) {
+                if (i0 % YB == 0) {
+                    __syncthreads();  // every thread is done with the previous block of y
+                    yb0 = i0;
+                    for (int e = tid; e < YB * KQ; e += SVB_THREADS) {
+                        const int i = i0 + e / KQ, q = e % KQ;
+                        ys[e] = (i < n && q < k) ? (float)Y[(int64_t)i * ldy + q] : 0.f;
+                    }
+                    __syncthreads();
+                }
                 uint4 raw[RB][LPG];
 #pragma unroll
                 for (int j = 0; j < RB; ++j) {
@@ -640,21 +661,20 @@ sty_cols_kernel(const TS* __restrict__ S, int n, int64_t m, int64_t lds, const f
                         }
                     }
                 }
-                auto y_at = [&](int j, int q) -> float {
-                    return (i0 + j < n && q < k) ? (float)__ldg(Y + (int64_t)(i0 + j) * ldy + q) : 0.f;
-                };
-                float ya[Y_AHEAD ? RB : 1][KQ];
-                if constexpr (Y_AHEAD) {
-#pragma unroll
-                    for (int j = 0; j < RB; ++j)
-#pragma unroll
-                        for (int q = 0; q < KQ; ++q) ya[j][q] = y_at(j, q);
-                }
 #pragma unroll
                 for (int j = 0; j < RB; ++j) {
                     float yv[KQ];
+                    const float* yr = ys + (i0 - yb0 + j) * KQ;
+                    if constexpr (KQ == 4) {
+                        const float4 t = *reinterpret_cast<const float4*>(yr);
+                        yv[0] = t.x, yv[1] = t.y, yv[2] = t.z, yv[3] = t.w;
+                    } else if constexpr (KQ == 2) {
+                        const float2 t = *reinterpret_cast<const float2*>(yr);
+                        yv[0] = t.x, yv[1] = t.y;
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < KQ; ++q) yv[q] = Y_AHEAD ? ya[Y_AHEAD ? j : 0][q] : y_at(j, q);
+                        for (int q = 0; q < KQ; ++q) yv[q] = yr[q];
+                    }
                     float sv[8];
                     svb_unpack_raw<TS>(raw[j], sv);
 #pragma unroll
@@ -884,13 +904,13 @@ sv_ring_kernel(const float* __restrict__ S, int n, int n_rows, int64_t m, int64_
 // ||x_new - x_old||^2 per RHS (U2part, 2 KQ doubles per CTA).  Each warp owns whole k-blocks (64
 // columns): lane (chunk c = lane % 8, row group lane / 8) reads the 16-byte logical chunk c (8
 // columns) of rows lane / 8, + 4, + 8, ... (the four rows of a step are whole 128-byte lines), 8
-// steps in flight; with 8 right-hand sides 16 lanes of 8 bytes cover a row and a warp has two row
-// groups.  dy sits in shared memory, each value twice, so that one 16-byte load gives the
+// steps in flight (16 with 4 right-hand sides); with 8 right-hand sides 16 lanes of 8 bytes cover a
+// row, a warp has two row groups and 32 steps in flight.  dy sits in shared memory, each value twice, so that one 16-byte load gives the
 // operands of two right-hand sides' paired multiply-adds (each lane of a pair an IEEE fmaf, as in
 // scalar code); the row groups are added with shuffles and the lanes of row group 0 update their
 // columns of x in place.
 constexpr int TC_CORR_THREADS = 512;
-constexpr int TC_CORR_ROWS = 32;  // n_rows is a multiple of the rows a warp has in flight
+constexpr int TC_CORR_ROWS = 64;  // n_rows is a multiple of the rows a warp has in flight
 
 template <int KQ>
 __global__ void __launch_bounds__(TC_CORR_THREADS)
@@ -902,7 +922,9 @@ tile_correct_kernel(const unsigned char* __restrict__ Sp, int n, int n_rows, int
     constexpr int CPL = KQ >= 8 ? 4 : 8;
     constexpr int LPRC = 64 / CPL;  // lanes per row
     constexpr int RG = 32 / LPRC;   // row groups of a warp
-    constexpr int UNROLL = CPL == 4 ? 16 : 8;  // rows in flight per thread (128 bytes either way)
+    // rows in flight per thread: 128 bytes, or 256 with 4 or more right-hand sides, whose
+    // accumulators leave room for one CTA per SM only (the bytes in flight then come from the rows)
+    constexpr int UNROLL = CPL == 4 ? 32 : (KQ >= 4 ? 16 : 8);
     static_assert(RG * UNROLL <= TC_CORR_ROWS && TC_CORR_ROWS % (RG * UNROLL) == 0, "row step");
     // dy twice per entry, [row][q][2]: the pair operand of the paired multiply-adds
     extern __shared__ float sdy[];  // n_rows x KQ x 2
