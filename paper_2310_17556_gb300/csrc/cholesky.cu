@@ -154,7 +154,7 @@ __device__ __noinline__ bool factor_diag(T* W, int64_t ld, int kb, T* Linv, DevS
         CT d = __shfl_sync(0xffffffffu, a[0], 0);
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-            if (fail < 0 && (!(d > (CT)0) || !isfinite(d))) fail = isfinite(d) ? j : -2 - j;
+            if (fail == -1 && (!(d > (CT)0) || !isfinite(d))) fail = isfinite(d) ? j : -2 - j;  // the first bad pivot
             const CT r = rsqrt_ct(d);
             const CT l = a[j] * r;
             a[j] = (lane >= j) ? l : (CT)0;
@@ -173,7 +173,7 @@ __device__ __noinline__ bool factor_diag(T* W, int64_t ld, int kb, T* Linv, DevS
             }
         }
         if (lane == 0) *s_fail = fail;
-        if (fail < 0) {
+        if (fail == -1) {
             // a[lane] by an unrolled select: a dynamic index would move all of a[] to local memory
             CT dl = (CT)0;
 #pragma unroll
@@ -250,8 +250,124 @@ __device__ __forceinline__ void load_linv(const T* Linv, int kb, T (*sLi)[NB + 1
     __syncthreads();
 }
 
+// Lane 0 waits (acquire) until *f >= target, as block_wait but for one warp; warp-uniform result.
+__device__ bool warp_wait(const int* f, int target, DevStatus* st) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0 && ld_acquire_gpu(f) < target) {
+        const volatile int* vs = &st->status;
+        const uint64_t limit_ns = wait_limit(st);
+        const uint64_t t0 = tc::globaltimer_ns();
+        for (;;) {
+            if (ld_acquire_gpu(f) >= target) break;
+            if (*vs != 0) {
+                ok = 0;
+                break;
+            }
+            if (tc::globaltimer_ns() - t0 > limit_ns) {
+                set_status(st, DFS_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();  // the other lanes' reads come after lane 0's acquire
+    return ok != 0;
+}
+
+// Warp-private tiles of the trailing update, rows padded to a multiple of 4 (16-byte row loads).
+constexpr int WT_LD = NB + 4;
+constexpr int CC_WARPS = CC_THREADS / 32;
+constexpr size_t CC_WARP_SMEM = (size_t)CC_WARPS * 2 * NB * WT_LD * sizeof(float);
+
+// sum_q a[q] b[q] over 32 terms, in order: a is a shared-memory row read as 16-byte broadcasts,
+// b is in registers.
+__device__ __forceinline__ float warp_dot32(const float* a, const float (&b)[NB]) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < NB; q += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(a + q);
+        s = fmaf(x.x, b[q], s);
+        s = fmaf(x.y, b[q + 1], s);
+        s = fmaf(x.z, b[q + 2], s);
+        s = fmaf(x.w, b[q + 3], s);
+    }
+    return s;
+}
+
+// sA <- sA Linv^T for one warp (FP32): lane c forms column c, acc[r] = sum_q A[r][q] Li[c][q], with
+// Li's row c in registers and A's rows read as 16-byte broadcasts (warp_dot32).
+__device__ __forceinline__ void warp_times_linv_t(float (*sA)[WT_LD], const float (*sLi)[NB + 1]) {
+    const int lane = threadIdx.x & 31;
+    float li[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) li[q] = sLi[lane][q];
+    float acc[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) acc[r] = warp_dot32(&sA[r][0], li);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < NB; ++r) sA[r][lane] = acc[r];
+    __syncwarp();
+}
+
+// One tile of the trailing update by one warp (FP32 W): A[i, p] -= P_i P_p^T with
+// P = A[., j] Linv_j^T, after the waits for tiles (i, j) and (p, j).  Used for the tiles of columns
+// beyond j + 1 (no flag to publish: their last update comes in a later step).  The two panel tiles
+// come in with 16-byte asynchronous copies (all in flight at once), and the target tile's 32
+// rows are loaded together before it is written back.  Lane c
+// owns column c of the tile: its loads and stores of W are whole 128-byte rows.  Returns false
+// when a wait gave up (the device status says why).
+__device__ bool warp_tile_update(float* W, int64_t ld, int j, int i, int p, const float (*sLi)[NB + 1],
+                                 float (*sPw)[WT_LD], float (*sQw)[WT_LD], const int* done, DevStatus* st) {
+    const int lane = threadIdx.x & 31;
+    if (j > 0) {
+        if (!warp_wait(&done[tile_id(i, j)], 1, st)) return false;
+        if (p != i && !warp_wait(&done[tile_id(p, j)], 1, st)) return false;
+    }
+    const int64_t c0 = (int64_t)j * NB;
+    // 32 rows x 8 chunks of 16 bytes per tile: lane takes chunk lane % 8 of rows lane / 8 + 4 u
+#pragma unroll
+    for (int u = 0; u < NB / 4; ++u) {
+        const int r = (lane >> 3) + 4 * u, ch = lane & 7;
+        const float* gp = W + ((int64_t)i * NB + r) * ld + c0 + 4 * ch;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         static_cast<uint32_t>(__cvta_generic_to_shared(&sPw[r][4 * ch]))), "l"(gp) : "memory");
+        if (p != i) {
+            const float* gq = W + ((int64_t)p * NB + r) * ld + c0 + 4 * ch;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             static_cast<uint32_t>(__cvta_generic_to_shared(&sQw[r][4 * ch]))), "l"(gq) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    warp_times_linv_t(sPw, sLi);
+    if (p != i) warp_times_linv_t(sQw, sLi);
+    const float(*pq)[WT_LD] = (p != i) ? sQw : sPw;
+    // D[r][lane] = sum_q P_i[r][q] P_p[lane][q], into sQw (free once every lane holds its row of P_p)
+    float qrow[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) qrow[q] = pq[lane][q];
+    __syncwarp();
+#pragma unroll 4
+    for (int r = 0; r < NB; ++r) sQw[r][lane] = warp_dot32(&sPw[r][0], qrow);
+    // A[i, p] -= D: the target tile's column `lane`, all rows in flight at once
+    float wv[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) wv[r] = __ldcg(W + ((int64_t)i * NB + r) * ld + (int64_t)p * NB + lane);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        if (i == p && lane > r) continue;
+        if (!DFS_IN_BOUNDS(st, p <= i)) continue;
+        W[((int64_t)i * NB + r) * ld + (int64_t)p * NB + lane] = wv[r] - sQw[r][lane];
+    }
+    __syncwarp();  // sPw / sQw are reused by the warp's next tile
+    return true;
+}
+
 // flags (int32, zeroed before the launch): diag[nb] | done[nb (nb + 1) / 2] | finished-CTA count
-template <typename T, typename CT>
+template <typename T, typename CT, bool WARP_TILES>
 __global__ void __launch_bounds__(CC_THREADS)
 chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
     __shared__ __align__(16) T sLi[NB][NB + 1];
@@ -262,6 +378,13 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
     __shared__ __align__(16) CT sCol[2][NB];
     __shared__ T s_rinv[NB];
     __shared__ int s_ok, s_fail;
+    // WARP_TILES (FP32 W and FP32 diagonal blocks, n >= 2048): the bulk of each step's trailing
+    // update (tiles of columns beyond j + 1) runs one tile per warp, 8 tiles at once per CTA, in
+    // warp-private tiles (dynamic shared memory); column j + 1, on the critical path, keeps the
+    // whole CTA per tile.  Below 2048 rows a CTA rarely has three such tiles in a step, and the
+    // kernel without them (fewer registers, no dynamic shared memory) is the faster one.
+    constexpr bool kWarpTiles = WARP_TILES && sizeof(T) == 4 && sizeof(CT) == 4;
+    extern __shared__ __align__(16) float wtiles[];  // [warp][P | Q][NB][WT_LD] (FP32 W only)
     if (block_should_exit(st, 0)) return;
     // every tile of the nb x nb block grid lies inside W's rows of ld elements (uniform over the
     // grid: all CTAs return alike)
@@ -304,6 +427,35 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
         load_linv<T>(Linv, j, sLi);
         // pass 0: tiles of column j + 1 (diagonal first: it has the smallest id); pass 1: the rest
         for (int pass = 0; pass < 2; ++pass) {
+            // With three or more tiles in the pass (large n), they are dealt to the CTA's warps (a
+            // warp takes about twice as long over a tile as the whole CTA, but eight run at once);
+            // with fewer (small n, where the step's latency matters more than its throughput) the
+            // whole CTA takes one tile at a time, as for column j + 1.
+            int npass1 = 0;
+            if (kWarpTiles && pass == 1) {
+                for (int t = cta; t < ntiles; t += G) {
+                    int i, p;
+                    tile_ij(t, i, p);
+                    npass1 += p > j + 1;
+                }
+            }
+            if (kWarpTiles && pass == 1 && npass1 >= 3) {
+                // the CTA's tiles of the pass dealt to its warps in order, one tile per warp at a time
+                const int warp = tid >> 5;
+                float (*sPw)[WT_LD] = reinterpret_cast<float (*)[WT_LD]>(wtiles + (size_t)warp * 2 * NB * WT_LD);
+                float (*sQw)[WT_LD] = sPw + NB;
+                const float(*sLif)[NB + 1] = reinterpret_cast<const float(*)[NB + 1]>(sLi);
+                int kk = 0;
+                for (int t = cta; t < ntiles; t += G) {
+                    int i, p;
+                    tile_ij(t, i, p);
+                    if (p <= j + 1) continue;
+                    if ((kk++ % CC_WARPS) != warp) continue;
+                    // a wait that gave up leaves the rest to the next block_wait, which sees the status
+                    if (!warp_tile_update(reinterpret_cast<float*>(W), ld, j, i, p, sLif, sPw, sQw, done, st)) break;
+                }
+                continue;
+            }
             for (int t = cta; t < ntiles; t += G) {
                 int i, p;
                 tile_ij(t, i, p);
@@ -457,8 +609,12 @@ static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* 
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    auto kern = chol_coop_kernel<T, CT>;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CC_THREADS, 0)) != cudaSuccess) return e;
+    const bool warp_tiles = sizeof(T) == 4 && sizeof(CT) == 4 && nb >= 64;
+    auto kern = warp_tiles ? chol_coop_kernel<T, CT, true> : chol_coop_kernel<T, CT, false>;
+    const size_t dsmem = warp_tiles ? CC_WARP_SMEM : 0;  // warp tiles of the FP32 trailing update
+    if (dsmem && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CC_THREADS, dsmem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     // two CTAs per SM where they fit (all resident): a CTA waiting on an L2 round trip leaves the
     // SM to the other
@@ -469,7 +625,7 @@ static cudaError_t launch_cholesky_t(void* W_, int64_t ld, int64_t n_pad, void* 
     if (G > ntiles) G = ntiles;
     if ((e = cudaMemsetAsync(flags, 0, cholesky_flag_bytes(n_pad), stream)) != cudaSuccess) return e;
     void* args[] = {&W, &ld, &nb, &Linv, &flags, &st};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(CC_THREADS), args, 0, stream);
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(CC_THREADS), args, dsmem, stream);
     count_launch();
     return e;
 }

@@ -28,6 +28,7 @@ SHORT_NS = 5_000_000  # 5 ms
 
 @pytest.mark.parametrize("fault,prec,n,m", [
     (DFS_TEST_FAULT_CHOLESKY, "fp32", 512, 20000),       # the Cholesky's flag waits
+    (DFS_TEST_FAULT_CHOLESKY, "fp32", 2304, 20000),      # the same with the per-warp trailing tiles
     (DFS_TEST_FAULT_CLUSTER_PASS, "bf16", 1024, 65536),  # the refinement pass's cluster exchange
     (DFS_TEST_FAULT_FUSED_GRAM, "bf16", 1024, 65536),    # the fused first pass's tile waits
 ])

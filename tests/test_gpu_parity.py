@@ -617,7 +617,8 @@ def test_cholesky_step(dtype, n, tol):
 
 
 @pytest.mark.parametrize("n,bad,value,status", [(1024, 700, -1.0, 2), (1024, 1023, 0.0, 2),
-                                                (600, 31, float("nan"), 4), (300, 0, -2.0, 2)])
+                                                (600, 31, float("nan"), 4), (300, 0, -2.0, 2),
+                                                (2304, 2200, -1.0, 2), (2304, 100, float("nan"), 4)])
 def test_cholesky_failure_anywhere(n, bad, value, status):
     # every CTA of the factorisation must see the failure and stop (no wait runs out)
     A = wl.gaussian(n, 2 * n, seed=43, device=dev(), dtype=torch.float64)
