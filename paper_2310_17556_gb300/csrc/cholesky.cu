@@ -295,9 +295,11 @@ __device__ __forceinline__ float warp_dot32(const float* a, const float (&b)[NB]
     return s;
 }
 
-// sA <- sA Linv^T for one warp (FP32): lane c forms column c, acc[r] = sum_q A[r][q] Li[c][q], with
-// Li's row c in registers and A's rows read as 16-byte broadcasts (warp_dot32).
-__device__ __forceinline__ void warp_times_linv_t(float (*sA)[WT_LD], const float (*sLi)[NB + 1]) {
+// sOut <- sA Li^T for one warp (FP32; sOut may be sA): lane c forms column c,
+// acc[r] = sum_q A[r][q] Li[c][q], with Li's row c in registers and A's rows read as 16-byte
+// broadcasts (warp_dot32).
+__device__ __forceinline__ void warp_times_linv_t(const float (*sA)[WT_LD], const float (*sLi)[NB + 1],
+                                                  float (*sOut)[WT_LD]) {
     const int lane = threadIdx.x & 31;
     float li[NB];
 #pragma unroll
@@ -307,18 +309,20 @@ __device__ __forceinline__ void warp_times_linv_t(float (*sA)[WT_LD], const floa
     for (int r = 0; r < NB; ++r) acc[r] = warp_dot32(&sA[r][0], li);
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < NB; ++r) sA[r][lane] = acc[r];
+    for (int r = 0; r < NB; ++r) sOut[r][lane] = acc[r];
     __syncwarp();
 }
 
-// One tile of the trailing update by one warp (FP32 W): A[i, p] -= P_i P_p^T with
-// P = A[., j] Linv_j^T, after the waits for tiles (i, j) and (p, j).  Used for the tiles of columns
-// beyond j + 1 (no flag to publish: their last update comes in a later step).  The two panel tiles
-// come in with 16-byte asynchronous copies (all in flight at once), and the target tile's 32
-// rows are loaded together before it is written back.  Lane c
-// owns column c of the tile: its loads and stores of W are whole 128-byte rows.  Returns false
-// when a wait gave up (the device status says why).
-__device__ bool warp_tile_update(float* W, int64_t ld, int j, int i, int p, const float (*sLi)[NB + 1],
+// One tile of the trailing update by one warp (FP32 W): A[i, p] -= P_i P_p^T with P = A[., j]
+// Linv_j^T, evaluated as (A[i, j] M_j) A[p, j]^T with M_j = Linv_j^T Linv_j (the inverse of the
+// factored diagonal block, formed once per step by the CTA), so a tile costs two 32^3 products
+// instead of three.  Waits for tiles (i, j) and (p, j) first.  Used for the tiles of columns
+// beyond j + 1 (no flag to publish: their last update comes in a later step).  The two panel
+// tiles come in with 16-byte asynchronous copies (all in flight at once), and the target tile's
+// 32 rows are loaded together before it is written back.  Lane c owns column c of the tile: its
+// loads and stores of W are whole 128-byte rows.  Returns false when a wait gave up (the device
+// status says why).
+__device__ bool warp_tile_update(float* W, int64_t ld, int j, int i, int p, const float (*sM)[NB + 1],
                                  float (*sPw)[WT_LD], float (*sQw)[WT_LD], const int* done, DevStatus* st) {
     const int lane = threadIdx.x & 31;
     if (j > 0) {
@@ -342,16 +346,18 @@ __device__ bool warp_tile_update(float* W, int64_t ld, int j, int i, int p, cons
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
-    warp_times_linv_t(sPw, sLi);
-    if (p != i) warp_times_linv_t(sQw, sLi);
-    const float(*pq)[WT_LD] = (p != i) ? sQw : sPw;
-    // D[r][lane] = sum_q P_i[r][q] P_p[lane][q], into sQw (free once every lane holds its row of P_p)
+    // T = A[i, j] M_j (M_j symmetric: its row c is its column c), in place, or into the unused
+    // second buffer on a diagonal tile, whose unscaled rows are the other operand
+    float(*sT)[WT_LD] = (p != i) ? sPw : sQw;
+    float(*sB)[WT_LD] = (p != i) ? sQw : sPw;  // A[p, j], unscaled: M_j carries both solves
+    warp_times_linv_t(sPw, sM, sT);
     float qrow[NB];
 #pragma unroll
-    for (int q = 0; q < NB; ++q) qrow[q] = pq[lane][q];
-    __syncwarp();
+    for (int q = 0; q < NB; ++q) qrow[q] = sB[lane][q];
+    __syncwarp();  // every lane holds its row of A[p, j]: sB takes the product
+    // D[r][lane] = sum_q T[r][q] A_p[lane][q]
 #pragma unroll 4
-    for (int r = 0; r < NB; ++r) sQw[r][lane] = warp_dot32(&sPw[r][0], qrow);
+    for (int r = 0; r < NB; ++r) sB[r][lane] = warp_dot32(&sT[r][0], qrow);
     // A[i, p] -= D: the target tile's column `lane`, all rows in flight at once
     float wv[NB];
 #pragma unroll
@@ -360,7 +366,7 @@ __device__ bool warp_tile_update(float* W, int64_t ld, int j, int i, int p, cons
     for (int r = 0; r < NB; ++r) {
         if (i == p && lane > r) continue;
         if (!DFS_IN_BOUNDS(st, p <= i)) continue;
-        W[((int64_t)i * NB + r) * ld + (int64_t)p * NB + lane] = wv[r] - sQw[r][lane];
+        W[((int64_t)i * NB + r) * ld + (int64_t)p * NB + lane] = wv[r] - sB[r][lane];
     }
     __syncwarp();  // sPw / sQw are reused by the warp's next tile
     return true;
@@ -371,6 +377,7 @@ template <typename T, typename CT, bool WARP_TILES>
 __global__ void __launch_bounds__(CC_THREADS)
 chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
     __shared__ __align__(16) T sLi[NB][NB + 1];
+    __shared__ __align__(16) T sM[WARP_TILES ? NB : 1][NB + 1];  // Linv_j^T Linv_j (warp-tile steps)
     __shared__ __align__(16) T sP[NB][NB + 1];
     __shared__ __align__(16) T sQ[NB][NB + 1];
     __shared__ __align__(16) T sD[NB][NB + 1];  // the next diagonal tile (owner only), before its update
@@ -425,6 +432,21 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
         }
         if (!block_wait(&diag[j], 1, st, &s_ok, 0)) return;
         load_linv<T>(Linv, j, sLi);
+        if constexpr (kWarpTiles) {
+            // M_j = Linv_j^T Linv_j = (L_jj L_jj^T)^{-1} for this step's per-warp tiles:
+            // M[r][c] = sum_q Li[q][r] Li[q][c] (Li lower triangular: q >= max(r, c))
+            const int r = tid >> 3, cb = tid & 7;
+            T acc[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const T a = sLi[q][r];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma(a, sLi[q][cb + 8 * u], acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sM[r][cb + 8 * u] = acc[u];
+            __syncthreads();
+        }
         // pass 0: tiles of column j + 1 (diagonal first: it has the smallest id); pass 1: the rest
         for (int pass = 0; pass < 2; ++pass) {
             // With three or more tiles in the pass (large n), they are dealt to the CTA's warps (a
@@ -444,7 +466,7 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
                 const int warp = tid >> 5;
                 float (*sPw)[WT_LD] = reinterpret_cast<float (*)[WT_LD]>(wtiles + (size_t)warp * 2 * NB * WT_LD);
                 float (*sQw)[WT_LD] = sPw + NB;
-                const float(*sLif)[NB + 1] = reinterpret_cast<const float(*)[NB + 1]>(sLi);
+                const float(*sMf)[NB + 1] = reinterpret_cast<const float(*)[NB + 1]>(sM);
                 int kk = 0;
                 for (int t = cta; t < ntiles; t += G) {
                     int i, p;
@@ -452,7 +474,7 @@ chol_coop_kernel(T* W, int64_t ld, int nb, T* Linv, int* flags, DevStatus* st) {
                     if (p <= j + 1) continue;
                     if ((kk++ % CC_WARPS) != warp) continue;
                     // a wait that gave up leaves the rest to the next block_wait, which sees the status
-                    if (!warp_tile_update(reinterpret_cast<float*>(W), ld, j, i, p, sLif, sPw, sQw, done, st)) break;
+                    if (!warp_tile_update(reinterpret_cast<float*>(W), ld, j, i, p, sMf, sPw, sQw, done, st)) break;
                 }
                 continue;
             }
