@@ -383,7 +383,7 @@ template <typename TS, int KQ, int PACK>
 __global__ void __launch_bounds__(SVB_THREADS, 1)
 sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t lds, const float* __restrict__ V,
                int64_t ldv, int k, double* __restrict__ Rpart, unsigned char* __restrict__ Sp, int nchunks,
-               const DevStatus* st, double scale, int honor_stop) {
+               const DevStatus* st, double scale, int honor_stop, const float* __restrict__ rinv) {
     constexpr int R = SvbRows<KQ>::R;
     constexpr int VEC = Vec16<TS>::N;  // elements per 16-byte load: 4 (FP32) or 8 (BF16)
     constexpr int LPG = 8 / VEC;       // 16-byte loads per row and 8-column group
@@ -396,7 +396,9 @@ sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
     const int nrb = n_rows / R;
     const int rb = blockIdx.x % nrb, chunk = blockIdx.x / nrb;
     const int i0 = rb * R;
-    const int64_t nkb_all = ceil_div(m, 64);
+    // 64-column units of the columns the tiles cover (FP8 tiles: 128 columns, two units, so that
+    // every tile column is written, zeros past m)
+    const int64_t nkb_all = PACK == 4 ? 2 * ceil_div(m, 128) : ceil_div(m, 64);
     const int64_t per = ceil_div(nkb_all, nchunks);
     const int64_t g0 = (int64_t)chunk * per * 8;  // this CTA's 8-column groups [g0, g1)
     const int64_t g1 = g0 + per * 8 < nkb_all * 8 ? g0 + per * 8 : nkb_all * 8;
@@ -510,6 +512,25 @@ sv_rows_kernel(const TS* __restrict__ S, int n, int n_rows, int64_t m, int64_t l
                     }
                 }
             }
+            if constexpr (PACK == 4) {
+                if (gin) {
+                    // 8 e4m3 bytes (row i scaled by rinv[i], round to nearest even, saturating) at
+                    // columns (g & 15) * 8 of FP8 k-block g >> 4, in tile row i & 127
+                    const int nblk = n_rows >> 7, col = (int)(g & 15) * 8;
+                    unsigned char* tk = Sp + (((g >> 4) * (int64_t)nblk) << 14);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        const int i = i0 + j;
+                        const float q = i < n ? __ldg(rinv + i) : 0.f;
+                        float f[8];
+                        svb_unpack_raw<TS>(raw[u][j], f);
+                        uint2 w8;
+                        w8.x = e4m3x4(f[0] * q, f[1] * q, f[2] * q, f[3] * q);
+                        w8.y = e4m3x4(f[4] * q, f[5] * q, f[6] * q, f[7] * q);
+                        *reinterpret_cast<uint2*>(tk + ((int64_t)(i >> 7) << 14) + fp8_tile_offset(i & 127, col)) = w8;
+                    }
+                }
+            }
             if constexpr (PACK == 1) {
                 if (gin) {
                     // 16-byte chunk c = g & 7 of k-block g >> 3 in tile row i & 127 (128-byte swizzle)
@@ -562,11 +583,12 @@ static int sv_rows_chunks(int nrb, int64_t m, int num_sms) {
 template <typename TS, int KQ, int PACK>
 static cudaError_t launch_sv_rows_t(int nchunks, const void* S, int n, int n_rows, int64_t m, int64_t lds,
                                     const void* V, int64_t ldv, int k, double* Rpart, void* Sp, const DevStatus* st,
-                                    cudaStream_t stream, double scale = 1.0, int honor_stop = 0) {
+                                    cudaStream_t stream, double scale = 1.0, int honor_stop = 0,
+                                    const float* rinv = nullptr) {
     const int64_t grid = (int64_t)nchunks * (n_rows / SvbRows<KQ>::R);
     sv_rows_kernel<TS, KQ, PACK><<<(unsigned)grid, SVB_THREADS, 0, stream>>>(
         static_cast<const TS*>(S), n, n_rows, m, lds, static_cast<const float*>(V), ldv, k, Rpart,
-        static_cast<unsigned char*>(Sp), nchunks, st, scale, honor_stop);
+        static_cast<unsigned char*>(Sp), nchunks, st, scale, honor_stop, rinv);
     count_launch();
     return cudaGetLastError();
 }
@@ -1673,7 +1695,10 @@ static cudaError_t launch_sv_ring_t(int grid, const void* S, int n, int n_rows, 
 template <typename TS, int KQ>
 static cudaError_t launch_sv_rows_kq(int pack, int nchunks, const void* S, int n, int n_rows, int64_t m, int64_t lds,
                                      const void* V, int64_t ldv, int k, double* Rpart, void* Sp, const DevStatus* st,
-                                     cudaStream_t stream) {
+                                     cudaStream_t stream, const float* rinv) {
+    if (pack == 4)
+        return launch_sv_rows_t<TS, KQ, 4>(nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, st, stream, 1.0, 0,
+                                           rinv);
     return pack ? launch_sv_rows_t<TS, KQ, 1>(nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, st, stream)
                 : launch_sv_rows_t<TS, KQ, 0>(nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, st, stream);
 }
@@ -1682,9 +1707,10 @@ cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, 
                            int64_t lds, const void* V, int64_t ldv, int k, double* Rpart, void* Sp,
                            const DevStatus* st, cudaStream_t stream, const float* rinv, int* parts) {
     if (parts) *parts = plan.sv_grid;
-    // rows far apart (FP32 S beyond the streaming form's 1024 rows, or BF16 S), BF16 tiles or none:
-    // the row-blocked form
-    if (pack <= 1 && (s_dtype == DFS_BF16 || (s_dtype == DFS_F32 && round_up(n, 256) > SVR_MAXNR * (PASS_THREADS / 16)))) {
+    // rows far apart (FP32 S beyond the streaming form's 1024 rows, or BF16 S), BF16 or row-scaled
+    // e4m3 tiles or none: the row-blocked form
+    if ((pack <= 1 || (pack == 4 && rinv != nullptr)) &&
+        (s_dtype == DFS_BF16 || (s_dtype == DFS_F32 && round_up(n, 256) > SVR_MAXNR * (PASS_THREADS / 16)))) {
         const int n_rows = (int)round_up(n, pack ? 256 : 8);
         const int nchunks = sv_rows_chunks(n_rows / (kq >= 8 ? SvbRows<8>::R : SvbRows<1>::R), m, plan.sv_grid);
         if (parts) *parts = nchunks;
@@ -1692,9 +1718,9 @@ cudaError_t launch_sv_pack(const PassPlan& plan, int s_dtype, int kq, int pack, 
     case KQ:                                                                                                 \
         return s_dtype == DFS_F32                                                                            \
                    ? launch_sv_rows_kq<float, KQ>(pack, nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, Sp, st, \
-                                                  stream)                                                    \
+                                                  stream, rinv)                                              \
                    : launch_sv_rows_kq<__nv_bfloat16, KQ>(pack, nchunks, S, n, n_rows, m, lds, V, ldv, k, Rpart, \
-                                                          Sp, st, stream);
+                                                          Sp, st, stream, rinv);
         switch (kq) {
             DFS_SVB(1)
             DFS_SVB(2)
