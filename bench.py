@@ -828,7 +828,8 @@ def run_workload(args):
 
 def run_profile_solve(args):
     """One small BF16 solve for an ncu capture (--profile-solve M): Gaussian S of n x M
-    (--profile-n, default 1024; FP32, or BF16 with --profile-bf16; seed 1), v seed 2, lambda 1e-4,
+    (--profile-n, default 1024; FP32, or BF16 with --profile-bf16; seed 1), V (--profile-k right-hand
+    sides, default 1) seed 2, lambda 1e-4,
     after --warmup solves.  Prints the device status."""
     import torch
 
@@ -842,7 +843,7 @@ def run_profile_solve(args):
     n = args.profile_n or N_SAMPLES
     S = wl.gaussian(n, args.profile_solve, seed=1, device="cuda",
                     dtype=torch.bfloat16 if args.profile_bf16 else torch.float32)
-    v = wl.rhs(args.profile_solve, 1, seed=2, device="cuda")
+    v = wl.rhs(args.profile_solve, args.profile_k or 1, seed=2, device="cuda")
     X = torch.empty_like(v)
     for _ in range(args.warmup + 1):
         dfs.dfs_solve(S, v, LAMBDA, X=X, precision=PRECISION, sync=False)
@@ -865,6 +866,7 @@ def main():
                     help="run one small solve (n=1024, m=M) after --warmup solves, for ncu captures")
     ap.add_argument("--profile-n", type=int, default=0, metavar="N", help="rows of S for --profile-solve")
     ap.add_argument("--profile-bf16", action="store_true", help="BF16 S for --profile-solve")
+    ap.add_argument("--profile-k", type=int, default=0, metavar="K", help="right-hand sides for --profile-solve")
     args = ap.parse_args()
     if args.profile_solve:
         return run_profile_solve(args)
