@@ -443,13 +443,18 @@ def run_ours(args):
     for _ in range(2):
         dfs.dfs_solve_host_async(S_h, v_h, LAMBDA, X_h, precision=PRECISION)
     torch.cuda.synchronize()
-    # the host -> device link rate of this machine (one plain upload of S), which bounds the e2e value
+    # the host -> device link rate of this machine (plain uploads of S, the best of three: the first
+    # touches fresh device memory), which bounds the e2e value
     S_probe = torch.empty(S_h.shape, dtype=S_h.dtype, device=dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    S_probe.copy_(S_h, non_blocking=True)
-    torch.cuda.synchronize()
-    link_gbs = S_h.numel() * S_h.element_size() / (time.perf_counter() - t0) / 1e9
+    best_s = None
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S_probe.copy_(S_h, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        best_s = dt if best_s is None else min(best_s, dt)
+    link_gbs = S_h.numel() * S_h.element_size() / best_s / 1e9
     del S_probe
     torch.cuda.empty_cache()
     ke = max(3, args.steps // 10)
